@@ -1,0 +1,305 @@
+"""Benchmark of the Taylor–Couette AB2BD2 time step (libtc on one GB300 per rank).
+
+Workload (one "step" = one full AB2BD2 step, Sec. 3.2 steps 1-5, through the C ABI):
+plain FP64 step at N_r = 64 radial nodes, m = -32..32, k = -64..64, 3/2-dealiased physical
+grid 64 x 96 x 192, eta = 0.5, Re_i = 1000, outer cylinder at rest, dt = 5e-4, initial state
+circular Couette flow plus a seeded Taylor-vortex-like perturbation (amp 1e-2).
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle (the reference arm of this
+benchmark) on the same workload on the host cores.  Under torchrun each rank advances its
+own independent simulation (seed 42 + rank); no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+CFG2 = dict(N_r=64, M=32, K=64, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)
+WORKLOAD = ("FP64 AB2BD2 step: eta=0.5, Re_i=1000, Re_o=0, N_r=64 clustered nodes (alpha=0.5), "
+            "m=-32..32 (m_p=1), k=-64..64 (L_z=2pi/3.16), phys grid 64x96x192, dt=5e-4, "
+            "init Couette + Taylor-vortex-like perturbation amp 1e-2 (seed 42)")
+METRIC = "time-steps/s (FP64 plain AB2BD2 step)"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def gdof(cfg):
+    return 3 * cfg["N_r"] * (2 * cfg["M"] + 1) * (2 * cfg["K"] + 1)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in (getattr(self, "out", "") or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, v in enumerate(flags) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def theta_flops(cfg, Pt, Pz):
+    """Algorithmic FP64 flops of one k_theta launch: 6 inverse and 1.5 forward complex
+    transforms of length P_theta per (r, z) at 5 n log2 n, plus 25 flops of products per
+    physical point."""
+    n = Pt
+    per_line = 5.0 * n * math.log2(n)
+    return cfg["N_r"] * Pz * (7.5 * per_line + 25.0 * n)
+
+
+def zpass_flops(cfg, Pz, lines):
+    return cfg["N_r"] * (cfg["M"] + 1) * lines * 5.0 * Pz * math.log2(Pz)
+
+
+def run_ours(args):
+    import torch
+    from paper_1311_2481_gb300 import build as B
+    from paper_1311_2481_gb300 import inputs as I
+    from paper_1311_2481_gb300 import tc
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    if rank == 0 or world == 1:
+        B.build()
+    if dist:
+        dist.barrier()
+    cfg = CFG2
+    plan = tc.Plan(**cfg, device=f"cuda:{local}")
+    r = plan.nodes()
+    u0 = I.initial_state(r, cfg["M"], cfg["K"], cfg["m_p"], cfg["L_z"], cfg["eta"], cfg["Re_i"],
+                         cfg["Re_o"], kind="taylor", amp=1e-2, seed=42 + rank)
+    u0_t = torch.from_numpy(u0)
+    st = tc.State(plan, u0_t.cuda())
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_step():
+        plan.step(st, 1)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed before each, events around each step
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for i in range(K):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            one_step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / K
+    value = world * K / (total_ms / 1e3)
+
+    # per-kernel breakdown (tracing pass over the same number of steps)
+    plan.profile(True)
+    for i in range(K):
+        flush.fill_(float(i))
+        one_step()
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    plan.profile(False)
+    launches = sum(n for n, _ in prof.values())
+    nl_ms = sum(prof[k][1] for k in ("k_zinv", "k_theta", "k_zfwd") if k in prof) / K
+    pc_ms = sum(v[1] for k, v in prof.items() if k not in ("k_zinv", "k_theta", "k_zfwd")) / K
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    Pt, Pz = 3 * cfg["M"], 3 * cfg["K"]
+    flops = {"k_theta": theta_flops(cfg, Pt, Pz), "k_zinv": zpass_flops(cfg, Pz, 9),
+             "k_zfwd": zpass_flops(cfg, Pz, 3)}
+    fp64_peak = 1.21e12   # measured DFMA-loop peak on this GB300 (nominal 1.25 TFLOP/s)
+    roof = None
+    if top[0] in flops:
+        avg_s = top[1][1] / top[1][0] / 1e3
+        ach = flops[top[0]] / avg_s
+        roof = {"kernel": top[0], "bound": "alu", "achieved": ach / 1e12, "peak": fp64_peak / 1e12,
+                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": "FP64 DFMA loop measured on GB300 (152 SMs x 2 DFMA/clk x 2 flop x ~2.0 GHz)",
+                "algorithmic": "7.5 complex FFTs of P_theta at 5 n log2 n + 25 flop/point per (r, z)"}
+
+    # end to end through the C ABI with host buffers: H2D state, step, D2H state
+    host = {k: torch.empty_like(getattr(st, k), device="cpu").pin_memory() for k in ("u", "u_prev", "N_prev", "p")}
+    for k in host:
+        host[k].copy_(getattr(st, k))
+    bi = sum(t.numel() * t.element_size() for t in host.values())
+    bo = host["u"].numel() * host["u"].element_size() + host["p"].numel() * host["p"].element_size()
+    torch.cuda.synchronize()
+    E = min(K, 20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(E):
+        for k in host:
+            getattr(st, k).copy_(host[k], non_blocking=True)
+        one_step()
+        host["u"].copy_(st.u, non_blocking=True)
+        host["p"].copy_(st.p, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = world * E / (e0.elapsed_time(e1) / 1e3)
+    diag = plan.diagnostics(st.u)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N_r": cfg["N_r"], "M": cfg["M"], "K": cfg["K"],
+                   "P_theta": Pt, "P_z": Pz, "dt": cfg["dt"], "gdof": gdof(cfg),
+                   "l2": "flushed before every timed step (256 MiB fill outside the per-step events)",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+        "gdof_steps_per_s": value * gdof(cfg) / 1e9,
+        "phases_ms": {"nonlinear": nl_ms, "predictor_corrector": pc_ms},
+        "kernels_ms_per_step": {k: v[1] / K for k, v in sorted(prof.items())},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "wall_s_timed_region": wall,
+        "state_finite": bool(diag.finite),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _oracle_steps(seconds, max_steps=None):
+    """Time the oracle's step on the benchmark workload for about `seconds` (host cores)."""
+    import oracle as O
+    from paper_1311_2481_gb300 import inputs as I
+    ops = O.Operators(O.Params(**CFG2))
+    ops.mats
+    u0 = I.initial_state(ops.r, CFG2["M"], CFG2["K"], CFG2["m_p"], CFG2["L_z"], CFG2["eta"],
+                         CFG2["Re_i"], CFG2["Re_o"], kind="taylor", amp=1e-2, seed=42)
+    st = O.step(ops, O.cold_state(u0))       # start-up outside the sample
+    n, t0 = 0, time.perf_counter()
+    while True:
+        st = O.step(ops, st)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_steps and n >= max_steps):
+            return n, el
+
+
+def cpu_baseline(seconds):
+    n, el = _oracle_steps(seconds)
+    return {"value": n / el, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} oracle steps of the benchmark workload after its start-up step "
+                      f"(numpy FP64, dense DFT matrices and dense per-mode solves)"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    secs = max(1.0, args.cpu_seconds)
+    for _ in range(args.warmup):
+        _oracle_steps(0.0, max_steps=1)
+    n, el = _oracle_steps(secs * max(1, args.steps) / 10.0, max_steps=max(1, args.steps))
+    v = n / el
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world,
+           "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD},
+           "cpu_baseline": {"value": v, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"{n} oracle steps after the start-up step"},
+           "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,156 @@
+/*
+ * tc.h -- C ABI of libtc, the GB300 (sm_103a) hot path of one Taylor–Couette DNS time step
+ * (Shi, Rampp, Hof & Avila, "A hybrid MPI-OpenMP parallel implementation for pseudospectral
+ * simulations with application to Taylor–Couette flow").
+ *
+ * Discretisation (Sec. 3.1): Fourier–Galerkin in theta and z, high-order finite differences on
+ * N_r clustered radial nodes r_j (Eq. nodeDist), time stepping by the AB2BD2 projection scheme
+ * of Sec. 3.2 (Eq. timeScheme .. Eq. update).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Spectral arrays are complex128 (interleaved re, im doubles), C order, device memory owned
+ *    by the caller.  A vector field is [3][N_r][M+1][2K+1] holding (u_+, u_-, u_z) with
+ *    u_+- = u_r +- i u_theta per Fourier mode (Sec. 3.1, before Eq. modalNSdecoup); a scalar
+ *    field is [N_r][M+1][2K+1].  Index [c][j][m][k+K] is radial node j, azimuthal mode
+ *    m = 0..M (wavenumber m * m_p), axial mode k = -K..K (wavenumber k * k_z, k_z = 2 pi / L_z).
+ *    The m < 0 half follows from the reality of the physical fields; in the inverse transform
+ *    the m = 0 line of u_r, u_theta, u_z contributes through its real part.
+ *  - Physical grid for the nonlinear term: P_theta x P_z points per radial node (default
+ *    3M x 3K, the 3/2 rule of Sec. 3.1 / Sec. 3.2 step 1).
+ *  - Every call validates its arguments on the host before any launch and returns a
+ *    tc_status; nothing aborts.  Kernels are enqueued on the caller's stream (cudaStream_t
+ *    passed as void*; NULL = legacy default stream); calls return before the GPU finishes.
+ *    Asynchronous CUDA errors surface as TC_ERR_CUDA on a later call.
+ *  - ws is caller-owned device scratch of at least tc_plan_workspace_bytes() bytes, 256-byte
+ *    aligned; its contents are undefined between calls.  A plan and its workspace may be used
+ *    by one stream at a time.  Plans are not thread safe.
+ *  - Input and output arrays must not overlap unless stated.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tc_plan tc_plan; /* opaque; owns nodes, FD weights, twiddles and LU factors */
+
+typedef enum {
+    TC_OK = 0,
+    TC_ERR_ARG = 1,       /* invalid argument (checked on the host before any launch) */
+    TC_ERR_CUDA = 2,      /* a CUDA runtime call failed (see tc_plan_last_error) */
+    TC_ERR_OOM = 3,       /* device or host allocation failed */
+    TC_ERR_NONFINITE = 4, /* a NaN/Inf was found in the state (tc_diagnostics) */
+    TC_ERR_TIMEOUT = 5,   /* reserved: a bounded device wait gave up (no such wait exists yet) */
+    TC_ERR_STATE = 6      /* call not allowed in this plan state (e.g. host-only plan) */
+} tc_status;
+
+/* Which of the five banded systems of Sec. 3.2 (steps 2-4) tc_helmholtz_solve solves. */
+typedef enum {
+    TC_P_STAR = 0,  /* Eq. pressure: Lap_h p* = rhs, Neumann rows at both walls */
+    TC_U_PLUS = 1,  /* Eq. vel, u_+ : (3/(2dt) - L_+) u = rhs, Dirichlet rows */
+    TC_U_MINUS = 2, /* Eq. vel, u_- : (3/(2dt) - L_-) u = rhs, Dirichlet rows */
+    TC_U_Z = 3,     /* Eq. vel, u_z : (3/(2dt) - Lap_h) u = rhs, Dirichlet rows */
+    TC_PHI = 4      /* Eq. correction: same matrix as TC_P_STAR */
+} tc_system;
+
+typedef enum { TC_FP64 = 0, TC_MIXED = 1 } tc_precision;
+
+/* Optional plan settings; zero-initialise and set what differs from the defaults. */
+typedef struct {
+    double alpha;     /* node clustering of Eq. nodeDist; 0 -> default 0.5; use a negative
+                         value for the Chebyshev limit alpha -> 0 */
+    int P_theta;      /* physical points in theta; 0 -> 3M.  Must be 2^a 3^b >= 2M+1 */
+    int P_z;          /* physical points in z;     0 -> 3K.  Must be 2^a 3^b >= 2K+1 */
+    int precision;    /* tc_precision; TC_MIXED runs the transforms and products in FP32 */
+    int host_only;    /* 1: build the host plan only (no device memory); for inspection */
+} tc_options;
+
+/* Step state (Sec. 3.2): u = u^i, u_prev = u^{i-1}, N_prev = N^{i-1} (vector fields), p = p^i
+ * (scalar field), started = 0 for a cold state whose history is built by the first step. */
+typedef struct {
+    void* u;
+    void* u_prev;
+    void* N_prev;
+    void* p;
+    int started;
+} tc_state;
+
+/* Diagnostics of a velocity field (Sec. 5): perturbation energy about analytic Couette flow
+ * J = 1/2 sum_j w_j r_j sum_{m,k} c_m |u - U|^2 (trapezoid weights w_j, c_0 = 1, c_m = 2),
+ * torque T = r^3 d_r(u_theta^{00} / r) at r_i and r_o (Sec. 5.4 quasi-Nusselt number =
+ * T / T_laminar), max |div_h u| over interior rows, and whether every entry is finite. */
+typedef struct {
+    double energy;
+    double torque_inner;
+    double torque_outer;
+    double max_div;
+    int finite;
+} tc_diag;
+
+/* Create a plan: nodes (Eq. nodeDist, paper's M = N_r - 1), FD weights of fd_order + 1 points
+ * (Sec. 3.1; shortened centred stencils near the walls, one-sided fd_order/2 + 1 points on
+ * the wall rows), twiddles, and the banded LU factors with partial pivoting of the Poisson
+ * and three Helmholtz matrices of every mode (m, |k|) (Sec. 3.2, "precomputed at the
+ * beginning").  Requires N_r >= fd_order + 1, M >= 1, K >= 1, m_p >= 1, 0 < eta < 1,
+ * L_z > 0, dt > 0, fd_order in {2, 4, 6, 8}.  *out receives the plan or NULL on error. */
+tc_status tc_plan_create(tc_plan** out, int N_r, int M, int K, int m_p, double eta,
+                         double Re_i, double Re_o, double L_z, double dt, int fd_order);
+tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, double eta,
+                            double Re_i, double Re_o, double L_z, double dt, int fd_order,
+                            const tc_options* opt);
+void tc_plan_destroy(tc_plan* plan);
+
+/* Device scratch needed by every call that takes ws. */
+tc_status tc_plan_workspace_bytes(const tc_plan* plan, size_t* bytes);
+/* Radial nodes r_j, j = 0..N_r-1, into host memory r_host[N_r]. */
+tc_status tc_plan_nodes(const tc_plan* plan, double* r_host);
+/* FD weights into host memory: w[N_r][fd_order+1] applied to nodes col0[j] + t
+ * (zero-padded), deriv = 1 or 2. */
+tc_status tc_plan_fd_weights(const tc_plan* plan, int deriv, double* w_host, int* col0_host);
+/* Text of the last CUDA error seen by this plan (static storage inside the plan). */
+const char* tc_plan_last_error(const tc_plan* plan);
+const char* tc_status_string(tc_status s);
+
+/* Nonlinear term, Sec. 3.2 step 1: N_hat = N(u) = u . grad u with the curvature terms of
+ * Eq. NS_cyl, evaluated pseudospectrally on the P_theta x P_z grid (d_r by the FD stencil,
+ * d_theta and d_z as mode multiplies, inverse transforms, pointwise products, forward
+ * transforms truncated to |m| <= M, |k| <= K).  u_hat, N_hat: device vector fields
+ * (N_pm = N_r +- i N_theta). */
+tc_status tc_nonlinear(tc_plan* plan, const void* u_hat, void* N_hat, void* ws, void* stream);
+
+/* One of the five banded systems of Sec. 3.2 for every mode: rhs and x are device scalar
+ * fields; rows 0 and N_r - 1 of rhs hold the boundary values (Dirichlet value, or the
+ * Neumann value d_r x; for (m,k) = (0,0) the Poisson systems take a Dirichlet value at r_o,
+ * Sec. 3.2).  x may equal rhs (in place). */
+tc_status tc_helmholtz_solve(tc_plan* plan, int which, const void* rhs, void* x, void* ws,
+                             void* stream);
+
+/* nsteps AB2BD2 steps (Sec. 3.2 steps 1-5) in place on the caller's state.  A cold state
+ * (started == 0) first gets its history: one implicit Euler step of size 2dt/3 (the scheme
+ * with u^{-1} = u^0, N^{-1} = N^0, same factors), u^{-1} = u^0 - 1.5 (u_E - u^0),
+ * N^{-1} = N(u^{-1}); started is then set to 1. */
+tc_status tc_step(tc_plan* plan, tc_state* st, int nsteps, void* ws, void* stream);
+
+/* Diagnostics of the velocity field u (device vector field); synchronises the stream and
+ * writes *out (host).  Returns TC_ERR_NONFINITE if u holds a NaN/Inf. */
+tc_status tc_diagnostics(tc_plan* plan, const void* u, tc_diag* out, void* ws, void* stream);
+
+/* Tracing (no counterpart in the paper beyond its per-phase timings, Table efficiency):
+ * when enabled, every kernel the plan launches is bracketed by CUDA events recorded on the
+ * launching stream.  tc_profile_enable(plan, 1) also clears earlier records.
+ * tc_profile_read(plan, index, ...) synchronises on the recorded events and reports, for
+ * kernel `index` (0 <= index < 15, see name), the launches and total milliseconds recorded
+ * since the last enable; TC_ERR_ARG past the last index.  name points to static storage. */
+tc_status tc_profile_enable(tc_plan* plan, int enable);
+tc_status tc_profile_read(tc_plan* plan, int index, const char** name, long long* launches,
+                          double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

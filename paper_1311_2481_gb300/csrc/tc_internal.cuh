@@ -1,0 +1,136 @@
+// Internal declarations of libtc (plan layout, complex helpers, launch helpers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/tc.h"
+
+namespace tc {
+
+constexpr int kMaxRadix = 16;   // passes of a mixed-radix 2^a 3^b transform
+constexpr int kStencil = 9;     // padded FD stencil width (fd_order <= 8)
+constexpr int kBands = 13;      // stored doubles per LU row: 4 L multipliers, 1/U_jj, 8 U
+constexpr int kKl = 4;          // sub/super diagonals of the mode matrices (fd_order/2 <= 4)
+
+// Factor sets of Sec. 3.2: Poisson (p*, phi), Helmholtz for u_+, u_-, u_z.
+enum FactorSet { kSetP = 0, kSetHp = 1, kSetHm = 2, kSetHz = 3, kNumSets = 4 };
+
+struct Radices {
+    int n;
+    int count;
+    int r[kMaxRadix];
+};
+
+// Byte offsets of the workspace regions (all 256-byte aligned).
+struct Workspace {
+    size_t H1;      // inverse z-pass output: 9 fields x N_r x (M+1) x P_z complex
+    size_t H2;      // theta-pass output: 3 fields x N_r x (M+1) x P_z complex
+    size_t Ncur;    // N^i: vector field
+    size_t pstar;   // p*: scalar field
+    size_t ustar;   // u*: vector field
+    size_t phi;     // phi: scalar field
+    size_t uE;      // start-up Euler result: vector field
+    size_t red;     // diagnostics reduction buffer
+    size_t total;
+};
+
+}  // namespace tc
+
+struct tc_plan {
+    // parameters
+    int N_r, M, K, m_p, fd_order, half, P_t, P_z, precision;
+    double eta, Re_i, Re_o, L_z, dt, alpha, k_z, r_i, r_o;
+    bool host_only;
+    // derived sizes
+    size_t S;        // complex entries of a scalar spectral field
+    size_t Hfield;   // complex entries of one z-pass line set: N_r (M+1) P_z
+    int nmode;       // (M+1)(2K+1)
+    int nmode_half;  // (M+1)(K+1)
+    tc::Radices rad_z, rad_t;
+    int zt, zt32;                  // z values per theta-pass block (FP64 / FP32 lines)
+    int zinv_lines, zinv_lines32;  // lines per inverse z-pass block (FP64 / FP32 lines)
+    tc::Workspace ws;
+    // host plan
+    std::vector<double> r, w1, w2;   // nodes; weights [N_r][9]
+    std::vector<int> col0;           // first node of each padded stencil
+    std::vector<double> fac;         // [set][j][band][m][ka]
+    std::vector<uint8_t> piv;        // [set][j][m][ka] pivot offset 0..4
+    std::vector<double> tw_z, tw_t;  // interleaved complex exp(+2 pi i j / n)
+    // device plan
+    double* d_r = nullptr;
+    double* d_w1 = nullptr;
+    double* d_w2 = nullptr;
+    int* d_col0 = nullptr;
+    double* d_fac = nullptr;
+    uint8_t* d_piv = nullptr;
+    double2* d_tw_z = nullptr;
+    double2* d_tw_t = nullptr;
+    float2* d_tw_z32 = nullptr;
+    float2* d_tw_t32 = nullptr;
+    int device = -1;
+    char err[512];
+    // per-kernel CUDA-event tracing
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;         // event pool, two per record
+    std::vector<int> prof_kid;                // kernel id of each record
+    size_t prof_used = 0;                     // records in use
+};
+
+namespace tc {
+
+// ------------------------------------------------------------------ complex helpers
+template <typename T> struct C2;
+template <> struct C2<double> { using type = double2; };
+template <> struct C2<float> { using type = float2; };
+
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+template <typename V> __host__ __device__ __forceinline__ V cadd(V a, V b) { V c; c.x = a.x + b.x; c.y = a.y + b.y; return c; }
+template <typename V> __host__ __device__ __forceinline__ V csub(V a, V b) { V c; c.x = a.x - b.x; c.y = a.y - b.y; return c; }
+template <typename V> __host__ __device__ __forceinline__ V cmul(V a, V b) {
+    V c; c.x = a.x * b.x - a.y * b.y; c.y = a.x * b.y + a.y * b.x; return c;
+}
+template <typename V> __host__ __device__ __forceinline__ V cconj(V a) { a.y = -a.y; return a; }
+template <typename V, typename T> __host__ __device__ __forceinline__ V cscale(V a, T s) { a.x *= s; a.y *= s; return a; }
+// i * a
+template <typename V> __host__ __device__ __forceinline__ V cmuli(V a) { V c; c.x = -a.y; c.y = a.x; return c; }
+
+// ------------------------------------------------------------------ error helpers
+tc_status cuda_fail(tc_plan* p, cudaError_t e, const char* where);
+#define TC_CUDA(plan, call)                                            \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return tc::cuda_fail(plan, e_, #call);  \
+    } while (0)
+#define TC_LAUNCHED(plan, what)                                        \
+    do {                                                               \
+        cudaError_t e_ = cudaGetLastError();                           \
+        if (e_ != cudaSuccess) return tc::cuda_fail(plan, e_, what);   \
+    } while (0)
+
+tc_status check_device_ptr(tc_plan* p, const void* ptr, const char* name);
+
+// ------------------------------------------------------------------ tracing
+enum KernelId {
+    kKZinv = 0, kKTheta, kKZfwd, kKRhsPressure, kKSolveP, kKRhsVelocity, kKSolveH, kKRhsDiv,
+    kKUpdate, kKAxpby, kKDiag, kKZinv32, kKTheta32, kKZfwd32, kKMeanFlow, kNumKernels
+};
+extern const char* const kKernelNames[kNumKernels];
+int prof_begin(tc_plan* p, int kid, cudaStream_t s);
+void prof_end(tc_plan* p, int slot, cudaStream_t s);
+
+// ------------------------------------------------------------------ launchers
+tc_status launch_nonlinear(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s);
+tc_status launch_solve(tc_plan* p, int set, double2* x, int nfields, cudaStream_t s);
+tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const double2* Ncur,
+                         double2* N_prev, double2* p_out, double2* u_out, char* ws,
+                         bool commit, cudaStream_t s);
+tc_status launch_axpby(tc_plan* p, double2* y, const double2* a, double ca, const double2* b,
+                       double cb, size_t n, cudaStream_t s);
+tc_status launch_diagnostics(tc_plan* p, const double2* u, double* red, cudaStream_t s);
+
+}  // namespace tc

@@ -1,0 +1,460 @@
+// Host plan of libtc: radial nodes (Eq. nodeDist), finite-difference weights (Sec. 3.1,
+// Fornberg's recursion in long double), twiddle tables, and the banded LU factors with partial
+// pivoting of the per-mode Poisson / Helmholtz matrices (Sec. 3.2, precomputed once).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <thread>
+
+#include "tc_internal.cuh"
+
+namespace tc {
+
+static const long double kPiL = 3.141592653589793238462643383279502884197L;
+
+tc_status cuda_fail(tc_plan* p, cudaError_t e, const char* where) {
+    if (p) snprintf(p->err, sizeof(p->err), "%s: %s", where, cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return TC_ERR_OOM;
+    return TC_ERR_CUDA;
+}
+
+tc_status check_device_ptr(tc_plan* p, const void* ptr, const char* name) {
+    if (!ptr) {
+        snprintf(p->err, sizeof(p->err), "%s is NULL", name);
+        return TC_ERR_ARG;
+    }
+    if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0) {
+        snprintf(p->err, sizeof(p->err), "%s is not 16-byte aligned", name);
+        return TC_ERR_ARG;
+    }
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(p->err, sizeof(p->err), "%s: %s", name, cudaGetErrorString(e));
+        return TC_ERR_ARG;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
+        snprintf(p->err, sizeof(p->err), "%s is not device memory", name);
+        return TC_ERR_ARG;
+    }
+    return TC_OK;
+}
+
+// Fornberg's recursion for the weights of derivatives 0..md at z on nodes x[0..n-1]
+// (B. Fornberg, Math. Comp. 51 (1988) 699): c[i * (md+1) + k] is the weight of node i for
+// derivative k.
+static void fornberg(long double z, const long double* x, int n, int md, long double* c) {
+    for (int i = 0; i < n * (md + 1); ++i) c[i] = 0.0L;
+    long double c1 = 1.0L, c4 = x[0] - z;
+    c[0] = 1.0L;
+    for (int i = 1; i < n; ++i) {
+        int mn = std::min(i, md);
+        long double c2 = 1.0L, c5 = c4;
+        c4 = x[i] - z;
+        for (int j = 0; j < i; ++j) {
+            long double c3 = x[i] - x[j];
+            c2 *= c3;
+            if (j == i - 1) {
+                for (int k = mn; k >= 1; --k)
+                    c[i * (md + 1) + k] = c1 * (k * c[(i - 1) * (md + 1) + k - 1] -
+                                                c5 * c[(i - 1) * (md + 1) + k]) / c2;
+                c[i * (md + 1)] = -c1 * c5 * c[(i - 1) * (md + 1)] / c2;
+            }
+            for (int k = mn; k >= 1; --k)
+                c[j * (md + 1) + k] = (c4 * c[j * (md + 1) + k] - k * c[j * (md + 1) + k - 1]) / c3;
+            c[j * (md + 1)] = c4 * c[j * (md + 1)] / c3;
+        }
+        c1 = c2;
+    }
+}
+
+static bool factor_radices(int n, Radices& rad) {
+    rad.n = n;
+    rad.count = 0;
+    int m = n;
+    while (m % 4 == 0 && rad.count < kMaxRadix) { rad.r[rad.count++] = 4; m /= 4; }
+    while (m % 2 == 0 && rad.count < kMaxRadix) { rad.r[rad.count++] = 2; m /= 2; }
+    while (m % 3 == 0 && rad.count < kMaxRadix) { rad.r[rad.count++] = 3; m /= 3; }
+    return m == 1 && n > 1;
+}
+
+static void twiddles(int n, std::vector<double>& tw) {
+    tw.resize(2 * (size_t)n);
+    for (int j = 0; j < n; ++j) {
+        long double a = 2.0L * kPiL * (long double)j / (long double)n;
+        tw[2 * j] = (double)cosl(a);
+        tw[2 * j + 1] = (double)sinl(a);
+    }
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Banded LU with partial pivoting of one matrix given in row windows W[i][t] = A[i][i-kl+t],
+// t in [0, 2kl+ku] (kl = ku = 4).  On return W holds the multipliers of step j in
+// W[j+q][kl-q] (q = 1..kl, column j of L, LAPACK convention: not permuted by later steps)
+// and row j of U in W[j][kl..2kl+ku]; piv[j] = pivot row - j.  Returns false if singular.
+static bool band_lu(int n, double* W, uint8_t* piv) {
+    const int kl = kKl, w = 3 * kKl + 1;
+    auto at = [&](int i, int c) -> double& { return W[(size_t)i * w + (c - i + kl)]; };
+    for (int j = 0; j < n; ++j) {
+        int last = std::min(n - 1, j + kl);
+        int p = j;
+        double best = std::fabs(at(j, j));
+        for (int i = j + 1; i <= last; ++i)
+            if (std::fabs(at(i, j)) > best) { best = std::fabs(at(i, j)); p = i; }
+        if (best == 0.0) return false;
+        piv[j] = (uint8_t)(p - j);
+        int cmax = std::min(n - 1, j + 2 * kl);
+        if (p != j)
+            for (int c = j; c <= cmax; ++c) std::swap(at(j, c), at(p, c));
+        double d = at(j, j);
+        for (int i = j + 1; i <= last; ++i) {
+            double l = at(i, j) / d;
+            at(i, j) = l;
+            if (l != 0.0)
+                for (int c = j + 1; c <= cmax; ++c) at(i, c) -= l * at(j, c);
+        }
+    }
+    return true;
+}
+
+// Assemble the matrix of (set, m, ka) into row windows.
+static void assemble(const tc_plan* p, int set, int m, int ka, double* W) {
+    const int n = p->N_r, kl = kKl, w = 3 * kKl + 1;
+    std::fill(W, W + (size_t)n * w, 0.0);
+    auto at = [&](int i, int c) -> double& { return W[(size_t)i * w + (c - i + kl)]; };
+    const double mm = (double)m * p->m_p, kk = (double)ka * p->k_z;
+    const double c0 = 3.0 / (2.0 * p->dt);
+    for (int j = 0; j < n; ++j) {
+        const double* w1 = &p->w1[(size_t)j * kStencil];
+        const double* w2 = &p->w2[(size_t)j * kStencil];
+        const int c0l = p->col0[j];
+        const double r = p->r[j], ir = 1.0 / r, ir2 = 1.0 / (r * r);
+        bool wall = (j == 0 || j == n - 1);
+        if (set == kSetP) {
+            if (wall) {
+                if (j == n - 1 && m == 0 && ka == 0) { at(j, j) = 1.0; continue; }
+                for (int t = 0; t < kStencil; ++t)
+                    if (w1[t] != 0.0) at(j, c0l + t) += w1[t];
+                continue;
+            }
+            for (int t = 0; t < kStencil; ++t) {
+                double v = w2[t] + ir * w1[t];
+                if (v != 0.0) at(j, c0l + t) += v;
+            }
+            at(j, j) += -mm * mm * ir2 - kk * kk;
+        } else {
+            if (wall) { at(j, j) = 1.0; continue; }
+            for (int t = 0; t < kStencil; ++t) {
+                double v = -(w2[t] + ir * w1[t]);
+                if (v != 0.0) at(j, c0l + t) += v;
+            }
+            double diag = c0 + mm * mm * ir2 + kk * kk;
+            if (set == kSetHp) diag += ir2 + 2.0 * mm * ir2;
+            if (set == kSetHm) diag += ir2 - 2.0 * mm * ir2;
+            at(j, j) += diag;
+        }
+    }
+}
+
+static bool build_factors(tc_plan* p) {
+    const int n = p->N_r, M1 = p->M + 1, K1 = p->K + 1, w = 3 * kKl + 1;
+    const size_t per_set = (size_t)n * kBands * M1 * K1;
+    p->fac.assign((size_t)kNumSets * per_set, 0.0);
+    p->piv.assign((size_t)kNumSets * n * M1 * K1, 0);
+    bool ok = true;
+    unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    std::vector<char> good(nth, 1);
+    for (unsigned t = 0; t < nth; ++t) {
+        th.emplace_back([&, t]() {
+            std::vector<double> W((size_t)n * w);
+            std::vector<uint8_t> pv(n);
+            for (int job = t; job < kNumSets * M1; job += nth) {
+                int set = job / M1, m = job % M1;
+                for (int ka = 0; ka < K1; ++ka) {
+                    assemble(p, set, m, ka, W.data());
+                    if (!band_lu(n, W.data(), pv.data())) { good[t] = 0; return; }
+                    for (int j = 0; j < n; ++j) {
+                        auto dst = [&](int q) -> double& {
+                            return p->fac[(size_t)set * per_set + (((size_t)j * kBands + q) * M1 + m) * K1 + ka];
+                        };
+                        const double* row = &W[(size_t)j * w];
+                        for (int q = 1; q <= kKl; ++q)                       // L multipliers
+                            dst(q - 1) = (j + q < n) ? W[(size_t)(j + q) * w + (kKl - q)] : 0.0;
+                        dst(4) = 1.0 / row[kKl];                            // 1 / U_jj
+                        for (int q = 1; q <= 2 * kKl; ++q)                  // U_{j, j+q}
+                            dst(4 + q) = (j + q < n) ? row[kKl + q] : 0.0;
+                        p->piv[(((size_t)set * n + j) * M1 + m) * K1 + ka] = pv[j];
+                    }
+                }
+            }
+        });
+    }
+    for (auto& x : th) x.join();
+    for (char g : good) ok = ok && g;
+    return ok;
+}
+
+static tc_status upload(tc_plan* p) {
+    TC_CUDA(p, cudaGetDevice(&p->device));
+    auto put = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMalloc(dst, bytes);
+        if (e != cudaSuccess) return e;
+        return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    TC_CUDA(p, put((void**)&p->d_r, p->r.data(), p->r.size() * sizeof(double)));
+    TC_CUDA(p, put((void**)&p->d_w1, p->w1.data(), p->w1.size() * sizeof(double)));
+    TC_CUDA(p, put((void**)&p->d_w2, p->w2.data(), p->w2.size() * sizeof(double)));
+    TC_CUDA(p, put((void**)&p->d_col0, p->col0.data(), p->col0.size() * sizeof(int)));
+    TC_CUDA(p, put((void**)&p->d_fac, p->fac.data(), p->fac.size() * sizeof(double)));
+    TC_CUDA(p, put((void**)&p->d_piv, p->piv.data(), p->piv.size()));
+    TC_CUDA(p, put((void**)&p->d_tw_z, p->tw_z.data(), p->tw_z.size() * sizeof(double)));
+    TC_CUDA(p, put((void**)&p->d_tw_t, p->tw_t.data(), p->tw_t.size() * sizeof(double)));
+    std::vector<float> f(p->tw_z.begin(), p->tw_z.end());
+    TC_CUDA(p, put((void**)&p->d_tw_z32, f.data(), f.size() * sizeof(float)));
+    f.assign(p->tw_t.begin(), p->tw_t.end());
+    TC_CUDA(p, put((void**)&p->d_tw_t32, f.data(), f.size() * sizeof(float)));
+    return TC_OK;
+}
+
+const char* const kKernelNames[kNumKernels] = {
+    "k_zinv", "k_theta", "k_zfwd", "k_rhs_pressure", "k_band_solve_P", "k_rhs_velocity",
+    "k_band_solve_H", "k_rhs_div", "k_update", "k_axpby", "k_diag", "k_zinv_f32",
+    "k_theta_f32", "k_zfwd_f32", "k_mean_flow"};
+
+int prof_begin(tc_plan* p, int kid, cudaStream_t s) {
+    if (!p->prof_on) return -1;
+    if (2 * (p->prof_used + 1) > p->prof_ev.size()) {
+        size_t grow = std::max<size_t>(256, p->prof_ev.size());
+        for (size_t i = 0; i < grow; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return -1; }
+            p->prof_ev.push_back(e);
+        }
+    }
+    int slot = (int)p->prof_used++;
+    if ((size_t)slot >= p->prof_kid.size()) p->prof_kid.resize(slot + 1);
+    p->prof_kid[slot] = kid;
+    cudaEventRecord(p->prof_ev[2 * slot], s);
+    return slot;
+}
+
+void prof_end(tc_plan* p, int slot, cudaStream_t s) {
+    if (slot < 0) return;
+    cudaEventRecord(p->prof_ev[2 * slot + 1], s);
+}
+
+static void free_device(tc_plan* p) {
+    for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
+    p->prof_ev.clear();
+    void* ptrs[] = {p->d_r, p->d_w1, p->d_w2, p->d_col0, p->d_fac, p->d_piv,
+                    p->d_tw_z, p->d_tw_t, p->d_tw_z32, p->d_tw_t32};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+extern "C" {
+
+const char* tc_status_string(tc_status s) {
+    switch (s) {
+        case TC_OK: return "ok";
+        case TC_ERR_ARG: return "invalid argument";
+        case TC_ERR_CUDA: return "CUDA error";
+        case TC_ERR_OOM: return "out of memory";
+        case TC_ERR_NONFINITE: return "non-finite value in state";
+        case TC_ERR_TIMEOUT: return "device wait timed out";
+        case TC_ERR_STATE: return "call not allowed in this plan state";
+    }
+    return "unknown status";
+}
+
+const char* tc_plan_last_error(const tc_plan* plan) { return plan ? plan->err : "no plan"; }
+
+tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, double eta,
+                            double Re_i, double Re_o, double L_z, double dt, int fd_order,
+                            const tc_options* opt) {
+    if (!out) return TC_ERR_ARG;
+    *out = nullptr;
+    tc_options o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    if (fd_order < 2 || fd_order > 8 || fd_order % 2) return TC_ERR_ARG;
+    if (N_r < fd_order + 1 || N_r > 4096 || M < 1 || K < 1 || m_p < 1) return TC_ERR_ARG;
+    if (!(eta > 0.0 && eta < 1.0) || !(L_z > 0.0) || !(dt > 0.0)) return TC_ERR_ARG;
+    if (!std::isfinite(Re_i) || !std::isfinite(Re_o) || !std::isfinite(L_z) || !std::isfinite(dt))
+        return TC_ERR_ARG;
+    if (o.precision != TC_FP64 && o.precision != TC_MIXED) return TC_ERR_ARG;
+    double alpha = o.alpha == 0.0 ? 0.5 : (o.alpha < 0.0 ? 0.0 : o.alpha);
+    if (alpha > 1.0) return TC_ERR_ARG;
+    int Pt = o.P_theta ? o.P_theta : 3 * M;
+    int Pz = o.P_z ? o.P_z : 3 * K;
+    Radices rz, rt;
+    if (Pt < 2 * M + 1 || Pz < 2 * K + 1 || !factor_radices(Pz, rz) || !factor_radices(Pt, rt))
+        return TC_ERR_ARG;
+    if ((size_t)N_r * (M + 1) * (size_t)(2 * K + 1) > ((size_t)1 << 40)) return TC_ERR_ARG;
+
+    tc_plan* p = new (std::nothrow) tc_plan();
+    if (!p) return TC_ERR_OOM;
+    p->err[0] = 0;
+    p->N_r = N_r; p->M = M; p->K = K; p->m_p = m_p; p->fd_order = fd_order; p->half = fd_order / 2;
+    p->P_t = Pt; p->P_z = Pz; p->precision = o.precision;
+    p->eta = eta; p->Re_i = Re_i; p->Re_o = Re_o; p->L_z = L_z; p->dt = dt; p->alpha = alpha;
+    p->k_z = (double)(2.0L * kPiL / (long double)L_z);
+    p->r_i = eta / (1.0 - eta);
+    p->r_o = 1.0 / (1.0 - eta);
+    p->host_only = o.host_only != 0;
+    p->rad_z = rz;
+    p->rad_t = rt;
+    p->S = (size_t)N_r * (M + 1) * (2 * K + 1);
+    p->Hfield = (size_t)N_r * (M + 1) * Pz;
+    p->nmode = (M + 1) * (2 * K + 1);
+    p->nmode_half = (M + 1) * (K + 1);
+
+    // nodes, Eq. nodeDist with paper-M = N_r - 1, in long double
+    p->r.resize(N_r);
+    std::vector<long double> rl(N_r);
+    long double etal = eta, centre = (1.0L + etal) / (2.0L * (1.0L - etal));
+    for (int j = 0; j < N_r; ++j) {
+        long double c = cosl(kPiL * (long double)j / (long double)(N_r - 1));
+        long double s = alpha == 0.0 ? -c / 2.0L
+                                     : asinl(-(long double)alpha * c) / (2.0L * asinl((long double)alpha));
+        rl[j] = centre + s;
+        p->r[j] = (double)rl[j];
+    }
+    // FD weights, padded to 9 entries starting at col0
+    const int half = p->half;
+    p->w1.assign((size_t)N_r * kStencil, 0.0);
+    p->w2.assign((size_t)N_r * kStencil, 0.0);
+    p->col0.resize(N_r);
+    for (int j = 0; j < N_r; ++j) {
+        int lo, hi;
+        if (j == 0) { lo = 0; hi = half; }
+        else if (j == N_r - 1) { lo = N_r - 1 - half; hi = N_r - 1; }
+        else { int h = std::min(std::min(j, N_r - 1 - j), half); lo = j - h; hi = j + h; }
+        int c0 = std::min(std::max(j - kStencil / 2, 0), N_r - kStencil);
+        p->col0[j] = c0;
+        int n = hi - lo + 1;
+        long double c[kStencil * 3];
+        fornberg(rl[j], &rl[lo], n, 2, c);
+        for (int i = 0; i < n; ++i) {
+            p->w1[(size_t)j * kStencil + (lo + i - c0)] = (double)c[i * 3 + 1];
+            p->w2[(size_t)j * kStencil + (lo + i - c0)] = n >= 3 ? (double)c[i * 3 + 2] : 0.0;
+        }
+    }
+    twiddles(Pz, p->tw_z);
+    twiddles(Pt, p->tw_t);
+    if (!build_factors(p)) {
+        delete p;
+        return TC_ERR_ARG;  // a singular mode matrix (parameters out of range)
+    }
+    // launch geometry and workspace
+    const size_t cplx = sizeof(double2);
+    auto lines_for = [&](size_t esz) {
+        int L = 9;
+        while (L > 1 && (size_t)2 * L * Pz * esz > 200 * 1024) L = L == 9 ? 3 : 1;
+        return L;
+    };
+    auto zt_for = [&](size_t esz, int zmax) {
+        int zt = zmax;
+        while (zt > 1 && (size_t)2 * 6 * zt * Pt * esz > 200 * 1024) zt /= 2;
+        while (zt > 1 && Pz % zt) zt /= 2;
+        return zt;
+    };
+    p->zinv_lines = lines_for(sizeof(double2));
+    p->zinv_lines32 = lines_for(sizeof(float2));
+    p->zt = zt_for(sizeof(double2), 8);
+    p->zt32 = zt_for(sizeof(float2), 16);
+    if ((size_t)2 * 3 * Pz * cplx > 220 * 1024 || (size_t)2 * 6 * Pt * cplx > 220 * 1024) {
+        delete p;
+        return TC_ERR_ARG;   // transform lines too long for one block's shared memory
+    }
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o2 = off; off = align256(off + bytes); return o2; };
+    p->ws.H1 = take(9 * p->Hfield * cplx);
+    p->ws.H2 = take(3 * p->Hfield * cplx);
+    p->ws.Ncur = take(3 * p->S * cplx);
+    p->ws.pstar = take(p->S * cplx);
+    p->ws.ustar = take(3 * p->S * cplx);
+    p->ws.phi = take(p->S * cplx);
+    p->ws.uE = take(3 * p->S * cplx);
+    p->ws.red = take(4096 * sizeof(double));
+    p->ws.total = off;
+    if (!p->host_only) {
+        tc_status st = upload(p);
+        if (st != TC_OK) {
+            free_device(p);
+            delete p;
+            return st;
+        }
+    }
+    *out = p;
+    return TC_OK;
+}
+
+tc_status tc_plan_create(tc_plan** out, int N_r, int M, int K, int m_p, double eta, double Re_i,
+                         double Re_o, double L_z, double dt, int fd_order) {
+    return tc_plan_create_ex(out, N_r, M, K, m_p, eta, Re_i, Re_o, L_z, dt, fd_order, nullptr);
+}
+
+void tc_plan_destroy(tc_plan* plan) {
+    if (!plan) return;
+    free_device(plan);
+    delete plan;
+}
+
+tc_status tc_plan_workspace_bytes(const tc_plan* plan, size_t* bytes) {
+    if (!plan || !bytes) return TC_ERR_ARG;
+    *bytes = plan->ws.total;
+    return TC_OK;
+}
+
+tc_status tc_plan_nodes(const tc_plan* plan, double* r_host) {
+    if (!plan || !r_host) return TC_ERR_ARG;
+    memcpy(r_host, plan->r.data(), plan->r.size() * sizeof(double));
+    return TC_OK;
+}
+
+tc_status tc_profile_enable(tc_plan* plan, int enable) {
+    if (!plan) return TC_ERR_ARG;
+    if (plan->host_only) return TC_ERR_STATE;
+    plan->prof_on = enable != 0;
+    plan->prof_used = 0;
+    return TC_OK;
+}
+
+tc_status tc_profile_read(tc_plan* plan, int index, const char** name, long long* launches,
+                          double* total_ms) {
+    if (!plan || index < 0 || index >= kNumKernels) return TC_ERR_ARG;
+    if (plan->host_only) return TC_ERR_STATE;
+    long long n = 0;
+    double ms = 0.0;
+    for (size_t i = 0; i < plan->prof_used; ++i) {
+        if (plan->prof_kid[i] != index) continue;
+        TC_CUDA(plan, cudaEventSynchronize(plan->prof_ev[2 * i + 1]));
+        float t = 0.0f;
+        TC_CUDA(plan, cudaEventElapsedTime(&t, plan->prof_ev[2 * i], plan->prof_ev[2 * i + 1]));
+        ms += t;
+        ++n;
+    }
+    if (name) *name = kKernelNames[index];
+    if (launches) *launches = n;
+    if (total_ms) *total_ms = ms;
+    return TC_OK;
+}
+
+tc_status tc_plan_fd_weights(const tc_plan* plan, int deriv, double* w_host, int* col0_host) {
+    if (!plan || !w_host || (deriv != 1 && deriv != 2)) return TC_ERR_ARG;
+    const std::vector<double>& w = deriv == 1 ? plan->w1 : plan->w2;
+    memcpy(w_host, w.data(), w.size() * sizeof(double));
+    if (col0_host) memcpy(col0_host, plan->col0.data(), plan->col0.size() * sizeof(int));
+    return TC_OK;
+}
+
+}  // extern "C"

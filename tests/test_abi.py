@@ -1,0 +1,74 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol include/tc.h
+declares, validates arguments on the host, and its host plan (nodes, FD weights) agrees
+with the oracle's independent construction."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1311_2481_gb300 import build as B
+from paper_1311_2481_gb300 import tc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return tc.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "tc.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"\b(tc_[a-z_0-9]+)\s*\(", hdr))
+    assert names, "no declarations found"
+    for n in names:
+        assert hasattr(lib, n), n
+    assert names == set(tc.SYMBOLS)
+
+
+def test_argument_validation_before_any_launch(lib):
+    L = 2 * math.pi / 3.16
+    bad = [
+        dict(N_r=8, M=8, K=16),            # N_r < fd_order + 1
+        dict(N_r=32, M=0, K=16),
+        dict(N_r=32, M=8, K=16, eta=1.5),
+        dict(N_r=32, M=8, K=16, dt=-1.0),
+        dict(N_r=32, M=5, K=16),           # P_theta = 15 is not 2^a 3^b
+    ]
+    for kw in bad:
+        args = dict(N_r=32, M=8, K=16, m_p=1, eta=0.5, Re_i=50.0, Re_o=0.0, L_z=L, dt=1e-3)
+        args.update(kw)
+        with pytest.raises(tc.TCError) as e:
+            tc.Plan(**args, host_only=True)
+        assert e.value.status == tc.TC_ERR_ARG
+    with pytest.raises(tc.TCError):
+        tc.Plan(32, 8, 16, 1, 0.5, 50.0, 0.0, L, 1e-3, P_theta=16, host_only=True)   # < 2M+1
+
+
+def test_host_only_plan_rejects_compute_calls(lib):
+    p = tc.Plan(16, 4, 4, 1, 0.5, 50.0, 0.0, 2.0, 1e-3, host_only=True)
+    st = lib.tc_nonlinear(p.handle, None, None, None, None)
+    assert st == tc.TC_ERR_STATE
+    st = lib.tc_step(p.handle, None, 1, None, None)
+    assert st == tc.TC_ERR_STATE
+    assert p.ws_bytes > 0
+    assert lib.tc_status_string(tc.TC_ERR_NONFINITE).decode() == "non-finite value in state"
+
+
+def test_host_plan_matches_oracle_nodes_and_weights(lib):
+    import oracle as O
+    for (N, alpha) in ((32, 0.5), (45, 1.0), (24, 0.0)):
+        L = 2 * math.pi / 3.16
+        p = tc.Plan(N, 4, 4, 1, 0.5, 50.0, 0.0, L, 1e-3, alpha=alpha, host_only=True)
+        ops = O.Operators(O.Params(N, 4, 4, 1, 0.5, 50.0, 0.0, L, 1e-3, alpha=alpha))
+        np.testing.assert_array_max_ulp(p.nodes(), ops.r, maxulp=1)
+        for deriv, ref in ((1, ops.D1), (2, ops.D2)):
+            w, c = p.fd_weights(deriv)
+            D = np.zeros((N, N))
+            for j in range(N):
+                D[j, c[j]:c[j] + 9] = w[j]
+            assert np.abs(D - ref).max() <= 1e-13 * np.abs(ref).max()

@@ -1,0 +1,155 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on seeded inputs.
+
+Tolerances: relative L2 over all stored coefficients <= 1e-12 for one nonlinear evaluation
+and <= 1e-10 after 20 time steps (config: N_r = 32, m = -8..8, k = -16..16, Re_i = 50,
+dt = 1e-3); solves <= 1e-12 relative to the solution norm.  The oracle evaluates the same
+discrete method with naive DFT matrices and dense solves, so only rounding order differs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+from paper_1311_2481_gb300 import build as B  # noqa: E402
+from paper_1311_2481_gb300 import inputs as I  # noqa: E402
+from paper_1311_2481_gb300 import tc  # noqa: E402
+
+B.build()
+LZ = 2 * math.pi / 3.16
+CFG1 = dict(N_r=32, M=8, K=16, m_p=1, eta=0.5, Re_i=50.0, Re_o=0.0, L_z=LZ, dt=1e-3)
+CFG2 = dict(N_r=64, M=32, K=64, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=LZ, dt=5e-4)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def pair(cfg, **opt):
+    prm = O.Params(**cfg, **{k: v for k, v in opt.items() if k in ("alpha", "P_theta", "P_z")})
+    ops = O.Operators(prm)
+    plan = tc.Plan(**cfg, **opt)
+    return ops, plan
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def init(ops, kind="box", amp=1e-3, **kw):
+    prm = ops.prm
+    return I.initial_state(ops.r, prm.M, prm.K, prm.m_p, prm.L_z, prm.eta, prm.Re_i, prm.Re_o,
+                           kind=kind, amp=amp, **kw)
+
+
+@pytest.mark.parametrize("shape", [
+    dict(),                                               # config 1 (3/2 grid 24 x 48)
+    dict(N_r=20, M=6, K=9),                               # radix-2/3 only, ragged sizes
+    dict(N_r=11, M=4, K=5, P_theta=16, P_z=16),           # explicit grids (exact 3/2+ rule)
+    dict(N_r=9, M=1, K=1),                                # smallest: 3 x 3 grid, 9 nodes
+])
+def test_nonlinear_matches_oracle(shape):
+    cfg = {**CFG1, **{k: v for k, v in shape.items() if k in CFG1}}
+    opt = {k: v for k, v in shape.items() if k not in CFG1}
+    ops, plan = pair(cfg, **opt)
+    prm = ops.prm
+    for seed, u in ((0, init(ops, amp=1e-2, mbox=min(4, prm.M), kbox=min(4, prm.K))),
+                    (1, I.random_spectral((3,) + prm.shape(), seed=7))):
+        ref = O.nonlinear(ops, u)
+        got = host(plan.nonlinear(dev(u)))
+        assert rel(got, ref) <= 1e-12, (seed, rel(got, ref))
+
+
+def test_nonlinear_full_size_config2():
+    ops, plan = pair(CFG2)
+    u = init(ops, kind="taylor", amp=1e-2)
+    ref = O.nonlinear(ops, u)
+    got = host(plan.nonlinear(dev(u)))
+    assert rel(got, ref) <= 1e-12
+    pert = np.ones(got.shape, bool)
+    pert[:, :, 0, ops.prm.K] = False
+    assert rel(got[pert], ref[pert]) <= 1e-11
+
+
+@pytest.mark.parametrize("which,name", [(tc.TC_P_STAR, "P"), (tc.TC_U_PLUS, "Hp"),
+                                        (tc.TC_U_MINUS, "Hm"), (tc.TC_U_Z, "Hz"), (tc.TC_PHI, "P")])
+def test_banded_solves_match_dense(which, name):
+    ops, plan = pair({**CFG1, "N_r": 40})
+    prm = ops.prm
+    b = I.random_spectral(prm.shape(), seed=100 + which)
+    ref = O.solve_modes(ops, ops.mats[name], b)
+    got = host(plan.helmholtz_solve(which, dev(b)))
+    assert rel(got, ref) <= 1e-12, rel(got, ref)
+    x = dev(b)
+    plan.helmholtz_solve(which, x, x)          # in place
+    assert rel(host(x), ref) <= 1e-12
+
+
+def test_twenty_steps_match_oracle():
+    ops, plan = pair(CFG1)
+    u0 = init(ops)
+    st_o = O.cold_state(u0)
+    st_o = O.run(ops, st_o, 20)
+    st = tc.State(plan, dev(u0))
+    plan.step(st, 20)
+    for name in ("u", "u_prev", "N_prev", "p"):
+        got, ref = host(getattr(st, name)), getattr(st_o, name)
+        assert rel(got, ref) <= 1e-10, (name, rel(got, ref))
+    ref = st_o.u
+    pert = np.ones(ref.shape, bool)
+    pert[:, :, 0, ops.prm.K] = False
+    assert rel(host(st.u)[pert], ref[pert]) <= 1e-9
+    # stepping in two calls is the same as one call
+    st2 = tc.State(plan, dev(u0))
+    plan.step(st2, 7)
+    plan.step(st2, 13)
+    assert rel(host(st2.u), host(st.u)) <= 1e-14
+
+
+def test_step_full_size_config2():
+    ops, plan = pair(CFG2)
+    u0 = init(ops, kind="taylor", amp=1e-2)
+    st_o = O.run(ops, O.cold_state(u0), 2)
+    st = tc.State(plan, dev(u0))
+    plan.step(st, 2)
+    assert rel(host(st.u), st_o.u) <= 1e-11
+    assert rel(host(st.p), st_o.p) <= 1e-10
+
+
+def test_diagnostics_match_oracle():
+    ops, plan = pair(CFG1)
+    u = O.run(ops, O.cold_state(init(ops)), 3).u
+    d = plan.diagnostics(dev(u))
+    assert d.finite == 1
+    assert abs(d.energy / O.perturbation_energy(ops, u) - 1) < 1e-12
+    Ti, To = O.torque(ops, u)
+    assert abs(d.torque_inner / Ti - 1) < 1e-12 and abs(d.torque_outer / To - 1) < 1e-12
+    assert abs(d.max_div / O.max_divergence(ops, u) - 1) < 1e-10
+    bad = u.copy()
+    bad[2, 5, 1, 3] = np.nan
+    d = plan.diagnostics(dev(bad))
+    assert d.finite == 0
+
+
+def test_invalid_pointers_rejected():
+    ops, plan = pair(CFG1)
+    u = dev(init(ops))
+    lib = tc.load_library()
+    hostbuf = np.zeros(8, np.complex128)
+    st = lib.tc_nonlinear(plan.handle, hostbuf.ctypes.data, u.data_ptr(), plan._ws(), None)
+    assert st == tc.TC_ERR_ARG
+    st = lib.tc_nonlinear(plan.handle, u.data_ptr(), u.data_ptr(), plan._ws(), None)
+    assert st == tc.TC_ERR_ARG
+    st = lib.tc_helmholtz_solve(plan.handle, 7, u.data_ptr(), u.data_ptr(), plan._ws(), None)
+    assert st == tc.TC_ERR_ARG
