@@ -153,3 +153,44 @@ def test_invalid_pointers_rejected():
     assert st == tc.TC_ERR_ARG
     st = lib.tc_helmholtz_solve(plan.handle, 7, u.data_ptr(), u.data_ptr(), plan._ws(), None)
     assert st == tc.TC_ERR_ARG
+
+
+# ------------------------------------------------------------------ mixed precision form
+
+def _mean_removed(ops, u):
+    K = ops.prm.K
+    up = u.copy()
+    U = np.imag(u[0, :, 0, K] - u[1, :, 0, K]) / 2
+    up[0, :, 0, K] -= 1j * U
+    up[1, :, 0, K] += 1j * U
+    return up
+
+
+@pytest.mark.parametrize("cfg", [CFG1, CFG2])
+def test_mixed_nonlinear_error_is_fp32_level_of_the_perturbation_part(cfg):
+    """FP32 transforms of N(u') plus FP64 mean-flow terms: the error against the FP64
+    oracle is bounded by a few FP32 roundings of the perturbation part N(u')."""
+    ops = O.Operators(O.Params(**cfg))
+    plan = tc.Plan(**cfg, precision=tc.TC_MIXED)
+    u = init(ops, kind="taylor" if cfg is CFG2 else "box", amp=1e-2)
+    ref = O.nonlinear(ops, u)
+    ref_pert = O.nonlinear(ops, _mean_removed(ops, u))
+    got = host(plan.nonlinear(dev(u)))
+    err = np.linalg.norm(got - ref)
+    assert err <= 2e-6 * np.linalg.norm(ref_pert), err / np.linalg.norm(ref_pert)
+    assert err <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_mixed_twenty_steps_track_fp64():
+    ops = O.Operators(O.Params(**CFG1))
+    u0 = init(ops, amp=1e-2)
+    ref = O.run(ops, O.cold_state(u0), 20)
+    plan = tc.Plan(**CFG1, precision=tc.TC_MIXED)
+    st = tc.State(plan, dev(u0))
+    plan.step(st, 20)
+    got = host(st.u)
+    pert = np.ones(got.shape, bool)
+    pert[:, :, 0, ops.prm.K] = False
+    e_pert = np.linalg.norm(got[pert] - ref.u[pert]) / np.linalg.norm(ref.u[pert])
+    assert e_pert <= 1e-5, e_pert
+    assert rel(got, ref.u) <= 1e-8
