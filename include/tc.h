@@ -139,6 +139,16 @@ tc_status tc_step(tc_plan* plan, tc_state* st, int nsteps, void* ws, void* strea
  * writes *out (host).  Returns TC_ERR_NONFINITE if u holds a NaN/Inf. */
 tc_status tc_diagnostics(tc_plan* plan, const void* u, tc_diag* out, void* ws, void* stream);
 
+/* Nonlinear term exactly as tc_nonlinear, for callers that cannot allocate device memory
+ * (the paper has no counterpart: it is a packaging choice of this library).  Instead of a
+ * caller workspace, the staging lines between the transform kernels live in one static
+ * 80 MiB device array that every GPU loading the library keeps until the process exits.
+ * Plans needing more staging (12 * N_r * (M+1) * P_z complex values) get TC_ERR_ARG before
+ * any launch.  Allocates nothing.  The first call on each device looks up the array's
+ * address once (cudaGetSymbolAddress); make it before any stream capture.  All calls share
+ * the array: calls whose GPU work overlaps (other streams, unordered plans) race on it. */
+tc_status tc_nonlinear_noalloc(tc_plan* plan, const void* u_hat, void* N_hat, void* stream);
+
 /* Tracing (no counterpart in the paper beyond its per-phase timings, Table efficiency):
  * when enabled, every kernel the plan launches is bracketed by CUDA events recorded on the
  * launching stream.  tc_profile_enable(plan, 1) also clears earlier records.

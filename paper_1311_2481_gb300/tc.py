@@ -22,7 +22,7 @@ SYMBOLS = [
     "tc_plan_create", "tc_plan_create_ex", "tc_plan_destroy", "tc_plan_workspace_bytes",
     "tc_plan_nodes", "tc_plan_fd_weights", "tc_plan_last_error", "tc_status_string",
     "tc_nonlinear", "tc_helmholtz_solve", "tc_step", "tc_diagnostics",
-    "tc_profile_enable", "tc_profile_read",
+    "tc_nonlinear_noalloc", "tc_profile_enable", "tc_profile_read",
 ]
 
 
@@ -74,6 +74,7 @@ def load_library(path: str = LIB_PATH):
         "tc_helmholtz_solve": (I, [P, I, P, P, P, P]),
         "tc_step": (I, [P, ctypes.POINTER(tc_state), I, P, P]),
         "tc_diagnostics": (I, [P, P, ctypes.POINTER(tc_diag), P, P]),
+        "tc_nonlinear_noalloc": (I, [P, P, P, P]),
         "tc_profile_enable": (I, [P, I]),
         "tc_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(D)]),
