@@ -67,6 +67,8 @@ typedef struct {
     int P_z;          /* physical points in z;     0 -> 3K.  Must be 2^a 3^b >= 2K+1 */
     int precision;    /* tc_precision; TC_MIXED runs the transforms and products in FP32 */
     int host_only;    /* 1: build the host plan only (no device memory); for inspection */
+    int theta_zt;     /* launch tuning: z values per theta-pass block (0: automatic) */
+    int pc_modes;     /* launch tuning: modes per block of the steps-2-5 kernel (0: automatic) */
 } tc_options;
 
 /* Step state (Sec. 3.2): u = u^i, u_prev = u^{i-1}, N_prev = N^{i-1} (vector fields), p = p^i
@@ -132,12 +134,40 @@ tc_status tc_helmholtz_solve(tc_plan* plan, int which, const void* rhs, void* x,
 /* nsteps AB2BD2 steps (Sec. 3.2 steps 1-5) in place on the caller's state.  A cold state
  * (started == 0) first gets its history: one implicit Euler step of size 2dt/3 (the scheme
  * with u^{-1} = u^0, N^{-1} = N^0, same factors), u^{-1} = u^0 - 1.5 (u_E - u^0),
- * N^{-1} = N(u^{-1}); started is then set to 1. */
+ * N^{-1} = N(u^{-1}); started is then set to 1.  nsteps = 0 on a cold state builds only
+ * that history. */
 tc_status tc_step(tc_plan* plan, tc_state* st, int nsteps, void* ws, void* stream);
 
 /* Diagnostics of the velocity field u (device vector field); synchronises the stream and
  * writes *out (host).  Returns TC_ERR_NONFINITE if u holds a NaN/Inf. */
 tc_status tc_diagnostics(tc_plan* plan, const void* u, tc_diag* out, void* ws, void* stream);
+
+/* Adjoint state: adjoints (w.r.t. the Euclidean inner product on the stored (Re, Im) pairs)
+ * of the three vector fields a step carries forward. */
+typedef struct {
+    void* u;
+    void* u_prev;
+    void* N_prev;
+} tc_state_bar;
+
+/* Adjoint of one AB2BD2 step (differentiation form; the paper has no adjoint).  fwd is the
+ * forward state before the step (u^i, u^{i-1}, N^{i-1}; started = 1).  On entry bar holds the
+ * adjoints of the step's outputs (u^{i+1}, u^i, N^i); on return those of its inputs
+ * (u^i, u^{i-1}, N^{i-1}), in place.  The linear part is the transposed chain of Sec. 3.2
+ * steps 2-5 (transposed banded solves and stencils); the nonlinear part is the transposed
+ * linearisation of N(u) = u . grad u about fwd->u (recomputed).  Runs in FP64 for every plan
+ * precision.  The three bar arrays must be distinct. */
+tc_status tc_adjoint_step(tc_plan* plan, const tc_state* fwd, tc_state_bar* bar, void* ws,
+                          void* stream);
+/* Adjoint of the cold-start map u^0 -> (u^0, u^{-1}, N^{-1}) that tc_step applies to a state
+ * with started == 0 (its Euler step is recomputed from u0): given the adjoints in bar of
+ * (u^0, u^{-1}, N^{-1}), writes the adjoint of u^0 into u0_bar (distinct from u0 and from
+ * bar->u_prev, bar->N_prev). */
+tc_status tc_adjoint_start(tc_plan* plan, const void* u0, const tc_state_bar* bar, void* u0_bar,
+                           void* ws, void* stream);
+/* g = dJ/du for the perturbation energy J of tc_diag (gradient w.r.t. the stored (Re, Im)
+ * pairs, as complex numbers); u, g device vector fields. */
+tc_status tc_energy_gradient(tc_plan* plan, const void* u, void* g, void* stream);
 
 /* Nonlinear term exactly as tc_nonlinear, for callers that cannot allocate device memory
  * (the paper has no counterpart: it is a packaging choice of this library).  Instead of a

@@ -47,7 +47,9 @@ __all__ = [
     "derivative_matrices", "build_operators", "to_physical", "to_spectral",
     "physical_fields", "nonlinear", "mode_matrices", "div_h", "grad_h", "vector_laplacian_r",
     "solve_modes", "advance", "start_up", "step", "run", "couette_state", "perturbation_energy", "torque",
-    "max_divergence", "cold_state",
+    "max_divergence", "cold_state", "nonlinear_tangent", "tangent_step", "nonlinear_adjoint",
+    "adjoint_step", "adjoint_advance", "adjoint_start_up", "energy_gradient",
+    "gradient_final_energy", "inner",
 ]
 
 LD = np.longdouble
@@ -488,3 +490,239 @@ def torque(ops, u):
 def max_divergence(ops, u, interior=True):
     d = np.abs(div_h(ops, u))
     return float(d[1:-1].max() if interior else d.max())
+
+
+# ----------------------------------------------------------------------------------------
+# Tangent-linear and adjoint of one step (differentiation form; not in the paper)
+#
+# The step maps (u^i, u^{i-1}, N^{i-1}) -> (u^{i+1}, u^i, N^i); p^{i+1} is an output that is
+# not fed back.  Everything but N is affine, with the Dirichlet wall values as the only
+# constants, so the tangent is the step with N replaced by N'(u) du and zero wall values.
+# The adjoint is written with explicit transposes for the Euclidean inner product on the
+# stored (Re, Im) pairs: <a, b> = Re sum conj(a) b.
+# ----------------------------------------------------------------------------------------
+
+def _bilinear(ops, a_hat, b_hat):
+    """B(a, b) = (a . grad) b with the curvature terms, dealiased, so N(u) = B(u, u)."""
+    (ar, _, _, _), (at, _, _, _), (az, _, _, _) = physical_fields(ops, a_hat)
+    (br, brr, brt, brz), (bt, btr, btt, btz), (bz, bzr, bzt, bzz) = physical_fields(ops, b_hat)
+    r = ops.r[:, None, None]
+    Nr = ar * brr + (at / r) * brt + az * brz - at * bt / r
+    Nt = ar * btr + (at / r) * btt + az * btz + at * br / r
+    Nz = ar * bzr + (at / r) * bzt + az * bzz
+    Nr_h, Nt_h, Nz_h = (to_spectral(ops, f) for f in (Nr, Nt, Nz))
+    return np.stack([Nr_h + 1j * Nt_h, Nr_h - 1j * Nt_h, Nz_h])
+
+
+def nonlinear_tangent(ops, u, du):
+    """N'(u) du = B(du, u) + B(u, du)."""
+    return _bilinear(ops, du, u) + _bilinear(ops, u, du)
+
+
+def _advance_linear(ops, u, u_prev, N, N_prev):
+    """Steps 2-5 with zero Dirichlet wall values (the linear part of `advance`)."""
+    prm = ops.prm
+    mats = ops.mats
+    K, dt = prm.K, prm.dt
+    NN = 2.0 * N - N_prev
+    b = div_h(ops, -NN)
+    g = -(NN[0] + NN[1]) / 2.0 + 2.0 * vector_laplacian_r(ops, u) - vector_laplacian_r(ops, u_prev)
+    b[0] = g[0]
+    b[-1] = g[-1]
+    b[-1, 0, K] = 0.0
+    p_star = solve_modes(ops, mats["P"], b)
+    rhs = (4.0 * u - u_prev) / (2.0 * dt) - NN - grad_h(ops, p_star)
+    rhs[:, 0] = 0.0
+    rhs[:, -1] = 0.0
+    u_star = np.stack([solve_modes(ops, mats[n], rhs[c]) for c, n in enumerate(("Hp", "Hm", "Hz"))])
+    b = div_h(ops, u_star)
+    b[0] = 0.0
+    b[-1] = 0.0
+    phi = solve_modes(ops, mats["P"], b)
+    return u_star - grad_h(ops, phi)
+
+
+def tangent_step(ops, st: State, du, du_prev, dN_prev):
+    """Tangent of one step of a started state: returns (du^{i+1}, du^i, dN^i)."""
+    dN = nonlinear_tangent(ops, st.u, du)
+    return _advance_linear(ops, du, du_prev, dN, dN_prev), du, dN
+
+
+# transposes of the pieces ------------------------------------------------------------
+
+def _dr_T(ops, a):
+    return np.tensordot(ops.D1.T, a, axes=(1, 0))
+
+
+def _div_T(ops, b):
+    """Adjoint of div_h (all rows) for (v_+, v_-, v_z)."""
+    r = ops.r[:, None, None]
+    mm = ops.mm[None, :, None]
+    kk = ops.kk[None, None, :]
+    t = _dr_T(ops, b) + b / r                       # adjoint of D1 v_r + v_r / r w.r.t. v_r
+    vp = 0.5 * t + mm * b / (2.0 * r)
+    vm = 0.5 * t - mm * b / (2.0 * r)
+    vz = -1j * kk * b
+    return np.stack([vp, vm, vz])
+
+
+def _grad_T(ops, g):
+    """Adjoint of grad_h: (g_+, g_-, g_z) -> scalar."""
+    r = ops.r[:, None, None]
+    mm = ops.mm[None, :, None]
+    kk = ops.kk[None, None, :]
+    return _dr_T(ops, g[0] + g[1]) - mm * (g[0] - g[1]) / r - 1j * kk * g[2]
+
+
+def _lap_r_T_rows(ops, w, rows):
+    """Adjoint of the wall values ((L_+ u_+) + (L_- u_-))/2 at `rows` (w holds one value per
+    row in `rows`): returns (du_+, du_-) fields."""
+    prm = ops.prm
+    out = np.zeros((2,) + prm.shape(), np.complex128)
+    mm = ops.mm[:, None]
+    kk2 = (ops.kk ** 2)[None, :]
+    for wv, j in zip(w, rows):
+        r = ops.r[j]
+        for c, sg in ((0, -1.0), (1, 1.0)):
+            diag = -mm ** 2 / r ** 2 - kk2 - 1.0 / r ** 2 + sg * 2.0 * mm / r ** 2
+            out[c] += 0.5 * (ops.D2[j] + ops.D1[j] / r)[:, None, None] * wv[None]
+            out[c, j] += 0.5 * diag * wv
+    return out
+
+
+def _solve_T(ops, A, rhs):
+    """x = A^{-T} rhs for every mode (the matrices are real)."""
+    return solve_modes(ops, np.swapaxes(A, -1, -2), rhs)
+
+
+def _to_physical_T(ops, x):
+    """Adjoint of to_physical (complex (N_r, M+1, 2K+1) -> real (N_r, P_t, P_z))."""
+    g = np.matmul(np.conj(ops.G).T, x)              # (..., M+1, P_z)
+    return np.matmul(g, np.conj(ops.EzT).T)          # (..., M+1, 2K+1)
+
+
+def _to_spectral_T(ops, y):
+    """Adjoint of to_spectral: real field Re(Ft^H y FzT^H)."""
+    f = np.matmul(y, np.conj(ops.FzT).T)            # (..., M+1, P_z)
+    return np.real(np.matmul(np.conj(ops.Ft).T, f))
+
+
+def nonlinear_adjoint(ops, u, Nbar):
+    """(N'(u))^T Nbar."""
+    prm = ops.prm
+    r = ops.r[:, None, None]
+    (ur, urr, urt, urz), (ut, utr, utt, utz), (uz, uzr, uzt, uzz) = physical_fields(ops, u)
+    nr = _to_spectral_T(ops, Nbar[0] + Nbar[1])
+    nt = _to_spectral_T(ops, -1j * (Nbar[0] - Nbar[1]))
+    nz = _to_spectral_T(ops, Nbar[2])
+    bar = {
+        ("u", 0): nr * urr + nt * (utr + ut / r) + nz * uzr,
+        ("u", 1): nr * (urt - 2.0 * ut) / r + nt * (utt + ur) / r + nz * uzt / r,
+        ("u", 2): nr * urz + nt * utz + nz * uzz,
+        ("r", 0): ur * nr, ("t", 0): ut / r * nr, ("z", 0): uz * nr,
+        ("r", 1): ur * nt, ("t", 1): ut / r * nt, ("z", 1): uz * nt,
+        ("r", 2): ur * nz, ("t", 2): ut / r * nz, ("z", 2): uz * nz,
+    }
+    im = 1j * ops.mm[None, :, None]
+    ik = 1j * ops.kk[None, None, :]
+    comp = []
+    for c in range(3):
+        a = (_to_physical_T(ops, bar[("u", c)])
+             + _dr_T(ops, _to_physical_T(ops, bar[("r", c)]))
+             + np.conj(im) * _to_physical_T(ops, bar[("t", c)])
+             + np.conj(ik) * _to_physical_T(ops, bar[("z", c)]))
+        comp.append(a)
+    # (u_r, u_t, u_z) = ((u_+ + u_-)/2, (u_+ - u_-)/(2i), u_z): transpose
+    ub = np.empty((3,) + prm.shape(), np.complex128)
+    ub[0] = 0.5 * comp[0] + 0.5j * comp[1]
+    ub[1] = 0.5 * comp[0] - 0.5j * comp[1]
+    ub[2] = comp[2]
+    return ub
+
+
+def adjoint_advance(ops, ubar_new):
+    """Adjoint of the linear map (u, u_prev, N, N_prev) -> u^{i+1} of steps 2-5 (zero wall
+    values): returns the adjoints (u_b, up_b, N_b, Np_b) of its four inputs."""
+    prm = ops.prm
+    mats = ops.mats
+    K, dt = prm.K, prm.dt
+    # u^{i+1} = u* - grad phi
+    us_b = ubar_new.copy()
+    phi_b = -_grad_T(ops, ubar_new)
+    # phi = P^{-1} b, b = div u* on interior rows
+    b_b = _solve_T(ops, mats["P"], phi_b)
+    b_b[0] = 0.0
+    b_b[-1] = 0.0
+    us_b += _div_T(ops, b_b)
+    # u*_c = H_c^{-1} rhs_c, interior rows of rhs_c = (4u - u_prev)/(2dt) - NN - grad p*
+    rhs_b = np.stack([_solve_T(ops, mats[n], us_b[c]) for c, n in enumerate(("Hp", "Hm", "Hz"))])
+    rhs_b[:, 0] = 0.0
+    rhs_b[:, -1] = 0.0
+    u_b = 4.0 / (2.0 * dt) * rhs_b
+    up_b = -1.0 / (2.0 * dt) * rhs_b
+    NN_b = -rhs_b
+    ps_b = -_grad_T(ops, rhs_b)
+    # p* = P^{-1} b_p
+    bp_b = _solve_T(ops, mats["P"], ps_b)
+    wall = bp_b[[0, -1]].copy()
+    wall[1, 0, K] = 0.0                                 # (0,0) Dirichlet row at r_o
+    inside = bp_b.copy()
+    inside[0] = 0.0
+    inside[-1] = 0.0
+    NN_b += _div_T(ops, -inside)
+    # wall rows: -NN_r + 2 Lap_r(u) - Lap_r(u_prev), NN_r = (NN_+ + NN_-)/2
+    for i, j in enumerate((0, -1)):
+        NN_b[0, j] += -0.5 * wall[i]
+        NN_b[1, j] += -0.5 * wall[i]
+    L = _lap_r_T_rows(ops, wall, (0, prm.N_r - 1))
+    u_b[:2] += 2.0 * L
+    up_b[:2] -= L
+    # NN = 2N - N_prev
+    return u_b, up_b, 2.0 * NN_b, -NN_b
+
+
+def adjoint_step(ops, st: State, ubar_new, ubar_cur, Nbar_cur):
+    """Adjoint of one step of a started state st = (u^i, u^{i-1}, N^{i-1}): given the
+    adjoints of (u^{i+1}, u^i, N^i) returns those of (u^i, u^{i-1}, N^{i-1})."""
+    u_b, up_b, N_b, Np_b = adjoint_advance(ops, ubar_new)
+    u_b = u_b + ubar_cur + nonlinear_adjoint(ops, st.u, N_b + Nbar_cur)
+    return u_b, up_b, Np_b
+
+
+def adjoint_start_up(ops, u0, ubar, upbar, Npbar):
+    """Adjoint of the cold-start map u^0 -> (u^0, u^{-1}, N^{-1}) of `start_up`:
+    u^{-1} = 2.5 u^0 - 1.5 u_E(u^0), u_E = advance(u^0, u^0, N(u^0), N(u^0)),
+    N^{-1} = N(u^{-1})."""
+    u_m1 = start_up(ops, u0).u_prev
+    m1_b = upbar + nonlinear_adjoint(ops, u_m1, Npbar)
+    uE_b = -1.5 * m1_b
+    a_u, a_up, a_N, a_Np = adjoint_advance(ops, uE_b)
+    return ubar + 2.5 * m1_b + a_u + a_up + nonlinear_adjoint(ops, u0, a_N + a_Np)
+
+
+def energy_gradient(ops, u):
+    """Gradient of perturbation_energy w.r.t. the stored (Re, Im) pairs, as a complex array."""
+    base, _, _ = couette_state(ops)
+    d = u - base
+    w = _trapezoid_weights(ops.r) * ops.r
+    c = np.full(ops.prm.M + 1, 2.0)
+    c[0] = 1.0
+    wc = w[:, None, None] * c[None, :, None]
+    return np.stack([0.5 * wc * d[0], 0.5 * wc * d[1], wc * d[2]])
+
+
+def gradient_final_energy(ops, u0, nsteps):
+    """dJ/du^0 of J = perturbation_energy(u^n) after nsteps from the cold state u^0, by the
+    adjoint (states of the forward run kept in memory)."""
+    states = [start_up(ops, u0)]
+    for _ in range(nsteps - 1):
+        states.append(step(ops, states[-1]))
+    uN = step(ops, states[-1]).u
+    ub, upb, Npb = energy_gradient(ops, uN), np.zeros_like(u0), np.zeros_like(u0)
+    for st in reversed(states):
+        ub, upb, Npb = adjoint_step(ops, st, ub, upb, Npb)
+    return adjoint_start_up(ops, u0, ub, upb, Npb), perturbation_energy(ops, uN)
+
+
+def inner(a, b):
+    return float(np.real(np.vdot(a, b)))

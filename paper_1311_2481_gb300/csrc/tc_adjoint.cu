@@ -1,0 +1,791 @@
+// Adjoint of the AB2BD2 step (differentiation form; the paper has no adjoint).  The step maps
+// (u^i, u^{i-1}, N^{i-1}) -> (u^{i+1}, u^i, N^i) and is affine except for N(u) = u . grad u,
+// so its adjoint is the transposed chain of the linear part (steps 2-5 of Sec. 3.2:
+// transposed banded solves, transposed stencils) plus the transposed linearised nonlinear
+// term about the forward state (transposed forward transforms = unscaled inverse transforms
+// and vice versa, the transposed pointwise products, the transposed radial stencil).  The
+// inner product is the Euclidean one on the stored (Re, Im) pairs.
+#include "tc_fft_core.cuh"
+#include "tc_solve_core.cuh"
+
+namespace tc {
+
+static int ablocks(size_t n, int bs) { return (int)((n + bs - 1) / bs); }
+
+// x <- A^{-T} x on one real part of column t of a [N][T] smem array, for A = P L U stored
+// as in smem_band_solve: first U^T y = x (forward), then for j = N-1..0 the transposed
+// elimination x_j -= sum_q l_q(j) x_{j+q} followed by the row interchange j <-> j + piv_j.
+__device__ __forceinline__ void smem_band_solve_T(double2* col, int T, int t, int part, int N,
+                                                  const double* __restrict__ F,
+                                                  const uint8_t* __restrict__ P, int M1K1) {
+    double* x = reinterpret_cast<double*>(col) + 2 * t + part;
+    const int st = 2 * T;
+    // U^T y = b: y_j = (b_j - sum_{q=1..8} U(j-q, j) y_{j-q}) / U_jj; U(j-q, j) is band 4+q of row j-q
+    double y1 = 0.0, y2 = 0.0, y3 = 0.0, y4 = 0.0, y5 = 0.0, y6 = 0.0, y7 = 0.0, y8 = 0.0;
+    for (int j = 0; j < N; ++j) {
+        double s = x[(size_t)j * st];
+        const size_t b = (size_t)j * kBands * M1K1;
+        const size_t rs = (size_t)kBands * M1K1;   // one row of factors
+        if (j >= 8) s = fma(-__ldg(&F[b - 8 * rs + (size_t)12 * M1K1]), y8, s);
+        if (j >= 7) s = fma(-__ldg(&F[b - 7 * rs + (size_t)11 * M1K1]), y7, s);
+        if (j >= 6) s = fma(-__ldg(&F[b - 6 * rs + (size_t)10 * M1K1]), y6, s);
+        if (j >= 5) s = fma(-__ldg(&F[b - 5 * rs + (size_t)9 * M1K1]), y5, s);
+        if (j >= 4) s = fma(-__ldg(&F[b - 4 * rs + (size_t)8 * M1K1]), y4, s);
+        if (j >= 3) s = fma(-__ldg(&F[b - 3 * rs + (size_t)7 * M1K1]), y3, s);
+        if (j >= 2) s = fma(-__ldg(&F[b - 2 * rs + (size_t)6 * M1K1]), y2, s);
+        if (j >= 1) s = fma(-__ldg(&F[b - 1 * rs + (size_t)5 * M1K1]), y1, s);
+        const double yj = s * __ldg(&F[b + (size_t)4 * M1K1]);
+        x[(size_t)j * st] = yj;
+        y8 = y7; y7 = y6; y6 = y5; y5 = y4; y4 = y3; y3 = y2; y2 = y1; y1 = yj;
+    }
+    // transposed eliminations and interchanges, j = N-1 .. 0; w1..w4 hold x_{j+1..j+4}
+    double w1 = 0.0, w2 = 0.0, w3 = 0.0, w4 = 0.0;
+    for (int j = N - 1; j >= 0; --j) {
+        const double* Fj = F + (size_t)j * kBands * M1K1;
+        double w0 = x[(size_t)j * st];
+        w0 = fma(-__ldg(&Fj[0]), w1, w0);
+        w0 = fma(-__ldg(&Fj[(size_t)M1K1]), w2, w0);
+        w0 = fma(-__ldg(&Fj[(size_t)2 * M1K1]), w3, w0);
+        w0 = fma(-__ldg(&Fj[(size_t)3 * M1K1]), w4, w0);
+        const int pj = P[(size_t)j * M1K1];
+        if (pj == 1) { double q = w0; w0 = w1; w1 = q; }
+        else if (pj == 2) { double q = w0; w0 = w2; w2 = q; }
+        else if (pj == 3) { double q = w0; w0 = w3; w3 = q; }
+        else if (pj == 4) { double q = w0; w0 = w4; w4 = q; }
+        if (j + 4 < N) x[(size_t)(j + 4) * st] = w4;   // x_{j+4} is final
+        w4 = w3; w3 = w2; w2 = w1; w1 = w0;
+    }
+    // flush the window: x_0..x_3
+    if (N > 0) x[0] = w1;
+    if (N > 1) x[(size_t)st] = w2;
+    if (N > 2) x[(size_t)2 * st] = w3;
+    if (N > 3) x[(size_t)3 * st] = w4;
+}
+
+// (D1^T v)(c) for column t of smem array C ([N][T]): gather over the rows whose stencil
+// holds c, from the host-built table (row, weight) padded with zero weights.
+__device__ __forceinline__ double2 sdrowT(const double2* C, const int* __restrict__ trow,
+                                          const double* __restrict__ tw, int ntab, int c, int T, int t) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int e = 0; e < ntab; ++e) {
+        const double w = __ldg(&tw[c * ntab + e]);
+        const double2 v = C[__ldg(&trow[c * ntab + e]) * T + t];
+        s.x = fma(w, v.x, s.x);
+        s.y = fma(w, v.y, s.y);
+    }
+    return s;
+}
+
+struct PCAdjArgs {
+    const double2* ubar_new;   // adjoint of u^{i+1}
+    const double2* ubar_cur;   // adjoint of u^i from the later step (may be null: zero)
+    const double2* Nbar_cur;   // adjoint of N^i from the later step (may be null: zero)
+    double2* u_out;            // ubar_cur + linear-part adjoint of u^i (nonlinear part added later)
+    double2* up_out;           // adjoint of u^{i-1}
+    double2* N_out;            // total adjoint of N^i (input of the transposed nonlinear term)
+    double2* Np_out;           // adjoint of N^{i-1}
+    const double* rn;
+    const double* w1;
+    const double* w2;
+    const int* col0;
+    const int* trow;
+    const double* tw;
+    int ntab;
+    const double* fac;
+    const uint8_t* piv;
+};
+
+// Adjoint of k_pc (steps 2-5 of Sec. 3.2), phases in reverse order.  Shared memory as in
+// k_pc: C0 scalar column, C1..C3 vector columns, [N][T] each.
+__global__ void __launch_bounds__(256) k_pc_adj(PCAdjArgs a, Geo g, int T) {
+    extern __shared__ double2 sm[];
+    const int N = g.N;
+    const int items = N * T;
+    double2* C0 = sm;
+    double2* C1 = sm + items;
+    double2* C2 = C1 + items;
+    double2* C3 = C2 + items;
+    double2* Cv[3] = {C1, C2, C3};
+    const int mode0 = blockIdx.x * T;
+    const int nT = min(T, g.nmode - mode0);
+    const size_t per_set = (size_t)N * kBands * g.M1K1;
+    const double dt = g.dt;
+    auto minfo = [&](int t, int& m, int& k) {
+        const int mode = mode0 + t;
+        m = mode / g.nk;
+        k = mode - m * g.nk - g.K;
+    };
+
+    // G': u*bar = ubar_new; phibar = -grad_h^T ubar_new
+    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int j = idx / T, t = idx - (idx / T) * T;
+        double2 v0 = make_double2(0.0, 0.0), v1 = v0, v2 = v0;
+        if (t < nT) {
+            const size_t e = (size_t)j * g.nmode + mode0 + t;
+            v0 = a.ubar_new[e];
+            v1 = a.ubar_new[g.S + e];
+            v2 = a.ubar_new[2 * g.S + e];
+        }
+        C1[idx] = v0;
+        C2[idx] = v1;
+        C3[idx] = v2;
+    }
+    __syncthreads();
+    // grad_h^T g = D1^T(g_+ + g_-) - m m_p (g_+ - g_-)/r - i k k_z g_z  (into C0, negated)
+    auto gradT = [&](int j, int t) {
+        int m, k;
+        minfo(t, m, k);
+        const double2 dp = sdrowT(C1, a.trow, a.tw, a.ntab, j, T, t);
+        const double2 dm = sdrowT(C2, a.trow, a.tw, a.ntab, j, T, t);
+        const double2 gp = C1[j * T + t], gm = C2[j * T + t], gz = C3[j * T + t];
+        const double mm = g.mp * m / a.rn[j], kk = g.kz * k;
+        double2 o;
+        o.x = dp.x + dm.x - mm * (gp.x - gm.x) + kk * gz.y;
+        o.y = dp.y + dm.y - mm * (gp.y - gm.y) - kk * gz.x;
+        return o;
+    };
+    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int j = idx / T, t = idx - (idx / T) * T;
+        double2 o = make_double2(0.0, 0.0);
+        if (t < nT) {
+            const double2 q = gradT(j, t);
+            o = make_double2(-q.x, -q.y);
+        }
+        C0[idx] = o;
+    }
+    __syncthreads();
+    // F': bbar = P^{-T} phibar, wall rows carry no dependence
+    if (threadIdx.x < 2 * nT) {
+        const int t = threadIdx.x >> 1, part = threadIdx.x & 1;
+        int m, k;
+        minfo(t, m, k);
+        const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+        smem_band_solve_T(C0, T, t, part, N, a.fac + (size_t)kSetP * per_set + mk,
+                          a.piv + (size_t)kSetP * N * g.M1K1 + mk, g.M1K1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        C0[t] = make_double2(0.0, 0.0);
+        C0[(N - 1) * T + t] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    // E': u*bar += div_h^T bbar:  t = D1^T b + b/r;  +: t/2 + m m_p b/(2r), -: t/2 - .., z: -i k k_z b
+    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int j = idx / T, t = idx - (idx / T) * T;
+        if (t >= nT) continue;
+        int m, k;
+        minfo(t, m, k);
+        const double ir = 1.0 / a.rn[j];
+        const double2 d = sdrowT(C0, a.trow, a.tw, a.ntab, j, T, t);
+        const double2 b = C0[idx];
+        const double2 tt = make_double2(d.x + b.x * ir, d.y + b.y * ir);
+        const double mm = 0.5 * g.mp * m * ir, kk = g.kz * k;
+        double2 v;
+        v = C1[idx]; v.x += 0.5 * tt.x + mm * b.x; v.y += 0.5 * tt.y + mm * b.y; C1[idx] = v;
+        v = C2[idx]; v.x += 0.5 * tt.x - mm * b.x; v.y += 0.5 * tt.y - mm * b.y; C2[idx] = v;
+        v = C3[idx]; v.x += kk * b.y; v.y -= kk * b.x; C3[idx] = v;
+    }
+    __syncthreads();
+    // D': rhsbar_c = H_c^{-T} u*bar_c; wall rows of rhs are constants
+    if (threadIdx.x < 6 * nT) {
+        const int c = threadIdx.x / (2 * nT), rem = threadIdx.x - c * 2 * nT;
+        const int t = rem >> 1, part = rem & 1;
+        int m, k;
+        minfo(t, m, k);
+        const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+        const int set = kSetHp + c;
+        smem_band_solve_T(Cv[c], T, t, part, N, a.fac + (size_t)set * per_set + mk,
+                          a.piv + (size_t)set * N * g.M1K1 + mk, g.M1K1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += blockDim.x)
+        for (int c = 0; c < 3; ++c) {
+            Cv[c][t] = make_double2(0.0, 0.0);
+            Cv[c][(N - 1) * T + t] = make_double2(0.0, 0.0);
+        }
+    __syncthreads();
+    // C': ubar += (4/(2dt)) rhsbar, up_bar = -rhsbar/(2dt); p*bar = -grad_h^T rhsbar (C0)
+    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int j = idx / T, t = idx - (idx / T) * T;
+        double2 o = make_double2(0.0, 0.0);
+        if (t < nT) {
+            const size_t e = (size_t)j * g.nmode + mode0 + t;
+            for (int c = 0; c < 3; ++c) {
+                const size_t ec = (size_t)c * g.S + e;
+                const double2 rb = Cv[c][idx];
+                double2 ub = a.ubar_cur ? a.ubar_cur[ec] : make_double2(0.0, 0.0);
+                ub.x += 2.0 / dt * rb.x;
+                ub.y += 2.0 / dt * rb.y;
+                a.u_out[ec] = ub;
+                a.up_out[ec] = make_double2(-rb.x / (2.0 * dt), -rb.y / (2.0 * dt));
+            }
+            const double2 q = gradT(j, t);
+            o = make_double2(-q.x, -q.y);
+        }
+        C0[idx] = o;
+    }
+    __syncthreads();
+    // NNbar = -rhsbar (in place)
+    for (int idx = threadIdx.x; idx < 3 * items; idx += blockDim.x) {
+        double2* C = Cv[idx / items];
+        const int r = idx % items;
+        C[r] = make_double2(-C[r].x, -C[r].y);
+    }
+    __syncthreads();
+    // B': bpbar = P^{-T} p*bar
+    if (threadIdx.x < 2 * nT) {
+        const int t = threadIdx.x >> 1, part = threadIdx.x & 1;
+        int m, k;
+        minfo(t, m, k);
+        const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+        smem_band_solve_T(C0, T, t, part, N, a.fac + (size_t)kSetP * per_set + mk,
+                          a.piv + (size_t)kSetP * N * g.M1K1 + mk, g.M1K1);
+    }
+    __syncthreads();
+    // A': interior rows b_p = div_h(-NN): NNbar += div_h^T(-bpbar_interior);
+    //     wall rows b_p = -NN_r + 2 Lap_r(u) - Lap_r(u_prev) (not the (0,0) row at r_o)
+    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int j = idx / T, t = idx - (idx / T) * T;
+        if (t >= nT) continue;
+        int m, k;
+        minfo(t, m, k);
+        const double ir = 1.0 / a.rn[j];
+        // v = -bpbar on interior rows, 0 on wall rows
+        double2 d = make_double2(0.0, 0.0);
+        for (int e = 0; e < a.ntab; ++e) {
+            const int row = __ldg(&a.trow[j * a.ntab + e]);
+            if (row == 0 || row == N - 1) continue;
+            const double w = __ldg(&a.tw[j * a.ntab + e]);
+            const double2 b = C0[row * T + t];
+            d.x -= w * b.x;
+            d.y -= w * b.y;
+        }
+        double2 v = make_double2(0.0, 0.0);
+        if (j > 0 && j < N - 1) v = make_double2(-C0[idx].x, -C0[idx].y);
+        const double2 tt = make_double2(d.x + v.x * ir, d.y + v.y * ir);
+        const double mm = 0.5 * g.mp * m * ir, kk = g.kz * k;
+        double2 q;
+        q = C1[idx]; q.x += 0.5 * tt.x + mm * v.x; q.y += 0.5 * tt.y + mm * v.y;
+        if (j == 0 || (j == N - 1 && !(m == 0 && k == 0))) { q.x -= 0.5 * C0[idx].x; q.y -= 0.5 * C0[idx].y; }
+        C1[idx] = q;
+        q = C2[idx]; q.x += 0.5 * tt.x - mm * v.x; q.y += 0.5 * tt.y - mm * v.y;
+        if (j == 0 || (j == N - 1 && !(m == 0 && k == 0))) { q.x -= 0.5 * C0[idx].x; q.y -= 0.5 * C0[idx].y; }
+        C2[idx] = q;
+        q = C3[idx]; q.x += kk * v.y; q.y -= kk * v.x;
+        C3[idx] = q;
+    }
+    // wall Laplacian transposes: column c of the wall stencils receives, for wall row jw with
+    // value w: 1/2 (D2[jw][c] + D1[jw][c]/r_jw) w (+ 1/2 diag_pm w at c = jw), times 2 into
+    // ubar and -1 into up_bar.  One thread per (column, mode) of the two wall stencils.
+    for (int idx = threadIdx.x; idx < 2 * kStencil * T; idx += blockDim.x) {
+        const int side = idx / (kStencil * T);
+        const int rem = idx - side * kStencil * T;
+        const int q = rem / T, t = rem - (rem / T) * T;
+        if (t >= nT) continue;
+        int m, k;
+        minfo(t, m, k);
+        const int jw = side == 0 ? 0 : N - 1;
+        if (jw == N - 1 && m == 0 && k == 0) continue;
+        const int c = a.col0[jw] + q;
+        const double r = a.rn[jw], ir = 1.0 / r, ir2 = ir * ir;
+        const double wq = 0.5 * (a.w2[jw * kStencil + q] + ir * a.w1[jw * kStencil + q]);
+        const double2 w = C0[jw * T + t];
+        const double mm = g.mp * m, kk = g.kz * k;
+        const size_t e = (size_t)c * g.nmode + mode0 + t;
+        for (int cc = 0; cc < 2; ++cc) {
+            double coef = wq;
+            if (c == jw) {
+                const double sgn = cc == 0 ? -1.0 : 1.0;
+                coef += 0.5 * (-mm * mm * ir2 - kk * kk - ir2 + sgn * 2.0 * mm * ir2);
+            }
+            if (coef == 0.0) continue;
+            const size_t ec = (size_t)cc * g.S + e;
+            // rows of the two wall stencils may share a column only when N_r < 10; the
+            // two sides then run in sequence below to keep the read-modify-write race free
+            if (side == 1 && N < 2 * kStencil) continue;
+            double2 ub = a.u_out[ec], pb = a.up_out[ec];
+            ub.x += 2.0 * coef * w.x; ub.y += 2.0 * coef * w.y;
+            pb.x -= coef * w.x; pb.y -= coef * w.y;
+            a.u_out[ec] = ub;
+            a.up_out[ec] = pb;
+        }
+    }
+    __syncthreads();
+    if (N < 2 * kStencil) {   // second wall for small N_r, after the first
+        for (int idx = threadIdx.x; idx < kStencil * T; idx += blockDim.x) {
+            const int q = idx / T, t = idx - (idx / T) * T;
+            if (t >= nT) continue;
+            int m, k;
+            minfo(t, m, k);
+            const int jw = N - 1;
+            if (m == 0 && k == 0) continue;
+            const int c = a.col0[jw] + q;
+            const double r = a.rn[jw], ir = 1.0 / r, ir2 = ir * ir;
+            const double wq = 0.5 * (a.w2[jw * kStencil + q] + ir * a.w1[jw * kStencil + q]);
+            const double2 w = C0[jw * T + t];
+            const double mm = g.mp * m, kk = g.kz * k;
+            const size_t e = (size_t)c * g.nmode + mode0 + t;
+            for (int cc = 0; cc < 2; ++cc) {
+                double coef = wq;
+                if (c == jw) {
+                    const double sgn = cc == 0 ? -1.0 : 1.0;
+                    coef += 0.5 * (-mm * mm * ir2 - kk * kk - ir2 + sgn * 2.0 * mm * ir2);
+                }
+                if (coef == 0.0) continue;
+                const size_t ec = (size_t)cc * g.S + e;
+                double2 ub = a.u_out[ec], pb = a.up_out[ec];
+                ub.x += 2.0 * coef * w.x; ub.y += 2.0 * coef * w.y;
+                pb.x -= coef * w.x; pb.y -= coef * w.y;
+                a.u_out[ec] = ub;
+                a.up_out[ec] = pb;
+            }
+        }
+        __syncthreads();
+    }
+    // NN = 2N - N_prev:  Nbar = Nbar_cur + 2 NNbar,  Np_bar = -NNbar
+    for (int idx = threadIdx.x; idx < 3 * items; idx += blockDim.x) {
+        const int c = idx / items, rem = idx - c * items;
+        const int j = rem / T, t = rem - (rem / T) * T;
+        if (t >= nT) continue;
+        const size_t ec = (size_t)c * g.S + (size_t)j * g.nmode + mode0 + t;
+        const double2 nn = Cv[c][rem];
+        double2 nb = a.Nbar_cur ? a.Nbar_cur[ec] : make_double2(0.0, 0.0);
+        nb.x += 2.0 * nn.x;
+        nb.y += 2.0 * nn.y;
+        a.N_out[ec] = nb;
+        a.Np_out[ec] = make_double2(-nn.x, -nn.y);
+    }
+}
+
+// ---------------------------------------------------------------- transposed nonlinear term
+// Transposed forward transform: a physical field x = (1/(P_t P_z)) Re sum_{m>=0,k} w e^{i phi};
+// with the C2R convention (weight 2 for m > 0) the lines carry w/2 for m > 0.  Lines per
+// (r, m): s_r = (Nbar_+ + Nbar_-), s_t = -i (Nbar_+ - Nbar_-), s_z = Nbar_z.
+__global__ void __launch_bounds__(256) k_zinv_adjin(const double2* __restrict__ Nb, double2* __restrict__ H,
+                                                    int N_r, int M, int K, double scale,
+                                                    const double2* __restrict__ tw, Radices rad) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Pz = rad.n;
+    double2* a = reinterpret_cast<double2*>(smem_raw);
+    double2* b = a + (size_t)3 * Pz;
+    const int m = blockIdx.x % (M + 1);
+    const int r = blockIdx.x / (M + 1);
+    const int nk = 2 * K + 1;
+    const size_t S = (size_t)N_r * (M + 1) * nk;
+    const size_t o = ((size_t)r * (M + 1) + m) * nk;
+    const double cm = (m == 0 ? 1.0 : 0.5) * scale;
+    for (int idx = threadIdx.x; idx < 3 * Pz; idx += blockDim.x) {
+        const int l = idx / Pz, q = idx - l * Pz;
+        const int k = q <= K ? q : q - Pz;
+        double2 v = make_double2(0.0, 0.0);
+        if (k >= -K && k <= K) {
+            const size_t e = o + (k + K);
+            if (l == 0) { const double2 p = Nb[e], n = Nb[S + e]; v = make_double2(p.x + n.x, p.y + n.y); }
+            else if (l == 1) { const double2 p = Nb[e], n = Nb[S + e]; v = make_double2(p.y - n.y, -(p.x - n.x)); }
+            else v = Nb[2 * S + e];
+            v.x *= cm;
+            v.y *= cm;
+        }
+        a[idx] = v;
+    }
+    __syncthreads();
+    double2* res = smem_fft(a, b, 3, tw, true, rad);
+    const size_t fstride = (size_t)N_r * (M + 1) * Pz;
+    for (int idx = threadIdx.x; idx < 3 * Pz; idx += blockDim.x) {
+        const int l = idx / Pz, z = idx - l * Pz;
+        H[l * fstride + ((size_t)r * (M + 1) + m) * Pz + z] = res[idx];
+    }
+}
+
+// Per (r, z tile): recompute the 12 forward physical fields (6 lines per z as in k_theta),
+// the 3 adjoint physical fields (1 line (s_r, s_t) per z, s_z two z per line), the
+// transposed products, and the transposed inverse theta transform (unscaled forward DFT
+// times c_m) of the 12 adjoint fields as 6 paired lines.  Output per (r, m, z), 9 lines in
+// the (+, -, z) basis: A (u, with -i m m_p d_theta folded in), R (d_r), Z (d_z).
+__global__ void __launch_bounds__(256) k_theta_adj(const double2* __restrict__ H1, const double2* __restrict__ Ha,
+                                                   double2* __restrict__ H3, const double* __restrict__ rnodes,
+                                                   int N_r, int M, int Pz, double mp, int zt,
+                                                   const double2* __restrict__ tw, Radices rad) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Pt = rad.n;
+    const int nza = (zt + 1) / 2;
+    const int nl = 7 * zt + nza;               // 6 forward + 1 (s_r, s_t) per z + s_z pairs
+    const int nbuf = nl > 6 * zt ? nl : 6 * zt;
+    double2* A = reinterpret_cast<double2*>(smem_raw);
+    double2* B = A + (size_t)nbuf * Pt;
+    const int tiles = Pz / zt;
+    const int r = blockIdx.x / tiles;
+    const int z0 = (blockIdx.x % tiles) * zt;
+    const size_t fstride = (size_t)N_r * (M + 1) * Pz;
+    const double2* h = H1 + (size_t)r * (M + 1) * Pz + z0;
+    const double2* ha = Ha + (size_t)r * (M + 1) * Pz + z0;
+
+    for (int idx = threadIdx.x; idx < nl * Pt; idx += blockDim.x) A[idx] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < (7 * zt + nza) * (M + 1); idx += blockDim.x) {
+        const int m = idx % (M + 1);
+        const int L = idx / (M + 1);
+        const double mm = mp * m;
+        double2* line = A + (size_t)L * Pt;
+        if (L < 6 * zt) {   // forward lines, as in k_theta
+            const int zi = L / 6, pr = L - 6 * (L / 6);
+            const size_t o = (size_t)m * Pz + zi;
+            if (pr < 4) {
+                const int fa = pr == 0 ? 0 : pr == 1 ? 3 : pr == 2 ? 0 : 6;
+                double2 Av = h[fa * fstride + o], Bv = h[(fa + 1) * fstride + o];
+                if (pr == 2) { Av = make_double2(-mm * Av.y, mm * Av.x); Bv = make_double2(-mm * Bv.y, mm * Bv.x); }
+                if (m == 0) line[0] = make_double2(0.5 * (Av.x + Bv.x), 0.5 * (Av.y - Bv.y));
+                else { line[m] = Av; line[Pt - m] = cconj(Bv); }
+            } else {
+                double2 X, Y;
+                if (pr == 4) { X = h[2 * fstride + o]; Y = h[5 * fstride + o]; }
+                else { X = h[2 * fstride + o]; X = make_double2(-mm * X.y, mm * X.x); Y = h[8 * fstride + o]; }
+                if (m == 0) line[0] = make_double2(X.x, Y.x);
+                else {
+                    line[m] = make_double2(X.x - Y.y, X.y + Y.x);
+                    line[Pt - m] = make_double2(X.x + Y.y, Y.x - X.y);
+                }
+            }
+        } else if (L < 7 * zt) {   // adjoint (s_r, s_t) as two real fields
+            const int zi = L - 6 * zt;
+            const size_t o = (size_t)m * Pz + zi;
+            const double2 X = ha[o], Y = ha[fstride + o];
+            if (m == 0) line[0] = make_double2(X.x, Y.x);
+            else {
+                line[m] = make_double2(X.x - Y.y, X.y + Y.x);
+                line[Pt - m] = make_double2(X.x + Y.y, Y.x - X.y);
+            }
+        } else {                   // s_z of z values 2i and 2i+1
+            const int zp = L - 7 * zt;
+            const int za = 2 * zp, zb = 2 * zp + 1;
+            const double2 X = ha[2 * fstride + (size_t)m * Pz + za];
+            const double2 Y = zb < zt ? ha[2 * fstride + (size_t)m * Pz + zb] : make_double2(0.0, 0.0);
+            if (m == 0) line[0] = make_double2(X.x, Y.x);
+            else {
+                line[m] = make_double2(X.x - Y.y, X.y + Y.x);
+                line[Pt - m] = make_double2(X.x + Y.y, Y.x - X.y);
+            }
+        }
+    }
+    __syncthreads();
+    double2* phys = smem_fft(A, B, nl, tw, true, rad);
+    double2* out = phys == A ? B : A;
+    const double ir = 1.0 / rnodes[r];
+    for (int idx = threadIdx.x; idx < zt * Pt; idx += blockDim.x) {
+        const int zi = idx / Pt, th = idx - zi * Pt;
+        const double2* L0 = phys + (size_t)(zi * 6) * Pt + th;
+        const double2 p0 = L0[0], p1 = L0[Pt], p2 = L0[2 * Pt], p3 = L0[3 * Pt], p4 = L0[4 * Pt], p5 = L0[5 * Pt];
+        const double2 an = phys[(size_t)(6 * zt + zi) * Pt + th];
+        const double2 az = phys[(size_t)(7 * zt + zi / 2) * Pt + th];
+        const double nr = an.x, nt = an.y, nz = (zi & 1) ? az.y : az.x;
+        const double ur = p0.x, ut = p0.y, uz = p4.x;
+        const double urr = p1.x, utr = p1.y, urt = p2.x, utt = p2.y, urz = p3.x, utz = p3.y;
+        const double uzr = p4.y, uzt = p5.x, uzz = p5.y;
+        const double utr_ = ut * ir;
+        const double b_ur = nr * urr + nt * (utr + utr_) + nz * uzr;
+        const double b_ut = (nr * (urt - 2.0 * ut) + nt * (utt + ur) + nz * uzt) * ir;
+        const double b_uz = nr * urz + nt * utz + nz * uzz;
+        double2* o = out + (size_t)(zi * 6) * Pt + th;
+        o[0] = make_double2(b_ur, b_ut);                     // pair 0: (u_r, u_t)
+        o[Pt] = make_double2(b_uz, ur * nz);                 // pair 1: (u_z, d_r u_z)
+        o[2 * Pt] = make_double2(ur * nr, ur * nt);          // pair 2: (d_r u_r, d_r u_t)
+        o[3 * Pt] = make_double2(utr_ * nr, utr_ * nt);      // pair 3: (d_t u_r, d_t u_t)
+        o[4 * Pt] = make_double2(utr_ * nz, uz * nz);        // pair 4: (d_t u_z, d_z u_z)
+        o[5 * Pt] = make_double2(uz * nr, uz * nt);          // pair 5: (d_z u_r, d_z u_t)
+    }
+    __syncthreads();
+    double2* spare = out == A ? B : A;
+    double2* spec = smem_fft(out, spare, 6 * zt, tw, false, rad);
+    const size_t S9 = fstride;
+    for (int idx = threadIdx.x; idx < zt * (M + 1); idx += blockDim.x) {
+        const int m = idx / zt, zi = idx - m * zt;
+        const double cmw = m == 0 ? 1.0 : 2.0;
+        const double mm = mp * m;
+        double2 X[6], Y[6];
+        for (int pr = 0; pr < 6; ++pr) {
+            const double2* Ls = spec + (size_t)(zi * 6 + pr) * Pt;
+            const double2 Cp = Ls[m], Cm = cconj(Ls[m ? Pt - m : 0]);
+            X[pr] = make_double2(0.5 * cmw * (Cp.x + Cm.x), 0.5 * cmw * (Cp.y + Cm.y));
+            Y[pr] = make_double2(0.5 * cmw * (Cp.y - Cm.y), 0.5 * cmw * (Cm.x - Cp.x));
+        }
+        // A_c = G^T ubar_{u_c} - i m m_p G^T ubar_{d_t u_c}; R_c = G^T ubar_{d_r u_c}; Z_c = G^T ubar_{d_z u_c}
+        const double2 Ar = make_double2(X[0].x + mm * X[3].y, X[0].y - mm * X[3].x);
+        const double2 At = make_double2(Y[0].x + mm * Y[3].y, Y[0].y - mm * Y[3].x);
+        const double2 Az = make_double2(X[1].x + mm * X[4].y, X[1].y - mm * X[4].x);
+        const double2 Rr = X[2], Rt = Y[2], Rz = Y[1];
+        const double2 Zr = X[5], Zt = Y[5], Zz = Y[4];
+        // (r, t, z) -> (+, -, z):  bar_+ = a_r/2 + i a_t/2,  bar_- = a_r/2 - i a_t/2
+        auto plus = [](double2 ar, double2 at) { return make_double2(0.5 * (ar.x - at.y), 0.5 * (ar.y + at.x)); };
+        auto minus = [](double2 ar, double2 at) { return make_double2(0.5 * (ar.x + at.y), 0.5 * (ar.y - at.x)); };
+        const size_t o = ((size_t)r * (M + 1) + m) * Pz + z0 + zi;
+        H3[0 * S9 + o] = plus(Ar, At);
+        H3[1 * S9 + o] = minus(Ar, At);
+        H3[2 * S9 + o] = Az;
+        H3[3 * S9 + o] = plus(Rr, Rt);
+        H3[4 * S9 + o] = minus(Rr, Rt);
+        H3[5 * S9 + o] = Rz;
+        H3[6 * S9 + o] = plus(Zr, Zt);
+        H3[7 * S9 + o] = minus(Zr, Zt);
+        H3[8 * S9 + o] = Zz;
+    }
+}
+
+// Per (r, m, component c): unscaled forward DFT along z of A_c, R_c, Z_c, truncation to
+// |k| <= K; ubar_c += A_c - i k k_z Z_c;  Rhat_c = R_c (transposed stencil applied next).
+__global__ void __launch_bounds__(256) k_zfwd_adj(const double2* __restrict__ H3, double2* __restrict__ ub,
+                                                  double2* __restrict__ Rh, int N_r, int M, int K, double kz,
+                                                  const double2* __restrict__ tw, Radices rad) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Pz = rad.n;
+    double2* a = reinterpret_cast<double2*>(smem_raw);
+    double2* b = a + (size_t)3 * Pz;
+    const int c = blockIdx.x % 3;
+    const int rm = blockIdx.x / 3;
+    const int m = rm % (M + 1), r = rm / (M + 1);
+    const size_t fstride = (size_t)N_r * (M + 1) * Pz;
+    const double2* h = H3 + ((size_t)r * (M + 1) + m) * Pz;
+    for (int idx = threadIdx.x; idx < 3 * Pz; idx += blockDim.x) {
+        const int l = idx / Pz, z = idx - l * Pz;   // l: 0 A, 1 R, 2 Z of component c
+        a[idx] = h[(size_t)(3 * l + c) * fstride + z];
+    }
+    __syncthreads();
+    double2* res = smem_fft(a, b, 3, tw, false, rad);
+    const int nk = 2 * K + 1;
+    const size_t S = (size_t)N_r * (M + 1) * nk;
+    for (int kk = threadIdx.x; kk < nk; kk += blockDim.x) {
+        const int k = kk - K;
+        const int q = k < 0 ? k + Pz : k;
+        const double2 Av = res[q], Rv = res[Pz + q], Zv = res[2 * Pz + q];
+        const double kzk = kz * k;
+        const size_t e = (size_t)c * S + ((size_t)r * (M + 1) + m) * nk + kk;
+        double2 u = ub[e];
+        u.x += Av.x + kzk * Zv.y;
+        u.y += Av.y - kzk * Zv.x;
+        ub[e] = u;
+        Rh[e] = Rv;
+    }
+}
+
+// ubar(c, j, mode) += (D1^T Rhat)(c, j, mode)
+__global__ void k_drT(double2* __restrict__ ub, const double2* __restrict__ Rh, const int* __restrict__ trow,
+                      const double* __restrict__ tw, int ntab, Geo g) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * g.S) return;
+    const int c = (int)(e / g.S);
+    const size_t es = e - (size_t)c * g.S;
+    const int j = (int)(es / g.nmode);
+    const int mode = (int)(es - (size_t)j * g.nmode);
+    double2 s = ub[e];
+    for (int q = 0; q < ntab; ++q) {
+        const double w = __ldg(&tw[j * ntab + q]);
+        const double2 v = Rh[(size_t)c * g.S + (size_t)__ldg(&trow[j * ntab + q]) * g.nmode + mode];
+        s.x = fma(w, v.x, s.x);
+        s.y = fma(w, v.y, s.y);
+    }
+    ub[e] = s;
+}
+
+tc_status launch_adjoint_advance(tc_plan* p, const double2* ubar_new, const double2* ubar_cur,
+                                 const double2* Nbar_cur, double2* u_out, double2* up_out,
+                                 double2* N_out, double2* Np_out, cudaStream_t s) {
+    Geo g = geo(p);
+    int T = p->pc_modes > 0 ? p->pc_modes : 8;
+    while (T > 1 && (size_t)4 * p->N_r * T * sizeof(double2) > 96 * 1024) T /= 2;
+    PCAdjArgs a;
+    a.ubar_new = ubar_new; a.ubar_cur = ubar_cur; a.Nbar_cur = Nbar_cur;
+    a.u_out = u_out; a.up_out = up_out; a.N_out = N_out; a.Np_out = Np_out;
+    a.rn = p->d_r; a.w1 = p->d_w1; a.w2 = p->d_w2; a.col0 = p->d_col0;
+    a.trow = p->d_d1t_row; a.tw = p->d_d1t_w; a.ntab = p->d1t_n;
+    a.fac = p->d_fac; a.piv = p->d_piv;
+    const size_t sm = (size_t)4 * p->N_r * T * sizeof(double2);
+    int threads = ((6 * T + 31) / 32) * 32;
+    if (threads < 128) threads = 128;
+    if (threads > 256) threads = 256;
+    TC_CUDA(p, cudaFuncSetAttribute(k_pc_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int slot = prof_begin(p, kKPCAdj, s);
+    k_pc_adj<<<ablocks(g.nmode, T), threads, sm, s>>>(a, g, T);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_pc_adj");
+    return TC_OK;
+}
+
+tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* Nbar, double2* ubar,
+                                   char* ws, cudaStream_t s) {
+    Geo g = geo(p);
+    double2* H1 = reinterpret_cast<double2*>(ws + p->ws.H1);
+    double2* Ha = reinterpret_cast<double2*>(ws + p->ws.H2);
+    double2* H3 = reinterpret_cast<double2*>(ws + p->ws.H3);
+    double2* Rh = reinterpret_cast<double2*>(ws + p->ws.Rhat);
+    // forward lines of u (same kernel as the forward nonlinear term, FP64)
+    tc_status st = launch_zinv_fp64(p, u, H1, s);
+    if (st != TC_OK) return st;
+    const size_t smz = (size_t)2 * 3 * p->P_z * sizeof(double2);
+    TC_CUDA(p, cudaFuncSetAttribute(k_zinv_adjin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
+    int slot = prof_begin(p, kKZinvAdj, s);
+    k_zinv_adjin<<<p->N_r * (p->M + 1), 256, smz, s>>>(Nbar, Ha, p->N_r, p->M, p->K,
+                                                         1.0 / ((double)p->P_t * (double)p->P_z), p->d_tw_z, p->rad_z);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_zinv_adjin");
+    int zt = 4;
+    auto smem_for = [&](int z) {
+        const int nza = (z + 1) / 2, nl = 7 * z + nza;
+        const int nbuf = nl > 6 * z ? nl : 6 * z;
+        return (size_t)2 * nbuf * p->P_t * sizeof(double2);
+    };
+    while (zt > 1 && (smem_for(zt) > 200 * 1024 || p->P_z % zt)) zt /= 2;
+    if (smem_for(zt) > 220 * 1024) {
+        snprintf(p->err, sizeof(p->err), "adjoint theta pass: P_theta = %d too long for shared memory", p->P_t);
+        return TC_ERR_ARG;
+    }
+    const size_t smt = smem_for(zt);
+    TC_CUDA(p, cudaFuncSetAttribute(k_theta_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt));
+    slot = prof_begin(p, kKThetaAdj, s);
+    k_theta_adj<<<p->N_r * (p->P_z / zt), 256, smt, s>>>(H1, Ha, H3, p->d_r, p->N_r, p->M, p->P_z,
+                                                           (double)p->m_p, zt, p->d_tw_t, p->rad_t);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_theta_adj");
+    TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
+    slot = prof_begin(p, kKZfwdAdj, s);
+    k_zfwd_adj<<<p->N_r * (p->M + 1) * 3, 256, smz, s>>>(H3, ubar, Rh, p->N_r, p->M, p->K, p->k_z,
+                                                           p->d_tw_z, p->rad_z);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_zfwd_adj");
+    slot = prof_begin(p, kKDrT, s);
+    k_drT<<<ablocks(3 * g.S, 256), 256, 0, s>>>(ubar, Rh, p->d_d1t_row, p->d_d1t_w, p->d1t_n, g);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_drT");
+    return TC_OK;
+}
+
+// gradient of J = 1/2 sum_j w_j r_j sum c_m (|u'_+|^2/2 + |u'_-|^2/2 + |u'_z|^2), u' = u - Couette
+__global__ void k_energy_grad(const double2* __restrict__ u, double2* __restrict__ gr,
+                              const double* __restrict__ rn, double C1, double C2, Geo g) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * g.S) return;
+    const int c = (int)(e / g.S);
+    const size_t es = e - (size_t)c * g.S;
+    const int j = (int)(es / g.nmode);
+    const int mode = (int)(es - (size_t)j * g.nmode);
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    const double r = rn[j];
+    double wr = 0.0;
+    if (j > 0) wr += 0.5 * (r - rn[j - 1]);
+    if (j < g.N - 1) wr += 0.5 * (rn[j + 1] - r);
+    double2 d = u[e];
+    if (m == 0 && k == 0 && c < 2) d.y -= (c == 0 ? 1.0 : -1.0) * (C1 * r + C2 / r);
+    const double f = wr * r * (m == 0 ? 1.0 : 2.0) * (c < 2 ? 0.5 : 1.0);
+    gr[e] = make_double2(f * d.x, f * d.y);
+}
+
+tc_status launch_energy_gradient(tc_plan* p, const double2* u, double2* gr, cudaStream_t s) {
+    Geo g = geo(p);
+    const double eta = p->eta;
+    const double C1 = (p->Re_o - eta * p->Re_i) / (1.0 + eta);
+    const double C2 = eta * (p->Re_i - eta * p->Re_o) / ((1.0 - eta) * (1.0 - eta * eta));
+    k_energy_grad<<<ablocks(3 * g.S, 256), 256, 0, s>>>(u, gr, p->d_r, C1, C2, g);
+    TC_LAUNCHED(p, "k_energy_grad");
+    return TC_OK;
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+namespace {
+
+tc_status adj_ready(tc_plan* p, void* ws) {
+    if (!p) return TC_ERR_ARG;
+    if (p->host_only) return TC_ERR_STATE;
+    int dev = -1;
+    TC_CUDA(p, cudaGetDevice(&dev));
+    if (dev != p->device) return TC_ERR_STATE;
+    if (!ws || reinterpret_cast<uintptr_t>(ws) % 256 != 0) return TC_ERR_ARG;
+    return check_device_ptr(p, ws, "ws");
+}
+
+#define TC_TRY2(x)                   \
+    do {                             \
+        tc_status s_ = (x);          \
+        if (s_ != TC_OK) return s_;  \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+tc_status tc_adjoint_step(tc_plan* plan, const tc_state* fwd, tc_state_bar* bar, void* ws, void* stream) {
+    TC_TRY2(adj_ready(plan, ws));
+    if (!fwd || !bar) return TC_ERR_ARG;
+    if (!fwd->started) {
+        snprintf(plan->err, sizeof(plan->err), "tc_adjoint_step needs a started forward state (use tc_adjoint_start for the cold start)");
+        return TC_ERR_STATE;
+    }
+    TC_TRY2(check_device_ptr(plan, fwd->u, "fwd->u"));
+    TC_TRY2(check_device_ptr(plan, bar->u, "bar->u"));
+    TC_TRY2(check_device_ptr(plan, bar->u_prev, "bar->u_prev"));
+    TC_TRY2(check_device_ptr(plan, bar->N_prev, "bar->N_prev"));
+    if (bar->u == bar->u_prev || bar->u == bar->N_prev || bar->u_prev == bar->N_prev) return TC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* w = static_cast<char*>(ws);
+    double2* ub = static_cast<double2*>(bar->u);
+    double2* upb = static_cast<double2*>(bar->u_prev);
+    double2* Npb = static_cast<double2*>(bar->N_prev);
+    double2* Nb = reinterpret_cast<double2*>(w + plan->ws.Nbar);
+    TC_TRY2(launch_adjoint_advance(plan, ub, upb, Npb, ub, upb, Nb, Npb, s));
+    return launch_nonlinear_adjoint(plan, static_cast<const double2*>(fwd->u), Nb, ub, w, s);
+}
+
+tc_status tc_adjoint_start(tc_plan* plan, const void* u0, const tc_state_bar* bar, void* u0_bar,
+                           void* ws, void* stream) {
+    TC_TRY2(adj_ready(plan, ws));
+    if (!bar) return TC_ERR_ARG;
+    TC_TRY2(check_device_ptr(plan, u0, "u0"));
+    TC_TRY2(check_device_ptr(plan, u0_bar, "u0_bar"));
+    TC_TRY2(check_device_ptr(plan, bar->u, "bar->u"));
+    TC_TRY2(check_device_ptr(plan, bar->u_prev, "bar->u_prev"));
+    TC_TRY2(check_device_ptr(plan, bar->N_prev, "bar->N_prev"));
+    if (u0_bar == u0 || u0_bar == bar->u_prev || u0_bar == bar->N_prev) return TC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* w = static_cast<char*>(ws);
+    const size_t n3 = 3 * plan->S;
+    const double2* u = static_cast<const double2*>(u0);
+    double2* out = static_cast<double2*>(u0_bar);
+    double2* Nc = reinterpret_cast<double2*>(w + plan->ws.Ncur);
+    double2* uE = reinterpret_cast<double2*>(w + plan->ws.uE);
+    double2* Nb = reinterpret_cast<double2*>(w + plan->ws.Nbar);
+    double2* um1 = reinterpret_cast<double2*>(w + plan->ws.abar);
+    double2* m1b = um1 + n3;
+    double2* uEb = m1b + n3;
+    // forward recomputation of the start-up: N0 = N(u0), u_E, u^{-1}
+    TC_TRY2(launch_nonlinear(plan, u, Nc, w, s));
+    TC_TRY2(launch_advance(plan, u, const_cast<double2*>(u), Nc, Nc, nullptr, uE, w, false, s));
+    TC_TRY2(launch_axpby(plan, um1, u, 2.5, uE, -1.5, n3, s));
+    // m1_bar = ubar_prev + N'(u^{-1})^T Nbar_prev
+    TC_CUDA(plan, cudaMemcpyAsync(m1b, bar->u_prev, n3 * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    TC_TRY2(launch_nonlinear_adjoint(plan, um1, static_cast<const double2*>(bar->N_prev), m1b, w, s));
+    // u_E bar = -1.5 m1_bar; adjoint of the Euler step (u, u_prev, N, N_prev all = u0 / N0)
+    TC_TRY2(launch_axpby(plan, uEb, m1b, -1.5, m1b, 0.0, n3, s));
+    double2* a_u = out;   // adjoint of its u input
+    double2* a_up = uE;   // adjoint of its u_prev input
+    double2* a_N = Nb;    // adjoint of its N input
+    double2* a_Np = Nc;   // adjoint of its N_prev input
+    TC_TRY2(launch_adjoint_advance(plan, uEb, nullptr, nullptr, a_u, a_up, a_N, a_Np, s));
+    // u0_bar = ubar + 2.5 m1_bar + a_u + a_up + N'(u0)^T (a_N + a_Np)
+    TC_TRY2(launch_axpby(plan, out, out, 1.0, a_up, 1.0, n3, s));
+    TC_TRY2(launch_axpby(plan, out, out, 1.0, m1b, 2.5, n3, s));
+    TC_TRY2(launch_axpby(plan, out, out, 1.0, static_cast<const double2*>(bar->u), 1.0, n3, s));
+    TC_TRY2(launch_axpby(plan, a_N, a_N, 1.0, a_Np, 1.0, n3, s));
+    return launch_nonlinear_adjoint(plan, u, a_N, out, w, s);
+}
+
+tc_status tc_energy_gradient(tc_plan* plan, const void* u, void* g, void* stream) {
+    if (!plan) return TC_ERR_ARG;
+    if (plan->host_only) return TC_ERR_STATE;
+    TC_TRY2(check_device_ptr(plan, u, "u"));
+    TC_TRY2(check_device_ptr(plan, g, "g"));
+    return launch_energy_gradient(plan, static_cast<const double2*>(u), static_cast<double2*>(g),
+                                  static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -87,7 +87,7 @@ tc_status tc_step(tc_plan* plan, tc_state* st, int nsteps, void* ws, void* strea
     double2* Nc = reinterpret_cast<double2*>(w + plan->ws.Ncur);
     double2* uE = reinterpret_cast<double2*>(w + plan->ws.uE);
     const size_t n3 = 3 * plan->S;
-    if (!st->started && nsteps > 0) {
+    if (!st->started) {
         // history for AB2BD2: implicit Euler step of 2dt/3, then u^{-1}, N^{-1}
         TC_TRY(launch_nonlinear(plan, u, Nc, w, s));
         TC_TRY(launch_advance(plan, u, u, Nc, Nc, p, uE, w, false, s));

@@ -15,100 +15,9 @@
 // The transforms are mixed-radix (4, 2, 3) Stockham passes in shared memory with twiddles
 // from a long-double table.
 #include "tc_internal.cuh"
+#include "tc_fft_core.cuh"
 
 namespace tc {
-
-template <typename V> struct Real;
-template <> struct Real<double2> { using type = double; };
-template <> struct Real<float2> { using type = float; };
-
-// small DFTs of the Stockham passes; inv selects exp(+2 pi i / R)
-template <typename V>
-__device__ __forceinline__ void dft2(V& a, V& b) {
-    V t = a;
-    a = cadd(t, b);
-    b = csub(t, b);
-}
-
-template <typename V>
-__device__ __forceinline__ void dft3(V& v0, V& v1, V& v2, bool inv) {
-    using T = typename Real<V>::type;
-    const T s3 = (T)0.866025403784438646763723170752936183L;
-    V t1 = cadd(v1, v2), t2 = csub(v1, v2);
-    V m1;
-    m1.x = v0.x - (T)0.5 * t1.x;
-    m1.y = v0.y - (T)0.5 * t1.y;
-    V m2;  // (inv ? +i : -i) * s3 * t2
-    if (inv) { m2.x = -s3 * t2.y; m2.y = s3 * t2.x; }
-    else     { m2.x = s3 * t2.y;  m2.y = -s3 * t2.x; }
-    v0 = cadd(v0, t1);
-    v1 = cadd(m1, m2);
-    v2 = csub(m1, m2);
-}
-
-template <typename V>
-__device__ __forceinline__ void dft4(V& v0, V& v1, V& v2, V& v3, bool inv) {
-    V a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), d = csub(v1, v3);
-    V a3;
-    if (inv) { a3.x = -d.y; a3.y = d.x; }   // +i d
-    else     { a3.x = d.y;  a3.y = -d.x; }  // -i d
-    v0 = cadd(a0, a2);
-    v2 = csub(a0, a2);
-    v1 = cadd(a1, a3);
-    v3 = csub(a1, a3);
-}
-
-template <int R, typename V>
-__device__ __forceinline__ void stockham_pass(const V* in, V* out, int n, int nlines, int Ns,
-                                              const V* __restrict__ tw, bool inv) {
-    const int nb = n / R;
-    const int step = n / (Ns * R);
-    for (int idx = threadIdx.x; idx < nb * nlines; idx += blockDim.x) {
-        const int line = idx / nb;
-        const int j = idx - line * nb;
-        const V* src = in + (size_t)line * n;
-        V* dst = out + (size_t)line * n;
-        const int k = j % Ns;
-        V v[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) v[q] = src[j + q * nb];
-        if (k) {
-#pragma unroll
-            for (int q = 1; q < R; ++q) {
-                V w = __ldg(&tw[q * k * step]);
-                if (!inv) w.y = -w.y;
-                v[q] = cmul(v[q], w);
-            }
-        }
-        if (R == 2) dft2(v[0], v[1]);
-        if (R == 3) dft3(v[0], v[1], v[2 % R], inv);
-        if (R == 4) dft4(v[0], v[1], v[2 % R], v[3 % R], inv);
-        const int o = (j / Ns) * Ns * R + k;
-#pragma unroll
-        for (int q = 0; q < R; ++q) dst[o + q * Ns] = v[q];
-    }
-}
-
-// nlines transforms of length rad.n held contiguously in a; b is scratch of equal size.
-// Returns the buffer holding the result.  Must be called by every thread of the block.
-template <typename V>
-__device__ V* smem_fft(V* a, V* b, int nlines, const V* __restrict__ tw, bool inv, const Radices& rad) {
-    int Ns = 1;
-    const int n = rad.n;
-    for (int p = 0; p < rad.count; ++p) {
-        const int R = rad.r[p];
-        if (R == 4) stockham_pass<4>(a, b, n, nlines, Ns, tw, inv);
-        else if (R == 2) stockham_pass<2>(a, b, n, nlines, Ns, tw, inv);
-        else stockham_pass<3>(a, b, n, nlines, Ns, tw, inv);
-        __syncthreads();
-        V* t = a; a = b; b = t;
-        Ns *= R;
-    }
-    return a;
-}
-
-template <typename V>
-__device__ __forceinline__ V from_d2(double2 a) { V v; v.x = (typename Real<V>::type)a.x; v.y = (typename Real<V>::type)a.y; return v; }
 
 // ---------------------------------------------------------------- inverse z-pass
 // Field f of H1: f = 3 d + c, c in {+, -, z}, d in {u, d_r u, d_z u}.
@@ -376,20 +285,32 @@ static tc_status run_nonlinear(tc_plan* p, const double2* u, double2* N, char* w
     TC_CUDA(p, cudaFuncSetAttribute(k_zfwd<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
     const int blocks1 = p->N_r * (p->M + 1) * (9 / L);
     int slot = prof_begin(p, sizeof(V) == 16 ? kKZinv : kKZinv32, s);
-    k_zinv<V><<<blocks1, 256, sm1, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M, p->K, p->k_z, L, mixed ? 1 : 0, twz, p->rad_z);
+    k_zinv<V><<<blocks1, mixed ? 256 : p->thr_zinv, sm1, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M, p->K, p->k_z, L, mixed ? 1 : 0, twz, p->rad_z);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_zinv");
     const int blocks2 = p->N_r * (p->P_z / zt);
     slot = prof_begin(p, sizeof(V) == 16 ? kKTheta : kKTheta32, s);
-    k_theta<V><<<blocks2, 256, sm2, s>>>(H1, H2, p->d_r, p->N_r, p->M, p->P_z, (double)p->m_p, zt, twt, p->rad_t);
+    k_theta<V><<<blocks2, mixed ? 256 : p->thr_theta, sm2, s>>>(H1, H2, p->d_r, p->N_r, p->M, p->P_z, (double)p->m_p, zt, twt, p->rad_t);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_theta");
     const double scale = 1.0 / ((double)p->P_t * (double)p->P_z);
     slot = prof_begin(p, sizeof(V) == 16 ? kKZfwd : kKZfwd32, s);
-    k_zfwd<V><<<p->N_r * (p->M + 1), 256, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, twz, p->rad_z,
+    k_zfwd<V><<<p->N_r * (p->M + 1), mixed ? 256 : p->thr_zfwd, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, twz, p->rad_z,
                                                      u, p->d_r, p->d_w1, p->d_col0, (double)p->m_p, mixed ? 1 : 0);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_zfwd");
+    return TC_OK;
+}
+
+tc_status launch_zinv_fp64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s) {
+    const int L = p->zinv_lines;
+    const size_t sm1 = (size_t)2 * L * p->P_z * sizeof(double2);
+    TC_CUDA(p, cudaFuncSetAttribute(k_zinv<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+    const int slot = prof_begin(p, kKZinv, s);
+    k_zinv<double2><<<p->N_r * (p->M + 1) * (9 / L), p->thr_zinv, sm1, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M, p->K,
+                                                                     p->k_z, L, 0, p->d_tw_z, p->rad_z);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_zinv");
     return TC_OK;
 }
 

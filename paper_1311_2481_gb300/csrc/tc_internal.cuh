@@ -35,6 +35,10 @@ struct Workspace {
     size_t phi;     // phi: scalar field
     size_t uE;      // start-up Euler result: vector field
     size_t red;     // diagnostics reduction buffer
+    size_t H3;      // adjoint theta-pass output: 9 fields x N_r x (M+1) x P_z complex
+    size_t Nbar;    // adjoint of N: vector field
+    size_t Rhat;    // adjoint d_r lines before the transposed stencil: vector field
+    size_t abar;    // start-up adjoint temporaries: 3 vector fields
     size_t total;
 };
 
@@ -52,11 +56,16 @@ struct tc_plan {
     int nmode_half;  // (M+1)(K+1)
     tc::Radices rad_z, rad_t;
     int zt, zt32;                  // z values per theta-pass block (FP64 / FP32 lines)
+    int pc_modes;                  // modes per block of the fused steps-2-5 kernel (0: auto)
+    int thr_zinv, thr_theta, thr_zfwd;  // block sizes of the FP64 transform kernels
     int zinv_lines, zinv_lines32;  // lines per inverse z-pass block (FP64 / FP32 lines)
     tc::Workspace ws;
     // host plan
     std::vector<double> r, w1, w2;   // nodes; weights [N_r][9]
     std::vector<int> col0;           // first node of each padded stencil
+    int d1t_n = 0;                   // entries per column of the transposed D1 gather table
+    std::vector<int> d1t_row;        // [N_r][d1t_n] rows j with D1[j][col] != 0 (padded)
+    std::vector<double> d1t_w;       // [N_r][d1t_n] matching weights D1[j][col] (0 padding)
     std::vector<double> fac;         // [set][j][band][m][ka]
     std::vector<uint8_t> piv;        // [set][j][m][ka] pivot offset 0..4
     std::vector<double> tw_z, tw_t;  // interleaved complex exp(+2 pi i j / n)
@@ -65,6 +74,8 @@ struct tc_plan {
     double* d_w1 = nullptr;
     double* d_w2 = nullptr;
     int* d_col0 = nullptr;
+    int* d_d1t_row = nullptr;
+    double* d_d1t_w = nullptr;
     double* d_fac = nullptr;
     uint8_t* d_piv = nullptr;
     double2* d_tw_z = nullptr;
@@ -117,7 +128,8 @@ tc_status check_device_ptr(tc_plan* p, const void* ptr, const char* name);
 // ------------------------------------------------------------------ tracing
 enum KernelId {
     kKZinv = 0, kKTheta, kKZfwd, kKRhsPressure, kKSolveP, kKRhsVelocity, kKSolveH, kKRhsDiv,
-    kKUpdate, kKAxpby, kKDiag, kKZinv32, kKTheta32, kKZfwd32, kKMeanFlow, kNumKernels
+    kKUpdate, kKAxpby, kKDiag, kKZinv32, kKTheta32, kKZfwd32, kKMeanFlow, kKPC, kKPCAdj,
+    kKZinvAdj, kKThetaAdj, kKZfwdAdj, kKDrT, kNumKernels
 };
 extern const char* const kKernelNames[kNumKernels];
 int prof_begin(tc_plan* p, int kid, cudaStream_t s);
@@ -125,6 +137,7 @@ void prof_end(tc_plan* p, int slot, cudaStream_t s);
 
 // ------------------------------------------------------------------ launchers
 tc_status launch_nonlinear(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s);
+tc_status launch_zinv_fp64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s);
 tc_status launch_solve(tc_plan* p, int set, double2* x, int nfields, cudaStream_t s);
 tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const double2* Ncur,
                          double2* N_prev, double2* p_out, double2* u_out, char* ws,
@@ -132,5 +145,11 @@ tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const do
 tc_status launch_axpby(tc_plan* p, double2* y, const double2* a, double ca, const double2* b,
                        double cb, size_t n, cudaStream_t s);
 tc_status launch_diagnostics(tc_plan* p, const double2* u, double* red, cudaStream_t s);
+tc_status launch_adjoint_advance(tc_plan* p, const double2* ubar_new, const double2* ubar_cur,
+                                 const double2* Nbar_cur, double2* u_out, double2* up_out,
+                                 double2* N_out, double2* Np_out, cudaStream_t s);
+tc_status launch_energy_gradient(tc_plan* p, const double2* u, double2* g, cudaStream_t s);
+tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* Nbar, double2* ubar,
+                                   char* ws, cudaStream_t s);
 
 }  // namespace tc

@@ -91,6 +91,29 @@ static void twiddles(int n, std::vector<double>& tw) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Block size for a kernel whose FP64 work is Stockham passes over `lines` transforms of
+// length rad.n (plus `lines2` of a second batch): the FP64 pipe is charged per warp
+// instruction, so pick the size that wastes the fewest lanes over all passes.
+static int choose_threads(const Radices& rad, int lines, int lines2) {
+    double best = -1.0;
+    int bestT = 256;
+    for (int T = 96; T <= 256; T += 32) {
+        double items = 0.0, slots = 0.0;
+        for (int batch = 0; batch < 2; ++batch) {
+            const int L = batch ? lines2 : lines;
+            if (L <= 0) continue;
+            for (int q = 0; q < rad.count; ++q) {
+                const double it = (double)L * rad.n / rad.r[q];
+                items += it;
+                slots += std::ceil(it / T) * T;
+            }
+        }
+        const double e = items / slots;
+        if (e > best + 1e-9 || (std::fabs(e - best) <= 1e-9 && T > bestT)) { best = e; bestT = T; }
+    }
+    return bestT;
+}
+
 // Banded LU with partial pivoting of one matrix given in row windows W[i][t] = A[i][i-kl+t],
 // t in [0, 2kl+ku] (kl = ku = 4).  On return W holds the multipliers of step j in
 // W[j+q][kl-q] (q = 1..kl, column j of L, LAPACK convention: not permuted by later steps)
@@ -209,6 +232,8 @@ static tc_status upload(tc_plan* p) {
     TC_CUDA(p, put((void**)&p->d_w1, p->w1.data(), p->w1.size() * sizeof(double)));
     TC_CUDA(p, put((void**)&p->d_w2, p->w2.data(), p->w2.size() * sizeof(double)));
     TC_CUDA(p, put((void**)&p->d_col0, p->col0.data(), p->col0.size() * sizeof(int)));
+    TC_CUDA(p, put((void**)&p->d_d1t_row, p->d1t_row.data(), p->d1t_row.size() * sizeof(int)));
+    TC_CUDA(p, put((void**)&p->d_d1t_w, p->d1t_w.data(), p->d1t_w.size() * sizeof(double)));
     TC_CUDA(p, put((void**)&p->d_fac, p->fac.data(), p->fac.size() * sizeof(double)));
     TC_CUDA(p, put((void**)&p->d_piv, p->piv.data(), p->piv.size()));
     TC_CUDA(p, put((void**)&p->d_tw_z, p->tw_z.data(), p->tw_z.size() * sizeof(double)));
@@ -223,7 +248,8 @@ static tc_status upload(tc_plan* p) {
 const char* const kKernelNames[kNumKernels] = {
     "k_zinv", "k_theta", "k_zfwd", "k_rhs_pressure", "k_band_solve_P", "k_rhs_velocity",
     "k_band_solve_H", "k_rhs_div", "k_update", "k_axpby", "k_diag", "k_zinv_f32",
-    "k_theta_f32", "k_zfwd_f32", "k_mean_flow"};
+    "k_theta_f32", "k_zfwd_f32", "k_mean_flow", "k_pc", "k_pc_adj", "k_zinv_adjin",
+    "k_theta_adj", "k_zfwd_adj", "k_drT"};
 
 int prof_begin(tc_plan* p, int kid, cudaStream_t s) {
     if (!p->prof_on) return -1;
@@ -250,7 +276,7 @@ void prof_end(tc_plan* p, int slot, cudaStream_t s) {
 static void free_device(tc_plan* p) {
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     p->prof_ev.clear();
-    void* ptrs[] = {p->d_r, p->d_w1, p->d_w2, p->d_col0, p->d_fac, p->d_piv,
+    void* ptrs[] = {p->d_r, p->d_w1, p->d_w2, p->d_col0, p->d_d1t_row, p->d_d1t_w, p->d_fac, p->d_piv,
                     p->d_tw_z, p->d_tw_t, p->d_tw_z32, p->d_tw_t32};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -348,6 +374,25 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
             p->w2[(size_t)j * kStencil + (lo + i - c0)] = n >= 3 ? (double)c[i * 3 + 2] : 0.0;
         }
     }
+    // transposed D1 as a gather table: column c collects w1[j][c - col0[j]] from rows j
+    {
+        std::vector<std::vector<std::pair<int, double>>> cols(N_r);
+        for (int j = 0; j < N_r; ++j)
+            for (int t = 0; t < kStencil; ++t) {
+                double w = p->w1[(size_t)j * kStencil + t];
+                if (w != 0.0) cols[p->col0[j] + t].push_back({j, w});
+            }
+        int n = 1;
+        for (auto& c : cols) n = std::max<int>(n, (int)c.size());
+        p->d1t_n = n;
+        p->d1t_row.assign((size_t)N_r * n, 0);
+        p->d1t_w.assign((size_t)N_r * n, 0.0);
+        for (int c = 0; c < N_r; ++c)
+            for (size_t e = 0; e < cols[c].size(); ++e) {
+                p->d1t_row[(size_t)c * n + e] = cols[c][e].first;
+                p->d1t_w[(size_t)c * n + e] = cols[c][e].second;
+            }
+    }
     twiddles(Pz, p->tw_z);
     twiddles(Pt, p->tw_t);
     if (!build_factors(p)) {
@@ -369,8 +414,13 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     };
     p->zinv_lines = lines_for(sizeof(double2));
     p->zinv_lines32 = lines_for(sizeof(float2));
-    p->zt = zt_for(sizeof(double2), 8);
-    p->zt32 = zt_for(sizeof(float2), 16);
+    p->zt = zt_for(sizeof(double2), o.theta_zt > 0 ? o.theta_zt : 4);
+    p->zt32 = zt_for(sizeof(float2), o.theta_zt > 0 ? o.theta_zt : 8);
+    p->pc_modes = o.pc_modes;
+    p->thr_zinv = choose_threads(rz, p->zinv_lines, 0);
+    p->thr_theta = choose_threads(rt, 6 * p->zt, p->zt + (p->zt + 1) / 2);
+    p->thr_zfwd = choose_threads(rz, 3, 0);
+    if (o.theta_zt < 0 || o.theta_zt > 64 || o.pc_modes < 0 || o.pc_modes > 32) { delete p; return TC_ERR_ARG; }
     if ((size_t)2 * 3 * Pz * cplx > 220 * 1024 || (size_t)2 * 6 * Pt * cplx > 220 * 1024) {
         delete p;
         return TC_ERR_ARG;   // transform lines too long for one block's shared memory
@@ -385,6 +435,10 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     p->ws.phi = take(p->S * cplx);
     p->ws.uE = take(3 * p->S * cplx);
     p->ws.red = take(4096 * sizeof(double));
+    p->ws.H3 = take(9 * p->Hfield * cplx);
+    p->ws.Nbar = take(3 * p->S * cplx);
+    p->ws.Rhat = take(3 * p->S * cplx);
+    p->ws.abar = take(9 * p->S * cplx);
     p->ws.total = off;
     if (!p->host_only) {
         tc_status st = upload(p);

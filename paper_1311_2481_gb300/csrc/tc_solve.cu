@@ -4,278 +4,236 @@
 // consecutive k, so every access to a field [r][m][k] or to the factors [j][band][m][|k|]
 // is coalesced.
 #include "tc_internal.cuh"
+#include "tc_solve_core.cuh"
 
 namespace tc {
 
-struct Geo {
-    int N, M, K, nk, nmode, K1, M1K1;
-    size_t S;
-    double mp, kz, dt;
+struct PCArgs {
+    const double2* u;   // u^i
+    const double2* up;  // u^{i-1}
+    const double2* Nc;  // N^i
+    const double2* Np;  // N^{i-1}
+    double2* u_out;     // commit: u (in place); otherwise the result u^{i+1} only
+    double2* up_out;    // commit: u_prev <- u^i
+    double2* Np_out;    // commit: N_prev <- N^i
+    double2* p;         // commit: p <- p^{i+1}
+    const double* rn;
+    const double* w1;
+    const double* w2;
+    const int* col0;
+    const double* fac;
+    const uint8_t* piv;
+    double Re_i, Re_o;
+    int commit;
 };
 
-static Geo geo(const tc_plan* p) {
-    Geo g;
-    g.N = p->N_r; g.M = p->M; g.K = p->K; g.nk = 2 * p->K + 1; g.nmode = p->nmode;
-    g.K1 = p->K + 1; g.M1K1 = (p->M + 1) * (p->K + 1); g.S = p->S;
-    g.mp = (double)p->m_p; g.kz = p->k_z; g.dt = p->dt;
-    return g;
-}
-
-// first and second radial derivative of column `mode` of a scalar field at row j
-__device__ __forceinline__ double2 drow(const double2* __restrict__ f, const double* __restrict__ w,
-                                        const int* __restrict__ col0, int j, int nmode, int mode) {
-    const int c0 = col0[j];
-    double2 s = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int t = 0; t < kStencil; ++t) {
-        const double wt = __ldg(&w[j * kStencil + t]);
-        const double2 v = f[(size_t)(c0 + t) * nmode + mode];
-        s.x += wt * v.x;
-        s.y += wt * v.y;
-    }
-    return s;
-}
-
-// (Lap u)_r = ((L_+ u_+) + (L_- u_-)) / 2 at row j, L_pm = Lap_h - 1/r^2 -+ 2 m m_p / r^2
-__device__ double2 lap_r(const double2* __restrict__ u, const double* __restrict__ w1,
-                         const double* __restrict__ w2, const int* __restrict__ col0,
-                         double r, int j, int mode, double mm, double kk, const Geo& g) {
-    double2 acc = make_double2(0.0, 0.0);
-    const double ir = 1.0 / r, ir2 = ir * ir;
-    for (int c = 0; c < 2; ++c) {
-        const double2* f = u + (size_t)c * g.S;
-        const double2 d1 = drow(f, w1, col0, j, g.nmode, mode);
-        const double2 d2 = drow(f, w2, col0, j, g.nmode, mode);
-        const double2 v = f[(size_t)j * g.nmode + mode];
-        const double sgn = c == 0 ? -1.0 : 1.0;
-        const double diag = -mm * mm * ir2 - kk * kk - ir2 + sgn * 2.0 * mm * ir2;
-        acc.x += d2.x + ir * d1.x + diag * v.x;
-        acc.y += d2.y + ir * d1.y + diag * v.y;
-    }
-    acc.x *= 0.5;
-    acc.y *= 0.5;
-    return acc;
-}
-
-// Step 2 right-hand side: interior rows div_h(-(2N - N_prev)); wall rows the consistent
-// Neumann value of Eq. ppBC; (0,0) at r_o the Dirichlet value 0.
-__global__ void k_rhs_pressure(const double2* __restrict__ u, const double2* __restrict__ up,
-                               const double2* __restrict__ Nc, const double2* __restrict__ Np,
-                               double2* __restrict__ b, const double* __restrict__ rn,
-                               const double* __restrict__ w1, const double* __restrict__ w2,
-                               const int* __restrict__ col0, Geo g) {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= g.S) return;
-    const int j = (int)(e / g.nmode);
-    const int mode = (int)(e - (size_t)j * g.nmode);
-    const int m = mode / g.nk;
-    const int k = mode - m * g.nk - g.K;
-    const double mm = g.mp * m, kk = g.kz * k;
-    const double r = rn[j], ir = 1.0 / r;
-    auto NN = [&](int c, int row) {
-        const size_t o = (size_t)c * g.S + (size_t)row * g.nmode + mode;
-        const double2 a = Nc[o], q = Np[o];
-        return make_double2(2.0 * a.x - q.x, 2.0 * a.y - q.y);
-    };
-    double2 out;
-    if (j == 0 || j == g.N - 1) {
-        if (j == g.N - 1 && m == 0 && k == 0) {
-            out = make_double2(0.0, 0.0);
-        } else {
-            const double2 np = NN(0, j), nm = NN(1, j);
-            const double2 l0 = lap_r(u, w1, w2, col0, r, j, mode, mm, kk, g);
-            const double2 l1 = lap_r(up, w1, w2, col0, r, j, mode, mm, kk, g);
-            out.x = -0.5 * (np.x + nm.x) + 2.0 * l0.x - l1.x;
-            out.y = -0.5 * (np.y + nm.y) + 2.0 * l0.y - l1.y;
-        }
-    } else {
-        // D1 of NN_r = (NN_+ + NN_-)/2
-        const int c0 = col0[j];
-        double2 d = make_double2(0.0, 0.0);
-#pragma unroll
-        for (int t = 0; t < kStencil; ++t) {
-            const double wt = __ldg(&w1[j * kStencil + t]);
-            const double2 a = NN(0, c0 + t), q = NN(1, c0 + t);
-            d.x += wt * 0.5 * (a.x + q.x);
-            d.y += wt * 0.5 * (a.y + q.y);
-        }
-        const double2 np = NN(0, j), nm = NN(1, j), nz = NN(2, j);
-        const double2 vr = make_double2(0.5 * (np.x + nm.x), 0.5 * (np.y + nm.y));
-        double2 div;
-        div.x = d.x + vr.x * ir + mm * (np.x - nm.x) * 0.5 * ir - kk * nz.y;
-        div.y = d.y + vr.y * ir + mm * (np.y - nm.y) * 0.5 * ir + kk * nz.x;
-        out = make_double2(-div.x, -div.y);
-    }
-    b[e] = out;
-}
-
-// Step 3 right-hand sides: (4u - u_prev)/(2dt) - (2N - N_prev) - grad_h p*; Dirichlet rows.
-__global__ void k_rhs_velocity(const double2* __restrict__ u, const double2* __restrict__ up,
-                               const double2* __restrict__ Nc, const double2* __restrict__ Np,
-                               const double2* __restrict__ ps, double2* __restrict__ rhs,
-                               const double* __restrict__ rn, const double* __restrict__ w1,
-                               const int* __restrict__ col0, double Re_i, double Re_o, Geo g) {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 3 * g.S) return;
-    const int c = (int)(e / g.S);
-    const size_t es = e - (size_t)c * g.S;
-    const int j = (int)(es / g.nmode);
-    const int mode = (int)(es - (size_t)j * g.nmode);
-    const int m = mode / g.nk;
-    const int k = mode - m * g.nk - g.K;
-    double2 out;
-    if (j == 0 || j == g.N - 1) {
-        out = make_double2(0.0, 0.0);
-        if (m == 0 && k == 0 && c < 2) {
-            const double Re = j == 0 ? Re_i : Re_o;
-            out.y = c == 0 ? Re : -Re;  // u_pm = +-i u_theta
-        }
-    } else {
-        const double r = rn[j];
-        const double c1 = 1.0 / (2.0 * g.dt);
-        const double2 a = u[e], q = up[e], n1 = Nc[e], n0 = Np[e];
-        double2 gp;
-        const double2 pv = ps[es];
-        if (c == 2) {
-            const double kk = g.kz * k;
-            gp = make_double2(-kk * pv.y, kk * pv.x);
-        } else {
-            const double2 d = drow(ps, w1, col0, j, g.nmode, mode);
-            const double t = (c == 0 ? -1.0 : 1.0) * g.mp * m / r;
-            gp = make_double2(d.x + t * pv.x, d.y + t * pv.y);
-        }
-        out.x = (4.0 * a.x - q.x) * c1 - (2.0 * n1.x - n0.x) - gp.x;
-        out.y = (4.0 * a.y - q.y) * c1 - (2.0 * n1.y - n0.y) - gp.y;
-    }
-    rhs[e] = out;
-}
-
-// Step 4 right-hand side: div_h u* on interior rows, homogeneous Neumann / Dirichlet rows.
-__global__ void k_rhs_div(const double2* __restrict__ us, double2* __restrict__ b,
-                          const double* __restrict__ rn, const double* __restrict__ w1,
-                          const int* __restrict__ col0, Geo g) {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= g.S) return;
-    const int j = (int)(e / g.nmode);
-    const int mode = (int)(e - (size_t)j * g.nmode);
-    if (j == 0 || j == g.N - 1) { b[e] = make_double2(0.0, 0.0); return; }
-    const int m = mode / g.nk;
-    const int k = mode - m * g.nk - g.K;
-    const double mm = g.mp * m, kk = g.kz * k, ir = 1.0 / rn[j];
-    const int c0 = col0[j];
-    double2 d = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int t = 0; t < kStencil; ++t) {
-        const double wt = __ldg(&w1[j * kStencil + t]);
-        const size_t o = (size_t)(c0 + t) * g.nmode + mode;
-        const double2 a = us[o], q = us[g.S + o];
-        d.x += wt * 0.5 * (a.x + q.x);
-        d.y += wt * 0.5 * (a.y + q.y);
-    }
-    const double2 vp = us[e], vm = us[g.S + e], vz = us[2 * g.S + e];
-    double2 div;
-    div.x = d.x + 0.5 * (vp.x + vm.x) * ir + mm * (vp.x - vm.x) * 0.5 * ir - kk * vz.y;
-    div.y = d.y + 0.5 * (vp.y + vm.y) * ir + mm * (vp.y - vm.y) * 0.5 * ir + kk * vz.x;
-    b[e] = div;
-}
-
-// Step 5: u^{i+1} = u* - grad_h phi; p^{i+1} = p* + 3 phi / (2 dt).  commit: rotate the
-// history in place (u_prev <- u^i, u <- u^{i+1}, N_prev <- N^i, p <- p^{i+1}); otherwise write
-// u^{i+1} to u_out only.
-__global__ void k_update(double2* __restrict__ u, double2* __restrict__ up, const double2* __restrict__ Nc,
-                         double2* __restrict__ Np, double2* __restrict__ p, const double2* __restrict__ us,
-                         const double2* __restrict__ ps, const double2* __restrict__ phi,
-                         double2* __restrict__ u_out, const double* __restrict__ rn,
-                         const double* __restrict__ w1, const int* __restrict__ col0, int commit, Geo g) {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 3 * g.S) return;
-    const int c = (int)(e / g.S);
-    const size_t es = e - (size_t)c * g.S;
-    const int j = (int)(es / g.nmode);
-    const int mode = (int)(es - (size_t)j * g.nmode);
-    const int m = mode / g.nk;
-    const int k = mode - m * g.nk - g.K;
-    const double2 f = phi[es];
-    double2 gphi;
-    if (c == 2) {
-        const double kk = g.kz * k;
-        gphi = make_double2(-kk * f.y, kk * f.x);
-    } else {
-        const double2 d = drow(phi, w1, col0, j, g.nmode, mode);
-        const double t = (c == 0 ? -1.0 : 1.0) * g.mp * m / rn[j];
-        gphi = make_double2(d.x + t * f.x, d.y + t * f.y);
-    }
-    const double2 s = us[e];
-    const double2 un = make_double2(s.x - gphi.x, s.y - gphi.y);
-    if (commit) {
-        up[e] = u[e];
-        u[e] = un;
-        Np[e] = Nc[e];
-        if (c == 0) {
-            const double q = 3.0 / (2.0 * g.dt);
-            const double2 a = ps[es];
-            p[es] = make_double2(a.x + q * f.x, a.y + q * f.y);
-        }
-    } else {
-        u_out[e] = un;
-    }
-}
-
-// Banded substitution with the pivoted LU of Sec. 3.2 (LAPACK band convention): forward
-// elimination applying row interchange j <-> j + piv_j then the 4 multipliers of column j,
-// backward substitution with the 8 super-diagonals of U and the stored 1/U_jj.
-__global__ void k_band_solve(double2* __restrict__ x, const double* __restrict__ fac,
-                             const uint8_t* __restrict__ piv, int set0, int nfields, Geo g) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nfields * g.nmode) return;
-    const int fld = t / g.nmode;
-    const int mode = t - fld * g.nmode;
-    const int m = mode / g.nk;
-    const int k = mode - m * g.nk - g.K;
-    const int ka = k < 0 ? -k : k;
-    const int set = set0 + fld;
-    const size_t mk = (size_t)m * g.K1 + ka;
-    const size_t per_set = (size_t)g.N * kBands * g.M1K1;
-    const double* F = fac + (size_t)set * per_set + mk;
-    const uint8_t* P = piv + (size_t)set * g.N * g.M1K1 + mk;
-    double2* X = x + (size_t)fld * g.S + mode;
+// Steps 2-5 of Sec. 3.2 for the T modes of this block: pressure prediction (Eq. pressure
+// with the Neumann rows of Eq. ppBC), velocity prediction (Eq. vel), correction potential
+// (Eq. correction) and update (Eq. update).
+__global__ void __launch_bounds__(256) k_pc(PCArgs a, Geo g, int T) {
+    extern __shared__ double2 sm[];
     const int N = g.N;
-    const size_t st = g.nmode;
-    for (int j = 0; j < N; ++j) {
-        const int pj = P[(size_t)j * g.M1K1];
-        double2 xj = X[(size_t)j * st];
-        if (pj) {
-            const double2 xp = X[(size_t)(j + pj) * st];
-            X[(size_t)(j + pj) * st] = xj;
-            xj = xp;
-            X[(size_t)j * st] = xj;
+    const int items = N * T;
+    double2* C0 = sm;
+    double2* C1 = sm + items;
+    double2* C2 = C1 + items;
+    double2* C3 = C2 + items;
+    const int mode0 = blockIdx.x * T;
+    const int nT = min(T, g.nmode - mode0);
+    const size_t per_set = (size_t)N * kBands * g.M1K1;
+    const double c1 = 1.0 / (2.0 * g.dt);
+
+    // A1: X = (2N - N_prev)_r into C1
+    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int j = idx / T, t = idx - (idx / T) * T;
+        double2 x = make_double2(0.0, 0.0);
+        if (t < nT) {
+            const size_t e = (size_t)j * g.nmode + mode0 + t;
+            const double2 n1 = a.Nc[e], n0 = a.Np[e], m1 = a.Nc[g.S + e], m0 = a.Np[g.S + e];
+            x.x = 0.5 * ((2.0 * n1.x - n0.x) + (2.0 * m1.x - m0.x));
+            x.y = 0.5 * ((2.0 * n1.y - n0.y) + (2.0 * m1.y - m0.y));
         }
-        const double* Fj = F + (size_t)j * kBands * g.M1K1;
-#pragma unroll
-        for (int q = 1; q <= kKl; ++q) {
-            if (j + q < N) {
-                const double l = __ldg(&Fj[(size_t)(q - 1) * g.M1K1]);
-                double2 v = X[(size_t)(j + q) * st];
-                v.x -= l * xj.x;
-                v.y -= l * xj.y;
-                X[(size_t)(j + q) * st] = v;
+        C1[idx] = x;
+    }
+    __syncthreads();
+    // A2: pressure right-hand side into C0
+    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int j = idx / T, t = idx - (idx / T) * T;
+        double2 out = make_double2(0.0, 0.0);
+        if (t < nT) {
+            const int mode = mode0 + t;
+            const int m = mode / g.nk;
+            const int k = mode - m * g.nk - g.K;
+            const double mm = g.mp * m, kk = g.kz * k;
+            const double r = a.rn[j], ir = 1.0 / r;
+            const size_t e = (size_t)j * g.nmode + mode;
+            if (j == 0 || j == N - 1) {
+                if (!(j == N - 1 && m == 0 && k == 0)) {
+                    const double2 l0 = lap_r(a.u, a.w1, a.w2, a.col0, r, j, mode, mm, kk, g);
+                    const double2 l1 = lap_r(a.up, a.w1, a.w2, a.col0, r, j, mode, mm, kk, g);
+                    const double2 X = C1[idx];
+                    out.x = -X.x + 2.0 * l0.x - l1.x;
+                    out.y = -X.y + 2.0 * l0.y - l1.y;
+                }
+            } else {
+                const double2 d = sdrow(C1, a.w1, a.col0, j, T, t);
+                const double2 X = C1[idx];
+                const double2 n1 = a.Nc[e], n0 = a.Np[e], m1 = a.Nc[g.S + e], m0 = a.Np[g.S + e];
+                const double2 z1 = a.Nc[2 * g.S + e], z0 = a.Np[2 * g.S + e];
+                const double dpx = (2.0 * n1.x - n0.x) - (2.0 * m1.x - m0.x);
+                const double dpy = (2.0 * n1.y - n0.y) - (2.0 * m1.y - m0.y);
+                const double nzx = 2.0 * z1.x - z0.x, nzy = 2.0 * z1.y - z0.y;
+                out.x = -(d.x + X.x * ir + 0.5 * mm * ir * dpx - kk * nzy);
+                out.y = -(d.y + X.y * ir + 0.5 * mm * ir * dpy + kk * nzx);
             }
+        }
+        C0[idx] = out;
+    }
+    __syncthreads();
+    // B: p* = P^{-1} b_p (real and imaginary parts by separate threads)
+    if (threadIdx.x < 2 * nT) {
+        const int t = threadIdx.x >> 1, part = threadIdx.x & 1;
+        const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
+        const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+        smem_band_solve(C0, T, t, part, N, a.fac + (size_t)kSetP * per_set + mk,
+                        a.piv + (size_t)kSetP * N * g.M1K1 + mk, g.M1K1);
+    }
+    __syncthreads();
+    // C: velocity right-hand sides into C1..C3; p <- p* (commit)
+    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int j = idx / T, t = idx - (idx / T) * T;
+        double2 o0 = make_double2(0.0, 0.0), o1 = o0, o2 = o0;
+        if (t < nT) {
+            const int mode = mode0 + t;
+            const int m = mode / g.nk;
+            const int k = mode - m * g.nk - g.K;
+            const size_t e = (size_t)j * g.nmode + mode;
+            const double2 pv = C0[idx];
+            if (a.commit) a.p[e] = pv;
+            if (j == 0 || j == N - 1) {
+                if (m == 0 && k == 0) {
+                    const double Re = j == 0 ? a.Re_i : a.Re_o;
+                    o0.y = Re;
+                    o1.y = -Re;
+                }
+            } else {
+                const double2 d = sdrow(C0, a.w1, a.col0, j, T, t);
+                const double tt = g.mp * m / a.rn[j];
+                const double kk = g.kz * k;
+                const double2 gp0 = make_double2(d.x - tt * pv.x, d.y - tt * pv.y);
+                const double2 gp1 = make_double2(d.x + tt * pv.x, d.y + tt * pv.y);
+                const double2 gp2 = make_double2(-kk * pv.y, kk * pv.x);
+                const double2* gps[3] = {&gp0, &gp1, &gp2};
+                double2* outs[3] = {&o0, &o1, &o2};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const size_t ec = (size_t)c * g.S + e;
+                    const double2 uu = a.u[ec], q = a.up[ec], n1 = a.Nc[ec], n0 = a.Np[ec];
+                    outs[c]->x = (4.0 * uu.x - q.x) * c1 - (2.0 * n1.x - n0.x) - gps[c]->x;
+                    outs[c]->y = (4.0 * uu.y - q.y) * c1 - (2.0 * n1.y - n0.y) - gps[c]->y;
+                }
+            }
+        }
+        C1[idx] = o0;
+        C2[idx] = o1;
+        C3[idx] = o2;
+    }
+    __syncthreads();
+    // D: the three Helmholtz solves
+    if (threadIdx.x < 6 * nT) {
+        const int c = threadIdx.x / (2 * nT), rem = threadIdx.x - c * 2 * nT;
+        const int t = rem >> 1, part = rem & 1;
+        const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
+        const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+        const int set = kSetHp + c;
+        smem_band_solve(C1 + (size_t)c * items, T, t, part, N, a.fac + (size_t)set * per_set + mk,
+                        a.piv + (size_t)set * N * g.M1K1 + mk, g.M1K1);
+    }
+    __syncthreads();
+    // E: div_h u* into C0 (homogeneous Neumann / Dirichlet rows)
+    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int j = idx / T, t = idx - (idx / T) * T;
+        double2 out = make_double2(0.0, 0.0);
+        if (t < nT && j > 0 && j < N - 1) {
+            const int mode = mode0 + t;
+            const int m = mode / g.nk;
+            const int k = mode - m * g.nk - g.K;
+            const double mm = g.mp * m, kk = g.kz * k, ir = 1.0 / a.rn[j];
+            const double2 dp = sdrow(C1, a.w1, a.col0, j, T, t), dm = sdrow(C2, a.w1, a.col0, j, T, t);
+            const double2 vp = C1[idx], vm = C2[idx], vz = C3[idx];
+            out.x = 0.5 * (dp.x + dm.x) + 0.5 * (vp.x + vm.x) * ir + 0.5 * mm * ir * (vp.x - vm.x) - kk * vz.y;
+            out.y = 0.5 * (dp.y + dm.y) + 0.5 * (vp.y + vm.y) * ir + 0.5 * mm * ir * (vp.y - vm.y) + kk * vz.x;
+        }
+        C0[idx] = out;
+    }
+    __syncthreads();
+    // F: phi = P^{-1} div_h u*
+    if (threadIdx.x < 2 * nT) {
+        const int t = threadIdx.x >> 1, part = threadIdx.x & 1;
+        const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
+        const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+        smem_band_solve(C0, T, t, part, N, a.fac + (size_t)kSetP * per_set + mk,
+                        a.piv + (size_t)kSetP * N * g.M1K1 + mk, g.M1K1);
+    }
+    __syncthreads();
+    // G: u^{i+1} = u* - grad_h phi, p^{i+1} = p* + 3 phi / (2 dt), history rotation
+    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int j = idx / T, t = idx - (idx / T) * T;
+        if (t >= nT) continue;
+        const int mode = mode0 + t;
+        const int m = mode / g.nk;
+        const int k = mode - m * g.nk - g.K;
+        const size_t e = (size_t)j * g.nmode + mode;
+        const double2 f = C0[idx];
+        const double2 d = sdrow(C0, a.w1, a.col0, j, T, t);
+        const double tt = g.mp * m / a.rn[j];
+        const double kk = g.kz * k;
+        const double2 gph[3] = {make_double2(d.x - tt * f.x, d.y - tt * f.y),
+                                make_double2(d.x + tt * f.x, d.y + tt * f.y),
+                                make_double2(-kk * f.y, kk * f.x)};
+        const double2 us[3] = {C1[idx], C2[idx], C3[idx]};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t ec = (size_t)c * g.S + e;
+            const double2 un = make_double2(us[c].x - gph[c].x, us[c].y - gph[c].y);
+            if (a.commit) {
+                a.up_out[ec] = a.u[ec];
+                a.Np_out[ec] = a.Nc[ec];
+            }
+            a.u_out[ec] = un;
+        }
+        if (a.commit) {
+            const double q = 3.0 / (2.0 * g.dt);
+            const double2 ps = a.p[e];
+            a.p[e] = make_double2(ps.x + q * f.x, ps.y + q * f.y);
         }
     }
-    for (int j = N - 1; j >= 0; --j) {
-        const double* Fj = F + (size_t)j * kBands * g.M1K1;
-        double2 s = X[(size_t)j * st];
-#pragma unroll
-        for (int q = 1; q <= 2 * kKl; ++q) {
-            if (j + q < N) {
-                const double uq = __ldg(&Fj[(size_t)(4 + q) * g.M1K1]);
-                const double2 v = X[(size_t)(j + q) * st];
-                s.x -= uq * v.x;
-                s.y -= uq * v.y;
-            }
-        }
-        const double id = __ldg(&Fj[(size_t)4 * g.M1K1]);
-        X[(size_t)j * st] = make_double2(s.x * id, s.y * id);
+}
+
+// Stand-alone solve of one system set for all modes (tc_helmholtz_solve): columns staged in
+// shared memory, real and imaginary parts by separate threads.
+__global__ void __launch_bounds__(256) k_band_solve_s(double2* __restrict__ x, const double* __restrict__ fac,
+                                                      const uint8_t* __restrict__ piv, int set, Geo g, int T) {
+    extern __shared__ double2 sm[];
+    const int N = g.N;
+    const int mode0 = blockIdx.x * T;
+    const int nT = min(T, g.nmode - mode0);
+    for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
+        const int j = idx / T, t = idx - (idx / T) * T;
+        sm[idx] = t < nT ? x[(size_t)j * g.nmode + mode0 + t] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * nT) {
+        const int t = threadIdx.x >> 1, part = threadIdx.x & 1;
+        const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
+        const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+        const size_t per_set = (size_t)N * kBands * g.M1K1;
+        smem_band_solve(sm, T, t, part, N, fac + (size_t)set * per_set + mk, piv + (size_t)set * N * g.M1K1 + mk, g.M1K1);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
+        const int j = idx / T, t = idx - (idx / T) * T;
+        if (t < nT) x[(size_t)j * g.nmode + mode0 + t] = sm[idx];
     }
 }
 
@@ -355,37 +313,53 @@ __global__ void k_diag(const double2* __restrict__ u, double* __restrict__ red,
 
 static int blocks_for(size_t n, int bs) { return (int)((n + bs - 1) / bs); }
 
+// modes per block of the fused kernel: four complex columns of N_r rows in shared memory
+static int pc_modes(const tc_plan* p) {
+    int T = p->pc_modes > 0 ? p->pc_modes : 8;
+    while (T > 1 && (size_t)4 * p->N_r * T * sizeof(double2) > 96 * 1024) T /= 2;
+    return T;
+}
+
 tc_status launch_solve(tc_plan* p, int set, double2* x, int nfields, cudaStream_t s) {
     Geo g = geo(p);
-    const int n = nfields * g.nmode;
-    { const int slot_ = prof_begin(p, set == kSetP ? kKSolveP : kKSolveH, s); k_band_solve<<<blocks_for(n, 128), 128, 0, s>>>(x, p->d_fac, p->d_piv, set, nfields, g); prof_end(p, slot_, s); }
-    TC_LAUNCHED(p, "k_band_solve");
+    int T = 32;
+    while (T > 1 && (size_t)p->N_r * T * sizeof(double2) > 96 * 1024) T /= 2;
+    const size_t sm = (size_t)p->N_r * T * sizeof(double2);
+    TC_CUDA(p, cudaFuncSetAttribute(k_band_solve_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    for (int f = 0; f < nfields; ++f) {
+        const int slot = prof_begin(p, set == kSetP ? kKSolveP : kKSolveH, s);
+        k_band_solve_s<<<blocks_for(g.nmode, T), 64, sm, s>>>(x + (size_t)f * g.S, p->d_fac, p->d_piv, set + f, g, T);
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_band_solve_s");
+    }
     return TC_OK;
 }
 
 tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const double2* Ncur,
                          double2* N_prev, double2* p_out, double2* u_out, char* ws, bool commit,
                          cudaStream_t s) {
+    (void)ws;
     Geo g = geo(p);
-    double2* ps = reinterpret_cast<double2*>(ws + p->ws.pstar);
-    double2* us = reinterpret_cast<double2*>(ws + p->ws.ustar);
-    double2* phi = reinterpret_cast<double2*>(ws + p->ws.phi);
-    const int bs = 256;
-    { const int slot_ = prof_begin(p, kKRhsPressure, s); k_rhs_pressure<<<blocks_for(g.S, bs), bs, 0, s>>>(u, u_prev, Ncur, N_prev, ps, p->d_r, p->d_w1, p->d_w2, p->d_col0, g); prof_end(p, slot_, s); }
-    TC_LAUNCHED(p, "k_rhs_pressure");
-    tc_status st = launch_solve(p, kSetP, ps, 1, s);
-    if (st != TC_OK) return st;
-    { const int slot_ = prof_begin(p, kKRhsVelocity, s); k_rhs_velocity<<<blocks_for(3 * g.S, bs), bs, 0, s>>>(u, u_prev, Ncur, N_prev, ps, us, p->d_r, p->d_w1, p->d_col0, p->Re_i, p->Re_o, g); prof_end(p, slot_, s); }
-    TC_LAUNCHED(p, "k_rhs_velocity");
-    st = launch_solve(p, kSetHp, us, 3, s);
-    if (st != TC_OK) return st;
-    { const int slot_ = prof_begin(p, kKRhsDiv, s); k_rhs_div<<<blocks_for(g.S, bs), bs, 0, s>>>(us, phi, p->d_r, p->d_w1, p->d_col0, g); prof_end(p, slot_, s); }
-    TC_LAUNCHED(p, "k_rhs_div");
-    st = launch_solve(p, kSetP, phi, 1, s);
-    if (st != TC_OK) return st;
-    { const int slot_ = prof_begin(p, kKUpdate, s); k_update<<<blocks_for(3 * g.S, bs), bs, 0, s>>>(const_cast<double2*>(u), u_prev, Ncur, N_prev, p_out, us, ps, phi, u_out,
-                                                    p->d_r, p->d_w1, p->d_col0, commit ? 1 : 0, g); prof_end(p, slot_, s); }
-    TC_LAUNCHED(p, "k_update");
+    const int T = pc_modes(p);
+    PCArgs a;
+    a.u = u; a.up = u_prev; a.Nc = Ncur; a.Np = N_prev;
+    a.u_out = commit ? const_cast<double2*>(u) : u_out;
+    a.up_out = commit ? u_prev : nullptr;
+    a.Np_out = commit ? N_prev : nullptr;
+    a.p = commit ? p_out : nullptr;
+    a.rn = p->d_r; a.w1 = p->d_w1; a.w2 = p->d_w2; a.col0 = p->d_col0;
+    a.fac = p->d_fac; a.piv = p->d_piv;
+    a.Re_i = p->Re_i; a.Re_o = p->Re_o;
+    a.commit = commit ? 1 : 0;
+    const size_t sm = (size_t)4 * p->N_r * T * sizeof(double2);
+    int threads = ((6 * T + 31) / 32) * 32;
+    if (threads < 128) threads = 128;
+    if (threads > 256) threads = 256;
+    TC_CUDA(p, cudaFuncSetAttribute(k_pc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int slot = prof_begin(p, kKPC, s);
+    k_pc<<<blocks_for(g.nmode, T), threads, sm, s>>>(a, g, T);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_pc");
     return TC_OK;
 }
 

@@ -22,18 +22,24 @@ SYMBOLS = [
     "tc_plan_create", "tc_plan_create_ex", "tc_plan_destroy", "tc_plan_workspace_bytes",
     "tc_plan_nodes", "tc_plan_fd_weights", "tc_plan_last_error", "tc_status_string",
     "tc_nonlinear", "tc_helmholtz_solve", "tc_step", "tc_diagnostics",
+    "tc_adjoint_step", "tc_adjoint_start", "tc_energy_gradient",
     "tc_nonlinear_noalloc", "tc_profile_enable", "tc_profile_read",
 ]
 
 
 class tc_options(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("P_theta", ctypes.c_int), ("P_z", ctypes.c_int),
-                ("precision", ctypes.c_int), ("host_only", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("host_only", ctypes.c_int), ("theta_zt", ctypes.c_int),
+                ("pc_modes", ctypes.c_int)]
 
 
 class tc_state(ctypes.Structure):
     _fields_ = [("u", ctypes.c_void_p), ("u_prev", ctypes.c_void_p), ("N_prev", ctypes.c_void_p),
                 ("p", ctypes.c_void_p), ("started", ctypes.c_int)]
+
+
+class tc_state_bar(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("u_prev", ctypes.c_void_p), ("N_prev", ctypes.c_void_p)]
 
 
 class tc_diag(ctypes.Structure):
@@ -74,6 +80,9 @@ def load_library(path: str = LIB_PATH):
         "tc_helmholtz_solve": (I, [P, I, P, P, P, P]),
         "tc_step": (I, [P, ctypes.POINTER(tc_state), I, P, P]),
         "tc_diagnostics": (I, [P, P, ctypes.POINTER(tc_diag), P, P]),
+        "tc_adjoint_step": (I, [P, ctypes.POINTER(tc_state), ctypes.POINTER(tc_state_bar), P, P]),
+        "tc_adjoint_start": (I, [P, P, ctypes.POINTER(tc_state_bar), P, P, P]),
+        "tc_energy_gradient": (I, [P, P, P, P]),
         "tc_nonlinear_noalloc": (I, [P, P, P, P]),
         "tc_profile_enable": (I, [P, I]),
         "tc_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
@@ -171,8 +180,10 @@ class Plan:
     """A libtc plan plus a device workspace (torch-allocated)."""
 
     def __init__(self, N_r, M, K, m_p, eta, Re_i, Re_o, L_z, dt, fd_order=8, alpha=0.5,
-                 P_theta=0, P_z=0, precision=TC_FP64, host_only=False, device=None):
-        opt = tc_options(alpha if alpha != 0.0 else -1.0, P_theta, P_z, precision, int(host_only))
+                 P_theta=0, P_z=0, precision=TC_FP64, host_only=False, device=None, theta_zt=0,
+                 pc_modes=0):
+        opt = tc_options(alpha if alpha != 0.0 else -1.0, P_theta, P_z, precision, int(host_only),
+                         theta_zt, pc_modes)
         self.N_r, self.M, self.K = N_r, M, K
         self.handle = None
         torch = _torch()
@@ -236,6 +247,30 @@ class Plan:
     def diagnostics(self, u, stream=None):
         return tc_diagnostics(self.handle, _ptr(u), self._ws(), _stream_ptr(stream))
 
+    def adjoint_step(self, fwd: "State", bar: "StateBar", stream=None):
+        """In place: bar (adjoints of u^{i+1}, u^i, N^i) -> adjoints of (u^i, u^{i-1}, N^{i-1})."""
+        cs = fwd.c_struct()
+        cb = bar.c_struct()
+        _check(load_library().tc_adjoint_step(self.handle, ctypes.byref(cs), ctypes.byref(cb), self._ws(),
+                                              _stream_ptr(stream)), self.handle)
+        return bar
+
+    def adjoint_start(self, u0, bar: "StateBar", out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty_like(u0)
+        cb = bar.c_struct()
+        _check(load_library().tc_adjoint_start(self.handle, _ptr(u0), ctypes.byref(cb), _ptr(out), self._ws(),
+                                               _stream_ptr(stream)), self.handle)
+        return out
+
+    def energy_gradient(self, u, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty_like(u)
+        _check(load_library().tc_energy_gradient(self.handle, _ptr(u), _ptr(out), _stream_ptr(stream)), self.handle)
+        return out
+
     def profile(self, enable=True):
         _check(load_library().tc_profile_enable(self.handle, int(enable)), self.handle)
 
@@ -267,6 +302,16 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class StateBar:
+    """Adjoint state (device tensors): adjoints of u, u_prev, N_prev."""
+
+    def __init__(self, u, u_prev, N_prev):
+        self.u, self.u_prev, self.N_prev = u, u_prev, N_prev
+
+    def c_struct(self):
+        return tc_state_bar(self.u.data_ptr(), self.u_prev.data_ptr(), self.N_prev.data_ptr())
 
 
 class State:

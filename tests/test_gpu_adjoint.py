@@ -1,0 +1,141 @@
+"""Adjoint of the CUDA step (through the C ABI) against the oracle's adjoint, dot-product
+tests against central differences of the CUDA step itself (exact for the quadratic step up
+to rounding), and the gradient of the final perturbation energy against central finite
+differences (h = 1e-7, 8 directions, <= 1e-6) and against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+from paper_1311_2481_gb300 import adjoint as A  # noqa: E402
+from paper_1311_2481_gb300 import build as B  # noqa: E402
+from paper_1311_2481_gb300 import inputs as I  # noqa: E402
+from paper_1311_2481_gb300 import tc  # noqa: E402
+
+B.build()
+LZ = 2 * math.pi / 3.16
+CFG1 = dict(N_r=32, M=8, K=16, m_p=1, eta=0.5, Re_i=50.0, Re_o=0.0, L_z=LZ, dt=1e-3)
+SMALL = dict(N_r=12, M=3, K=4, m_p=1, eta=0.5, Re_i=50.0, Re_o=0.0, L_z=LZ, dt=1e-3)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def setup(cfg, amp=1e-2):
+    ops = O.Operators(O.Params(**cfg))
+    plan = tc.Plan(**cfg)
+    prm = ops.prm
+    u0 = I.initial_state(ops.r, prm.M, prm.K, prm.m_p, prm.L_z, prm.eta, prm.Re_i, prm.Re_o,
+                         kind="box", amp=amp, mbox=min(4, prm.M), kbox=min(4, prm.K))
+    return ops, plan, u0
+
+
+def gpu_state(plan, st_o):
+    st = tc.State(plan, dev(st_o.u))
+    st.u_prev.copy_(dev(st_o.u_prev))
+    st.N_prev.copy_(dev(st_o.N_prev))
+    st.started = True
+    return st
+
+
+@pytest.mark.parametrize("cfg", [CFG1, SMALL])
+def test_adjoint_step_matches_oracle(cfg):
+    ops, plan, u0 = setup(cfg)
+    st_o = O.step(ops, O.cold_state(u0))
+    sh = (3,) + ops.prm.shape()
+    y = [I.random_spectral(sh, seed=s) for s in (11, 12, 13)]
+    ref = O.adjoint_step(ops, st_o, *y)
+    bar = tc.StateBar(*[dev(v) for v in y])
+    plan.adjoint_step(gpu_state(plan, st_o), bar)
+    for got, want in zip((bar.u, bar.u_prev, bar.N_prev), ref):
+        assert rel(host(got), want) <= 1e-11
+
+
+def test_adjoint_start_matches_oracle():
+    ops, plan, u0 = setup(CFG1)
+    sh = (3,) + ops.prm.shape()
+    y = [I.random_spectral(sh, seed=s) for s in (21, 22, 23)]
+    ref = O.adjoint_start_up(ops, u0, *y)
+    bar = tc.StateBar(*[dev(v) for v in y])
+    got = host(plan.adjoint_start(dev(u0), bar))
+    assert rel(got, ref) <= 1e-11
+
+
+def test_dot_product_against_gpu_central_differences():
+    """<ybar, dF(s)[x]> = <F^T ybar, x>; F is quadratic so the central difference of the CUDA
+    step with h = 1e-2 gives dF(s)[x] up to rounding."""
+    ops, plan, u0 = setup(CFG1)
+    st_o = O.step(ops, O.cold_state(u0))
+    sh = (3,) + ops.prm.shape()
+    x = [I.random_spectral(sh, seed=s) for s in (31, 32, 33)]
+    y = [I.random_spectral(sh, seed=s) for s in (34, 35, 36)]
+    h = 1e-2
+    outs = []
+    for sg in (1.0, -1.0):
+        st = tc.State(plan, dev(st_o.u + sg * h * x[0]))
+        st.u_prev.copy_(dev(st_o.u_prev + sg * h * x[1]))
+        st.N_prev.copy_(dev(st_o.N_prev + sg * h * x[2]))
+        st.started = True
+        plan.step(st, 1)
+        outs.append([host(st.u), host(st.u_prev), host(st.N_prev)])
+    tl = [(a - b) / (2 * h) for a, b in zip(*outs)]
+    lhs = sum(O.inner(a, b) for a, b in zip(y, tl))
+    bar = tc.StateBar(*[dev(v) for v in y])
+    plan.adjoint_step(gpu_state(plan, st_o), bar)
+    rhs = sum(O.inner(host(a), b) for a, b in zip((bar.u, bar.u_prev, bar.N_prev), x))
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs), (lhs, rhs)
+
+
+def test_energy_gradient_kernel_matches_oracle():
+    ops, plan, u0 = setup(CFG1)
+    got = host(plan.energy_gradient(dev(u0)))
+    assert rel(got, O.energy_gradient(ops, u0)) <= 1e-14
+
+
+def test_final_energy_gradient_fd_and_oracle():
+    """dJ/du0 after 10 steps (checkpoint every 4): central differences with h = 1e-7 on
+    8 random directions agree to <= 1e-6; the gradient agrees with the oracle's."""
+    ops, plan, u0 = setup(CFG1)
+    n = 10
+    u = dev(u0).requires_grad_(False)
+    x = u.clone().requires_grad_(True)
+    J = A.final_energy(x, plan, n, checkpoint=4)
+    J.backward()
+    g = host(x.grad)
+    g_ref, J_ref = O.gradient_final_energy(ops, u0, n)
+    assert abs(J.item() / J_ref - 1) <= 1e-10
+    assert rel(g, g_ref) <= 1e-9
+    # checkpointing does not change the gradient
+    x2 = u.clone().requires_grad_(True)
+    A.final_energy(x2, plan, n, checkpoint=n).backward()
+    assert rel(host(x2.grad), g) <= 1e-13
+    rng = np.random.default_rng(5)
+    h = 1e-7
+    for _ in range(8):
+        d = I.random_spectral((3,) + ops.prm.shape(), seed=int(rng.integers(1 << 30)), hermitian_K=ops.prm.K)
+        d[:, 0] = 0.0
+        d[:, -1] = 0.0
+        dd = dev(d)
+        with torch.no_grad():
+            Jp = A.final_energy(u + h * dd, plan, n, checkpoint=n).item()
+            Jm = A.final_energy(u - h * dd, plan, n, checkpoint=n).item()
+        fd = (Jp - Jm) / (2 * h)
+        ad = O.inner(g, d)
+        assert abs(fd - ad) <= 1e-6 * abs(fd), (fd, ad)
