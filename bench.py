@@ -25,6 +25,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 CFG2 = dict(N_r=64, M=32, K=64, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)
+# adjoint workload: N_r = 96, m = -32..32, k = -64..64, Re_i = 2000, 200 steps, checkpoint every 20
+CFG3 = dict(N_r=96, M=32, K=64, m_p=1, eta=0.5, Re_i=2000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)
+# mixed vs FP64 at the same size: quasi-Keplerian (Re_o = sqrt(eta) Re_i), 256 x 768 x 1536 grid
+CFG4 = dict(N_r=256, M=256, K=512, m_p=1, eta=0.5, Re_i=1e4, Re_o=math.sqrt(0.5) * 1e4,
+            L_z=2 * math.pi / 3.16, dt=1e-4)
 WORKLOAD = ("FP64 AB2BD2 step: eta=0.5, Re_i=1000, Re_o=0, N_r=64 clustered nodes (alpha=0.5), "
             "m=-32..32 (m_p=1), k=-64..64 (L_z=2pi/3.16), phys grid 64x96x192, dt=5e-4, "
             "init Couette + Taylor-vortex-like perturbation amp 1e-2 (seed 42)")
@@ -38,6 +43,26 @@ def gdof(cfg):
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def replica_seed(rank):
+    """Each rank advances its own independent simulation (weak scaling, no data exchange)."""
+    return 42 + rank
+
+
+def max_over_ranks(dist, value, device):
+    """Max of a per-rank float over all ranks (the timed region is as slow as the slowest)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world, steps, max_ms):
+    """Whole-job steps/s: all ranks' steps over the slowest rank's time."""
+    return world * steps / (max_ms / 1e3)
 
 
 def init_dist(world, backend):
@@ -110,6 +135,87 @@ def zpass_flops(cfg, Pz, lines):
     return cfg["N_r"] * (cfg["M"] + 1) * lines * 5.0 * Pz * math.log2(Pz)
 
 
+def stable_dt(tc, torch, cfg, u0_t, dev, nsteps=200):
+    """Stated dt halved until nsteps FP64 steps stay finite with < 10x energy growth."""
+    dt = cfg["dt"]
+    for _ in range(12):
+        plan = tc.Plan(**{**cfg, "dt": dt}, device=dev)
+        st = tc.State(plan, u0_t.to(dev))
+        e0 = plan.diagnostics(st.u).energy
+        plan.step(st, nsteps)
+        d = plan.diagnostics(st.u)
+        del plan, st
+        if d.finite and d.energy < 10.0 * e0:
+            return dt
+        dt /= 2.0
+    return dt
+
+
+def adjoint_ratio(tc, torch, I, dev):
+    """Cost of the checkpointed adjoint of 200 steps (N_r = 96) against the forward run."""
+    from paper_1311_2481_gb300 import adjoint as A
+    cfg = CFG3
+    probe = tc.Plan(**cfg, device=dev)
+    r = probe.nodes()
+    del probe
+    u0 = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"],
+                                          cfg["Re_o"], kind="box", amp=1e-4, seed=42))
+    dt = stable_dt(tc, torch, cfg, u0, dev)
+    plan = tc.Plan(**{**cfg, "dt": dt}, device=dev)
+    n, C = 200, 20
+    x = u0.to(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    A.final_energy(x, plan, 20, checkpoint=C)                 # warm-up
+    torch.cuda.synchronize()
+    ev[0].record()
+    with torch.no_grad():
+        J0 = A.final_energy(x, plan, n, checkpoint=C)
+    ev[1].record()
+    xg = x.clone().requires_grad_(True)
+    ev[2].record()
+    J = A.final_energy(xg, plan, n, checkpoint=C)
+    J.backward()
+    ev[3].record()
+    torch.cuda.synchronize()
+    t_f = ev[0].elapsed_time(ev[1])
+    t_fb = ev[2].elapsed_time(ev[3])
+    g = xg.grad
+    return {"workload": "N_r=96, m=-32..32, k=-64..64, Re_i=2000, 200 steps, checkpoint every 20, "
+                        "J = final perturbation energy, init amp 1e-4 (seed 42)",
+            "dt": dt, "forward_ms": t_f, "forward_plus_adjoint_ms": t_fb,
+            "adjoint_to_forward_ratio": (t_fb - t_f) / t_f, "J": float(J0),
+            "grad_finite": bool(torch.isfinite(torch.view_as_real(g)).all())}
+
+
+def large_mixed(tc, torch, I, dev, steps=4):
+    """FP64 plain vs mixed step at N_r = 256, m = -256..256, k = -512..512 (same size)."""
+    cfg = CFG4
+    out = {"workload": "quasi-Keplerian eta=0.5, Re_i=1e4, Re_o=sqrt(eta) Re_i, N_r=256, m=-256..256, "
+                       "k=-512..512, phys 256x768x1536, dt=1e-4, broadband amp 0.05 (seed 42)",
+           "gdof": gdof(cfg)}
+    res = {}
+    for name, prec in (("fp64", tc.TC_FP64), ("mixed", tc.TC_MIXED)):
+        plan = tc.Plan(**cfg, precision=prec, device=dev)
+        r = plan.nodes()
+        u0 = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"],
+                                              cfg["Re_o"], kind="broadband", amp=0.05, seed=42)).to(dev)
+        st = tc.State(plan, u0)
+        plan.step(st, 2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.step(st, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[name] = ms
+        out[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "gdof_steps_per_s": gdof(cfg) / ms / 1e6}
+        del plan, st, u0
+        torch.cuda.empty_cache()
+    out["mixed_speedup_vs_fp64"] = res["fp64"] / res["mixed"]
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_1311_2481_gb300 import build as B
@@ -127,7 +233,7 @@ def run_ours(args):
     plan = tc.Plan(**cfg, device=f"cuda:{local}")
     r = plan.nodes()
     u0 = I.initial_state(r, cfg["M"], cfg["K"], cfg["m_p"], cfg["L_z"], cfg["eta"], cfg["Re_i"],
-                         cfg["Re_o"], kind="taylor", amp=1e-2, seed=42 + rank)
+                         cfg["Re_o"], kind="taylor", amp=1e-2, seed=replica_seed(rank))
     u0_t = torch.from_numpy(u0)
     st = tc.State(plan, u0_t.cuda())
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -177,13 +283,9 @@ def run_ours(args):
         wall = time.perf_counter() - t0
     if dist:
         dist.barrier()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(dist, sum(step_ms), "cuda")
     ms_per_step = total_ms / K
-    value = world * K / (total_ms / 1e3)
+    value = aggregate_value(world, K, total_ms)
 
     # per-kernel breakdown: a tracing pass over the same number of steps
     _, prof, _ = timed_steps(plan, st, K, profile=True)
@@ -195,14 +297,19 @@ def run_ours(args):
     Pt, Pz = 3 * cfg["M"], 3 * cfg["K"]
     flops = {"k_theta": theta_flops(cfg, Pt, Pz), "k_zinv": zpass_flops(cfg, Pz, 9),
              "k_zfwd": zpass_flops(cfg, Pz, 3)}
-    fp64_peak = 1.21e12   # measured DFMA-loop peak on this GB300 (nominal 1.25 TFLOP/s)
+    # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk/SM (ncu peak_sustained of
+    # sm__sass_thread_inst_executed_op_dfma_pred_on) x 2 flop x 2.07 GHz
+    fp64_peak = 152 * 2 * 2 * 2.07e9
     roof = None
     if top[0] in flops:
         avg_s = top[1][1] / top[1][0] / 1e3
         ach = flops[top[0]] / avg_s
         roof = {"kernel": top[0], "bound": "alu", "achieved": ach / 1e12, "peak": fp64_peak / 1e12,
-                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
-                "peak_source": "FP64 DFMA loop measured on GB300 (152 SMs x 2 DFMA/clk x 2 flop x ~2.0 GHz)",
+                "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                # dram__bytes_read.sum + dram__bytes_write.sum of k_theta<double2> per launch,
+                # from profiles/k_theta_fp64__Nr64_M32_K64.md (kernel unchanged since)
+                "traffic": (58.437376e6 + 3.228672e6) if top[0] == "k_theta" else None,
+                "peak_source": "152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (unit counts and max clock)",
                 "algorithmic": "7.5 complex FFTs of P_theta at 5 n log2 n + 25 flop/point per (r, z)"}
     else:
         roof = {"kernel": top[0], "bound": "alu", "achieved": None, "peak": fp64_peak / 1e12,
@@ -212,22 +319,40 @@ def run_ours(args):
     mplan = tc.Plan(**cfg, precision=tc.TC_MIXED, device=f"cuda:{local}")
     mst = tc.State(mplan, u0_t.cuda())
     m_ms, mprof, m_finite = timed_steps(mplan, mst, K)
-    a = tc.State(plan, u0_t.cuda())
-    b = tc.State(mplan, u0_t.cuda())
-    plan.step(a, CHUNK)
-    mplan.step(b, CHUNK)
-    da, db = plan.diagnostics(a.u), mplan.diagnostics(b.u)
+    # error of the mixed form at the largest stable dt (stated dt halved until 200 FP64
+    # steps stay finite and the perturbation energy grows by less than 10x)
     base = torch.from_numpy(I.base_state(r, cfg["M"], cfg["K"], cfg["eta"], cfg["Re_i"], cfg["Re_o"])).cuda()
+    NERR = 200
+    dt_eff = cfg["dt"]
+    for _ in range(10):
+        tplan = tc.Plan(**{**cfg, "dt": dt_eff}, device=f"cuda:{local}")
+        ts = tc.State(tplan, u0_t.cuda())
+        e0 = tplan.diagnostics(ts.u).energy
+        tplan.step(ts, NERR)
+        d = tplan.diagnostics(ts.u)
+        del tplan
+        if d.finite and d.energy < 10.0 * e0:
+            break
+        dt_eff /= 2.0
+    fplan = tc.Plan(**{**cfg, "dt": dt_eff}, device=f"cuda:{local}")
+    eplan = tc.Plan(**{**cfg, "dt": dt_eff}, precision=tc.TC_MIXED, device=f"cuda:{local}")
+    a = tc.State(fplan, u0_t.cuda())
+    b = tc.State(eplan, u0_t.cuda())
+    fplan.step(a, NERR)
+    eplan.step(b, NERR)
+    da, db = fplan.diagnostics(a.u), eplan.diagnostics(b.u)
     pa, pb = a.u - base, b.u - base
     mixed = {"value": world * K / (sum(m_ms) / 1e3), "unit": "steps/s", "ms_per_step": sum(m_ms) / K,
              "speedup_vs_fp64": (total_ms / K) / (sum(m_ms) / K),
              "dtype": "f32 transforms/products + f64 mean flow, solves, factors",
-             "error_after_steps": CHUNK,
+             "error_dt": dt_eff, "error_after_steps": NERR,
              "rel_err_velocity_perturbation": float(torch.linalg.vector_norm(pb - pa) / torch.linalg.vector_norm(pa)),
              "rel_err_velocity": float(torch.linalg.vector_norm(b.u - a.u) / torch.linalg.vector_norm(a.u)),
              "rel_err_torque_inner": abs(db.torque_inner / da.torque_inner - 1),
-             "rel_err_max_div": abs(db.max_div / da.max_div - 1) if da.max_div else None,
-             "state_finite": m_finite}
+             "rel_err_torque_outer": abs(db.torque_outer / da.torque_outer - 1),
+             "max_div_fp64": da.max_div, "max_div_mixed": db.max_div,
+             "state_finite": m_finite and bool(db.finite)}
+    del fplan, eplan
     del mplan
 
     # end to end through the C ABI with host buffers: H2D state, step, D2H state
@@ -271,6 +396,14 @@ def run_ours(args):
         "wall_s_timed_region": wall,
         "state_finite": bool(finite),
     }
+    if not args.no_extras:
+        for key, fn in (("adjoint", lambda: adjoint_ratio(tc, torch, I, f"cuda:{local}")),
+                        ("large_same_size", lambda: large_mixed(tc, torch, I, f"cuda:{local}"))):
+            try:
+                out[key] = fn()
+            except Exception as exc:  # keep the main line even if an extra measurement fails
+                out[key] = {"error": repr(exc)[:300]}
+            torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -332,6 +465,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and large-size measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:
