@@ -25,6 +25,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 CFG2 = dict(N_r=64, M=32, K=64, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)
+# mid-size case for profiling (inputs larger than L2, a few GB on the device)
+CFG_MID = dict(N_r=128, M=128, K=256, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)
 # adjoint workload: N_r = 96, m = -32..32, k = -64..64, Re_i = 2000, 200 steps, checkpoint every 20
 CFG3 = dict(N_r=96, M=32, K=64, m_p=1, eta=0.5, Re_i=2000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)
 # mixed vs FP64 at the same size: quasi-Keplerian (Re_o = sqrt(eta) Re_i), 256 x 768 x 1536 grid
@@ -208,12 +210,55 @@ def large_mixed(tc, torch, I, dev, steps=4):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
+        plan.profile(True)
+        plan.step(st, 1)
+        torch.cuda.synchronize()
+        kern = {k: v[1] for k, v in plan.profile_read().items()}
+        plan.profile(False)
         res[name] = ms
-        out[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "gdof_steps_per_s": gdof(cfg) / ms / 1e6}
+        out[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "gdof_steps_per_s": gdof(cfg) / ms / 1e6,
+                     "kernels_ms": kern}
         del plan, st, u0
         torch.cuda.empty_cache()
     out["mixed_speedup_vs_fp64"] = res["fp64"] / res["mixed"]
     return out
+
+
+# largest single-GPU workload: N_r = 384, m = -384..384, k = -768..768, grid 384 x 1152 x 2304
+CFG5 = dict(N_r=384, M=384, K=768, m_p=1, eta=0.5, Re_i=3e4, Re_o=math.sqrt(0.5) * 3e4,
+            L_z=2 * math.pi / 3.16, dt=5e-5)
+
+
+def largest_mixed(tc, torch, I, dev, steps=3):
+    """Mixed form at the largest workload, forward only (no adjoint workspace)."""
+    cfg = CFG5
+    t0 = time.perf_counter()
+    plan = tc.Plan(**cfg, precision=tc.TC_MIXED, no_adjoint=True, device=dev)
+    t_plan = time.perf_counter() - t0
+    r = plan.nodes()
+    u0 = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"],
+                                          cfg["Re_o"], kind="broadband", amp=0.05, seed=42)).to(dev)
+    st = tc.State(plan, u0)
+    del u0
+    plan.step(st, 2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.step(st, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    plan.profile(True)
+    plan.step(st, 1)
+    torch.cuda.synchronize()
+    kern = {k: v[1] for k, v in plan.profile_read().items()}
+    plan.profile(False)
+    d = plan.diagnostics(st.u)
+    return {"workload": "quasi-Keplerian eta=0.5, Re_i=3e4, Re_o=sqrt(eta) Re_i, N_r=384, m=-384..384, "
+                        "k=-768..768, phys 384x1152x2304, dt=5e-5, broadband amp 0.05 (seed 42), mixed form",
+            "gdof": gdof(cfg), "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+            "gdof_steps_per_s": gdof(cfg) / ms / 1e6, "kernels_ms": kern, "plan_create_s": t_plan,
+            "device_memory_gb": torch.cuda.max_memory_allocated() / 1e9, "state_finite": bool(d.finite)}
 
 
 def run_ours(args):
@@ -229,8 +274,10 @@ def run_ours(args):
         B.build()
     if dist:
         dist.barrier()
-    cfg = CFG2
-    plan = tc.Plan(**cfg, device=f"cuda:{local}")
+    cfg = CFG_MID if args.size == "mid" else CFG2
+    main_is_bench = args.size == "bench" and args.workload == "fp64"
+    prec = tc.TC_MIXED if args.workload == "mixed" else tc.TC_FP64
+    plan = tc.Plan(**cfg, precision=prec, no_adjoint=True, device=f"cuda:{local}")
     r = plan.nodes()
     u0 = I.initial_state(r, cfg["M"], cfg["K"], cfg["m_p"], cfg["L_z"], cfg["eta"], cfg["Re_i"],
                          cfg["Re_o"], kind="taylor", amp=1e-2, seed=replica_seed(rank))
@@ -308,7 +355,7 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": ach / fp64_peak,
                 # dram__bytes_read.sum + dram__bytes_write.sum of k_theta<double2> per launch,
                 # from profiles/k_theta_fp64__Nr64_M32_K64.md (kernel unchanged since)
-                "traffic": (58.437376e6 + 3.228672e6) if top[0] == "k_theta" else None,
+                "traffic": (58.437376e6 + 3.228672e6) if (top[0] == "k_theta" and main_is_bench) else None,
                 "peak_source": "152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (unit counts and max clock)",
                 "algorithmic": "7.5 complex FFTs of P_theta at 5 n log2 n + 25 flop/point per (r, z)"}
     else:
@@ -378,10 +425,14 @@ def run_ours(args):
     e2e_value = world * E / (e0.elapsed_time(e1) / 1e3)
 
     out = {
-        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
+        "metric": METRIC if main_is_bench else METRIC.replace("FP64 plain", args.workload + " " + args.size),
+        "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N_r": cfg["N_r"], "M": cfg["M"], "K": cfg["K"],
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.workload == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if main_is_bench else
+                   f"{args.workload} step at N_r={cfg['N_r']}, M={cfg['M']}, K={cfg['K']} (profiling case)",
+                   "N_r": cfg["N_r"], "M": cfg["M"], "K": cfg["K"],
                    "P_theta": Pt, "P_z": Pz, "dt": cfg["dt"], "gdof": gdof(cfg),
                    "l2": "flushed before every timed step (256 MiB fill outside the per-step events)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
@@ -404,6 +455,12 @@ def run_ours(args):
             except Exception as exc:  # keep the main line even if an extra measurement fails
                 out[key] = {"error": repr(exc)[:300]}
             torch.cuda.empty_cache()
+    if args.largest:
+        try:
+            out["largest"] = largest_mixed(tc, torch, I, f"cuda:{local}")
+        except Exception as exc:
+            out["largest"] = {"error": repr(exc)[:300]}
+        torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -466,6 +523,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and large-size measurements")
+    ap.add_argument("--largest", action="store_true", help="also time the mixed form at N_r = 384, 384 x 1152 x 2304")
+    ap.add_argument("--workload", default="fp64", choices=["fp64", "mixed"],
+                    help="precision of the main timed step (the reported metric is the FP64 step)")
+    ap.add_argument("--size", default="bench", choices=["bench", "mid"],
+                    help="bench: N_r=64, M=32, K=64; mid: N_r=128, M=128, K=256 (for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:

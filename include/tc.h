@@ -69,6 +69,10 @@ typedef struct {
     int host_only;    /* 1: build the host plan only (no device memory); for inspection */
     int theta_zt;     /* launch tuning: z values per theta-pass block (0: automatic) */
     int pc_modes;     /* launch tuning: modes per block of the steps-2-5 kernel (0: automatic) */
+    int no_adjoint;   /* 1: size the workspace without the adjoint regions (tc_adjoint_* then
+                         return TC_ERR_STATE); a TC_MIXED plan also stages its transforms in FP32 */
+    int pc_split;     /* steps 2-5 as one fused kernel (-1) or as separate kernels (1);
+                         0: fused while N_r <= 192, separate beyond */
 } tc_options;
 
 /* Step state (Sec. 3.2): u = u^i, u_prev = u^{i-1}, N_prev = N^{i-1} (vector fields), p = p^i
@@ -97,7 +101,7 @@ typedef struct {
  * (Sec. 3.1; shortened centred stencils near the walls, one-sided fd_order/2 + 1 points on
  * the wall rows), twiddles, and the banded LU factors with partial pivoting of the Poisson
  * and three Helmholtz matrices of every mode (m, |k|) (Sec. 3.2, "precomputed at the
- * beginning").  Requires N_r >= fd_order + 1, M >= 1, K >= 1, m_p >= 1, 0 < eta < 1,
+ * beginning").  Requires fd_order + 1 <= N_r <= 2048, M >= 1, K >= 1, m_p >= 1, 0 < eta < 1,
  * L_z > 0, dt > 0, fd_order in {2, 4, 6, 8}.  *out receives the plan or NULL on error. */
 tc_status tc_plan_create(tc_plan** out, int N_r, int M, int K, int m_p, double eta,
                          double Re_i, double Re_o, double L_z, double dt, int fd_order);

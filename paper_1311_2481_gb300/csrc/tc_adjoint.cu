@@ -569,12 +569,11 @@ __global__ void __launch_bounds__(256) k_zfwd_adj(const double2* __restrict__ H3
 // ubar(c, j, mode) += (D1^T Rhat)(c, j, mode)
 __global__ void k_drT(double2* __restrict__ ub, const double2* __restrict__ Rh, const int* __restrict__ trow,
                       const double* __restrict__ tw, int ntab, Geo g) {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 3 * g.S) return;
-    const int c = (int)(e / g.S);
-    const size_t es = e - (size_t)c * g.S;
-    const int j = (int)(es / g.nmode);
-    const int mode = (int)(es - (size_t)j * g.nmode);
+    // grid: x = radial row (fastest: the gathered rows stay in cache), y over modes, z = component
+    const int mode = blockIdx.y * blockDim.x + threadIdx.x;
+    if (mode >= g.nmode) return;
+    const int j = blockIdx.x, c = blockIdx.z;
+    const size_t e = (size_t)c * g.S + (size_t)j * g.nmode + mode;
     double2 s = ub[e];
     for (int q = 0; q < ntab; ++q) {
         const double w = __ldg(&tw[j * ntab + q]);
@@ -651,7 +650,7 @@ tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* 
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_zfwd_adj");
     slot = prof_begin(p, kKDrT, s);
-    k_drT<<<ablocks(3 * g.S, 256), 256, 0, s>>>(ubar, Rh, p->d_d1t_row, p->d_d1t_w, p->d1t_n, g);
+    k_drT<<<dim3(g.N, ablocks(g.nmode, 128), 3), 128, 0, s>>>(ubar, Rh, p->d_d1t_row, p->d_d1t_w, p->d1t_n, g);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_drT");
     return TC_OK;
@@ -660,12 +659,10 @@ tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* 
 // gradient of J = 1/2 sum_j w_j r_j sum c_m (|u'_+|^2/2 + |u'_-|^2/2 + |u'_z|^2), u' = u - Couette
 __global__ void k_energy_grad(const double2* __restrict__ u, double2* __restrict__ gr,
                               const double* __restrict__ rn, double C1, double C2, Geo g) {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 3 * g.S) return;
-    const int c = (int)(e / g.S);
-    const size_t es = e - (size_t)c * g.S;
-    const int j = (int)(es / g.nmode);
-    const int mode = (int)(es - (size_t)j * g.nmode);
+    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode >= g.nmode) return;
+    const int j = blockIdx.y, c = blockIdx.z;
+    const size_t e = (size_t)c * g.S + (size_t)j * g.nmode + mode;
     const int m = mode / g.nk;
     const int k = mode - m * g.nk - g.K;
     const double r = rn[j];
@@ -683,7 +680,7 @@ tc_status launch_energy_gradient(tc_plan* p, const double2* u, double2* gr, cuda
     const double eta = p->eta;
     const double C1 = (p->Re_o - eta * p->Re_i) / (1.0 + eta);
     const double C2 = eta * (p->Re_i - eta * p->Re_o) / ((1.0 - eta) * (1.0 - eta * eta));
-    k_energy_grad<<<ablocks(3 * g.S, 256), 256, 0, s>>>(u, gr, p->d_r, C1, C2, g);
+    k_energy_grad<<<dim3(ablocks(g.nmode, 128), g.N, 3), 128, 0, s>>>(u, gr, p->d_r, C1, C2, g);
     TC_LAUNCHED(p, "k_energy_grad");
     return TC_OK;
 }
@@ -697,6 +694,10 @@ namespace {
 tc_status adj_ready(tc_plan* p, void* ws) {
     if (!p) return TC_ERR_ARG;
     if (p->host_only) return TC_ERR_STATE;
+    if (!p->adjoint) {
+        snprintf(p->err, sizeof(p->err), "plan created with no_adjoint: its workspace has no adjoint regions");
+        return TC_ERR_STATE;
+    }
     int dev = -1;
     TC_CUDA(p, cudaGetDevice(&dev));
     if (dev != p->device) return TC_ERR_STATE;

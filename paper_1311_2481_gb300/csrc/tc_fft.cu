@@ -33,8 +33,8 @@ __global__ void __launch_bounds__(256) k_zinv(const double2* __restrict__ u, V* 
     const int groups = 9 / L;
     const int g = blockIdx.x % groups;
     const int rm = blockIdx.x / groups;
-    const int m = rm % (M + 1);
-    const int r = rm / (M + 1);
+    const int r = rm % N_r;        // r fastest: blocks sharing stencil rows run together
+    const int m = rm / N_r;
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
     const size_t colstride = (size_t)(M + 1) * nk;
@@ -110,10 +110,11 @@ __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __re
     __syncthreads();
     // spectra of the 6 complex lines per z
     for (int idx = threadIdx.x; idx < 6 * zt * (M + 1); idx += blockDim.x) {
-        const int m = idx % (M + 1);
-        const int t = idx / (M + 1);
-        const int zi = t % zt;
-        const int pr = t / zt;
+        // z fastest: neighbouring threads read neighbouring z of one (field, m) line
+        const int zi = idx % zt;
+        const int t = idx / zt;
+        const int m = t % (M + 1);
+        const int pr = t / (M + 1);
         V* line = a + (size_t)(zi * 6 + pr) * Pt;
         const size_t o = (size_t)m * Pz + zi;
         const T mm = (T)(mp * m);
@@ -198,22 +199,23 @@ __global__ void __launch_bounds__(256) k_zfwd(const V* __restrict__ H2, double2*
                                               const V* __restrict__ tw, Radices rad,
                                               const double2* __restrict__ u, const double* __restrict__ rnodes,
                                               const double* __restrict__ w1, const int* __restrict__ col0,
-                                              double mp, int mean_add) {
+                                              double mp, int mean_add, int Lf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double s_mf[2];
     const int Pz = rad.n;
     V* a = reinterpret_cast<V*>(smem_raw);
-    V* b = a + (size_t)3 * Pz;
-    const int m = blockIdx.x % (M + 1);
-    const int r = blockIdx.x / (M + 1);
+    V* b = a + (size_t)Lf * Pz;
+    const int cg = blockIdx.x % (3 / Lf);     // component group (Lf = 3: all three)
+    const int m = (blockIdx.x / (3 / Lf)) % (M + 1);
+    const int r = (blockIdx.x / (3 / Lf)) / (M + 1);
     const size_t fstride = (size_t)N_r * (M + 1) * Pz;
     const V* h = H2 + ((size_t)r * (M + 1) + m) * Pz;
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
-    for (int idx = threadIdx.x; idx < 3 * Pz; idx += blockDim.x) {
-        const int c = idx / Pz;
-        const int z = idx - c * Pz;
-        a[idx] = h[c * fstride + z];
+    for (int idx = threadIdx.x; idx < Lf * Pz; idx += blockDim.x) {
+        const int l = idx / Pz;
+        const int z = idx - l * Pz;
+        a[idx] = h[(cg * Lf + l) * fstride + z];
     }
     if (mean_add && threadIdx.x == 0) {
         // U(r)/r and d_r U(r) from the (0,0) column, U = Im(u_+ - u_-)/2
@@ -229,17 +231,18 @@ __global__ void __launch_bounds__(256) k_zfwd(const V* __restrict__ H2, double2*
         s_mf[1] = dU;
     }
     __syncthreads();
-    V* res = smem_fft(a, b, 3, tw, false, rad);
+    V* res = smem_fft(a, b, Lf, tw, false, rad);
     double Ur = 0.0, q = 0.0;
     if (mean_add) {
         Ur = s_mf[0];
         q = 0.5 * (s_mf[1] + Ur);
     }
-    for (int idx = threadIdx.x; idx < 3 * nk; idx += blockDim.x) {
-        const int c = idx / nk;
-        const int kk = idx - c * nk;
+    for (int idx = threadIdx.x; idx < Lf * nk; idx += blockDim.x) {
+        const int l = idx / nk;
+        const int c = cg * Lf + l;
+        const int kk = idx - l * nk;
         const int k = kk - K;
-        const V v = res[(size_t)c * Pz + (k < 0 ? k + Pz : k)];
+        const V v = res[(size_t)l * Pz + (k < 0 ? k + Pz : k)];
         double2 o = make_double2((double)v.x * scale, (double)v.y * scale);
         if (mean_add) {
             const size_t e = ((size_t)r * (M + 1) + m) * nk + kk;
@@ -279,7 +282,8 @@ static tc_status run_nonlinear(tc_plan* p, const double2* u, double2* N, char* w
     const int zt = mixed ? p->zt32 : p->zt;
     size_t sm1 = (size_t)2 * L * p->P_z * sizeof(V);
     size_t sm2 = (size_t)2 * 6 * zt * p->P_t * sizeof(V);
-    size_t sm3 = (size_t)2 * 3 * p->P_z * sizeof(V);
+    const int Lf = mixed ? p->zfwd_lines32 : p->zfwd_lines;
+    size_t sm3 = (size_t)2 * Lf * p->P_z * sizeof(V);
     TC_CUDA(p, cudaFuncSetAttribute(k_zinv<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
     TC_CUDA(p, cudaFuncSetAttribute(k_theta<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     TC_CUDA(p, cudaFuncSetAttribute(k_zfwd<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
@@ -295,8 +299,8 @@ static tc_status run_nonlinear(tc_plan* p, const double2* u, double2* N, char* w
     TC_LAUNCHED(p, "k_theta");
     const double scale = 1.0 / ((double)p->P_t * (double)p->P_z);
     slot = prof_begin(p, sizeof(V) == 16 ? kKZfwd : kKZfwd32, s);
-    k_zfwd<V><<<p->N_r * (p->M + 1), mixed ? 256 : p->thr_zfwd, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, twz, p->rad_z,
-                                                     u, p->d_r, p->d_w1, p->d_col0, (double)p->m_p, mixed ? 1 : 0);
+    k_zfwd<V><<<p->N_r * (p->M + 1) * (3 / Lf), mixed ? 256 : p->thr_zfwd, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, twz, p->rad_z,
+                                                     u, p->d_r, p->d_w1, p->d_col0, (double)p->m_p, mixed ? 1 : 0, Lf);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_zfwd");
     return TC_OK;

@@ -15,6 +15,7 @@ constexpr int kMaxRadix = 16;   // passes of a mixed-radix 2^a 3^b transform
 constexpr int kStencil = 9;     // padded FD stencil width (fd_order <= 8)
 constexpr int kBands = 13;      // stored doubles per LU row: 4 L multipliers, 1/U_jj, 8 U
 constexpr int kKl = 4;          // sub/super diagonals of the mode matrices (fd_order/2 <= 4)
+constexpr int kPCThreads = 128;         // block size of the fused steps-2-5 kernel
 
 // Factor sets of Sec. 3.2: Poisson (p*, phi), Helmholtz for u_+, u_-, u_z.
 enum FactorSet { kSetP = 0, kSetHp = 1, kSetHm = 2, kSetHz = 3, kNumSets = 4 };
@@ -30,11 +31,12 @@ struct Workspace {
     size_t H1;      // inverse z-pass output: 9 fields x N_r x (M+1) x P_z complex
     size_t H2;      // theta-pass output: 3 fields x N_r x (M+1) x P_z complex
     size_t Ncur;    // N^i: vector field
-    size_t pstar;   // p*: scalar field
-    size_t ustar;   // u*: vector field
-    size_t phi;     // phi: scalar field
     size_t uE;      // start-up Euler result: vector field
+    size_t pstar;   // split path only: p* (scalar), u* (vector), phi (scalar)
+    size_t ustar;
+    size_t phi;
     size_t red;     // diagnostics reduction buffer
+    // adjoint regions (absent with tc_options.no_adjoint)
     size_t H3;      // adjoint theta-pass output: 9 fields x N_r x (M+1) x P_z complex
     size_t Nbar;    // adjoint of N: vector field
     size_t Rhat;    // adjoint d_r lines before the transposed stencil: vector field
@@ -49,6 +51,7 @@ struct tc_plan {
     int N_r, M, K, m_p, fd_order, half, P_t, P_z, precision;
     double eta, Re_i, Re_o, L_z, dt, alpha, k_z, r_i, r_o;
     bool host_only;
+    bool adjoint;    // workspace holds the adjoint regions
     // derived sizes
     size_t S;        // complex entries of a scalar spectral field
     size_t Hfield;   // complex entries of one z-pass line set: N_r (M+1) P_z
@@ -58,7 +61,9 @@ struct tc_plan {
     int zt, zt32;                  // z values per theta-pass block (FP64 / FP32 lines)
     int pc_modes;                  // modes per block of the fused steps-2-5 kernel (0: auto)
     int thr_zinv, thr_theta, thr_zfwd;  // block sizes of the FP64 transform kernels
+    bool pc_split;                      // steps 2-5 as separate kernels (large N_r)
     int zinv_lines, zinv_lines32;  // lines per inverse z-pass block (FP64 / FP32 lines)
+    int zfwd_lines, zfwd_lines32;  // lines per forward z-pass block (3 or 1)
     tc::Workspace ws;
     // host plan
     std::vector<double> r, w1, w2;   // nodes; weights [N_r][9]
@@ -71,6 +76,7 @@ struct tc_plan {
     std::vector<double> tw_z, tw_t;  // interleaved complex exp(+2 pi i j / n)
     // device plan
     double* d_r = nullptr;
+    double* d_ir = nullptr;          // 1 / r_j
     double* d_w1 = nullptr;
     double* d_w2 = nullptr;
     int* d_col0 = nullptr;

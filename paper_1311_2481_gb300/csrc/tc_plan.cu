@@ -229,6 +229,9 @@ static tc_status upload(tc_plan* p) {
         return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
     };
     TC_CUDA(p, put((void**)&p->d_r, p->r.data(), p->r.size() * sizeof(double)));
+    std::vector<double> ir(p->r.size());
+    for (size_t j = 0; j < ir.size(); ++j) ir[j] = 1.0 / p->r[j];
+    TC_CUDA(p, put((void**)&p->d_ir, ir.data(), ir.size() * sizeof(double)));
     TC_CUDA(p, put((void**)&p->d_w1, p->w1.data(), p->w1.size() * sizeof(double)));
     TC_CUDA(p, put((void**)&p->d_w2, p->w2.data(), p->w2.size() * sizeof(double)));
     TC_CUDA(p, put((void**)&p->d_col0, p->col0.data(), p->col0.size() * sizeof(int)));
@@ -276,7 +279,7 @@ void prof_end(tc_plan* p, int slot, cudaStream_t s) {
 static void free_device(tc_plan* p) {
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     p->prof_ev.clear();
-    void* ptrs[] = {p->d_r, p->d_w1, p->d_w2, p->d_col0, p->d_d1t_row, p->d_d1t_w, p->d_fac, p->d_piv,
+    void* ptrs[] = {p->d_r, p->d_ir, p->d_w1, p->d_w2, p->d_col0, p->d_d1t_row, p->d_d1t_w, p->d_fac, p->d_piv,
                     p->d_tw_z, p->d_tw_t, p->d_tw_z32, p->d_tw_t32};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -312,7 +315,7 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
     if (fd_order < 2 || fd_order > 8 || fd_order % 2) return TC_ERR_ARG;
-    if (N_r < fd_order + 1 || N_r > 4096 || M < 1 || K < 1 || m_p < 1) return TC_ERR_ARG;
+    if (N_r < fd_order + 1 || N_r > 2048 || M < 1 || K < 1 || m_p < 1) return TC_ERR_ARG;
     if (!(eta > 0.0 && eta < 1.0) || !(L_z > 0.0) || !(dt > 0.0)) return TC_ERR_ARG;
     if (!std::isfinite(Re_i) || !std::isfinite(Re_o) || !std::isfinite(L_z) || !std::isfinite(dt))
         return TC_ERR_ARG;
@@ -401,44 +404,63 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     }
     // launch geometry and workspace
     const size_t cplx = sizeof(double2);
-    auto lines_for = [&](size_t esz) {
-        int L = 9;
-        while (L > 1 && (size_t)2 * L * Pz * esz > 200 * 1024) L = L == 9 ? 3 : 1;
+    // lines per z-pass block: several blocks per SM (<= 76 KB of shared memory each)
+    auto lines_for = [&](size_t esz, int Lmax) {
+        int L = Lmax;
+        while (L > 1 && (size_t)2 * L * Pz * esz > 76 * 1024) L = L == 9 ? 3 : 1;
         return L;
     };
-    auto zt_for = [&](size_t esz, int zmax) {
+    // z values per theta block: at most `cap` bytes of shared memory, so that several blocks
+    // share an SM (the FP32 lines are latency-bound; three 76 KB blocks fit an SM)
+    auto zt_for = [&](size_t esz, int zmax, size_t cap) {
         int zt = zmax;
-        while (zt > 1 && (size_t)2 * 6 * zt * Pt * esz > 200 * 1024) zt /= 2;
+        while (zt > 1 && (size_t)2 * 6 * zt * Pt * esz > cap) zt /= 2;
         while (zt > 1 && Pz % zt) zt /= 2;
         return zt;
     };
-    p->zinv_lines = lines_for(sizeof(double2));
-    p->zinv_lines32 = lines_for(sizeof(float2));
-    p->zt = zt_for(sizeof(double2), o.theta_zt > 0 ? o.theta_zt : 4);
-    p->zt32 = zt_for(sizeof(float2), o.theta_zt > 0 ? o.theta_zt : 8);
+    p->zinv_lines = lines_for(sizeof(double2), 9);
+    p->zinv_lines32 = lines_for(sizeof(float2), 9);
+    p->zfwd_lines = lines_for(sizeof(double2), 3);
+    p->zfwd_lines32 = lines_for(sizeof(float2), 3);
+    p->zt = zt_for(sizeof(double2), o.theta_zt > 0 ? o.theta_zt : 4, 200 * 1024);
+    p->zt32 = zt_for(sizeof(float2), o.theta_zt > 0 ? o.theta_zt : 8, o.theta_zt > 0 ? 200 * 1024 : 76 * 1024);
     p->pc_modes = o.pc_modes;
     p->thr_zinv = choose_threads(rz, p->zinv_lines, 0);
     p->thr_theta = choose_threads(rt, 6 * p->zt, p->zt + (p->zt + 1) / 2);
-    p->thr_zfwd = choose_threads(rz, 3, 0);
-    if (o.theta_zt < 0 || o.theta_zt > 64 || o.pc_modes < 0 || o.pc_modes > 32) { delete p; return TC_ERR_ARG; }
+    p->thr_zfwd = choose_threads(rz, p->zfwd_lines, 0);
+    if (o.theta_zt < 0 || o.theta_zt > 64 || o.pc_modes < 0 || o.pc_modes > 32 || o.pc_split < -1 || o.pc_split > 1) {
+        delete p;
+        return TC_ERR_ARG;
+    }
     if ((size_t)2 * 3 * Pz * cplx > 220 * 1024 || (size_t)2 * 6 * Pt * cplx > 220 * 1024) {
         delete p;
         return TC_ERR_ARG;   // transform lines too long for one block's shared memory
     }
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o2 = off; off = align256(off + bytes); return o2; };
-    p->ws.H1 = take(9 * p->Hfield * cplx);
-    p->ws.H2 = take(3 * p->Hfield * cplx);
+    // transform staging in the plan's line precision; the FP64 adjoint also stages its
+    // recomputed forward lines in H1, so a plan with the adjoint keeps FP64-sized lines
+    p->adjoint = o.no_adjoint == 0;
+    const size_t lane = (p->precision == TC_MIXED && !p->adjoint) ? sizeof(float2) : cplx;
+    p->ws.H1 = take(9 * p->Hfield * lane);
+    p->ws.H2 = take(3 * p->Hfield * lane);
     p->ws.Ncur = take(3 * p->S * cplx);
-    p->ws.pstar = take(p->S * cplx);
-    p->ws.ustar = take(3 * p->S * cplx);
-    p->ws.phi = take(p->S * cplx);
     p->ws.uE = take(3 * p->S * cplx);
+    // steps 2-5: fused kernel while 8 modes' four columns fit in 96 KB of shared memory,
+    // split kernels beyond (tc_options.pc_split forces either)
+    p->pc_split = o.pc_split == 1 || (o.pc_split == 0 && (size_t)4 * N_r * 8 * cplx > 96 * 1024);
+    if (p->pc_split) {
+        p->ws.pstar = take(p->S * cplx);
+        p->ws.ustar = take(3 * p->S * cplx);
+        p->ws.phi = take(p->S * cplx);
+    }
     p->ws.red = take(4096 * sizeof(double));
-    p->ws.H3 = take(9 * p->Hfield * cplx);
-    p->ws.Nbar = take(3 * p->S * cplx);
-    p->ws.Rhat = take(3 * p->S * cplx);
-    p->ws.abar = take(9 * p->S * cplx);
+    if (p->adjoint) {
+        p->ws.H3 = take(9 * p->Hfield * cplx);
+        p->ws.Nbar = take(3 * p->S * cplx);
+        p->ws.Rhat = take(3 * p->S * cplx);
+        p->ws.abar = take(9 * p->S * cplx);
+    }
     p->ws.total = off;
     if (!p->host_only) {
         tc_status st = upload(p);
@@ -447,6 +469,9 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
             delete p;
             return st;
         }
+        // the device holds the factors now; release the host copy (tens of GB at N_r = 384)
+        std::vector<double>().swap(p->fac);
+        std::vector<uint8_t>().swap(p->piv);
     }
     *out = p;
     return TC_OK;

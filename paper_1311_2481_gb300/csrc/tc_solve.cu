@@ -3,6 +3,8 @@
 // O(N_r) per system), and the update.  One thread per (m, k) system; threads of a warp own
 // consecutive k, so every access to a field [r][m][k] or to the factors [j][band][m][|k|]
 // is coalesced.
+#include <algorithm>
+
 #include "tc_internal.cuh"
 #include "tc_solve_core.cuh"
 
@@ -18,6 +20,7 @@ struct PCArgs {
     double2* Np_out;    // commit: N_prev <- N^i
     double2* p;         // commit: p <- p^{i+1}
     const double* rn;
+    const double* ir;   // 1 / r_j
     const double* w1;
     const double* w2;
     const int* col0;
@@ -30,7 +33,7 @@ struct PCArgs {
 // Steps 2-5 of Sec. 3.2 for the T modes of this block: pressure prediction (Eq. pressure
 // with the Neumann rows of Eq. ppBC), velocity prediction (Eq. vel), correction potential
 // (Eq. correction) and update (Eq. update).
-__global__ void __launch_bounds__(256) k_pc(PCArgs a, Geo g, int T) {
+__global__ void __launch_bounds__(kPCThreads) k_pc(PCArgs a, Geo g, int T) {
     extern __shared__ double2 sm[];
     const int N = g.N;
     const int items = N * T;
@@ -65,7 +68,7 @@ __global__ void __launch_bounds__(256) k_pc(PCArgs a, Geo g, int T) {
             const int m = mode / g.nk;
             const int k = mode - m * g.nk - g.K;
             const double mm = g.mp * m, kk = g.kz * k;
-            const double r = a.rn[j], ir = 1.0 / r;
+            const double r = a.rn[j], ir = a.ir[j];
             const size_t e = (size_t)j * g.nmode + mode;
             if (j == 0 || j == N - 1) {
                 if (!(j == N - 1 && m == 0 && k == 0)) {
@@ -90,7 +93,10 @@ __global__ void __launch_bounds__(256) k_pc(PCArgs a, Geo g, int T) {
         C0[idx] = out;
     }
     __syncthreads();
-    // B: p* = P^{-1} b_p (real and imaginary parts by separate threads)
+    // B: p* = P^{-1} b_p (real and imaginary parts by separate threads).  Meanwhile the
+    // warps without a substitution precompute the part of the velocity right-hand sides that
+    // does not depend on p*: (4u - u_prev)/(2dt) - (2N - N_prev), and the Dirichlet rows.
+    const int helper0 = ((2 * nT + 31) / 32) * 32;
     if (threadIdx.x < 2 * nT) {
         const int t = threadIdx.x >> 1, part = threadIdx.x & 1;
         const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
@@ -98,48 +104,63 @@ __global__ void __launch_bounds__(256) k_pc(PCArgs a, Geo g, int T) {
         smem_band_solve(C0, T, t, part, N, a.fac + (size_t)kSetP * per_set + mk,
                         a.piv + (size_t)kSetP * N * g.M1K1 + mk, g.M1K1);
     }
-    __syncthreads();
-    // C: velocity right-hand sides into C1..C3; p <- p* (commit)
-    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
-        const int j = idx / T, t = idx - (idx / T) * T;
-        double2 o0 = make_double2(0.0, 0.0), o1 = o0, o2 = o0;
-        if (t < nT) {
-            const int mode = mode0 + t;
-            const int m = mode / g.nk;
-            const int k = mode - m * g.nk - g.K;
-            const size_t e = (size_t)j * g.nmode + mode;
-            const double2 pv = C0[idx];
-            if (a.commit) a.p[e] = pv;
-            if (j == 0 || j == N - 1) {
-                if (m == 0 && k == 0) {
-                    const double Re = j == 0 ? a.Re_i : a.Re_o;
-                    o0.y = Re;
-                    o1.y = -Re;
-                }
-            } else {
-                const double2 d = sdrow(C0, a.w1, a.col0, j, T, t);
-                const double tt = g.mp * m / a.rn[j];
-                const double kk = g.kz * k;
-                const double2 gp0 = make_double2(d.x - tt * pv.x, d.y - tt * pv.y);
-                const double2 gp1 = make_double2(d.x + tt * pv.x, d.y + tt * pv.y);
-                const double2 gp2 = make_double2(-kk * pv.y, kk * pv.x);
-                const double2* gps[3] = {&gp0, &gp1, &gp2};
-                double2* outs[3] = {&o0, &o1, &o2};
+    // (with no spare warp the whole block does this after the substitution)
+    const bool spare0 = helper0 < (int)blockDim.x;
+    if (!spare0) __syncthreads();
+    if (spare0 ? threadIdx.x >= helper0 : true) {
+        const int first = spare0 ? helper0 : 0;
+        for (int idx = threadIdx.x - first; idx < items; idx += blockDim.x - first) {
+            const int j = idx / T, t = idx - (idx / T) * T;
+            double2 o[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+            if (t < nT) {
+                const int mode = mode0 + t;
+                const int m = mode / g.nk;
+                const int k = mode - m * g.nk - g.K;
+                if (j == 0 || j == N - 1) {
+                    if (m == 0 && k == 0) {
+                        const double Re = j == 0 ? a.Re_i : a.Re_o;
+                        o[0].y = Re;
+                        o[1].y = -Re;
+                    }
+                } else {
+                    const size_t e = (size_t)j * g.nmode + mode;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const size_t ec = (size_t)c * g.S + e;
-                    const double2 uu = a.u[ec], q = a.up[ec], n1 = a.Nc[ec], n0 = a.Np[ec];
-                    outs[c]->x = (4.0 * uu.x - q.x) * c1 - (2.0 * n1.x - n0.x) - gps[c]->x;
-                    outs[c]->y = (4.0 * uu.y - q.y) * c1 - (2.0 * n1.y - n0.y) - gps[c]->y;
+                    for (int c = 0; c < 3; ++c) {
+                        const size_t ec = (size_t)c * g.S + e;
+                        const double2 uu = a.u[ec], q = a.up[ec], n1 = a.Nc[ec], n0 = a.Np[ec];
+                        o[c].x = (4.0 * uu.x - q.x) * c1 - (2.0 * n1.x - n0.x);
+                        o[c].y = (4.0 * uu.y - q.y) * c1 - (2.0 * n1.y - n0.y);
+                    }
                 }
             }
+            C1[idx] = o[0];
+            C2[idx] = o[1];
+            C3[idx] = o[2];
         }
-        C1[idx] = o0;
-        C2[idx] = o1;
-        C3[idx] = o2;
     }
     __syncthreads();
-    // D: the three Helmholtz solves
+    // C: velocity right-hand sides: subtract grad_h p* on interior rows; p <- p* (commit)
+    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int j = idx / T, t = idx - (idx / T) * T;
+        if (t >= nT) continue;
+        const int mode = mode0 + t;
+        const int m = mode / g.nk;
+        const int k = mode - m * g.nk - g.K;
+        const double2 pv = C0[idx];
+        if (a.commit) a.p[(size_t)j * g.nmode + mode] = pv;
+        if (j == 0 || j == N - 1) continue;
+        const double2 d = sdrow(C0, a.w1, a.col0, j, T, t);
+        const double tt = g.mp * m * a.ir[j];
+        const double kk = g.kz * k;
+        double2 v;
+        v = C1[idx]; v.x -= d.x - tt * pv.x; v.y -= d.y - tt * pv.y; C1[idx] = v;
+        v = C2[idx]; v.x -= d.x + tt * pv.x; v.y -= d.y + tt * pv.y; C2[idx] = v;
+        v = C3[idx]; v.x += kk * pv.y; v.y -= kk * pv.x; C3[idx] = v;
+    }
+    __syncthreads();
+    // D: the three Helmholtz solves.  Meanwhile the other warps rotate the history (nothing
+    // reads u_prev or N_prev after C): u_prev <- u^i, N_prev <- N^i (commit).
+    const int helper1 = ((6 * nT + 31) / 32) * 32;
     if (threadIdx.x < 6 * nT) {
         const int c = threadIdx.x / (2 * nT), rem = threadIdx.x - c * 2 * nT;
         const int t = rem >> 1, part = rem & 1;
@@ -148,8 +169,27 @@ __global__ void __launch_bounds__(256) k_pc(PCArgs a, Geo g, int T) {
         const int set = kSetHp + c;
         smem_band_solve(C1 + (size_t)c * items, T, t, part, N, a.fac + (size_t)set * per_set + mk,
                         a.piv + (size_t)set * N * g.M1K1 + mk, g.M1K1);
+    } else if (a.commit && threadIdx.x >= helper1) {
+        for (int idx = threadIdx.x - helper1; idx < 3 * items; idx += blockDim.x - helper1) {
+            const int c = idx / items, rem = idx - c * items;
+            const int j = rem / T, t = rem - (rem / T) * T;
+            if (t >= nT) continue;
+            const size_t ec = (size_t)c * g.S + (size_t)j * g.nmode + mode0 + t;
+            a.up_out[ec] = a.u[ec];
+            a.Np_out[ec] = a.Nc[ec];
+        }
     }
     __syncthreads();
+    if (a.commit && helper1 >= (int)blockDim.x) {   // no spare warp: rotate here
+        for (int idx = threadIdx.x; idx < 3 * items; idx += blockDim.x) {
+            const int c = idx / items, rem = idx - c * items;
+            const int j = rem / T, t = rem - (rem / T) * T;
+            if (t >= nT) continue;
+            const size_t ec = (size_t)c * g.S + (size_t)j * g.nmode + mode0 + t;
+            a.up_out[ec] = a.u[ec];
+            a.Np_out[ec] = a.Nc[ec];
+        }
+    }
     // E: div_h u* into C0 (homogeneous Neumann / Dirichlet rows)
     for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
         const int j = idx / T, t = idx - (idx / T) * T;
@@ -158,7 +198,7 @@ __global__ void __launch_bounds__(256) k_pc(PCArgs a, Geo g, int T) {
             const int mode = mode0 + t;
             const int m = mode / g.nk;
             const int k = mode - m * g.nk - g.K;
-            const double mm = g.mp * m, kk = g.kz * k, ir = 1.0 / a.rn[j];
+            const double mm = g.mp * m, kk = g.kz * k, ir = a.ir[j];
             const double2 dp = sdrow(C1, a.w1, a.col0, j, T, t), dm = sdrow(C2, a.w1, a.col0, j, T, t);
             const double2 vp = C1[idx], vm = C2[idx], vz = C3[idx];
             out.x = 0.5 * (dp.x + dm.x) + 0.5 * (vp.x + vm.x) * ir + 0.5 * mm * ir * (vp.x - vm.x) - kk * vz.y;
@@ -186,7 +226,7 @@ __global__ void __launch_bounds__(256) k_pc(PCArgs a, Geo g, int T) {
         const size_t e = (size_t)j * g.nmode + mode;
         const double2 f = C0[idx];
         const double2 d = sdrow(C0, a.w1, a.col0, j, T, t);
-        const double tt = g.mp * m / a.rn[j];
+        const double tt = g.mp * m * a.ir[j];
         const double kk = g.kz * k;
         const double2 gph[3] = {make_double2(d.x - tt * f.x, d.y - tt * f.y),
                                 make_double2(d.x + tt * f.x, d.y + tt * f.y),
@@ -195,19 +235,194 @@ __global__ void __launch_bounds__(256) k_pc(PCArgs a, Geo g, int T) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t ec = (size_t)c * g.S + e;
-            const double2 un = make_double2(us[c].x - gph[c].x, us[c].y - gph[c].y);
-            if (a.commit) {
-                a.up_out[ec] = a.u[ec];
-                a.Np_out[ec] = a.Nc[ec];
-            }
-            a.u_out[ec] = un;
+            a.u_out[ec] = make_double2(us[c].x - gph[c].x, us[c].y - gph[c].y);
         }
         if (a.commit) {
-            const double q = 3.0 / (2.0 * g.dt);
+            const double q = 3.0 * c1;   // 3 / (2 dt)
             const double2 ps = a.p[e];
             a.p[e] = make_double2(ps.x + q * f.x, ps.y + q * f.y);
         }
     }
+}
+
+// ---------------------------------------------------------------- split path (large N_r)
+// With few modes per block in shared memory the fused kernel leaves most lanes idle during
+// the substitutions; at large N_r there are enough modes to run each stage as its own
+// kernel instead: elementwise right-hand sides and update, and one thread per (system,
+// mode, real/imaginary part) walking its column in global memory.
+
+// X = (2N - N_prev)_r = ((2N - N_prev)_+ + (2N - N_prev)_-) / 2, once per element (the
+// pressure right-hand side applies the radial stencil to it).
+__global__ void k_nn_r(const double2* __restrict__ Nc, const double2* __restrict__ Np, double2* __restrict__ X, Geo g) {
+    const int mode = blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
+    if (mode >= g.nmode) return;
+    const size_t e = (size_t)blockIdx.x * g.nmode + mode;
+    const double2 n1 = Nc[e], n0 = Np[e], m1 = Nc[g.S + e], m0 = Np[g.S + e];
+    X[e] = make_double2(0.5 * ((2.0 * n1.x - n0.x) + (2.0 * m1.x - m0.x)),
+                        0.5 * ((2.0 * n1.y - n0.y) + (2.0 * m1.y - m0.y)));
+}
+
+// Step 2 right-hand side: interior rows div_h(-(2N - N_prev)); wall rows the consistent
+// Neumann value of Eq. ppBC; (0,0) at r_o the Dirichlet value 0.
+__global__ void k_rhs_pressure(const double2* __restrict__ u, const double2* __restrict__ up,
+                               const double2* __restrict__ Nc, const double2* __restrict__ Np,
+                               const double2* __restrict__ X, double2* __restrict__ b,
+                               const double* __restrict__ rn, const double* __restrict__ irn,
+                               const double* __restrict__ w1, const double* __restrict__ w2,
+                               const int* __restrict__ col0, Geo g) {
+    // grid: x = radial row (fastest, so neighbouring rows of a mode range run together and
+    // the stencil's rows stay in cache), y over modes
+    const int mode = blockIdx.y * blockDim.x + threadIdx.x;
+    if (mode >= g.nmode) return;
+    const int j = blockIdx.x;
+    const size_t e = (size_t)j * g.nmode + mode;
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    const double mm = g.mp * m, kk = g.kz * k;
+    const double r = rn[j], ir = irn[j];
+    double2 out = make_double2(0.0, 0.0);
+    if (j == 0 || j == g.N - 1) {
+        if (!(j == g.N - 1 && m == 0 && k == 0)) {
+            const double2 x = X[e];
+            const double2 l0 = lap_r(u, w1, w2, col0, r, j, mode, mm, kk, g);
+            const double2 l1 = lap_r(up, w1, w2, col0, r, j, mode, mm, kk, g);
+            out.x = -x.x + 2.0 * l0.x - l1.x;
+            out.y = -x.y + 2.0 * l0.y - l1.y;
+        }
+    } else {
+        const double2 d = drow(X, w1, col0, j, g.nmode, mode);
+        const double2 x = X[e];
+        const double2 n1 = Nc[e], n0 = Np[e], m1 = Nc[g.S + e], m0 = Np[g.S + e];
+        const double2 z1 = Nc[2 * g.S + e], z0 = Np[2 * g.S + e];
+        const double dpx = (2.0 * n1.x - n0.x) - (2.0 * m1.x - m0.x);
+        const double dpy = (2.0 * n1.y - n0.y) - (2.0 * m1.y - m0.y);
+        const double nzx = 2.0 * z1.x - z0.x, nzy = 2.0 * z1.y - z0.y;
+        out.x = -(d.x + x.x * ir + 0.5 * mm * ir * dpx - kk * nzy);
+        out.y = -(d.y + x.y * ir + 0.5 * mm * ir * dpy + kk * nzx);
+    }
+    b[e] = out;
+}
+
+// Step 3 right-hand sides, all three components per (row, mode) so that the radial
+// stencil of p* is applied once: (4u - u_prev)/(2dt) - (2N - N_prev) - grad_h p*;
+// Dirichlet rows.  commit: p <- p* (p^{i+1} is completed in the update).
+__global__ void k_rhs_velocity(const double2* __restrict__ u, const double2* __restrict__ up,
+                               const double2* __restrict__ Nc, const double2* __restrict__ Np,
+                               const double2* __restrict__ ps, double2* __restrict__ rhs,
+                               double2* __restrict__ p_out, const double* __restrict__ irn,
+                               const double* __restrict__ w1, const int* __restrict__ col0,
+                               double Re_i, double Re_o, Geo g) {
+    const int mode = blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
+    if (mode >= g.nmode) return;
+    const int j = blockIdx.x;
+    const size_t e = (size_t)j * g.nmode + mode;
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    const double2 pv = ps[e];
+    if (p_out) p_out[e] = pv;
+    if (j == 0 || j == g.N - 1) {
+        const double Re = (m == 0 && k == 0) ? (j == 0 ? Re_i : Re_o) : 0.0;
+        rhs[e] = make_double2(0.0, Re);
+        rhs[g.S + e] = make_double2(0.0, -Re);
+        rhs[2 * g.S + e] = make_double2(0.0, 0.0);
+        return;
+    }
+    const double2 d = drow(ps, w1, col0, j, g.nmode, mode);
+    const double tt = g.mp * m * irn[j], kk = g.kz * k;
+    const double2 gp[3] = {make_double2(d.x - tt * pv.x, d.y - tt * pv.y),
+                           make_double2(d.x + tt * pv.x, d.y + tt * pv.y),
+                           make_double2(-kk * pv.y, kk * pv.x)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const size_t ec = (size_t)c * g.S + e;
+        const double2 a = u[ec], q = up[ec], n1 = Nc[ec], n0 = Np[ec];
+        rhs[ec] = make_double2((4.0 * a.x - q.x) * g.c1 - (2.0 * n1.x - n0.x) - gp[c].x,
+                               (4.0 * a.y - q.y) * g.c1 - (2.0 * n1.y - n0.y) - gp[c].y);
+    }
+}
+
+// Step 4 right-hand side: div_h u* on interior rows, homogeneous Neumann / Dirichlet rows.
+__global__ void k_rhs_div(const double2* __restrict__ us, double2* __restrict__ b,
+                          const double* __restrict__ irn, const double* __restrict__ w1,
+                          const int* __restrict__ col0, Geo g) {
+    const int mode = blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
+    if (mode >= g.nmode) return;
+    const int j = blockIdx.x;
+    const size_t e = (size_t)j * g.nmode + mode;
+    if (j == 0 || j == g.N - 1) { b[e] = make_double2(0.0, 0.0); return; }
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    const double mm = g.mp * m, kk = g.kz * k, ir = irn[j];
+    const int c0 = col0[j];
+    double2 d = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int t = 0; t < kStencil; ++t) {
+        const double wt = __ldg(&w1[j * kStencil + t]);
+        const size_t o = (size_t)(c0 + t) * g.nmode + mode;
+        const double2 a = us[o], q = us[g.S + o];
+        d.x += wt * (a.x + q.x);
+        d.y += wt * (a.y + q.y);
+    }
+    const double2 vp = us[e], vm = us[g.S + e], vz = us[2 * g.S + e];
+    b[e] = make_double2(0.5 * d.x + 0.5 * (vp.x + vm.x) * ir + 0.5 * mm * ir * (vp.x - vm.x) - kk * vz.y,
+                        0.5 * d.y + 0.5 * (vp.y + vm.y) * ir + 0.5 * mm * ir * (vp.y - vm.y) + kk * vz.x);
+}
+
+// Step 5, all components per (row, mode): u^{i+1} = u* - grad_h phi; p^{i+1} = p* + 3 phi/(2dt).
+// commit: rotate the history in place (u_prev <- u^i, u <- u^{i+1}, N_prev <- N^i, p += 3 phi/(2dt));
+// otherwise write u^{i+1} to u_out only.
+__global__ void k_update(double2* u, double2* up, const double2* Nc, double2* Np, double2* p,
+                         const double2* __restrict__ us, const double2* __restrict__ phi,
+                         double2* __restrict__ u_out, const double* __restrict__ irn,
+                         const double* __restrict__ w1, const int* __restrict__ col0, int commit, Geo g) {
+    const int mode = blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
+    if (mode >= g.nmode) return;
+    const int j = blockIdx.x;
+    const size_t e = (size_t)j * g.nmode + mode;
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    const double2 f = phi[e];
+    const double2 d = drow(phi, w1, col0, j, g.nmode, mode);
+    const double tt = g.mp * m * irn[j], kk = g.kz * k;
+    const double2 gph[3] = {make_double2(d.x - tt * f.x, d.y - tt * f.y),
+                            make_double2(d.x + tt * f.x, d.y + tt * f.y),
+                            make_double2(-kk * f.y, kk * f.x)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const size_t ec = (size_t)c * g.S + e;
+        const double2 s = us[ec];
+        const double2 un = make_double2(s.x - gph[c].x, s.y - gph[c].y);
+        if (commit) {
+            up[ec] = u[ec];
+            u[ec] = un;
+            Np[ec] = Nc[ec];
+        } else {
+            u_out[ec] = un;
+        }
+    }
+    if (commit) {
+        const double q = 3.0 * g.c1;
+        const double2 a = p[e];
+        p[e] = make_double2(a.x + q * f.x, a.y + q * f.y);
+    }
+}
+
+// x <- A^{-1} x for every mode of nfields consecutive fields (system sets set0, set0+1, ...):
+// thread (field, mode, part) runs the register-window substitution down its global column.
+__global__ void k_band_solve_g(double2* __restrict__ x, const double* __restrict__ fac,
+                               const uint8_t* __restrict__ piv, int set0, int nfields, Geo g) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;   // (mode, part); y = field
+    if (t >= 2 * g.nmode) return;
+    const int part = t & 1;
+    const int mode = t >> 1;
+    const int fld = blockIdx.y;
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+    const size_t per_set = (size_t)g.N * kBands * g.M1K1;
+    const int set = set0 + fld;
+    smem_band_solve(x + (size_t)fld * g.S, g.nmode, mode, part, g.N, fac + (size_t)set * per_set + mk,
+                    piv + (size_t)set * g.N * g.M1K1 + mk, g.M1K1);
 }
 
 // Stand-alone solve of one system set for all modes (tc_helmholtz_solve): columns staged in
@@ -252,12 +467,12 @@ __global__ void k_diag(const double2* __restrict__ u, double* __restrict__ red,
     __shared__ double s_e[256];
     __shared__ unsigned long long s_d[256];
     __shared__ int s_n[256];
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int mode = blockIdx.x * blockDim.x + threadIdx.x;   // y = radial row
+    const int j = blockIdx.y;
+    const size_t e = (size_t)j * g.nmode + mode;
     double en = 0.0, dv = 0.0;
     int bad = 0;
-    if (e < g.S) {
-        const int j = (int)(e / g.nmode);
-        const int mode = (int)(e - (size_t)j * g.nmode);
+    if (mode < g.nmode) {
         const int m = mode / g.nk;
         const int k = mode - m * g.nk - g.K;
         const double r = rn[j];
@@ -315,7 +530,7 @@ static int blocks_for(size_t n, int bs) { return (int)((n + bs - 1) / bs); }
 
 // modes per block of the fused kernel: four complex columns of N_r rows in shared memory
 static int pc_modes(const tc_plan* p) {
-    int T = p->pc_modes > 0 ? p->pc_modes : 8;
+    int T = p->pc_modes > 0 ? std::min(p->pc_modes, 16) : 8;
     while (T > 1 && (size_t)4 * p->N_r * T * sizeof(double2) > 96 * 1024) T /= 2;
     return T;
 }
@@ -335,10 +550,53 @@ tc_status launch_solve(tc_plan* p, int set, double2* x, int nfields, cudaStream_
     return TC_OK;
 }
 
+static tc_status launch_advance_split(tc_plan* p, const double2* u, double2* u_prev, const double2* Ncur,
+                                      double2* N_prev, double2* p_out, double2* u_out, char* ws, bool commit,
+                                      cudaStream_t s) {
+    Geo g = geo(p);
+    double2* ps = reinterpret_cast<double2*>(ws + p->ws.pstar);
+    double2* us = reinterpret_cast<double2*>(ws + p->ws.ustar);
+    double2* phi = reinterpret_cast<double2*>(ws + p->ws.phi);   // also holds X before phi
+    const dim3 g1(g.N, blocks_for(g.nmode, 128));
+    auto sgrid = [&](int nf) { return dim3(blocks_for((size_t)2 * g.nmode, 128), nf); };
+    int slot = prof_begin(p, kKRhsPressure, s);
+    k_nn_r<<<g1, 128, 0, s>>>(Ncur, N_prev, phi, g);
+    k_rhs_pressure<<<g1, 128, 0, s>>>(u, u_prev, Ncur, N_prev, phi, ps, p->d_r, p->d_ir, p->d_w1, p->d_w2, p->d_col0, g);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_rhs_pressure");
+    slot = prof_begin(p, kKSolveP, s);
+    k_band_solve_g<<<sgrid(1), 128, 0, s>>>(ps, p->d_fac, p->d_piv, kSetP, 1, g);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_band_solve_g");
+    slot = prof_begin(p, kKRhsVelocity, s);
+    k_rhs_velocity<<<g1, 128, 0, s>>>(u, u_prev, Ncur, N_prev, ps, us, commit ? p_out : nullptr, p->d_ir, p->d_w1,
+                                       p->d_col0, p->Re_i, p->Re_o, g);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_rhs_velocity");
+    slot = prof_begin(p, kKSolveH, s);
+    k_band_solve_g<<<sgrid(3), 128, 0, s>>>(us, p->d_fac, p->d_piv, kSetHp, 3, g);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_band_solve_g");
+    slot = prof_begin(p, kKRhsDiv, s);
+    k_rhs_div<<<g1, 128, 0, s>>>(us, phi, p->d_ir, p->d_w1, p->d_col0, g);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_rhs_div");
+    slot = prof_begin(p, kKSolveP, s);
+    k_band_solve_g<<<sgrid(1), 128, 0, s>>>(phi, p->d_fac, p->d_piv, kSetP, 1, g);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_band_solve_g");
+    slot = prof_begin(p, kKUpdate, s);
+    k_update<<<g1, 128, 0, s>>>(const_cast<double2*>(u), u_prev, Ncur, N_prev, p_out, us, phi, u_out, p->d_ir,
+                                p->d_w1, p->d_col0, commit ? 1 : 0, g);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_update");
+    return TC_OK;
+}
+
 tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const double2* Ncur,
                          double2* N_prev, double2* p_out, double2* u_out, char* ws, bool commit,
                          cudaStream_t s) {
-    (void)ws;
+    if (p->pc_split) return launch_advance_split(p, u, u_prev, Ncur, N_prev, p_out, u_out, ws, commit, s);
     Geo g = geo(p);
     const int T = pc_modes(p);
     PCArgs a;
@@ -347,14 +605,12 @@ tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const do
     a.up_out = commit ? u_prev : nullptr;
     a.Np_out = commit ? N_prev : nullptr;
     a.p = commit ? p_out : nullptr;
-    a.rn = p->d_r; a.w1 = p->d_w1; a.w2 = p->d_w2; a.col0 = p->d_col0;
+    a.rn = p->d_r; a.ir = p->d_ir; a.w1 = p->d_w1; a.w2 = p->d_w2; a.col0 = p->d_col0;
     a.fac = p->d_fac; a.piv = p->d_piv;
     a.Re_i = p->Re_i; a.Re_o = p->Re_o;
     a.commit = commit ? 1 : 0;
     const size_t sm = (size_t)4 * p->N_r * T * sizeof(double2);
-    int threads = ((6 * T + 31) / 32) * 32;
-    if (threads < 128) threads = 128;
-    if (threads > 256) threads = 256;
+    const int threads = kPCThreads;   // T <= 16 keeps the 6T substitution threads within the block
     TC_CUDA(p, cudaFuncSetAttribute(k_pc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int slot = prof_begin(p, kKPC, s);
     k_pc<<<blocks_for(g.nmode, T), threads, sm, s>>>(a, g, T);
@@ -376,7 +632,7 @@ tc_status launch_diagnostics(tc_plan* p, const double2* u, double* red, cudaStre
     const double C1 = (p->Re_o - eta * p->Re_i) / (1.0 + eta);
     const double C2 = eta * (p->Re_i - eta * p->Re_o) / ((1.0 - eta) * (1.0 - eta * eta));
     TC_CUDA(p, cudaMemsetAsync(red, 0, 4 * sizeof(double), s));
-    { const int slot_ = prof_begin(p, kKDiag, s); k_diag<<<blocks_for(g.S, 256), 256, 0, s>>>(u, red, p->d_r, p->d_w1, p->d_col0, C1, C2, g); prof_end(p, slot_, s); }
+    { const int slot_ = prof_begin(p, kKDiag, s); k_diag<<<dim3(blocks_for(g.nmode, 256), g.N), 256, 0, s>>>(u, red, p->d_r, p->d_w1, p->d_col0, C1, C2, g); prof_end(p, slot_, s); }
     TC_LAUNCHED(p, "k_diag");
     return TC_OK;
 }

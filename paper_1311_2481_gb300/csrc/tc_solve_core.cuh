@@ -10,14 +10,14 @@ namespace tc {
 struct Geo {
     int N, M, K, nk, nmode, K1, M1K1;
     size_t S;
-    double mp, kz, dt;
+    double mp, kz, dt, c1;   // c1 = 1 / (2 dt)
 };
 
 static inline Geo geo(const tc_plan* p) {
     Geo g;
     g.N = p->N_r; g.M = p->M; g.K = p->K; g.nk = 2 * p->K + 1; g.nmode = p->nmode;
     g.K1 = p->K + 1; g.M1K1 = (p->M + 1) * (p->K + 1); g.S = p->S;
-    g.mp = (double)p->m_p; g.kz = p->k_z; g.dt = p->dt;
+    g.mp = (double)p->m_p; g.kz = p->k_z; g.dt = p->dt; g.c1 = 1.0 / (2.0 * p->dt);
     return g;
 }
 
@@ -72,15 +72,25 @@ __device__ __forceinline__ void smem_band_solve(double2* col, int T, int t, int 
     // forward: rows j .. j+4 live in w0..w4
     double w0 = x[0], w1 = N > 1 ? x[st] : 0.0, w2 = N > 2 ? x[2 * st] : 0.0,
            w3 = N > 3 ? x[3 * st] : 0.0, w4 = N > 4 ? x[4 * st] : 0.0;
+    // factors of the next row are loaded one row ahead
+    int pn = P[0];
+    double l1n = __ldg(&F[0]), l2n = __ldg(&F[(size_t)M1K1]), l3n = __ldg(&F[(size_t)2 * M1K1]),
+           l4n = __ldg(&F[(size_t)3 * M1K1]);
     for (int j = 0; j < N; ++j) {
-        const double* Fj = F + (size_t)j * kBands * M1K1;
-        const int pj = P[(size_t)j * M1K1];
+        const int pj = pn;
+        const double l1 = l1n, l2 = l2n, l3 = l3n, l4 = l4n;
+        if (j + 1 < N) {
+            const double* Fn = F + (size_t)(j + 1) * kBands * M1K1;
+            pn = P[(size_t)(j + 1) * M1K1];
+            l1n = __ldg(&Fn[0]);
+            l2n = __ldg(&Fn[(size_t)M1K1]);
+            l3n = __ldg(&Fn[(size_t)2 * M1K1]);
+            l4n = __ldg(&Fn[(size_t)3 * M1K1]);
+        }
         if (pj == 1) { double q = w0; w0 = w1; w1 = q; }
         else if (pj == 2) { double q = w0; w0 = w2; w2 = q; }
         else if (pj == 3) { double q = w0; w0 = w3; w3 = q; }
         else if (pj == 4) { double q = w0; w0 = w4; w4 = q; }
-        const double l1 = __ldg(&Fj[0]), l2 = __ldg(&Fj[(size_t)M1K1]),
-                     l3 = __ldg(&Fj[(size_t)2 * M1K1]), l4 = __ldg(&Fj[(size_t)3 * M1K1]);
         x[(size_t)j * st] = w0;
         w1 = fma(-l1, w0, w1);
         w2 = fma(-l2, w0, w2);
@@ -91,19 +101,31 @@ __device__ __forceinline__ void smem_band_solve(double2* col, int T, int t, int 
     }
     // backward: x_{j+1..j+8} in v1..v8
     double v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0, v5 = 0.0, v6 = 0.0, v7 = 0.0, v8 = 0.0;
+    double un[9];
+    {
+        const double* Fl = F + (size_t)(N - 1) * kBands * M1K1;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) un[q] = __ldg(&Fl[(size_t)(4 + q) * M1K1]);
+    }
     for (int j = N - 1; j >= 0; --j) {
-        const double* Fj = F + (size_t)j * kBands * M1K1;
-        const double id = __ldg(&Fj[(size_t)4 * M1K1]);
+        double uc[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) uc[q] = un[q];
+        if (j > 0) {
+            const double* Fp = F + (size_t)(j - 1) * kBands * M1K1;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) un[q] = __ldg(&Fp[(size_t)(4 + q) * M1K1]);
+        }
         double s = x[(size_t)j * st];
-        s = fma(-__ldg(&Fj[(size_t)12 * M1K1]), v8, s);
-        s = fma(-__ldg(&Fj[(size_t)11 * M1K1]), v7, s);
-        s = fma(-__ldg(&Fj[(size_t)10 * M1K1]), v6, s);
-        s = fma(-__ldg(&Fj[(size_t)9 * M1K1]), v5, s);
-        s = fma(-__ldg(&Fj[(size_t)8 * M1K1]), v4, s);
-        s = fma(-__ldg(&Fj[(size_t)7 * M1K1]), v3, s);
-        s = fma(-__ldg(&Fj[(size_t)6 * M1K1]), v2, s);
-        s = fma(-__ldg(&Fj[(size_t)5 * M1K1]), v1, s);
-        const double xj = s * id;
+        s = fma(-uc[8], v8, s);
+        s = fma(-uc[7], v7, s);
+        s = fma(-uc[6], v6, s);
+        s = fma(-uc[5], v5, s);
+        s = fma(-uc[4], v4, s);
+        s = fma(-uc[3], v3, s);
+        s = fma(-uc[2], v2, s);
+        s = fma(-uc[1], v1, s);
+        const double xj = s * uc[0];
         x[(size_t)j * st] = xj;
         v8 = v7; v7 = v6; v6 = v5; v5 = v4; v4 = v3; v3 = v2; v2 = v1; v1 = xj;
     }

@@ -96,8 +96,9 @@ def test_banded_solves_match_dense(which, name):
     assert rel(host(x), ref) <= 1e-12
 
 
-def test_twenty_steps_match_oracle():
-    ops, plan = pair(CFG1)
+@pytest.mark.parametrize("pc_split", [-1, 1])      # fused steps-2-5 kernel, split kernels
+def test_twenty_steps_match_oracle(pc_split):
+    ops, plan = pair(CFG1, pc_split=pc_split)
     u0 = init(ops)
     st_o = O.cold_state(u0)
     st_o = O.run(ops, st_o, 20)
@@ -117,8 +118,9 @@ def test_twenty_steps_match_oracle():
     assert rel(host(st2.u), host(st.u)) <= 1e-14
 
 
-def test_step_full_size_config2():
-    ops, plan = pair(CFG2)
+@pytest.mark.parametrize("pc_split", [0, 1])
+def test_step_full_size_config2(pc_split):
+    ops, plan = pair(CFG2, pc_split=pc_split)
     u0 = init(ops, kind="taylor", amp=1e-2)
     st_o = O.run(ops, O.cold_state(u0), 2)
     st = tc.State(plan, dev(u0))
