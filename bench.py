@@ -167,8 +167,10 @@ def adjoint_ratio(tc, torch, I, dev):
     n, C = 200, 20
     x = u0.to(dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    A.final_energy(x, plan, 20, checkpoint=C)                 # warm-up
+    xw = x.clone().requires_grad_(True)                       # warm-up: forward and backward
+    A.final_energy(xw, plan, 2 * C, checkpoint=C).backward()
     torch.cuda.synchronize()
+    del xw
     ev[0].record()
     with torch.no_grad():
         J0 = A.final_energy(x, plan, n, checkpoint=C)
@@ -185,23 +187,47 @@ def adjoint_ratio(tc, torch, I, dev):
     return {"workload": "N_r=96, m=-32..32, k=-64..64, Re_i=2000, 200 steps, checkpoint every 20, "
                         "J = final perturbation energy, init amp 1e-4 (seed 42)",
             "dt": dt, "forward_ms": t_f, "forward_plus_adjoint_ms": t_fb,
+            "backward_ms_per_step": (t_fb - t_f) / n, "forward_ms_per_step": t_f / n,
+            # backward (segment recomputation + adjoint steps) over the plain forward run
             "adjoint_to_forward_ratio": (t_fb - t_f) / t_f, "J": float(J0),
             "grad_finite": bool(torch.isfinite(torch.view_as_real(g)).all())}
 
 
+def cfl_dt(cfg, c=0.25):
+    """The stated dt, capped by the azimuthal advection limit of the explicit AB2 term:
+    dt * Omega_max * M * m_p <= c, with Omega_max the larger wall angular velocity
+    (|Re_i| / r_i, |Re_o| / r_o in viscous units)."""
+    r_i = cfg["eta"] / (1.0 - cfg["eta"])
+    r_o = 1.0 / (1.0 - cfg["eta"])
+    om = max(abs(cfg["Re_i"]) / r_i, abs(cfg["Re_o"]) / r_o)
+    return min(cfg["dt"], c / (om * cfg["M"] * cfg["m_p"]))
+
+
+def _rel(a, b, torch):
+    return float(torch.linalg.vector_norm(b - a) / torch.linalg.vector_norm(a))
+
+
 def large_mixed(tc, torch, I, dev, steps=4):
-    """FP64 plain vs mixed step at N_r = 256, m = -256..256, k = -512..512 (same size)."""
-    cfg = CFG4
+    """FP64 plain vs mixed step at N_r = 256, m = -256..256, k = -512..512 (same size), with
+    the mixed form's error against the FP64 GPU step from the same initial state."""
+    cfg = {**CFG4, "dt": cfl_dt(CFG4)}
     out = {"workload": "quasi-Keplerian eta=0.5, Re_i=1e4, Re_o=sqrt(eta) Re_i, N_r=256, m=-256..256, "
-                       "k=-512..512, phys 256x768x1536, dt=1e-4, broadband amp 0.05 (seed 42)",
-           "gdof": gdof(cfg)}
-    res = {}
+                       "k=-512..512, phys 256x768x1536, broadband amp 0.05 (seed 42)",
+           "gdof": gdof(cfg), "dt_stated": CFG4["dt"], "dt": cfg["dt"]}
+    res, keep = {}, {}
+    u0h = None
     for name, prec in (("fp64", tc.TC_FP64), ("mixed", tc.TC_MIXED)):
         plan = tc.Plan(**cfg, precision=prec, device=dev)
         r = plan.nodes()
-        u0 = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"],
-                                              cfg["Re_o"], kind="broadband", amp=0.05, seed=42)).to(dev)
+        if u0h is None:
+            u0h = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"],
+                                                   cfg["Re_i"], cfg["Re_o"], kind="broadband", amp=0.05,
+                                                   seed=42))
+        u0 = u0h.to(dev)
+        N0 = plan.nonlinear(u0)
         st = tc.State(plan, u0)
+        del u0
+        e_start = plan.diagnostics(st.u).energy
         plan.step(st, 2)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -215,12 +241,27 @@ def large_mixed(tc, torch, I, dev, steps=4):
         torch.cuda.synchronize()
         kern = {k: v[1] for k, v in plan.profile_read().items()}
         plan.profile(False)
+        d = plan.diagnostics(st.u)
         res[name] = ms
+        keep[name] = (N0, st.u.clone(), d)
         out[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "gdof_steps_per_s": gdof(cfg) / ms / 1e6,
-                     "kernels_ms": kern}
-        del plan, st, u0
+                     "kernels_ms": kern, "state_finite": bool(d.finite),
+                     "energy_growth": d.energy / e_start}
+        del plan, st
         torch.cuda.empty_cache()
     out["mixed_speedup_vs_fp64"] = res["fp64"] / res["mixed"]
+    (Na, ua, da), (Nb, ub, db) = keep["fp64"], keep["mixed"]
+    base = torch.from_numpy(I.base_state(r, cfg["M"], cfg["K"], cfg["eta"], cfg["Re_i"], cfg["Re_o"])).to(dev)
+    out["mixed_error"] = {
+        "after_steps": steps + 3, "dt": cfg["dt"],
+        "rel_err_nonlinear_term": _rel(Na, Nb, torch),
+        "rel_err_velocity_perturbation": _rel(ua - base, ub - base, torch),
+        "rel_err_velocity": _rel(ua, ub, torch),
+        "rel_err_torque_inner": abs(db.torque_inner / da.torque_inner - 1),
+        "rel_err_torque_outer": abs(db.torque_outer / da.torque_outer - 1),
+        "max_div_fp64": da.max_div, "max_div_mixed": db.max_div}
+    del keep, base
+    torch.cuda.empty_cache()
     return out
 
 
@@ -231,7 +272,7 @@ CFG5 = dict(N_r=384, M=384, K=768, m_p=1, eta=0.5, Re_i=3e4, Re_o=math.sqrt(0.5)
 
 def largest_mixed(tc, torch, I, dev, steps=3):
     """Mixed form at the largest workload, forward only (no adjoint workspace)."""
-    cfg = CFG5
+    cfg = {**CFG5, "dt": cfl_dt(CFG5)}
     t0 = time.perf_counter()
     plan = tc.Plan(**cfg, precision=tc.TC_MIXED, no_adjoint=True, device=dev)
     t_plan = time.perf_counter() - t0
@@ -240,6 +281,7 @@ def largest_mixed(tc, torch, I, dev, steps=3):
                                           cfg["Re_o"], kind="broadband", amp=0.05, seed=42)).to(dev)
     st = tc.State(plan, u0)
     del u0
+    e_start = plan.diagnostics(st.u).energy
     plan.step(st, 2)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -255,10 +297,12 @@ def largest_mixed(tc, torch, I, dev, steps=3):
     plan.profile(False)
     d = plan.diagnostics(st.u)
     return {"workload": "quasi-Keplerian eta=0.5, Re_i=3e4, Re_o=sqrt(eta) Re_i, N_r=384, m=-384..384, "
-                        "k=-768..768, phys 384x1152x2304, dt=5e-5, broadband amp 0.05 (seed 42), mixed form",
+                        "k=-768..768, phys 384x1152x2304, broadband amp 0.05 (seed 42), mixed form",
+            "dt_stated": CFG5["dt"], "dt": cfg["dt"],
             "gdof": gdof(cfg), "ms_per_step": ms, "steps_per_s": 1e3 / ms,
             "gdof_steps_per_s": gdof(cfg) / ms / 1e6, "kernels_ms": kern, "plan_create_s": t_plan,
-            "device_memory_gb": torch.cuda.max_memory_allocated() / 1e9, "state_finite": bool(d.finite)}
+            "device_memory_gb": torch.cuda.max_memory_allocated() / 1e9, "state_finite": bool(d.finite),
+            "energy_growth": d.energy / e_start}
 
 
 def run_ours(args):
@@ -353,9 +397,9 @@ def run_ours(args):
         ach = flops[top[0]] / avg_s
         roof = {"kernel": top[0], "bound": "alu", "achieved": ach / 1e12, "peak": fp64_peak / 1e12,
                 "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                # dram__bytes_read.sum + dram__bytes_write.sum of k_theta<double2> per launch,
-                # from profiles/k_theta_fp64__Nr64_M32_K64.md (kernel unchanged since)
-                "traffic": (58.437376e6 + 3.228672e6) if (top[0] == "k_theta" and main_is_bench) else None,
+                # dram__bytes_read.sum + dram__bytes_write.sum of k_theta<double2> per launch at
+                # this workload, from one ncu --set full capture (kernel unchanged since)
+                "traffic": (58.432256e6 + 3.170816e6) if (top[0] == "k_theta" and main_is_bench) else None,
                 "peak_source": "152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (unit counts and max clock)",
                 "algorithmic": "7.5 complex FFTs of P_theta at 5 n log2 n + 25 flop/point per (r, z)"}
     else:
