@@ -24,6 +24,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) of one FP64 theta-pass launch at the bench workload, from ncu
+THETA_TRAFFIC = 58.440448e6 + 3.061504e6
 CFG2 = dict(N_r=64, M=32, K=64, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)
 # mid-size case for profiling (inputs larger than L2, a few GB on the device)
 CFG_MID = dict(N_r=128, M=128, K=256, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)
@@ -397,9 +399,10 @@ def run_ours(args):
         ach = flops[top[0]] / avg_s
         roof = {"kernel": top[0], "bound": "alu", "achieved": ach / 1e12, "peak": fp64_peak / 1e12,
                 "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                # dram__bytes_read.sum + dram__bytes_write.sum of k_theta<double2> per launch at
-                # this workload, from one ncu --set full capture (kernel unchanged since)
-                "traffic": (58.432256e6 + 3.170816e6) if (top[0] == "k_theta" and main_is_bench) else None,
+                # dram__bytes_read.sum + dram__bytes_write.sum of the FP64 theta pass per launch at
+                # this workload from one ncu --set full capture; None until the current kernel
+                # has been captured
+                "traffic": THETA_TRAFFIC if (top[0] == "k_theta" and main_is_bench) else None,
                 "peak_source": "152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (unit counts and max clock)",
                 "algorithmic": "7.5 complex FFTs of P_theta at 5 n log2 n + 25 flop/point per (r, z)"}
     else:

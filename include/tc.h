@@ -67,12 +67,17 @@ typedef struct {
     int P_z;          /* physical points in z;     0 -> 3K.  Must be 2^a 3^b >= 2K+1 */
     int precision;    /* tc_precision; TC_MIXED runs the transforms and products in FP32 */
     int host_only;    /* 1: build the host plan only (no device memory); for inspection */
-    int theta_zt;     /* launch tuning: z values per theta-pass block (0: automatic) */
+    int theta_zt;     /* launch tuning: z values per theta-pass block (0: automatic); in the
+                         mixed form a value > 0 also selects the generic theta kernel over the
+                         length-specialised one */
     int pc_modes;     /* launch tuning: modes per block of the steps-2-5 kernel (0: automatic) */
     int no_adjoint;   /* 1: size the workspace without the adjoint regions (tc_adjoint_* then
                          return TC_ERR_STATE); a TC_MIXED plan also stages its transforms in FP32 */
     int pc_split;     /* steps 2-5 as one fused kernel (-1) or as separate kernels (1);
                          0: fused while N_r <= 192, separate beyond */
+    int theta_variant; /* launch tuning of the mixed form's length-specialised theta pass:
+                         0 or 1: radices <= 16, two blocks per SM; 2 and 3: radices <= 8 with
+                         half the z values per block, four / three blocks per SM */
 } tc_options;
 
 /* Step state (Sec. 3.2): u = u^i, u_prev = u^{i-1}, N_prev = N^{i-1} (vector fields), p = p^i

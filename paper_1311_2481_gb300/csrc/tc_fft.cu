@@ -12,6 +12,7 @@
 //                                                                          -> H2[3][r][m][z]
 //   k_zfwd   per (r, m): forward transforms along z, truncation to |k| <= K, 1/(P_theta P_z).
 //
+// The mixed-precision form (tc_mixed.cu) shares k_theta with FP32 lines.
 // The transforms are mixed-radix (4, 2, 3) Stockham passes in shared memory with twiddles
 // from a long-double table.
 #include "tc_internal.cuh"
@@ -21,15 +22,14 @@ namespace tc {
 
 // ---------------------------------------------------------------- inverse z-pass
 // Field f of H1: f = 3 d + c, c in {+, -, z}, d in {u, d_r u, d_z u}.
-template <typename V>
-__global__ void __launch_bounds__(256) k_zinv(const double2* __restrict__ u, V* __restrict__ H1,
+__global__ void __launch_bounds__(256) k_zinv(const double2* __restrict__ u, double2* __restrict__ H1,
                                               const double* __restrict__ w1, const int* __restrict__ col0,
-                                              int N_r, int M, int K, double kz, int L, int mean_sub,
-                                              const V* __restrict__ tw, Radices rad) {
+                                              int N_r, int M, int K, double kz, int L,
+                                              const double2* __restrict__ tw, Radices rad) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Pz = rad.n;
-    V* a = reinterpret_cast<V*>(smem_raw);
-    V* b = a + (size_t)L * Pz;
+    double2* a = reinterpret_cast<double2*>(smem_raw);
+    double2* b = a + (size_t)L * Pz;
     const int groups = 9 / L;
     const int g = blockIdx.x % groups;
     const int rm = blockIdx.x / groups;
@@ -43,41 +43,31 @@ __global__ void __launch_bounds__(256) k_zinv(const double2* __restrict__ u, V* 
         const int l = idx / Pz;
         const int q = idx - l * Pz;
         const int k = q <= K ? q : q - Pz;
-        V val;
-        val.x = 0; val.y = 0;
+        double2 x = make_double2(0.0, 0.0);
         if (k >= -K && k <= K) {
             const int f = g * L + l;
             const int c = f % 3, d = f / 3;
             const double2* base = u + (size_t)c * S + (size_t)m * nk + (k + K);
-            // mixed form: u' = u - U e_theta, i.e. on the (0,0) mode Im u'_+ = Im u'_- =
-            // (Im u_+ + Im u_-) / 2 (U = Im(u_+ - u_-) / 2)
-            const bool sub = mean_sub && m == 0 && k == 0 && c < 2;
-            const double2* other = u + (size_t)(1 - c) * S + (size_t)m * nk + (k + K);
-            double2 x;
             if (d == 1) {
-                x = make_double2(0.0, 0.0);
 #pragma unroll
                 for (int t = 0; t < kStencil; ++t) {
                     const double w = __ldg(&w1[r * kStencil + t]);
-                    double2 y = __ldg(&base[(size_t)(c0 + t) * colstride]);
-                    if (sub) y.y = 0.5 * (y.y + __ldg(&other[(size_t)(c0 + t) * colstride]).y);
+                    const double2 y = __ldg(&base[(size_t)(c0 + t) * colstride]);
                     x.x += w * y.x;
                     x.y += w * y.y;
                 }
             } else {
                 x = __ldg(&base[(size_t)r * colstride]);
-                if (sub) x.y = 0.5 * (x.y + __ldg(&other[(size_t)r * colstride]).y);
                 if (d == 2) {
                     const double kk = kz * k;
                     x = make_double2(-kk * x.y, kk * x.x);
                 }
             }
-            val = from_d2<V>(x);
         }
-        a[idx] = val;
+        a[idx] = x;
     }
     __syncthreads();
-    V* res = smem_fft(a, b, L, tw, true, rad);
+    double2* res = smem_fft(a, b, L, tw, true, rad);
     for (int idx = threadIdx.x; idx < L * Pz; idx += blockDim.x) {
         const int l = idx / Pz;
         const int z = idx - l * Pz;
@@ -188,28 +178,18 @@ __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __re
 }
 
 // ---------------------------------------------------------------- forward z-pass
-// With mean_add (mixed form) the FP64 mode-diagonal terms of the base flow U(r) e_theta,
-// U = Re u_theta^{(0,0)}, are added to the transformed N(u'):
-//   N_pm += (U/r) i m m_p u'_pm + i (U/r)(u'_+ - u'_-) +- (i/2)(d_r U + U/r)(u'_+ + u'_-),
-//   N_z  += (U/r) i m m_p u'_z,   and -U^2/r on the (0,0) mode of N_pm
-// (Eq. NS_cyl with u_theta = U + u'_theta; d_r U by the same FD stencil).
-template <typename V>
-__global__ void __launch_bounds__(256) k_zfwd(const V* __restrict__ H2, double2* __restrict__ N,
+__global__ void __launch_bounds__(256) k_zfwd(const double2* __restrict__ H2, double2* __restrict__ N,
                                               int N_r, int M, int K, double scale,
-                                              const V* __restrict__ tw, Radices rad,
-                                              const double2* __restrict__ u, const double* __restrict__ rnodes,
-                                              const double* __restrict__ w1, const int* __restrict__ col0,
-                                              double mp, int mean_add, int Lf) {
+                                              const double2* __restrict__ tw, Radices rad, int Lf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double s_mf[2];
     const int Pz = rad.n;
-    V* a = reinterpret_cast<V*>(smem_raw);
-    V* b = a + (size_t)Lf * Pz;
+    double2* a = reinterpret_cast<double2*>(smem_raw);
+    double2* b = a + (size_t)Lf * Pz;
     const int cg = blockIdx.x % (3 / Lf);     // component group (Lf = 3: all three)
     const int m = (blockIdx.x / (3 / Lf)) % (M + 1);
     const int r = (blockIdx.x / (3 / Lf)) / (M + 1);
     const size_t fstride = (size_t)N_r * (M + 1) * Pz;
-    const V* h = H2 + ((size_t)r * (M + 1) + m) * Pz;
+    const double2* h = H2 + ((size_t)r * (M + 1) + m) * Pz;
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
     for (int idx = threadIdx.x; idx < Lf * Pz; idx += blockDim.x) {
@@ -217,90 +197,42 @@ __global__ void __launch_bounds__(256) k_zfwd(const V* __restrict__ H2, double2*
         const int z = idx - l * Pz;
         a[idx] = h[(cg * Lf + l) * fstride + z];
     }
-    if (mean_add && threadIdx.x == 0) {
-        // U(r)/r and d_r U(r) from the (0,0) column, U = Im(u_+ - u_-)/2
-        const size_t col = (size_t)(M + 1) * nk;
-        const double2* up = u + K;
-        const double2* um = u + S + K;
-        double dU = 0.0;
-        const int c0 = col0[r];
-        for (int t = 0; t < kStencil; ++t)
-            dU += w1[r * kStencil + t] * 0.5 * (up[(size_t)(c0 + t) * col].y - um[(size_t)(c0 + t) * col].y);
-        const double U = 0.5 * (up[(size_t)r * col].y - um[(size_t)r * col].y);
-        s_mf[0] = U / rnodes[r];
-        s_mf[1] = dU;
-    }
     __syncthreads();
-    V* res = smem_fft(a, b, Lf, tw, false, rad);
-    double Ur = 0.0, q = 0.0;
-    if (mean_add) {
-        Ur = s_mf[0];
-        q = 0.5 * (s_mf[1] + Ur);
-    }
+    double2* res = smem_fft(a, b, Lf, tw, false, rad);
     for (int idx = threadIdx.x; idx < Lf * nk; idx += blockDim.x) {
         const int l = idx / nk;
         const int c = cg * Lf + l;
         const int kk = idx - l * nk;
         const int k = kk - K;
-        const V v = res[(size_t)l * Pz + (k < 0 ? k + Pz : k)];
-        double2 o = make_double2((double)v.x * scale, (double)v.y * scale);
-        if (mean_add) {
-            const size_t e = ((size_t)r * (M + 1) + m) * nk + kk;
-            const double t = Ur * mp * m;
-            if (c == 2) {
-                const double2 z = u[2 * S + e];
-                o.x -= t * z.y;
-                o.y += t * z.x;
-            } else {
-                double2 ap = u[e], am = u[S + e];
-                if (m == 0 && k == 0) {  // u'_pm on the (0,0) mode
-                    const double im = 0.5 * (ap.y + am.y);
-                    ap.y = im;
-                    am.y = im;
-                    const double U = Ur * rnodes[r];
-                    o.x -= Ur * U;
-                }
-                const double2 own = c == 0 ? ap : am;
-                const double sg = c == 0 ? 1.0 : -1.0;
-                const double dx = ap.x - am.x, dy = ap.y - am.y;   // u'_+ - u'_-
-                const double sx = ap.x + am.x, sy = ap.y + am.y;   // u'_+ + u'_-
-                o.x += -t * own.y - Ur * dy - sg * q * sy;
-                o.y += t * own.x + Ur * dx + sg * q * sx;
-            }
-        }
-        N[(size_t)c * S + ((size_t)r * (M + 1) + m) * nk + kk] = o;
+        const double2 v = res[(size_t)l * Pz + (k < 0 ? k + Pz : k)];
+        N[(size_t)c * S + ((size_t)r * (M + 1) + m) * nk + kk] = make_double2(v.x * scale, v.y * scale);
     }
 }
 
-template <typename V>
-static tc_status run_nonlinear(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s,
-                               const V* twz, const V* twt) {
-    const bool mixed = sizeof(V) == 8;
-    V* H1 = reinterpret_cast<V*>(ws + p->ws.H1);
-    V* H2 = reinterpret_cast<V*>(ws + p->ws.H2);
-    const int L = mixed ? p->zinv_lines32 : p->zinv_lines;
-    const int zt = mixed ? p->zt32 : p->zt;
-    size_t sm1 = (size_t)2 * L * p->P_z * sizeof(V);
-    size_t sm2 = (size_t)2 * 6 * zt * p->P_t * sizeof(V);
-    const int Lf = mixed ? p->zfwd_lines32 : p->zfwd_lines;
-    size_t sm3 = (size_t)2 * Lf * p->P_z * sizeof(V);
-    TC_CUDA(p, cudaFuncSetAttribute(k_zinv<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
-    TC_CUDA(p, cudaFuncSetAttribute(k_theta<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    TC_CUDA(p, cudaFuncSetAttribute(k_zfwd<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-    const int blocks1 = p->N_r * (p->M + 1) * (9 / L);
-    int slot = prof_begin(p, sizeof(V) == 16 ? kKZinv : kKZinv32, s);
-    k_zinv<V><<<blocks1, mixed ? 256 : p->thr_zinv, sm1, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M, p->K, p->k_z, L, mixed ? 1 : 0, twz, p->rad_z);
-    prof_end(p, slot, s);
-    TC_LAUNCHED(p, "k_zinv");
-    const int blocks2 = p->N_r * (p->P_z / zt);
-    slot = prof_begin(p, sizeof(V) == 16 ? kKTheta : kKTheta32, s);
-    k_theta<V><<<blocks2, mixed ? 256 : p->thr_theta, sm2, s>>>(H1, H2, p->d_r, p->N_r, p->M, p->P_z, (double)p->m_p, zt, twt, p->rad_t);
-    prof_end(p, slot, s);
-    TC_LAUNCHED(p, "k_theta");
+static tc_status run_nonlinear(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s) {
+    double2* H1 = reinterpret_cast<double2*>(ws + p->ws.H1);
+    double2* H2 = reinterpret_cast<double2*>(ws + p->ws.H2);
+    TC_TRY_STATUS(launch_zinv_fp64(p, u, H1, s));
+    const int zt = p->zt;
+    const size_t sm2 = (size_t)2 * 6 * zt * p->P_t * sizeof(double2);
+    const int Lf = p->zfwd_lines;
+    const size_t sm3 = (size_t)2 * Lf * p->P_z * sizeof(double2);
+    TC_CUDA(p, cudaFuncSetAttribute(k_theta<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    TC_CUDA(p, cudaFuncSetAttribute(k_zfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+    int slot;
+    if (p->theta_zt_forced == 0 && theta_s_zt(p, true) > 0) {
+        TC_TRY_STATUS(launch_theta_s64(p, H1, H2, s));   // length-specialised, streamed products
+    } else {
+        slot = prof_begin(p, kKTheta, s);
+        k_theta<double2><<<p->N_r * (p->P_z / zt), p->thr_theta, sm2, s>>>(H1, H2, p->d_r, p->N_r, p->M, p->P_z,
+                                                                          (double)p->m_p, zt, p->d_tw_t, p->rad_t);
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_theta");
+    }
     const double scale = 1.0 / ((double)p->P_t * (double)p->P_z);
-    slot = prof_begin(p, sizeof(V) == 16 ? kKZfwd : kKZfwd32, s);
-    k_zfwd<V><<<p->N_r * (p->M + 1) * (3 / Lf), mixed ? 256 : p->thr_zfwd, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, twz, p->rad_z,
-                                                     u, p->d_r, p->d_w1, p->d_col0, (double)p->m_p, mixed ? 1 : 0, Lf);
+    slot = prof_begin(p, kKZfwd, s);
+    k_zfwd<<<p->N_r * (p->M + 1) * (3 / Lf), p->thr_zfwd, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, p->d_tw_z,
+                                                                    p->rad_z, Lf);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_zfwd");
     return TC_OK;
@@ -309,18 +241,31 @@ static tc_status run_nonlinear(tc_plan* p, const double2* u, double2* N, char* w
 tc_status launch_zinv_fp64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s) {
     const int L = p->zinv_lines;
     const size_t sm1 = (size_t)2 * L * p->P_z * sizeof(double2);
-    TC_CUDA(p, cudaFuncSetAttribute(k_zinv<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+    TC_CUDA(p, cudaFuncSetAttribute(k_zinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
     const int slot = prof_begin(p, kKZinv, s);
-    k_zinv<double2><<<p->N_r * (p->M + 1) * (9 / L), p->thr_zinv, sm1, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M, p->K,
-                                                                     p->k_z, L, 0, p->d_tw_z, p->rad_z);
+    k_zinv<<<p->N_r * (p->M + 1) * (9 / L), p->thr_zinv, sm1, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M, p->K,
+                                                                   p->k_z, L, p->d_tw_z, p->rad_z);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_zinv");
     return TC_OK;
 }
 
+// theta pass of the mixed form: FP32 lines (H1, H2 in float2)
+tc_status launch_theta32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t s) {
+    const int zt = p->zt32;
+    const size_t sm2 = (size_t)2 * 6 * zt * p->P_t * sizeof(float2);
+    TC_CUDA(p, cudaFuncSetAttribute(k_theta<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    const int slot = prof_begin(p, kKTheta32, s);
+    k_theta<float2><<<p->N_r * (p->P_z / zt), 256, sm2, s>>>(H1, H2, p->d_r, p->N_r, p->M, p->P_z, (double)p->m_p,
+                                                             zt, p->d_tw_t32, p->rad_t);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_theta");
+    return TC_OK;
+}
+
 tc_status launch_nonlinear(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s) {
-    if (p->precision == TC_MIXED) return run_nonlinear<float2>(p, u, N, ws, s, p->d_tw_z32, p->d_tw_t32);
-    return run_nonlinear<double2>(p, u, N, ws, s, p->d_tw_z, p->d_tw_t);
+    if (p->precision == TC_MIXED) return launch_nonlinear_mixed(p, u, N, ws, s);
+    return run_nonlinear(p, u, N, ws, s);
 }
 
 }  // namespace tc

@@ -30,6 +30,7 @@ struct Radices {
 struct Workspace {
     size_t H1;      // inverse z-pass output: 9 fields x N_r x (M+1) x P_z complex
     size_t H2;      // theta-pass output: 3 fields x N_r x (M+1) x P_z complex
+    size_t P32;     // mixed form: u', d_r u' in FP32, 6 x S float2 (aliases H2, dead before it)
     size_t Ncur;    // N^i: vector field
     size_t uE;      // start-up Euler result: vector field
     size_t pstar;   // split path only: p* (scalar), u* (vector), phi (scalar)
@@ -59,6 +60,8 @@ struct tc_plan {
     int nmode_half;  // (M+1)(K+1)
     tc::Radices rad_z, rad_t;
     int zt, zt32;                  // z values per theta-pass block (FP64 / FP32 lines)
+    int theta_zt_forced;           // tc_options.theta_zt (> 0: generic transform kernels)
+    int theta_variant;             // tc_options.theta_variant (launch shape of the FP32 streamed theta pass)
     int pc_modes;                  // modes per block of the fused steps-2-5 kernel (0: auto)
     int thr_zinv, thr_theta, thr_zfwd;  // block sizes of the FP64 transform kernels
     bool pc_split;                      // steps 2-5 as separate kernels (large N_r)
@@ -78,6 +81,7 @@ struct tc_plan {
     double* d_r = nullptr;
     double* d_ir = nullptr;          // 1 / r_j
     double* d_w1 = nullptr;
+    float* d_w1f = nullptr;          // FP32 copy of w1 (mixed form)
     double* d_w2 = nullptr;
     int* d_col0 = nullptr;
     int* d_d1t_row = nullptr;
@@ -123,6 +127,11 @@ tc_status cuda_fail(tc_plan* p, cudaError_t e, const char* where);
         cudaError_t e_ = (call);                                       \
         if (e_ != cudaSuccess) return tc::cuda_fail(plan, e_, #call);  \
     } while (0)
+#define TC_TRY_STATUS(x)                                               \
+    do {                                                               \
+        tc_status s_ = (x);                                            \
+        if (s_ != TC_OK) return s_;                                    \
+    } while (0)
 #define TC_LAUNCHED(plan, what)                                        \
     do {                                                               \
         cudaError_t e_ = cudaGetLastError();                           \
@@ -135,7 +144,7 @@ tc_status check_device_ptr(tc_plan* p, const void* ptr, const char* name);
 enum KernelId {
     kKZinv = 0, kKTheta, kKZfwd, kKRhsPressure, kKSolveP, kKRhsVelocity, kKSolveH, kKRhsDiv,
     kKUpdate, kKAxpby, kKDiag, kKZinv32, kKTheta32, kKZfwd32, kKMeanFlow, kKPC, kKPCAdj,
-    kKZinvAdj, kKThetaAdj, kKZfwdAdj, kKDrT, kNumKernels
+    kKZinvAdj, kKThetaAdj, kKZfwdAdj, kKDrT, kKPrep32, kNumKernels
 };
 extern const char* const kKernelNames[kNumKernels];
 int prof_begin(tc_plan* p, int kid, cudaStream_t s);
@@ -144,6 +153,11 @@ void prof_end(tc_plan* p, int slot, cudaStream_t s);
 // ------------------------------------------------------------------ launchers
 tc_status launch_nonlinear(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s);
 tc_status launch_zinv_fp64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s);
+tc_status launch_theta32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t s);
+int theta_s_zt(const tc_plan* p, bool fp64);
+tc_status launch_theta_s(tc_plan* p, const float2* H1, float2* H2, cudaStream_t s);
+tc_status launch_theta_s64(tc_plan* p, const double2* H1, double2* H2, cudaStream_t s);
+tc_status launch_nonlinear_mixed(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s);
 tc_status launch_solve(tc_plan* p, int set, double2* x, int nfields, cudaStream_t s);
 tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const double2* Ncur,
                          double2* N_prev, double2* p_out, double2* u_out, char* ws,

@@ -1,0 +1,537 @@
+// Mixed-precision form of the nonlinear term (Sec. 3.2 step 1): the transforms and products
+// of the perturbation u' = u - U e_theta run in FP32; the radial derivative and the
+// mode-diagonal mean-flow terms keep FP64-grade accuracy without the FP64 pipe, which on
+// this GPU retires 2 lanes per SM per clock against 128 for FP32.
+//
+//   k_prep32    per (c, m, 32 k, 32 r): each FP64 coefficient is split once into an FP32 pair
+//               (hi, lo) by integer operations; d_r u' is the FD stencil (Sec. 3.1) applied to
+//               the differences u_t - u_r = (hi_t - hi_r) + (lo_t - lo_r). The weights of a
+//               derivative stencil sum to zero, so this is the same stencil; the differences
+//               are O(dr |d_r u|), which keeps the FP32 rounding of each term at the size of
+//               the result instead of the size of u / dr.           -> P[d][c][r][m][k]
+//   k_zinv_p32  per (r, m): u', d_r u', d_z u' = i k k_z u' of the 3 components, zero-padded
+//               inverse z transforms (FP32).                          -> H1[9][r][m][z]
+//   k_theta_s   length-specialised theta pass with streamed products (tc_theta32.cu), or
+//               the generic k_theta with FP32 lines for other lengths -> H2[3][r][m][z]
+//   k_zfwd32    per (r, m): forward z transforms, truncation, 1/(P_theta P_z), plus the
+//               mean-flow terms in double-FP32 arithmetic (error-free products and sums),
+//               assembled into FP64 by exact bit conversion and one FP64 add.
+//
+// Mean-flow terms (Eq. NS_cyl with u_theta = U + u'_theta, U = Re u_theta^{(0,0)}):
+//   N_pm += (U/r) i m m_p u'_pm + i (U/r)(u'_+ - u'_-) +- (i/2)(d_r U + U/r)(u'_+ + u'_-),
+//   N_z  += (U/r) i m m_p u'_z,   and -U^2/r on the (0,0) mode of N_pm.
+// Collected per output: N_+ += i (A u'_+ - B u'_-), N_- += i (C u'_- + B u'_+),
+// N_z += i t u'_z, with t = (U/r) m m_p, q = (d_r U + U/r)/2, A = t + U/r + q, B = U/r - q,
+// C = t - U/r - q.
+#include "tc_internal.cuh"
+#include "tc_fft_core.cuh"
+#include "tc_fftc.cuh"
+
+namespace tc {
+
+namespace {
+
+// ---------------------------------------------------------------- exact splitting
+// (hi, lo) with hi = d truncated to 24 significant bits and lo = the next 23 bits of d, both
+// read off the bit pattern: |d - hi - lo| < 2^-46 |d|.  |d| < 2^-126 gives (0, 0), which is
+// below any value the state carries at a resolvable level; |d| >= 2^128 gives +-inf and NaN
+// stays NaN, so a non-finite state still shows in the output.
+__device__ __forceinline__ float2 split_hl(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned int h = (unsigned int)(b >> 32);
+    const unsigned int l = (unsigned int)b;
+    const unsigned int s = h & 0x80000000u;
+    const int e = (int)((h >> 20) & 0x7ffu);
+    float2 r;
+    if (e <= 896) {
+        r.x = 0.f;
+        r.y = 0.f;
+        return r;
+    }
+    if (e >= 1151) {
+        const bool nan = e == 2047 && (((h & 0xfffffu) | l) != 0u);
+        r.x = __uint_as_float(s | 0x7f800000u | (nan ? 0x400000u : 0u));
+        r.y = 0.f;
+        return r;
+    }
+    const unsigned int top = ((h & 0xfffffu) << 3) | (l >> 29);
+    r.x = __uint_as_float(s | ((unsigned int)(e - 896) << 23) | top);
+    // low 29 mantissa bits have weight 2^(e - 1075); their top 23 (weight 2^(e - 1069)) as an
+    // exact float: 2^23 + n has the bit pattern 0x4b000000 | n for n < 2^23
+    const unsigned int rem = (l & 0x1fffffffu) >> 6;
+    const float fr = __fsub_rn(__uint_as_float(0x4b000000u | rem), 8388608.0f);
+    const int es = e - 942;   // biased FP32 exponent of 2^(e - 1069)
+    const float sc = es > 0 ? __uint_as_float((unsigned int)es << 23) : 0.f;
+    r.y = __uint_as_float(__float_as_uint(__fmul_rn(fr, sc)) | s);
+    return r;
+}
+
+// FP32 -> FP64 by the bit pattern (exact; FP32 subnormals, never produced here, give 0)
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xffu;
+    const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+    if (e == 0u) return __longlong_as_double((long long)s);
+    const unsigned long long ed = e == 255u ? 2047ull : (unsigned long long)(e + 896u);
+    const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
+    return __longlong_as_double((long long)(s | (ed << 52) | m));
+}
+
+// error-free transformations (Dekker's product via FMA, Knuth's sum); the _rn intrinsics keep
+// the compiler from contracting them into FMAs
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (ah + al)(xh + xl) + (bh + bl)(yh + yl) as an unevaluated pair (s, t), |error| ~ 2^-44 of
+// the larger product
+__device__ __forceinline__ void dot2(float ah, float al, float xh, float xl, float bh, float bl,
+                                     float yh, float yl, float& s, float& t) {
+    float p1, e1, p2, e2;
+    two_prod(ah, xh, p1, e1);
+    e1 = __fmaf_rn(ah, xl, __fmaf_rn(al, xh, e1));
+    two_prod(bh, yh, p2, e2);
+    e2 = __fmaf_rn(bh, yl, __fmaf_rn(bl, yh, e2));
+    two_sum(p1, p2, s, t);
+    t = __fadd_rn(t, __fadd_rn(e1, e2));
+}
+
+// v + (s + t) in FP64: the FP32 sum is formed error-free, then one FP64 add of exact parts
+__device__ __forceinline__ double assemble(float v, float s, float t) {
+    float a, b;
+    two_sum(v, s, a, b);
+    b = __fadd_rn(b, t);
+    return f2d_bits(a) + f2d_bits(b);
+}
+
+constexpr int kPrepK = 32;   // k values per block (one warp row)
+constexpr int kPrepR = 32;   // rows per block
+constexpr int kPrepWin = kPrepR + kStencil - 1;
+
+}  // namespace
+
+// ---------------------------------------------------------------- u' and d_r u' in FP32
+// P[(d * 3 + c) * S + (r (M+1) + m) nk + kk], d = 0: u', d = 1: d_r u'.
+__global__ void __launch_bounds__(256) k_prep32(const double2* __restrict__ u, float2* __restrict__ P,
+                                                const float* __restrict__ w1f, const int* __restrict__ col0,
+                                                int N_r, int M, int K, int nkt, int nrc) {
+    __shared__ float4 win[kPrepWin * kPrepK];
+    __shared__ float sw[kPrepR * kStencil];
+    int b = blockIdx.x;
+    const int kt = b % nkt;
+    b /= nkt;
+    const int rc = b % nrc;
+    b /= nrc;
+    const int m = b % (M + 1);
+    const int c = b / (M + 1);
+    const int nk = 2 * K + 1;
+    const size_t S = (size_t)N_r * (M + 1) * nk;
+    const size_t colstride = (size_t)(M + 1) * nk;
+    const int r0 = rc * kPrepR;
+    const int r1 = min(r0 + kPrepR, N_r) - 1;
+    const int jlo = col0[r0];
+    const int jhi = col0[r1] + kStencil - 1;   // window rows jlo..jhi, at most kPrepWin
+    const int kk = kt * kPrepK + threadIdx.x;
+    const bool kin = kk < nk;
+    // u' = u - U e_theta: on the (0,0) mode Im u'_+ = Im u'_- = (Im u_+ + Im u_-) / 2
+    const bool sub = m == 0 && kk == K && c < 2;
+    const int tid = threadIdx.y * kPrepK + threadIdx.x;
+    for (int i = tid; i < (r1 - r0 + 1) * kStencil; i += blockDim.x * blockDim.y)
+        sw[i] = w1f[(size_t)r0 * kStencil + i];
+    const double2* base = u + (size_t)c * S + (size_t)m * nk + kk;
+    const double2* other = u + (size_t)(c == 1 ? 0 : 1) * S + (size_t)m * nk + kk;   // read only if c < 2
+    for (int j = jlo + threadIdx.y; j <= jhi; j += blockDim.y) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kin) {
+            double2 x = base[(size_t)j * colstride];
+            if (sub) x.y = 0.5 * (x.y + other[(size_t)j * colstride].y);
+            const float2 a = split_hl(x.x), q = split_hl(x.y);
+            v = make_float4(a.x, q.x, a.y, q.y);   // (hi re, hi im, lo re, lo im)
+        }
+        win[(j - jlo) * kPrepK + threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (!kin) return;
+    float2* Pu = P + (size_t)c * S + (size_t)m * nk + kk;
+    float2* Pd = P + (size_t)(3 + c) * S + (size_t)m * nk + kk;
+    for (int r = r0 + threadIdx.y; r <= r1; r += blockDim.y) {
+        const float4 cen = win[(r - jlo) * kPrepK + threadIdx.x];
+        const int w0 = (col0[r] - jlo) * kPrepK + threadIdx.x;
+        const float* w = sw + (r - r0) * kStencil;
+        float dre = 0.f, dim = 0.f;
+#pragma unroll
+        for (int t = 0; t < kStencil; ++t) {
+            const float4 v = win[w0 + t * kPrepK];
+            const float ddr = __fadd_rn(__fsub_rn(v.x, cen.x), __fsub_rn(v.z, cen.z));
+            const float ddi = __fadd_rn(__fsub_rn(v.y, cen.y), __fsub_rn(v.w, cen.w));
+            dre = __fmaf_rn(w[t], ddr, dre);
+            dim = __fmaf_rn(w[t], ddi, dim);
+        }
+        Pu[(size_t)r * colstride] = make_float2(__fadd_rn(cen.x, cen.z), __fadd_rn(cen.y, cen.w));
+        Pd[(size_t)r * colstride] = make_float2(dre, dim);
+    }
+}
+
+// ---------------------------------------------------------------- inverse z-pass, FP32
+// Field f of H1: f = 3 d + c, d in {u', d_r u', d_z u'}.  Line q of the padded transform holds
+// wavenumber k = q (q <= K) or q - P_z (q >= P_z - K), zero between.
+__device__ __forceinline__ float2 zinv_input(const float2* __restrict__ P, size_t S, size_t line, int f,
+                                             int q, int K, int Pz, float kzf) {
+    const int k = q <= K ? q : q - Pz;
+    if (k < -K) return make_float2(0.f, 0.f);
+    const int c = f % 3, d = f / 3;
+    const float2 x = P[(size_t)((d == 1 ? 3 : 0) + c) * S + line + k];
+    if (d != 2) return x;
+    const float kk = kzf * (float)k;
+    return make_float2(-kk * x.y, kk * x.x);
+}
+
+// generic length: runtime radices, L lines per block
+__global__ void __launch_bounds__(256) k_zinv_p32(const float2* __restrict__ P, float2* __restrict__ H1,
+                                                  int N_r, int M, int K, float kzf, int L,
+                                                  const float2* __restrict__ tw, Radices rad) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Pz = rad.n;
+    float2* a = reinterpret_cast<float2*>(smem_raw);
+    float2* b = a + (size_t)L * Pz;
+    const int groups = 9 / L;
+    const int g = blockIdx.x % groups;
+    const int rm = blockIdx.x / groups;
+    const int r = rm % N_r;
+    const int m = rm / N_r;
+    const int nk = 2 * K + 1;
+    const size_t S = (size_t)N_r * (M + 1) * nk;
+    const size_t line = ((size_t)r * (M + 1) + m) * nk + K;
+    for (int idx = threadIdx.x; idx < L * Pz; idx += blockDim.x) {
+        const int l = idx / Pz;
+        const int q = idx - l * Pz;
+        a[idx] = zinv_input(P, S, line, g * L + l, q, K, Pz, kzf);
+    }
+    __syncthreads();
+    float2* res = smem_fft(a, b, L, tw, true, rad);
+    for (int idx = threadIdx.x; idx < L * Pz; idx += blockDim.x) {
+        const int l = idx / Pz;
+        const int z = idx - l * Pz;
+        const int f = g * L + l;
+        H1[(((size_t)f * N_r + r) * (M + 1) + m) * Pz + z] = res[idx];
+    }
+}
+
+// compile-time length PZ, L lines per block
+template <int PZ, int L, int NT>
+__global__ void __launch_bounds__(NT) k_zinv_s(const float2* __restrict__ P, float2* __restrict__ H1,
+                                               int N_r, int M, int K, float kzf, const float2* __restrict__ tw) {
+    constexpr int LP = cft::padded<PZ>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* a = reinterpret_cast<float2*>(smem_raw);
+    float2* b = a + L * LP;
+    constexpr int groups = 9 / L;
+    const int g = blockIdx.x % groups;
+    const int rm = blockIdx.x / groups;
+    const int r = rm % N_r;
+    const int m = rm / N_r;
+    const int nk = 2 * K + 1;
+    const size_t S = (size_t)N_r * (M + 1) * nk;
+    const size_t line = ((size_t)r * (M + 1) + m) * nk + K;
+    // all loads of the thread first (compile-time trip counts), then the shared-memory stores
+    constexpr int NQ = (PZ + NT - 1) / NT;
+    float2 vals[L][NQ];
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            const int q = threadIdx.x + i * NT;
+            vals[l][i] = q < PZ ? zinv_input(P, S, line, g * L + l, q, K, PZ, kzf) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            const int q = threadIdx.x + i * NT;
+            if (q < PZ) a[l * LP + cft::pd(q)] = vals[l][i];
+        }
+    __syncthreads();
+    const float2* X = cft::passes<PZ, 0, 1, L, NT, true, float2, false>(a, b, tw);
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        float2* dst = H1 + (((size_t)(g * L + l) * N_r + r) * (M + 1) + m) * PZ;
+        for (int z = threadIdx.x; z < PZ; z += NT) dst[z] = X[l * LP + cft::pd(z)];
+    }
+}
+
+// ---------------------------------------------------------------- forward z-pass, FP32
+// thread 0: U/r, q = (d_r U + U/r)/2 and U in FP64 from the (0,0) column; the coefficients
+// A, B, C, t of the mean-flow terms as (hi, lo) pairs
+__device__ __forceinline__ void mean_flow_coeffs(const double2* __restrict__ u, const double* __restrict__ rnodes,
+                                                 const double* __restrict__ w1, const int* __restrict__ col0,
+                                                 int r, int m, int M, int K, size_t S, double mp,
+                                                 float* s_cf, double* s_mf) {
+    const int nk = 2 * K + 1;
+    const size_t col = (size_t)(M + 1) * nk;
+    const double2* up = u + K;
+    const double2* um = u + S + K;
+    double dU = 0.0;
+    const int c0 = col0[r];
+    for (int t = 0; t < kStencil; ++t)
+        dU += w1[r * kStencil + t] * 0.5 * (up[(size_t)(c0 + t) * col].y - um[(size_t)(c0 + t) * col].y);
+    const double U = 0.5 * (up[(size_t)r * col].y - um[(size_t)r * col].y);
+    const double Ur = U / rnodes[r];
+    const double q = 0.5 * (dU + Ur);
+    const double t = Ur * mp * m;
+    const double cf[4] = {t + Ur + q, Ur - q, t - Ur - q, t};
+    for (int i = 0; i < 4; ++i) {
+        const float2 x = split_hl(cf[i]);
+        s_cf[2 * i] = x.x;
+        s_cf[2 * i + 1] = x.y;
+    }
+    s_mf[0] = Ur;
+    s_mf[1] = q;
+    s_mf[2] = U;
+}
+
+// one output coefficient: scale * v plus the mean-flow terms of component c at (r, m, k), e
+__device__ __forceinline__ double2 zfwd_coeff(float2 v, float scale, int c, int m, int k, size_t e, size_t S,
+                                              const double2* __restrict__ u, const float* s_cf,
+                                              const double* s_mf) {
+    const float vr = __fmul_rn(v.x, scale), vi = __fmul_rn(v.y, scale);
+    double2 o;
+    if (m == 0 && k == 0) {
+        // (0,0) mode: t = 0; u'_pm with the averaged imaginary part; -U^2/r on N_pm
+        o = make_double2(f2d_bits(vr), f2d_bits(vi));
+        if (c < 2) {
+            const double Ur = s_mf[0], q = s_mf[1], U = s_mf[2];
+            double2 ap = u[e], am = u[S + e];
+            const double im = 0.5 * (ap.y + am.y);
+            ap.y = im;
+            am.y = im;
+            const double sg = c == 0 ? 1.0 : -1.0;
+            const double dx = ap.x - am.x, dy = ap.y - am.y;
+            const double sx = ap.x + am.x, sy = ap.y + am.y;
+            o.x += -Ur * dy - sg * q * sy - Ur * U;
+            o.y += Ur * dx + sg * q * sx;
+        }
+        return o;
+    }
+    // N += i (alpha x + beta y)
+    float ah, al, bh = 0.f, bl = 0.f;
+    double2 x, y = make_double2(0.0, 0.0);
+    if (c == 0) {
+        ah = s_cf[0]; al = s_cf[1]; bh = -s_cf[2]; bl = -s_cf[3];
+        x = u[e]; y = u[S + e];
+    } else if (c == 1) {
+        ah = s_cf[4]; al = s_cf[5]; bh = s_cf[2]; bl = s_cf[3];
+        x = u[S + e]; y = u[e];
+    } else {
+        ah = s_cf[6]; al = s_cf[7];
+        x = u[2 * S + e];
+    }
+    const float2 xr = split_hl(x.x), xi = split_hl(x.y);
+    const float2 yr = split_hl(y.x), yi = split_hl(y.y);
+    float s, t;
+    dot2(ah, al, xi.x, xi.y, bh, bl, yi.x, yi.y, s, t);   // alpha Im x + beta Im y
+    o.x = assemble(vr, -s, -t);
+    dot2(ah, al, xr.x, xr.y, bh, bl, yr.x, yr.y, s, t);   // alpha Re x + beta Re y
+    o.y = assemble(vi, s, t);
+    return o;
+}
+
+// generic length
+__global__ void __launch_bounds__(256) k_zfwd32(const float2* __restrict__ H2, double2* __restrict__ N,
+                                                int N_r, int M, int K, float scale,
+                                                const float2* __restrict__ tw, Radices rad,
+                                                const double2* __restrict__ u, const double* __restrict__ rnodes,
+                                                const double* __restrict__ w1, const int* __restrict__ col0,
+                                                double mp, int Lf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float s_cf[8];    // A, B, C, t as (hi, lo)
+    __shared__ double s_mf[3];   // U/r, q, U (the (0,0) mode is assembled in FP64)
+    const int Pz = rad.n;
+    float2* a = reinterpret_cast<float2*>(smem_raw);
+    float2* b = a + (size_t)Lf * Pz;
+    const int cg = blockIdx.x % (3 / Lf);
+    const int m = (blockIdx.x / (3 / Lf)) % (M + 1);
+    const int r = (blockIdx.x / (3 / Lf)) / (M + 1);
+    const size_t fstride = (size_t)N_r * (M + 1) * Pz;
+    const float2* h = H2 + ((size_t)r * (M + 1) + m) * Pz;
+    const int nk = 2 * K + 1;
+    const size_t S = (size_t)N_r * (M + 1) * nk;
+    for (int idx = threadIdx.x; idx < Lf * Pz; idx += blockDim.x) {
+        const int l = idx / Pz;
+        const int z = idx - l * Pz;
+        a[idx] = h[(cg * Lf + l) * fstride + z];
+    }
+    if (threadIdx.x == 0) mean_flow_coeffs(u, rnodes, w1, col0, r, m, M, K, S, mp, s_cf, s_mf);
+    __syncthreads();
+    float2* res = smem_fft(a, b, Lf, tw, false, rad);
+    for (int idx = threadIdx.x; idx < Lf * nk; idx += blockDim.x) {
+        const int l = idx / nk;
+        const int kk = idx - l * nk;
+        const int k = kk - K;
+        const size_t e = ((size_t)r * (M + 1) + m) * nk + kk;
+        const int c = cg * Lf + l;
+        N[(size_t)c * S + e] = zfwd_coeff(res[(size_t)l * Pz + (k < 0 ? k + Pz : k)], scale, c, m, k, e, S, u, s_cf, s_mf);
+    }
+}
+
+// compile-time length PZ, LF components per block
+template <int PZ, int LF, int NT>
+__global__ void __launch_bounds__(NT) k_zfwd_s(const float2* __restrict__ H2, double2* __restrict__ N,
+                                               int N_r, int M, int K, float scale, const float2* __restrict__ tw,
+                                               const double2* __restrict__ u, const double* __restrict__ rnodes,
+                                               const double* __restrict__ w1, const int* __restrict__ col0,
+                                               double mp) {
+    constexpr int LP = cft::padded<PZ>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float s_cf[8];
+    __shared__ double s_mf[3];
+    float2* a = reinterpret_cast<float2*>(smem_raw);
+    float2* b = a + LF * LP;
+    constexpr int groups = 3 / LF;
+    const int cg = blockIdx.x % groups;
+    const int m = (blockIdx.x / groups) % (M + 1);
+    const int r = (blockIdx.x / groups) / (M + 1);
+    const size_t fstride = (size_t)N_r * (M + 1) * PZ;
+    const float2* h = H2 + ((size_t)r * (M + 1) + m) * PZ;
+    const int nk = 2 * K + 1;
+    const size_t S = (size_t)N_r * (M + 1) * nk;
+    constexpr int NQ = (PZ + NT - 1) / NT;
+    {
+        float2 vals[LF][NQ];
+#pragma unroll
+        for (int l = 0; l < LF; ++l)
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) {
+                const int z = threadIdx.x + i * NT;
+                vals[l][i] = z < PZ ? h[(cg * LF + l) * fstride + z] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+        for (int l = 0; l < LF; ++l)
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) {
+                const int z = threadIdx.x + i * NT;
+                if (z < PZ) a[l * LP + cft::pd(z)] = vals[l][i];
+            }
+    }
+    if (threadIdx.x == 0) mean_flow_coeffs(u, rnodes, w1, col0, r, m, M, K, S, mp, s_cf, s_mf);
+    __syncthreads();
+    const float2* X = cft::passes<PZ, 0, 1, LF, NT, false, float2, false>(a, b, tw);
+    const size_t e0 = ((size_t)r * (M + 1) + m) * nk;
+    // one thread per k for all LF components of the block
+    for (int kk = threadIdx.x; kk < nk; kk += NT) {
+        const int k = kk - K;
+        const int z = k < 0 ? k + PZ : k;
+#pragma unroll
+        for (int l = 0; l < LF; ++l) {
+            const int c = cg * LF + l;
+            N[(size_t)c * S + e0 + kk] = zfwd_coeff(X[l * LP + cft::pd(z)], scale, c, m, k, e0 + kk, S, u, s_cf, s_mf);
+        }
+    }
+}
+
+namespace {
+
+template <int PZ, int L, int LF, int NT>
+tc_status run_zpasses_s(tc_plan* p, const float2* P, float2* H1, const float2* H2, const double2* u, double2* N,
+                        cudaStream_t s, bool inverse) {
+    constexpr int LP = cft::padded<PZ>();
+    if (inverse) {
+        const size_t sm = (size_t)2 * L * LP * sizeof(float2);
+        TC_CUDA(p, cudaFuncSetAttribute(k_zinv_s<PZ, L, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        const int slot = prof_begin(p, kKZinv32, s);
+        k_zinv_s<PZ, L, NT><<<p->N_r * (p->M + 1) * (9 / L), NT, sm, s>>>(P, H1, p->N_r, p->M, p->K, (float)p->k_z,
+                                                                         p->d_tw_z32);
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_zinv_s");
+    } else {
+        const size_t sm = (size_t)2 * LF * LP * sizeof(float2);
+        TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_s<PZ, LF, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        const float scale = (float)(1.0 / ((double)p->P_t * (double)p->P_z));
+        const int slot = prof_begin(p, kKZfwd32, s);
+        k_zfwd_s<PZ, LF, NT><<<p->N_r * (p->M + 1) * (3 / LF), NT, sm, s>>>(H2, N, p->N_r, p->M, p->K, scale,
+                                                                           p->d_tw_z32, u, p->d_r, p->d_w1,
+                                                                           p->d_col0, (double)p->m_p);
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_zfwd_s");
+    }
+    return TC_OK;
+}
+
+// length-specialised z passes; TC_ERR_ARG if P_z has no compile-time plan
+tc_status zpass_s(tc_plan* p, const float2* P, float2* H1, const float2* H2, const double2* u, double2* N,
+                  cudaStream_t s, bool inverse) {
+    switch (p->P_z) {
+        case 12: return run_zpasses_s<12, 9, 3, 64>(p, P, H1, H2, u, N, s, inverse);
+        case 24: return run_zpasses_s<24, 9, 3, 64>(p, P, H1, H2, u, N, s, inverse);
+        case 48: return run_zpasses_s<48, 9, 3, 128>(p, P, H1, H2, u, N, s, inverse);
+        case 96: return run_zpasses_s<96, 9, 3, 128>(p, P, H1, H2, u, N, s, inverse);
+        case 192: return run_zpasses_s<192, 9, 3, 256>(p, P, H1, H2, u, N, s, inverse);
+        case 384: return run_zpasses_s<384, 3, 3, 128>(p, P, H1, H2, u, N, s, inverse);
+        case 768: return run_zpasses_s<768, 3, 3, 256>(p, P, H1, H2, u, N, s, inverse);
+        case 1152: return run_zpasses_s<1152, 3, 3, 256>(p, P, H1, H2, u, N, s, inverse);
+        case 1536: return run_zpasses_s<1536, 3, 3, 256>(p, P, H1, H2, u, N, s, inverse);
+        case 2304: return run_zpasses_s<2304, 1, 1, 256>(p, P, H1, H2, u, N, s, inverse);
+        case 3072: return run_zpasses_s<3072, 1, 1, 256>(p, P, H1, H2, u, N, s, inverse);
+    }
+    return TC_ERR_ARG;
+}
+
+bool zpass_s_ok(const tc_plan* p) {
+    switch (p->P_z) {
+        case 12: case 24: case 48: case 96: case 192: case 384: case 768: case 1152: case 1536: case 2304: case 3072:
+            return p->theta_zt_forced == 0;
+    }
+    return false;
+}
+
+}  // namespace
+
+tc_status launch_nonlinear_mixed(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s) {
+    float2* P = reinterpret_cast<float2*>(ws + p->ws.P32);   // aliases H2: dead before the theta pass
+    float2* H1 = reinterpret_cast<float2*>(ws + p->ws.H1);
+    float2* H2 = reinterpret_cast<float2*>(ws + p->ws.H2);
+    const int nk = 2 * p->K + 1;
+    const int nkt = (nk + kPrepK - 1) / kPrepK;
+    const int nrc = (p->N_r + kPrepR - 1) / kPrepR;
+    int slot = prof_begin(p, kKPrep32, s);
+    k_prep32<<<(unsigned)(nkt * nrc * (p->M + 1) * 3), dim3(kPrepK, 8), 0, s>>>(u, P, p->d_w1f, p->d_col0, p->N_r,
+                                                                             p->M, p->K, nkt, nrc);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_prep32");
+    // length-specialised kernels where the plan's lengths have compile-time radix plans, unless
+    // the plan fixed the generic theta kernel's z tile (tc_options.theta_zt)
+    const bool zs = zpass_s_ok(p);
+    if (zs) {
+        TC_TRY_STATUS(zpass_s(p, P, H1, H2, u, N, s, true));
+    } else {
+        const int L = p->zinv_lines32;
+        const size_t sm1 = (size_t)2 * L * p->P_z * sizeof(float2);
+        TC_CUDA(p, cudaFuncSetAttribute(k_zinv_p32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+        slot = prof_begin(p, kKZinv32, s);
+        k_zinv_p32<<<p->N_r * (p->M + 1) * (9 / L), 256, sm1, s>>>(P, H1, p->N_r, p->M, p->K, (float)p->k_z, L,
+                                                                    p->d_tw_z32, p->rad_z);
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_zinv_p32");
+    }
+    if (p->theta_zt_forced == 0 && theta_s_zt(p, false) > 0) TC_TRY_STATUS(launch_theta_s(p, H1, H2, s));
+    else TC_TRY_STATUS(launch_theta32(p, H1, H2, s));
+    if (zs) return zpass_s(p, P, H1, H2, u, N, s, false);
+    const int Lf = p->zfwd_lines32;
+    const size_t sm3 = (size_t)2 * Lf * p->P_z * sizeof(float2);
+    TC_CUDA(p, cudaFuncSetAttribute(k_zfwd32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+    const float scale = (float)(1.0 / ((double)p->P_t * (double)p->P_z));
+    slot = prof_begin(p, kKZfwd32, s);
+    k_zfwd32<<<p->N_r * (p->M + 1) * (3 / Lf), 256, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, p->d_tw_z32,
+                                                               p->rad_z, u, p->d_r, p->d_w1, p->d_col0,
+                                                               (double)p->m_p, Lf);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_zfwd32");
+    return TC_OK;
+}
+
+}  // namespace tc

@@ -233,6 +233,8 @@ static tc_status upload(tc_plan* p) {
     for (size_t j = 0; j < ir.size(); ++j) ir[j] = 1.0 / p->r[j];
     TC_CUDA(p, put((void**)&p->d_ir, ir.data(), ir.size() * sizeof(double)));
     TC_CUDA(p, put((void**)&p->d_w1, p->w1.data(), p->w1.size() * sizeof(double)));
+    std::vector<float> w1f(p->w1.begin(), p->w1.end());
+    TC_CUDA(p, put((void**)&p->d_w1f, w1f.data(), w1f.size() * sizeof(float)));
     TC_CUDA(p, put((void**)&p->d_w2, p->w2.data(), p->w2.size() * sizeof(double)));
     TC_CUDA(p, put((void**)&p->d_col0, p->col0.data(), p->col0.size() * sizeof(int)));
     TC_CUDA(p, put((void**)&p->d_d1t_row, p->d1t_row.data(), p->d1t_row.size() * sizeof(int)));
@@ -252,7 +254,7 @@ const char* const kKernelNames[kNumKernels] = {
     "k_zinv", "k_theta", "k_zfwd", "k_rhs_pressure", "k_band_solve_P", "k_rhs_velocity",
     "k_band_solve_H", "k_rhs_div", "k_update", "k_axpby", "k_diag", "k_zinv_f32",
     "k_theta_f32", "k_zfwd_f32", "k_mean_flow", "k_pc", "k_pc_adj", "k_zinv_adjin",
-    "k_theta_adj", "k_zfwd_adj", "k_drT"};
+    "k_theta_adj", "k_zfwd_adj", "k_drT", "k_prep_f32"};
 
 int prof_begin(tc_plan* p, int kid, cudaStream_t s) {
     if (!p->prof_on) return -1;
@@ -279,7 +281,7 @@ void prof_end(tc_plan* p, int slot, cudaStream_t s) {
 static void free_device(tc_plan* p) {
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     p->prof_ev.clear();
-    void* ptrs[] = {p->d_r, p->d_ir, p->d_w1, p->d_w2, p->d_col0, p->d_d1t_row, p->d_d1t_w, p->d_fac, p->d_piv,
+    void* ptrs[] = {p->d_r, p->d_ir, p->d_w1, p->d_w1f, p->d_w2, p->d_col0, p->d_d1t_row, p->d_d1t_w, p->d_fac, p->d_piv,
                     p->d_tw_z, p->d_tw_t, p->d_tw_z32, p->d_tw_t32};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -425,16 +427,23 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     p->zt = zt_for(sizeof(double2), o.theta_zt > 0 ? o.theta_zt : 4, 200 * 1024);
     p->zt32 = zt_for(sizeof(float2), o.theta_zt > 0 ? o.theta_zt : 8, o.theta_zt > 0 ? 200 * 1024 : 76 * 1024);
     p->pc_modes = o.pc_modes;
+    p->theta_zt_forced = o.theta_zt;
+    p->theta_variant = o.theta_variant;
     p->thr_zinv = choose_threads(rz, p->zinv_lines, 0);
     p->thr_theta = choose_threads(rt, 6 * p->zt, p->zt + (p->zt + 1) / 2);
     p->thr_zfwd = choose_threads(rz, p->zfwd_lines, 0);
-    if (o.theta_zt < 0 || o.theta_zt > 64 || o.pc_modes < 0 || o.pc_modes > 32 || o.pc_split < -1 || o.pc_split > 1) {
+    if (o.theta_zt < 0 || o.theta_zt > 64 || o.pc_modes < 0 || o.pc_modes > 32 || o.pc_split < -1 || o.pc_split > 1 ||
+        o.theta_variant < 0 || o.theta_variant > 3) {
         delete p;
         return TC_ERR_ARG;
     }
-    if ((size_t)2 * 3 * Pz * cplx > 220 * 1024 || (size_t)2 * 6 * Pt * cplx > 220 * 1024) {
-        delete p;
-        return TC_ERR_ARG;   // transform lines too long for one block's shared memory
+    {
+        // FP64 lines unless the plan is mixed without the (FP64) adjoint
+        const size_t lb = (o.precision == TC_MIXED && o.no_adjoint) ? sizeof(float2) : cplx;
+        if ((size_t)2 * 3 * Pz * lb > 220 * 1024 || (size_t)2 * 6 * Pt * lb > 220 * 1024) {
+            delete p;
+            return TC_ERR_ARG;   // transform lines too long for one block's shared memory
+        }
     }
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o2 = off; off = align256(off + bytes); return o2; };
@@ -443,7 +452,11 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     p->adjoint = o.no_adjoint == 0;
     const size_t lane = (p->precision == TC_MIXED && !p->adjoint) ? sizeof(float2) : cplx;
     p->ws.H1 = take(9 * p->Hfield * lane);
-    p->ws.H2 = take(3 * p->Hfield * lane);
+    // the mixed form's FP32 u', d_r u' live between k_prep32 and k_zinv_p32, before k_theta
+    // writes H2, so they share its region
+    const size_t p32 = p->precision == TC_MIXED ? 6 * p->S * sizeof(float2) : 0;
+    p->ws.H2 = take(std::max(3 * p->Hfield * lane, p32));
+    p->ws.P32 = p->ws.H2;
     p->ws.Ncur = take(3 * p->S * cplx);
     p->ws.uE = take(3 * p->S * cplx);
     // steps 2-5: fused kernel while 8 modes' four columns fit in 96 KB of shared memory,

@@ -1,0 +1,253 @@
+// Length-specialised theta pass (Sec. 3.2 step 1, Eq. NS_cyl) for the common transform
+// lengths, FP32 or FP64 lines.  Same input (H1) and output (H2) as k_theta, organised
+// differently:
+//
+//  * the radices of each length are compile-time constants (e.g. 768 = 16 * 16 * 3 for FP32
+//    lines), so the Stockham index arithmetic folds and fewer passes are needed;
+//  * lines sit in shared memory with one padding slot per 32 entries, which makes the
+//    stride-R stores of the first pass and all later accesses bank-conflict free;
+//  * the products are streamed: u is transformed first and kept per physical point (in shared
+//    memory, each point owned by one thread), then the derivative line pairs go through the
+//    transform two lines per z at a time and are accumulated into N.  Only 2 lines per z are
+//    resident instead of 6, so a block holds several z values, and the H1 loads and H2 stores
+//    of a (field, m) cover 16- or 32-byte runs along z.
+#include "tc_internal.cuh"
+#include "tc_fftc.cuh"
+
+namespace tc {
+
+using namespace cft;
+
+namespace {
+
+// ---------------------------------------------------------------- spectra of two line kinds
+// pair line x = c_r + i c_t from (A, B) = (c_+, c_-): spectrum A_m at m > 0, conj(B_m) at -m,
+// (A_0 + conj B_0)/2 at 0.  Real-pair line x + i y from (X, Y): X_m + i Y_m at m, conj(X_m) +
+// i conj(Y_m) at -m.
+template <typename V>
+__device__ __forceinline__ void put_pair(V* line, int PTn, int m, V A, V B) {
+    using T = typename Elem<V>::T;
+    if (m == 0) {
+        line[0] = vmk<V>((T)0.5 * (A.x + B.x), (T)0.5 * (A.y - B.y));
+    } else {
+        line[pd(m)] = A;
+        line[pd(PTn - m)] = vmk<V>(B.x, -B.y);
+    }
+}
+template <typename V>
+__device__ __forceinline__ void put_real2(V* line, int PTn, int m, V X, V Y) {
+    if (m == 0) {
+        line[0] = vmk<V>(X.x, Y.x);
+    } else {
+        line[pd(m)] = vmk<V>(X.x - Y.y, X.y + Y.x);
+        line[pd(PTn - m)] = vmk<V>(X.x + Y.y, Y.x - X.y);
+    }
+}
+template <typename V>
+__device__ __forceinline__ V imul(V a, typename Elem<V>::T s) { return vmk<V>(-s * a.y, s * a.x); }
+
+}  // namespace
+
+// H1 fields: f = 3 d + c, c in {+, -, z}, d in {u, d_r u, d_z u}.
+// Phase 0: lines (u_r, u_t) and (u_z, d_r u_z); phase 1: (d_r u_r, d_r u_t) and
+// (d_t u_r, d_t u_t); phase 2: (d_z u_r, d_z u_t) and (d_t u_z, d_z u_z); then the forward
+// transform of N_r + i N_t (one line per z) and of N_z (two z per line).
+template <typename V, int PT, int ZT, int NT, int MINB, bool R8>
+__global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, V* __restrict__ H2,
+                                                      const double* __restrict__ rnodes, int N_r, int M, int Pz,
+                                                      double mp, const V* __restrict__ tw) {
+    using T = typename Elem<V>::T;
+    constexpr int LP = padded<PT>();
+    constexpr int NL = 2 * ZT;             // resident lines in a phase
+    constexpr int NLF = ZT + (ZT + 1) / 2;  // lines of the forward transform
+    constexpr int NPT = ZT * PT;           // physical points of the block
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* A = reinterpret_cast<V*>(smem_raw);
+    V* B = A + NL * LP;
+    // per physical point: Ua = (u_r, u_t / r), Ub = (u_z, N_z), Nn = (N_r, N_t); each point is
+    // owned by one thread in every phase
+    V* Ua = B + NL * LP;
+    V* Ub = Ua + NPT;
+    V* Nn = Ub + NPT;
+    const int tiles = Pz / ZT;
+    const int r = blockIdx.x / tiles;
+    const int z0 = (blockIdx.x % tiles) * ZT;
+    const size_t fstride = (size_t)N_r * (M + 1) * Pz;
+    const V* h = H1 + (size_t)r * (M + 1) * Pz + z0;
+    const T ir = (T)(1.0 / rnodes[r]);
+    const T mpf = (T)mp;
+    const int zi = threadIdx.x % ZT;        // z of this thread in the load and store loops
+    const int mstep = NT / ZT;
+
+#pragma unroll 1
+    for (int phase = 0; phase < 3; ++phase) {
+        // spectra of the two lines of each z (lines 2 zi and 2 zi + 1)
+        for (int m = (int)threadIdx.x / ZT; m <= M; m += mstep) {
+            const size_t o = (size_t)m * Pz + zi;
+            const T mm = mpf * (T)m;
+            V* L0 = A + (2 * zi) * LP;
+            V* L1 = L0 + LP;
+            if (phase == 0) {
+                put_pair(L0, PT, m, h[0 * fstride + o], h[1 * fstride + o]);
+                put_real2(L1, PT, m, h[2 * fstride + o], h[5 * fstride + o]);
+            } else if (phase == 1) {
+                put_pair(L0, PT, m, h[3 * fstride + o], h[4 * fstride + o]);
+                put_pair(L1, PT, m, imul(h[0 * fstride + o], mm), imul(h[1 * fstride + o], mm));
+            } else {
+                put_pair(L0, PT, m, h[6 * fstride + o], h[7 * fstride + o]);
+                put_real2(L1, PT, m, imul(h[2 * fstride + o], mm), h[8 * fstride + o]);
+            }
+        }
+        // zero band M < p < PT - M of every line
+        for (int l = 0; l < NL; ++l)
+            for (int q = M + 1 + (int)threadIdx.x; q < PT - M; q += NT) A[l * LP + pd(q)] = vmk<V>(0, 0);
+        __syncthreads();
+        const V* X = passes<PT, 0, 1, NL, NT, true, V, R8>(A, B, tw);
+        for (int pt = threadIdx.x; pt < NPT; pt += NT) {
+            const int z = pt / PT;
+            const int th = pt - z * PT;
+            const V p0 = X[(2 * z) * LP + pd(th)];
+            const V p1 = X[(2 * z + 1) * LP + pd(th)];
+            if (phase == 0) {
+                const T utr = p0.y * ir;
+                Ua[pt] = vmk<V>(p0.x, utr);
+                Ub[pt] = vmk<V>(p1.x, p0.x * p1.y);                      // N_z = u_r d_r u_z
+                Nn[pt] = vmk<V>(-p0.y * utr, utr * p0.x);                // curvature terms
+            } else if (phase == 1) {
+                const V a = Ua[pt];
+                V n = Nn[pt];
+                n.x += a.x * p0.x + a.y * p1.x;
+                n.y += a.x * p0.y + a.y * p1.y;
+                Nn[pt] = n;
+            } else {
+                const V a = Ua[pt];
+                V b = Ub[pt];
+                V n = Nn[pt];
+                n.x += b.x * p0.x;
+                n.y += b.x * p0.y;
+                Nn[pt] = n;
+                b.y += a.y * p1.x + b.x * p1.y;
+                Ub[pt] = b;
+            }
+        }
+        if (result_in_first<PT, R8>()) __syncthreads();   // the next fill overwrites X
+    }
+
+    // forward transform: line z holds N_r + i N_t, line ZT + z/2 holds N_z of two z values
+    for (int pt = threadIdx.x; pt < NPT; pt += NT) {
+        const int z = pt / PT;
+        const int th = pt - z * PT;
+        A[z * LP + pd(th)] = Nn[pt];
+        T* zl = reinterpret_cast<T*>(A + (ZT + z / 2) * LP + pd(th));
+        const T nz = Ub[pt].y;
+        if (z & 1) {
+            zl[1] = nz;
+        } else {
+            zl[0] = nz;
+            if (z + 1 == ZT) zl[1] = 0;
+        }
+    }
+    __syncthreads();
+    const V* Y = passes<PT, 0, 1, NLF, NT, false, V, R8>(A, B, tw);
+    for (int m = (int)threadIdx.x / ZT; m <= M; m += mstep) {
+        const int mneg = m ? PT - m : 0;
+        const V Q = Y[zi * LP + pd(m)];
+        const V Qm = Y[zi * LP + pd(mneg)];
+        const V* SL = Y + (ZT + zi / 2) * LP;
+        const V Sp = SL[pd(m)];
+        const V Smc = SL[pd(mneg)];
+        const V Sm = vmk<V>(Smc.x, -Smc.y);
+        V nz;
+        if (zi & 1) nz = vmk<V>((T)0.5 * (Sp.y - Sm.y), (T)0.5 * (Sm.x - Sp.x));   // (S - conj S-)/(2i)
+        else nz = vmk<V>((T)0.5 * (Sp.x + Sm.x), (T)0.5 * (Sp.y + Sm.y));
+        const size_t o = ((size_t)r * (M + 1) + m) * Pz + z0 + zi;
+        H2[o] = Q;
+        H2[fstride + o] = vmk<V>(Qm.x, -Qm.y);
+        H2[2 * fstride + o] = nz;
+    }
+}
+
+namespace {
+
+template <typename V, int PT, int ZT, int NT, int MINB, bool R8>
+tc_status run_theta_s(tc_plan* p, const V* H1, V* H2, const V* tw, cudaStream_t s) {
+    constexpr int LP = padded<PT>();
+    const size_t sm = ((size_t)2 * 2 * ZT * LP + (size_t)3 * ZT * PT) * sizeof(V);
+    auto kern = k_theta_s<V, PT, ZT, NT, MINB, R8>;
+    TC_CUDA(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int slot = prof_begin(p, sizeof(V) == 8 ? kKTheta32 : kKTheta, s);
+    kern<<<p->N_r * (p->P_z / ZT), NT, sm, s>>>(H1, H2, p->d_r, p->N_r, p->M, p->P_z, (double)p->m_p, tw);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_theta_s");
+    return TC_OK;
+}
+
+// FP32 launch shapes per length: variant 1 radices <= 16, Z z values per block, 2 blocks per
+// SM; variants 2 and 3 radices <= 8 (64 / 76 registers), half the z values per block, 4 / 3
+// blocks per SM.  Default (0): variant 2 up to P_theta = 96, where occupancy decides, and
+// variant 1 beyond, where the extra pass of the radix-8 plan costs more (measured on GB300:
+// 0.057 vs 0.082 ms at P_theta = 96; 14.1 vs 18.5 ms at 768)
+template <int PT, int Z, int NT>
+tc_status theta_s32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t s) {
+    const float2* tw = p->d_tw_t32;
+    constexpr int Zh = Z > 1 ? Z / 2 : 1;
+    const int v = p->theta_variant ? p->theta_variant : (PT <= 96 ? 2 : 1);
+    switch (v) {
+        case 2: return run_theta_s<float2, PT, Zh, NT, (NT > 256 ? 3 : 4), true>(p, H1, H2, tw, s);
+        case 3: return run_theta_s<float2, PT, Zh, NT, (NT > 256 ? 2 : 3), true>(p, H1, H2, tw, s);
+        default: return run_theta_s<float2, PT, Z, NT, 2, false>(p, H1, H2, tw, s);
+    }
+}
+
+}  // namespace
+
+// z values per block of the streamed theta pass for this plan and line type, 0 if none
+int theta_s_zt(const tc_plan* p, bool fp64) {
+    int zt = 0;
+    if (fp64) {
+        switch (p->P_t) {
+            case 96: zt = 4; break;
+            case 192: case 384: zt = 2; break;
+            case 768: case 1152: zt = 1; break;
+            default: return 0;
+        }
+    } else {
+        switch (p->P_t) {
+            case 48: case 96: zt = 8; break;
+            case 192: case 384: zt = 4; break;
+            case 768: case 1152: case 1536: zt = 2; break;
+            default: return 0;
+        }
+    }
+    if (2 * p->M + 1 > p->P_t || p->P_z % zt) return 0;
+    return zt;
+}
+
+tc_status launch_theta_s(tc_plan* p, const float2* H1, float2* H2, cudaStream_t s) {
+    if (theta_s_zt(p, false) == 0) return TC_ERR_ARG;
+    switch (p->P_t) {
+        case 48: return theta_s32<48, 8, 128>(p, H1, H2, s);
+        case 96: return theta_s32<96, 8, 256>(p, H1, H2, s);
+        case 192: return theta_s32<192, 4, 256>(p, H1, H2, s);
+        case 384: return theta_s32<384, 4, 256>(p, H1, H2, s);
+        case 768: return theta_s32<768, 2, 256>(p, H1, H2, s);
+        case 1152: return theta_s32<1152, 2, 384>(p, H1, H2, s);
+        case 1536: return theta_s32<1536, 2, 256>(p, H1, H2, s);
+    }
+    return TC_ERR_ARG;
+}
+
+tc_status launch_theta_s64(tc_plan* p, const double2* H1, double2* H2, cudaStream_t s) {
+    if (theta_s_zt(p, true) == 0) return TC_ERR_ARG;
+    const double2* tw = p->d_tw_t;
+    switch (p->P_t) {
+        case 96: return run_theta_s<double2, 96, 4, 128, 3, true>(p, H1, H2, tw, s);
+        case 192: return run_theta_s<double2, 192, 2, 128, 3, true>(p, H1, H2, tw, s);
+        case 384: return run_theta_s<double2, 384, 2, 256, 2, true>(p, H1, H2, tw, s);
+        case 768: return run_theta_s<double2, 768, 1, 256, 2, true>(p, H1, H2, tw, s);
+        case 1152: return run_theta_s<double2, 1152, 1, 384, 1, true>(p, H1, H2, tw, s);
+    }
+    return TC_ERR_ARG;
+}
+
+}  // namespace tc

@@ -183,6 +183,55 @@ def test_mixed_nonlinear_error_is_fp32_level_of_the_perturbation_part(cfg):
     assert err <= 1e-8 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("M,K", [(16, 8), (32, 8), (64, 8), (128, 8), (256, 4), (384, 4), (512, 4)])
+def test_mixed_theta_pass_lengths(M, K):
+    """Every length-specialised theta pass (P_theta = 48 ... 1536) against the oracle and
+    against the generic theta kernel (selected by an explicit theta_zt), on a broadband state
+    with all stored modes excited."""
+    cfg = dict(N_r=12, M=M, K=K, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=LZ, dt=1e-4)
+    ops = O.Operators(O.Params(**cfg))
+    u = init(ops, kind="broadband", amp=1e-2, seed=5)
+    ref = O.nonlinear(ops, u)
+    nrm = np.linalg.norm(O.nonlinear(ops, _mean_removed(ops, u)))
+    got = {}
+    for zt, variant in ((0, 0), (1, 0), (0, 2), (0, 3)):
+        plan = tc.Plan(**cfg, precision=tc.TC_MIXED, theta_zt=zt, no_adjoint=True, theta_variant=variant)
+        got[zt, variant] = host(plan.nonlinear(dev(u)))
+        err = np.linalg.norm(got[zt, variant] - ref)
+        assert err <= 2e-6 * nrm, (zt, variant, err / nrm)
+    assert np.linalg.norm(got[0, 0] - got[1, 0]) <= 2e-6 * nrm
+
+
+@pytest.mark.parametrize("M,K", [(32, 8), (64, 8), (128, 8), (256, 4), (384, 4)])
+def test_fp64_theta_pass_lengths(M, K):
+    """The length-specialised FP64 theta pass (P_theta = 96 ... 1152) and the generic one
+    (explicit theta_zt) both match the oracle to 1e-12 on a broadband state."""
+    cfg = dict(N_r=12, M=M, K=K, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=LZ, dt=1e-4)
+    ops = O.Operators(O.Params(**cfg))
+    u = init(ops, kind="broadband", amp=1e-2, seed=7)
+    ref = O.nonlinear(ops, u)
+    for zt in (0, 1):
+        plan = tc.Plan(**cfg, theta_zt=zt)
+        assert rel(host(plan.nonlinear(dev(u))), ref) <= 1e-12, zt
+
+
+@pytest.mark.parametrize("K", [128, 256, 384, 512, 768, 1024])
+def test_mixed_z_pass_lengths(K):
+    """The length-specialised z passes (P_z = 384 ... 3072) against the oracle and against the
+    generic z kernels (selected by an explicit theta_zt)."""
+    cfg = dict(N_r=9, M=2, K=K, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=LZ, dt=1e-4)
+    ops = O.Operators(O.Params(**cfg))
+    u = init(ops, kind="broadband", amp=1e-2, seed=6)
+    ref = O.nonlinear(ops, u)
+    nrm = np.linalg.norm(O.nonlinear(ops, _mean_removed(ops, u)))
+    got = {}
+    for zt in (0, 1):
+        plan = tc.Plan(**cfg, precision=tc.TC_MIXED, theta_zt=zt, no_adjoint=True)
+        got[zt] = host(plan.nonlinear(dev(u)))
+        assert np.linalg.norm(got[zt] - ref) <= 2e-6 * nrm, zt
+    assert np.linalg.norm(got[0] - got[1]) <= 2e-6 * nrm
+
+
 def test_mixed_twenty_steps_track_fp64():
     ops = O.Operators(O.Params(**CFG1))
     u0 = init(ops, amp=1e-2)
