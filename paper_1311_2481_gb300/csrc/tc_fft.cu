@@ -17,6 +17,7 @@
 // from a long-double table.
 #include "tc_internal.cuh"
 #include "tc_fft_core.cuh"
+#include "tc_fftc.cuh"
 
 namespace tc {
 
@@ -209,6 +210,153 @@ __global__ void __launch_bounds__(256) k_zfwd(const double2* __restrict__ H2, do
     }
 }
 
+// ---------------------------------------------------------------- length-specialised z passes
+// Same work as k_zinv / k_zfwd with compile-time radix plans (radices <= 8) and padded lines.
+__device__ __forceinline__ double2 zinv_value(const double2* __restrict__ u, const double* __restrict__ w1,
+                                              int c0, size_t S, size_t colstride, int r, int m, int nk,
+                                              int K, int f, int k, double kz) {
+    const int c = f % 3, d = f / 3;
+    const double2* base = u + (size_t)c * S + (size_t)m * nk + (k + K);
+    double2 x = make_double2(0.0, 0.0);
+    if (d == 1) {
+#pragma unroll
+        for (int t = 0; t < kStencil; ++t) {
+            const double w = __ldg(&w1[r * kStencil + t]);
+            const double2 y = __ldg(&base[(size_t)(c0 + t) * colstride]);
+            x.x += w * y.x;
+            x.y += w * y.y;
+        }
+    } else {
+        x = __ldg(&base[(size_t)r * colstride]);
+        if (d == 2) {
+            const double kk = kz * k;
+            x = make_double2(-kk * x.y, kk * x.x);
+        }
+    }
+    return x;
+}
+
+template <int PZ, int L, int NT>
+__global__ void __launch_bounds__(NT, 2) k_zinv_s64(const double2* __restrict__ u, double2* __restrict__ H1,
+                                                    const double* __restrict__ w1, const int* __restrict__ col0,
+                                                    int N_r, int M, int K, double kz, const double2* __restrict__ tw) {
+    constexpr int LP = cft::padded<PZ>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* a = reinterpret_cast<double2*>(smem_raw);
+    double2* b = a + L * LP;
+    constexpr int groups = 9 / L;
+    const int g = blockIdx.x % groups;
+    const int rm = blockIdx.x / groups;
+    const int r = rm % N_r;
+    const int m = rm / N_r;
+    const int nk = 2 * K + 1;
+    const size_t S = (size_t)N_r * (M + 1) * nk;
+    const size_t colstride = (size_t)(M + 1) * nk;
+    const int c0 = col0[r];
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+        for (int q = threadIdx.x; q < PZ; q += NT) {
+            const int k = q <= K ? q : q - PZ;
+            a[l * LP + cft::pd(q)] = k >= -K ? zinv_value(u, w1, c0, S, colstride, r, m, nk, K, g * L + l, k, kz)
+                                             : make_double2(0.0, 0.0);
+        }
+    __syncthreads();
+    const double2* X = cft::passes<PZ, 0, 1, L, NT, true, double2, true>(a, b, tw);
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        double2* dst = H1 + (((size_t)(g * L + l) * N_r + r) * (M + 1) + m) * PZ;
+        for (int z = threadIdx.x; z < PZ; z += NT) dst[z] = X[l * LP + cft::pd(z)];
+    }
+}
+
+template <int PZ, int LF, int NT>
+__global__ void __launch_bounds__(NT, 2) k_zfwd_s64(const double2* __restrict__ H2, double2* __restrict__ N,
+                                                    int N_r, int M, int K, double scale,
+                                                    const double2* __restrict__ tw) {
+    constexpr int LP = cft::padded<PZ>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* a = reinterpret_cast<double2*>(smem_raw);
+    double2* b = a + LF * LP;
+    constexpr int groups = 3 / LF;
+    const int cg = blockIdx.x % groups;
+    const int m = (blockIdx.x / groups) % (M + 1);
+    const int r = (blockIdx.x / groups) / (M + 1);
+    const size_t fstride = (size_t)N_r * (M + 1) * PZ;
+    const double2* h = H2 + ((size_t)r * (M + 1) + m) * PZ;
+    const int nk = 2 * K + 1;
+    const size_t S = (size_t)N_r * (M + 1) * nk;
+#pragma unroll
+    for (int l = 0; l < LF; ++l)
+        for (int z = threadIdx.x; z < PZ; z += NT) a[l * LP + cft::pd(z)] = h[(cg * LF + l) * fstride + z];
+    __syncthreads();
+    const double2* X = cft::passes<PZ, 0, 1, LF, NT, false, double2, true>(a, b, tw);
+    const size_t e0 = ((size_t)r * (M + 1) + m) * nk;
+    for (int kk = threadIdx.x; kk < nk; kk += NT) {
+        const int k = kk - K;
+        const int z = k < 0 ? k + PZ : k;
+#pragma unroll
+        for (int l = 0; l < LF; ++l) {
+            const double2 v = X[l * LP + cft::pd(z)];
+            N[(size_t)(cg * LF + l) * S + e0 + kk] = make_double2(v.x * scale, v.y * scale);
+        }
+    }
+}
+
+namespace {
+
+template <int PZ, int L, int LF, int NT>
+tc_status zpass64(tc_plan* p, const double2* u, double2* H1, const double2* H2, double2* N, cudaStream_t s,
+                  bool inverse) {
+    constexpr int LP = cft::padded<PZ>();
+    if (inverse) {
+        const size_t sm = (size_t)2 * L * LP * sizeof(double2);
+        TC_CUDA(p, cudaFuncSetAttribute(k_zinv_s64<PZ, L, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        const int slot = prof_begin(p, kKZinv, s);
+        k_zinv_s64<PZ, L, NT><<<p->N_r * (p->M + 1) * (9 / L), NT, sm, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M,
+                                                                           p->K, p->k_z, p->d_tw_z);
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_zinv_s64");
+    } else {
+        const size_t sm = (size_t)2 * LF * LP * sizeof(double2);
+        TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_s64<PZ, LF, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        const double scale = 1.0 / ((double)p->P_t * (double)p->P_z);
+        const int slot = prof_begin(p, kKZfwd, s);
+        k_zfwd_s64<PZ, LF, NT><<<p->N_r * (p->M + 1) * (3 / LF), NT, sm, s>>>(H2, N, p->N_r, p->M, p->K, scale,
+                                                                             p->d_tw_z);
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_zfwd_s64");
+    }
+    return TC_OK;
+}
+
+// length-specialised FP64 z passes; TC_ERR_ARG if P_z has no compile-time plan
+tc_status zpass64_s(tc_plan* p, const double2* u, double2* H1, const double2* H2, double2* N, cudaStream_t s,
+                    bool inverse) {
+    switch (p->P_z) {
+        case 12: return zpass64<12, 9, 3, 64>(p, u, H1, H2, N, s, inverse);
+        case 24: return zpass64<24, 9, 3, 64>(p, u, H1, H2, N, s, inverse);
+        case 48: return zpass64<48, 9, 3, 128>(p, u, H1, H2, N, s, inverse);
+        case 96: return zpass64<96, 9, 3, 128>(p, u, H1, H2, N, s, inverse);
+        case 192: return zpass64<192, 9, 3, 256>(p, u, H1, H2, N, s, inverse);
+        case 384: return zpass64<384, 3, 3, 128>(p, u, H1, H2, N, s, inverse);
+        case 768: return zpass64<768, 3, 3, 256>(p, u, H1, H2, N, s, inverse);
+        case 1152: return zpass64<1152, 1, 3, 128>(p, u, H1, H2, N, s, inverse);
+        case 1536: return zpass64<1536, 1, 3, 256>(p, u, H1, H2, N, s, inverse);
+        case 2304: return zpass64<2304, 1, 1, 256>(p, u, H1, H2, N, s, inverse);
+    }
+    return TC_ERR_ARG;
+}
+
+bool zpass64_ok(const tc_plan* p) {
+    switch (p->P_z) {
+        case 12: case 24: case 48: case 96: case 192: case 384: case 768: case 1152: case 1536: case 2304:
+            return p->theta_zt_forced == 0;
+    }
+    return false;
+}
+
+}  // namespace
+
 static tc_status run_nonlinear(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s) {
     double2* H1 = reinterpret_cast<double2*>(ws + p->ws.H1);
     double2* H2 = reinterpret_cast<double2*>(ws + p->ws.H2);
@@ -229,6 +377,7 @@ static tc_status run_nonlinear(tc_plan* p, const double2* u, double2* N, char* w
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_theta");
     }
+    if (zpass64_ok(p)) return zpass64_s(p, u, H1, H2, N, s, false);
     const double scale = 1.0 / ((double)p->P_t * (double)p->P_z);
     slot = prof_begin(p, kKZfwd, s);
     k_zfwd<<<p->N_r * (p->M + 1) * (3 / Lf), p->thr_zfwd, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, p->d_tw_z,
@@ -239,6 +388,7 @@ static tc_status run_nonlinear(tc_plan* p, const double2* u, double2* N, char* w
 }
 
 tc_status launch_zinv_fp64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s) {
+    if (zpass64_ok(p)) return zpass64_s(p, u, H1, nullptr, nullptr, s, true);
     const int L = p->zinv_lines;
     const size_t sm1 = (size_t)2 * L * p->P_z * sizeof(double2);
     TC_CUDA(p, cudaFuncSetAttribute(k_zinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));

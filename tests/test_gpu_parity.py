@@ -215,6 +215,19 @@ def test_fp64_theta_pass_lengths(M, K):
         assert rel(host(plan.nonlinear(dev(u))), ref) <= 1e-12, zt
 
 
+@pytest.mark.parametrize("K", [128, 256, 384, 512])
+def test_fp64_z_pass_lengths(K):
+    """The length-specialised FP64 z passes (P_z = 384 ... 1536) and the generic ones
+    (explicit theta_zt) both match the oracle to 1e-12."""
+    cfg = dict(N_r=9, M=2, K=K, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=LZ, dt=1e-4)
+    ops = O.Operators(O.Params(**cfg))
+    u = init(ops, kind="broadband", amp=1e-2, seed=8)
+    ref = O.nonlinear(ops, u)
+    for zt in (0, 1):
+        plan = tc.Plan(**cfg, theta_zt=zt)
+        assert rel(host(plan.nonlinear(dev(u))), ref) <= 1e-12, zt
+
+
 @pytest.mark.parametrize("K", [128, 256, 384, 512, 768, 1024])
 def test_mixed_z_pass_lengths(K):
     """The length-specialised z passes (P_z = 384 ... 3072) against the oracle and against the
