@@ -139,6 +139,97 @@ def zpass_flops(cfg, Pz, lines):
     return cfg["N_r"] * (cfg["M"] + 1) * lines * 5.0 * Pz * math.log2(Pz)
 
 
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth (MEASURED_PEAKS.json), else the recipe's fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk/SM (ncu peak_sustained of
+# sm__sass_thread_inst_executed_op_dfma_pred_on) x 2 flop x 2.07 GHz
+FP64_PEAK = 152 * 2 * 2 * 2.07e9
+
+
+def kernel_rooflines(cfg, prof):
+    """Every traced kernel at this workload: algorithmic bytes (inputs read once, outputs
+    written once) and, for the FP64 transforms, algorithmic flops; the fraction of the
+    measured HBM bandwidth and of the FP64 peak, and the roof that binds."""
+    N, M, K = cfg["N_r"], cfg["M"], cfg["K"]
+    Pt, Pz = 3 * M, 3 * K
+    S = N * (M + 1) * (2 * K + 1)
+    H = N * (M + 1) * Pz
+    fac = 4 * N * (M + 1) * (K + 1) * (13 * 8 + 1)        # 4 factor sets, 13 doubles + pivot per row
+    state_rw = (4 * 3 * S + S) * 16 + (3 * 3 * S + S) * 16   # N, N_prev, u, u_prev, p in; u, u_prev, N_prev, p out
+    table = {
+        "k_zinv": (3 * S * 16 + 9 * H * 16, zpass_flops(cfg, Pz, 9) + 36.0 * 3 * S, "alu"),   # + 9-tap stencil
+        "k_theta": (9 * H * 16 + 3 * H * 16, theta_flops(cfg, Pt, Pz), "alu"),
+        "k_zfwd": (3 * H * 16 + 3 * S * 16, zpass_flops(cfg, Pz, 3), "alu"),
+        "k_pc": (fac + state_rw, None, "alu"),
+        "k_prep_f32": (3 * S * 16 + 6 * S * 8, None, "hbm"),
+        "k_zinv_f32": (6 * S * 8 + 9 * H * 8, None, "hbm"),
+        "k_theta_f32": (9 * H * 8 + 3 * H * 8, None, "hbm"),
+        "k_zfwd_f32": (3 * H * 8 + 3 * S * 16 + 3 * S * 16, None, "hbm"),
+    }
+    hbm, src = hbm_peak_gbs()
+    out = {}
+    for name, (n, ms) in prof.items():
+        if name not in table or n == 0:
+            continue
+        t = ms / n / 1e3
+        b, f, bound = table[name]
+        e = {"ms": ms / n, "bytes": b, "hbm_frac": b / t / (hbm * 1e9), "bound": bound}
+        if f:
+            e["flops"] = f
+            e["fp64_frac"] = f / t / FP64_PEAK
+        out[name] = e
+    return {"kernels": out, "hbm_peak_gbs": hbm, "hbm_peak_source": src,
+            "fp64_peak_tflops": FP64_PEAK / 1e12,
+            "note": "k_pc: DP instructions ~322 per (row, mode), bound by FP64 issue (16 cycles per warp instruction)"}
+
+
+def cufft_comparison(torch, cfg, dev, reps=20):
+    """cuFFT (through torch.fft) on the batch shapes of the four transform passes, FP64 and
+    FP32, as a comparison only.  The hand-written passes also apply the radial stencil, the
+    products, the real-pair packing and the layout changes; cuFFT here does transforms only,
+    each in its natural contiguous layout."""
+    N, M, K = cfg["N_r"], cfg["M"], cfg["K"]
+    Pt, Pz = 3 * M, 3 * K
+    out = {"workload": f"N_r={N}, M={M}, K={K}, P_theta={Pt}, P_z={Pz}",
+           "batches": {"z_inverse": f"{9 * N * (M + 1)} complex lines of {Pz}",
+                       "theta_inverse": f"{12 * N * Pz} C2R lines of {Pt} from {M + 1} modes",
+                       "theta_forward": f"{3 * N * Pz} R2C lines of {Pt}",
+                       "z_forward": f"{3 * N * (M + 1)} complex lines of {Pz}"}}
+    for name, tc_, tr_ in (("fp64", torch.complex128, torch.float64), ("fp32", torch.complex64, torch.float32)):
+        g = torch.Generator(device=dev).manual_seed(1)
+        zin = torch.randn(9 * N * (M + 1), Pz, dtype=tc_, device=dev, generator=g)
+        thin = torch.randn(12 * N * Pz, M + 1, dtype=tc_, device=dev, generator=g)
+        thfw = torch.randn(3 * N * Pz, Pt, dtype=tr_, device=dev, generator=g)
+        zfw = torch.randn(3 * N * (M + 1), Pz, dtype=tc_, device=dev, generator=g)
+        ops = {"z_inverse": lambda: torch.fft.ifft(zin, dim=-1),
+               "theta_inverse": lambda: torch.fft.irfft(thin, n=Pt, dim=-1),
+               "theta_forward": lambda: torch.fft.rfft(thfw, dim=-1),
+               "z_forward": lambda: torch.fft.fft(zfw, dim=-1)}
+        r = {}
+        for k, fn in ops.items():
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            r[k + "_ms"] = e0.elapsed_time(e1) / reps
+        r["total_ms"] = sum(r.values())
+        out[name] = r
+        del zin, thin, thfw, zfw
+        torch.cuda.empty_cache()
+    return out
+
+
 def stable_dt(tc, torch, cfg, u0_t, dev, nsteps=200):
     """Stated dt halved until nsteps FP64 steps stay finite with < 10x energy growth."""
     dt = cfg["dt"]
@@ -390,9 +481,7 @@ def run_ours(args):
     Pt, Pz = 3 * cfg["M"], 3 * cfg["K"]
     flops = {"k_theta": theta_flops(cfg, Pt, Pz), "k_zinv": zpass_flops(cfg, Pz, 9),
              "k_zfwd": zpass_flops(cfg, Pz, 3)}
-    # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk/SM (ncu peak_sustained of
-    # sm__sass_thread_inst_executed_op_dfma_pred_on) x 2 flop x 2.07 GHz
-    fp64_peak = 152 * 2 * 2 * 2.07e9
+    fp64_peak = FP64_PEAK
     roof = None
     if top[0] in flops:
         avg_s = top[1][1] / top[1][0] / 1e3
@@ -412,7 +501,8 @@ def run_ours(args):
     # mixed precision form at the same size: speed and error after CHUNK steps vs FP64
     mplan = tc.Plan(**cfg, precision=tc.TC_MIXED, device=f"cuda:{local}")
     mst = tc.State(mplan, u0_t.cuda())
-    m_ms, mprof, m_finite = timed_steps(mplan, mst, K)
+    m_ms, _, m_finite = timed_steps(mplan, mst, K)
+    _, mprof, _ = timed_steps(mplan, mst, K, profile=True)
     # error of the mixed form at the largest stable dt (stated dt halved until 200 FP64
     # steps stay finite and the perturbation energy grows by less than 10x)
     base = torch.from_numpy(I.base_state(r, cfg["M"], cfg["K"], cfg["eta"], cfg["Re_i"], cfg["Re_o"])).cuda()
@@ -486,6 +576,7 @@ def run_ours(args):
         "gdof_steps_per_s": value * gdof(cfg) / 1e9,
         "phases_ms": {"nonlinear": nl_ms, "predictor_corrector": pc_ms},
         "kernels_ms_per_step": {k: v[1] / K for k, v in sorted(prof.items())},
+        "kernel_rooflines": {"fp64": kernel_rooflines(cfg, prof), "mixed": kernel_rooflines(cfg, mprof)},
         "roofline": roof,
         "mixed": mixed,
         "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
@@ -495,7 +586,12 @@ def run_ours(args):
         "state_finite": bool(finite),
     }
     if not args.no_extras:
-        for key, fn in (("adjoint", lambda: adjoint_ratio(tc, torch, I, f"cuda:{local}")),
+        nl64 = sum(prof[k][1] for k in ("k_zinv", "k_theta", "k_zfwd") if k in prof) / K
+        nl32 = sum(v[1] for k, v in mprof.items() if k.endswith("_f32")) / K
+        for key, fn in (("cufft_comparison", lambda: {**cufft_comparison(torch, cfg, f"cuda:{local}"),
+                                                      "ours_fp64_nonlinear_ms": nl64,
+                                                      "ours_fp32_nonlinear_ms": nl32}),
+                        ("adjoint", lambda: adjoint_ratio(tc, torch, I, f"cuda:{local}")),
                         ("large_same_size", lambda: large_mixed(tc, torch, I, f"cuda:{local}"))):
             try:
                 out[key] = fn()

@@ -20,33 +20,48 @@ __device__ __forceinline__ void smem_band_solve_T(double2* col, int T, int t, in
                                                   const uint8_t* __restrict__ P, int M1K1) {
     double* x = reinterpret_cast<double*>(col) + 2 * t + part;
     const int st = 2 * T;
-    // U^T y = b: y_j = (b_j - sum_{q=1..8} U(j-q, j) y_{j-q}) / U_jj; U(j-q, j) is band 4+q of row j-q
-    double y1 = 0.0, y2 = 0.0, y3 = 0.0, y4 = 0.0, y5 = 0.0, y6 = 0.0, y7 = 0.0, y8 = 0.0;
+    // U^T y = b: y_j = (b_j - sum_{q=1..8} U(j-q, j) y_{j-q}) / U_jj, column-oriented: p0..p7
+    // hold the partial sums of rows j .. j+7, and y_j is taken out of rows j+1 .. j+8 as soon
+    // as it is known, with U(j, j+q) = band 4+q of row j (one FMA and one multiply between
+    // consecutive y)
+    const size_t rs = (size_t)kBands * M1K1;
+    double p0 = N > 0 ? x[0] : 0.0, p1 = N > 1 ? x[(size_t)st] : 0.0, p2 = N > 2 ? x[(size_t)2 * st] : 0.0;
+    double p3 = N > 3 ? x[(size_t)3 * st] : 0.0, p4 = N > 4 ? x[(size_t)4 * st] : 0.0;
+    double p5 = N > 5 ? x[(size_t)5 * st] : 0.0, p6 = N > 6 ? x[(size_t)6 * st] : 0.0;
+    double p7 = N > 7 ? x[(size_t)7 * st] : 0.0;
+    double un[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) un[q] = N > 0 ? __ldg(&F[(size_t)(4 + q) * M1K1]) : 0.0;
     for (int j = 0; j < N; ++j) {
-        double s = x[(size_t)j * st];
-        const size_t b = (size_t)j * kBands * M1K1;
-        const size_t rs = (size_t)kBands * M1K1;   // one row of factors
-        if (j >= 8) s = fma(-__ldg(&F[b - 8 * rs + (size_t)12 * M1K1]), y8, s);
-        if (j >= 7) s = fma(-__ldg(&F[b - 7 * rs + (size_t)11 * M1K1]), y7, s);
-        if (j >= 6) s = fma(-__ldg(&F[b - 6 * rs + (size_t)10 * M1K1]), y6, s);
-        if (j >= 5) s = fma(-__ldg(&F[b - 5 * rs + (size_t)9 * M1K1]), y5, s);
-        if (j >= 4) s = fma(-__ldg(&F[b - 4 * rs + (size_t)8 * M1K1]), y4, s);
-        if (j >= 3) s = fma(-__ldg(&F[b - 3 * rs + (size_t)7 * M1K1]), y3, s);
-        if (j >= 2) s = fma(-__ldg(&F[b - 2 * rs + (size_t)6 * M1K1]), y2, s);
-        if (j >= 1) s = fma(-__ldg(&F[b - 1 * rs + (size_t)5 * M1K1]), y1, s);
-        const double yj = s * __ldg(&F[b + (size_t)4 * M1K1]);
+        double u[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) u[q] = un[q];
+        if (j + 1 < N) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) un[q] = __ldg(&F[(size_t)(j + 1) * rs + (size_t)(4 + q) * M1K1]);
+        }
+        const double yj = p0 * u[0];
         x[(size_t)j * st] = yj;
-        y8 = y7; y7 = y6; y6 = y5; y5 = y4; y4 = y3; y3 = y2; y2 = y1; y1 = yj;
+        const double p8 = j + 8 < N ? x[(size_t)(j + 8) * st] : 0.0;
+        p0 = fma(-u[1], yj, p1);
+        p1 = fma(-u[2], yj, p2);
+        p2 = fma(-u[3], yj, p3);
+        p3 = fma(-u[4], yj, p4);
+        p4 = fma(-u[5], yj, p5);
+        p5 = fma(-u[6], yj, p6);
+        p6 = fma(-u[7], yj, p7);
+        p7 = fma(-u[8], yj, p8);
     }
     // transposed eliminations and interchanges, j = N-1 .. 0; w1..w4 hold x_{j+1..j+4}
     double w1 = 0.0, w2 = 0.0, w3 = 0.0, w4 = 0.0;
     for (int j = N - 1; j >= 0; --j) {
         const double* Fj = F + (size_t)j * kBands * M1K1;
         double w0 = x[(size_t)j * st];
-        w0 = fma(-__ldg(&Fj[0]), w1, w0);
-        w0 = fma(-__ldg(&Fj[(size_t)M1K1]), w2, w0);
-        w0 = fma(-__ldg(&Fj[(size_t)2 * M1K1]), w3, w0);
+        // oldest values first: without an interchange at row j+1 only w1 is new
         w0 = fma(-__ldg(&Fj[(size_t)3 * M1K1]), w4, w0);
+        w0 = fma(-__ldg(&Fj[(size_t)2 * M1K1]), w3, w0);
+        w0 = fma(-__ldg(&Fj[(size_t)M1K1]), w2, w0);
+        w0 = fma(-__ldg(&Fj[0]), w1, w0);
         const int pj = P[(size_t)j * M1K1];
         if (pj == 1) { double q = w0; w0 = w1; w1 = q; }
         else if (pj == 2) { double q = w0; w0 = w2; w2 = q; }

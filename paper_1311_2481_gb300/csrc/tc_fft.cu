@@ -339,9 +339,10 @@ tc_status zpass64_s(tc_plan* p, const double2* u, double2* H1, const double2* H2
         case 96: return zpass64<96, 9, 3, 128>(p, u, H1, H2, N, s, inverse);
         case 192: return zpass64<192, 9, 3, 256>(p, u, H1, H2, N, s, inverse);
         case 384: return zpass64<384, 3, 3, 128>(p, u, H1, H2, N, s, inverse);
-        case 768: return zpass64<768, 3, 3, 256>(p, u, H1, H2, N, s, inverse);
-        case 1152: return zpass64<1152, 1, 3, 128>(p, u, H1, H2, N, s, inverse);
-        case 1536: return zpass64<1536, 1, 3, 256>(p, u, H1, H2, N, s, inverse);
+        // one line per block from 768 on: three FP64 lines would take 76 KB and more
+        case 768: return zpass64<768, 3, 1, 256>(p, u, H1, H2, N, s, inverse);
+        case 1152: return zpass64<1152, 1, 1, 128>(p, u, H1, H2, N, s, inverse);
+        case 1536: return zpass64<1536, 1, 1, 256>(p, u, H1, H2, N, s, inverse);
         case 2304: return zpass64<2304, 1, 1, 256>(p, u, H1, H2, N, s, inverse);
     }
     return TC_ERR_ARG;

@@ -99,7 +99,10 @@ __device__ __forceinline__ void smem_band_solve(double2* col, int T, int t, int 
         w0 = w1; w1 = w2; w2 = w3; w3 = w4;
         w4 = (j + 5 < N) ? x[(size_t)(j + 5) * st] : 0.0;
     }
-    // backward: x_{j+1..j+8} in v1..v8
+    // backward: x_{j+1..j+8} in v1..v8.  Row-oriented; a column-oriented variant (each x_j
+    // taken out of the rows above at once: two dependent operations per row instead of nine)
+    // measured slower on GB300 in k_pc and k_band_solve_g (0.400 vs 0.364 ms at N_r = 64):
+    // the substitutions are bound by FP64 issue, not by the dependency chain
     double v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0, v5 = 0.0, v6 = 0.0, v7 = 0.0, v8 = 0.0;
     double un[9];
     {
