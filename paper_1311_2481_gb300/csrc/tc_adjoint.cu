@@ -6,6 +6,7 @@
 // and vice versa, the transposed pointwise products, the transposed radial stencil).  The
 // inner product is the Euclidean one on the stored (Re, Im) pairs.
 #include "tc_fft_core.cuh"
+#include "tc_fftc.cuh"
 #include "tc_solve_core.cuh"
 
 namespace tc {
@@ -545,6 +546,139 @@ __global__ void __launch_bounds__(256) k_theta_adj(const double2* __restrict__ H
     }
 }
 
+// Length-specialised form of k_theta_adj: compile-time radix plans (radices <= 8) over padded
+// lines; same fields, products and outputs.
+template <int PT, int ZT, int NT>
+__global__ void __launch_bounds__(NT) k_theta_adj_s(const double2* __restrict__ H1, const double2* __restrict__ Ha,
+                                                   double2* __restrict__ H3, const double* __restrict__ rnodes,
+                                                   int N_r, int M, int Pz, double mp,
+                                                   const double2* __restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int Pt = PT, zt = ZT;
+    constexpr int LP = cft::padded<PT>();
+    constexpr int nza = (ZT + 1) / 2;
+    constexpr int nl = 7 * ZT + nza;           // 6 forward + 1 (s_r, s_t) per z + s_z pairs
+    constexpr int nbuf = nl > 6 * ZT ? nl : 6 * ZT;
+    double2* A = reinterpret_cast<double2*>(smem_raw);
+    double2* B = A + (size_t)nbuf * LP;
+    const int tiles = Pz / zt;
+    const int r = blockIdx.x / tiles;
+    const int z0 = (blockIdx.x % tiles) * zt;
+    const size_t fstride = (size_t)N_r * (M + 1) * Pz;
+    const double2* h = H1 + (size_t)r * (M + 1) * Pz + z0;
+    const double2* ha = Ha + (size_t)r * (M + 1) * Pz + z0;
+
+    for (int idx = threadIdx.x; idx < nl * LP; idx += NT) A[idx] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < (7 * zt + nza) * (M + 1); idx += NT) {
+        const int m = idx % (M + 1);
+        const int L = idx / (M + 1);
+        const double mm = mp * m;
+        double2* line = A + (size_t)L * LP;
+        if (L < 6 * zt) {   // forward lines, as in k_theta
+            const int zi = L / 6, pr = L - 6 * (L / 6);
+            const size_t o = (size_t)m * Pz + zi;
+            if (pr < 4) {
+                const int fa = pr == 0 ? 0 : pr == 1 ? 3 : pr == 2 ? 0 : 6;
+                double2 Av = h[fa * fstride + o], Bv = h[(fa + 1) * fstride + o];
+                if (pr == 2) { Av = make_double2(-mm * Av.y, mm * Av.x); Bv = make_double2(-mm * Bv.y, mm * Bv.x); }
+                if (m == 0) line[0] = make_double2(0.5 * (Av.x + Bv.x), 0.5 * (Av.y - Bv.y));
+                else { line[cft::pd(m)] = Av; line[cft::pd(Pt - m)] = cconj(Bv); }
+            } else {
+                double2 X, Y;
+                if (pr == 4) { X = h[2 * fstride + o]; Y = h[5 * fstride + o]; }
+                else { X = h[2 * fstride + o]; X = make_double2(-mm * X.y, mm * X.x); Y = h[8 * fstride + o]; }
+                if (m == 0) line[0] = make_double2(X.x, Y.x);
+                else {
+                    line[cft::pd(m)] = make_double2(X.x - Y.y, X.y + Y.x);
+                    line[cft::pd(Pt - m)] = make_double2(X.x + Y.y, Y.x - X.y);
+                }
+            }
+        } else if (L < 7 * zt) {   // adjoint (s_r, s_t) as two real fields
+            const int zi = L - 6 * zt;
+            const size_t o = (size_t)m * Pz + zi;
+            const double2 X = ha[o], Y = ha[fstride + o];
+            if (m == 0) line[0] = make_double2(X.x, Y.x);
+            else {
+                line[cft::pd(m)] = make_double2(X.x - Y.y, X.y + Y.x);
+                line[cft::pd(Pt - m)] = make_double2(X.x + Y.y, Y.x - X.y);
+            }
+        } else {                   // s_z of z values 2i and 2i+1
+            const int zp = L - 7 * zt;
+            const int za = 2 * zp, zb = 2 * zp + 1;
+            const double2 X = ha[2 * fstride + (size_t)m * Pz + za];
+            const double2 Y = zb < zt ? ha[2 * fstride + (size_t)m * Pz + zb] : make_double2(0.0, 0.0);
+            if (m == 0) line[0] = make_double2(X.x, Y.x);
+            else {
+                line[cft::pd(m)] = make_double2(X.x - Y.y, X.y + Y.x);
+                line[cft::pd(Pt - m)] = make_double2(X.x + Y.y, Y.x - X.y);
+            }
+        }
+    }
+    __syncthreads();
+    const double2* phys = cft::passes<PT, 0, 1, nl, NT, true, double2, true>(A, B, tw);
+    double2* out = phys == A ? B : A;
+    const double ir = 1.0 / rnodes[r];
+    for (int idx = threadIdx.x; idx < zt * Pt; idx += NT) {
+        const int zi = idx / Pt, th = idx - zi * Pt;
+        const int pth = cft::pd(th);
+        const double2* L0 = phys + (size_t)(zi * 6) * LP + pth;
+        const double2 p0 = L0[0], p1 = L0[LP], p2 = L0[2 * LP], p3 = L0[3 * LP], p4 = L0[4 * LP], p5 = L0[5 * LP];
+        const double2 an = phys[(size_t)(6 * zt + zi) * LP + pth];
+        const double2 az = phys[(size_t)(7 * zt + zi / 2) * LP + pth];
+        const double nr = an.x, nt = an.y, nz = (zi & 1) ? az.y : az.x;
+        const double ur = p0.x, ut = p0.y, uz = p4.x;
+        const double urr = p1.x, utr = p1.y, urt = p2.x, utt = p2.y, urz = p3.x, utz = p3.y;
+        const double uzr = p4.y, uzt = p5.x, uzz = p5.y;
+        const double utr_ = ut * ir;
+        const double b_ur = nr * urr + nt * (utr + utr_) + nz * uzr;
+        const double b_ut = (nr * (urt - 2.0 * ut) + nt * (utt + ur) + nz * uzt) * ir;
+        const double b_uz = nr * urz + nt * utz + nz * uzz;
+        double2* o = out + (size_t)(zi * 6) * LP + pth;
+        o[0] = make_double2(b_ur, b_ut);                     // pair 0: (u_r, u_t)
+        o[LP] = make_double2(b_uz, ur * nz);                 // pair 1: (u_z, d_r u_z)
+        o[2 * LP] = make_double2(ur * nr, ur * nt);          // pair 2: (d_r u_r, d_r u_t)
+        o[3 * LP] = make_double2(utr_ * nr, utr_ * nt);      // pair 3: (d_t u_r, d_t u_t)
+        o[4 * LP] = make_double2(utr_ * nz, uz * nz);        // pair 4: (d_t u_z, d_z u_z)
+        o[5 * LP] = make_double2(uz * nr, uz * nt);          // pair 5: (d_z u_r, d_z u_t)
+    }
+    __syncthreads();
+    double2* spare = out == A ? B : A;
+    const double2* spec = cft::passes<PT, 0, 1, 6 * ZT, NT, false, double2, true>(out, spare, tw);
+    const size_t S9 = fstride;
+    for (int idx = threadIdx.x; idx < zt * (M + 1); idx += NT) {
+        const int m = idx / zt, zi = idx - m * zt;
+        const double cmw = m == 0 ? 1.0 : 2.0;
+        const double mm = mp * m;
+        double2 X[6], Y[6];
+        for (int pr = 0; pr < 6; ++pr) {
+            const double2* Ls = spec + (size_t)(zi * 6 + pr) * LP;
+            const double2 Cp = Ls[cft::pd(m)], Cm = cconj(Ls[cft::pd(m ? Pt - m : 0)]);
+            X[pr] = make_double2(0.5 * cmw * (Cp.x + Cm.x), 0.5 * cmw * (Cp.y + Cm.y));
+            Y[pr] = make_double2(0.5 * cmw * (Cp.y - Cm.y), 0.5 * cmw * (Cm.x - Cp.x));
+        }
+        // A_c = G^T ubar_{u_c} - i m m_p G^T ubar_{d_t u_c}; R_c = G^T ubar_{d_r u_c}; Z_c = G^T ubar_{d_z u_c}
+        const double2 Ar = make_double2(X[0].x + mm * X[3].y, X[0].y - mm * X[3].x);
+        const double2 At = make_double2(Y[0].x + mm * Y[3].y, Y[0].y - mm * Y[3].x);
+        const double2 Az = make_double2(X[1].x + mm * X[4].y, X[1].y - mm * X[4].x);
+        const double2 Rr = X[2], Rt = Y[2], Rz = Y[1];
+        const double2 Zr = X[5], Zt = Y[5], Zz = Y[4];
+        // (r, t, z) -> (+, -, z):  bar_+ = a_r/2 + i a_t/2,  bar_- = a_r/2 - i a_t/2
+        auto plus = [](double2 ar, double2 at) { return make_double2(0.5 * (ar.x - at.y), 0.5 * (ar.y + at.x)); };
+        auto minus = [](double2 ar, double2 at) { return make_double2(0.5 * (ar.x + at.y), 0.5 * (ar.y - at.x)); };
+        const size_t o = ((size_t)r * (M + 1) + m) * Pz + z0 + zi;
+        H3[0 * S9 + o] = plus(Ar, At);
+        H3[1 * S9 + o] = minus(Ar, At);
+        H3[2 * S9 + o] = Az;
+        H3[3 * S9 + o] = plus(Rr, Rt);
+        H3[4 * S9 + o] = minus(Rr, Rt);
+        H3[5 * S9 + o] = Rz;
+        H3[6 * S9 + o] = plus(Zr, Zt);
+        H3[7 * S9 + o] = minus(Zr, Zt);
+        H3[8 * S9 + o] = Zz;
+    }
+}
+
 // Per (r, m, component c): unscaled forward DFT along z of A_c, R_c, Z_c, truncation to
 // |k| <= K; ubar_c += A_c - i k k_z Z_c;  Rhat_c = R_c (transposed stencil applied next).
 __global__ void __launch_bounds__(256) k_zfwd_adj(const double2* __restrict__ H3, double2* __restrict__ ub,
@@ -623,6 +757,19 @@ tc_status launch_adjoint_advance(tc_plan* p, const double2* ubar_new, const doub
     return TC_OK;
 }
 
+template <int PT, int ZT, int NT>
+static tc_status theta_adj_s(tc_plan* p, const double2* H1, const double2* Ha, double2* H3, cudaStream_t s) {
+    constexpr int nl = 7 * ZT + (ZT + 1) / 2;
+    const size_t sm = (size_t)2 * nl * cft::padded<PT>() * sizeof(double2);
+    TC_CUDA(p, cudaFuncSetAttribute(k_theta_adj_s<PT, ZT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int slot = prof_begin(p, kKThetaAdj, s);
+    k_theta_adj_s<PT, ZT, NT><<<p->N_r * (p->P_z / ZT), NT, sm, s>>>(H1, Ha, H3, p->d_r, p->N_r, p->M, p->P_z,
+                                                                    (double)p->m_p, p->d_tw_t);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_theta_adj_s");
+    return TC_OK;
+}
+
 tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* Nbar, double2* ubar,
                                    char* ws, cudaStream_t s) {
     Geo g = geo(p);
@@ -651,13 +798,21 @@ tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* 
         snprintf(p->err, sizeof(p->err), "adjoint theta pass: P_theta = %d too long for shared memory", p->P_t);
         return TC_ERR_ARG;
     }
-    const size_t smt = smem_for(zt);
-    TC_CUDA(p, cudaFuncSetAttribute(k_theta_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt));
-    slot = prof_begin(p, kKThetaAdj, s);
-    k_theta_adj<<<p->N_r * (p->P_z / zt), 256, smt, s>>>(H1, Ha, H3, p->d_r, p->N_r, p->M, p->P_z,
-                                                           (double)p->m_p, zt, p->d_tw_t, p->rad_t);
-    prof_end(p, slot, s);
-    TC_LAUNCHED(p, "k_theta_adj");
+    if (p->theta_zt_forced == 0 && (p->P_t == 96 || p->P_t == 192 || p->P_t == 384) && p->P_z % 2 == 0) {
+        switch (p->P_t) {
+            case 96: TC_TRY_STATUS((theta_adj_s<96, 2, 128>(p, H1, Ha, H3, s))); break;
+            case 192: TC_TRY_STATUS((theta_adj_s<192, 2, 256>(p, H1, Ha, H3, s))); break;
+            default: TC_TRY_STATUS((theta_adj_s<384, 2, 256>(p, H1, Ha, H3, s))); break;
+        }
+    } else {
+        const size_t smt = smem_for(zt);
+        TC_CUDA(p, cudaFuncSetAttribute(k_theta_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt));
+        slot = prof_begin(p, kKThetaAdj, s);
+        k_theta_adj<<<p->N_r * (p->P_z / zt), 256, smt, s>>>(H1, Ha, H3, p->d_r, p->N_r, p->M, p->P_z,
+                                                               (double)p->m_p, zt, p->d_tw_t, p->rad_t);
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_theta_adj");
+    }
     TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
     slot = prof_begin(p, kKZfwdAdj, s);
     k_zfwd_adj<<<p->N_r * (p->M + 1) * 3, 256, smz, s>>>(H3, ubar, Rh, p->N_r, p->M, p->K, p->k_z,

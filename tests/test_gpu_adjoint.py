@@ -68,6 +68,27 @@ def test_adjoint_step_matches_oracle(cfg):
         assert rel(host(got), want) <= 1e-11
 
 
+@pytest.mark.parametrize("M", [32, 64, 128])
+def test_adjoint_step_theta_lengths(M):
+    """The length-specialised adjoint theta pass (P_theta = 96, 192, 384) and the generic one
+    (explicit theta_zt) both match the oracle's adjoint step."""
+    cfg = dict(N_r=12, M=M, K=4, m_p=1, eta=0.5, Re_i=50.0, Re_o=0.0, L_z=LZ, dt=1e-3)
+    ops = O.Operators(O.Params(**cfg))
+    prm = ops.prm
+    u0 = I.initial_state(ops.r, prm.M, prm.K, prm.m_p, prm.L_z, prm.eta, prm.Re_i, prm.Re_o,
+                         kind="broadband", amp=1e-2)
+    st_o = O.step(ops, O.cold_state(u0))
+    sh = (3,) + prm.shape()
+    y = [I.random_spectral(sh, seed=s) for s in (31, 32, 33)]
+    ref = O.adjoint_step(ops, st_o, *y)
+    for zt in (0, 1):
+        plan = tc.Plan(**cfg, theta_zt=zt)
+        bar = tc.StateBar(*[dev(v) for v in y])
+        plan.adjoint_step(gpu_state(plan, st_o), bar)
+        for got, want in zip((bar.u, bar.u_prev, bar.N_prev), ref):
+            assert rel(host(got), want) <= 1e-11, zt
+
+
 def test_adjoint_start_matches_oracle():
     ops, plan, u0 = setup(CFG1)
     sh = (3,) + ops.prm.shape()
