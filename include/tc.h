@@ -78,6 +78,10 @@ typedef struct {
     int theta_variant; /* launch tuning of the mixed form's length-specialised theta pass:
                          0 or 1: radices <= 16, two blocks per SM; 2 and 3: radices <= 8 with
                          half the z values per block, four / three blocks per SM */
+    int pipeline;     /* tc_step overlap: the modes are cut into this many chunks of m, and
+                         the forward z pass, steps 2-5 and the next inverse z pass of different
+                         chunks run concurrently on two internal streams (forked from and
+                         joined back to the caller's stream).  0 or 1: sequential */
 } tc_options;
 
 /* Step state (Sec. 3.2): u = u^i, u_prev = u^{i-1}, N_prev = N^{i-1} (vector fields), p = p^i

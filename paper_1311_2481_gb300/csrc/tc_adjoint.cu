@@ -800,7 +800,7 @@ tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* 
     }
     if (p->theta_zt_forced == 0 && (p->P_t == 96 || p->P_t == 192 || p->P_t == 384) && p->P_z % 2 == 0) {
         switch (p->P_t) {
-            case 96: TC_TRY_STATUS((theta_adj_s<96, 2, 128>(p, H1, Ha, H3, s))); break;
+            case 96: TC_TRY_STATUS((theta_adj_s<96, 2, 256>(p, H1, Ha, H3, s))); break;
             case 192: TC_TRY_STATUS((theta_adj_s<192, 2, 256>(p, H1, Ha, H3, s))); break;
             default: TC_TRY_STATUS((theta_adj_s<384, 2, 256>(p, H1, Ha, H3, s))); break;
         }

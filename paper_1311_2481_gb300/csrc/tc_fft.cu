@@ -26,7 +26,7 @@ namespace tc {
 __global__ void __launch_bounds__(256) k_zinv(const double2* __restrict__ u, double2* __restrict__ H1,
                                               const double* __restrict__ w1, const int* __restrict__ col0,
                                               int N_r, int M, int K, double kz, int L,
-                                              const double2* __restrict__ tw, Radices rad) {
+                                              const double2* __restrict__ tw, Radices rad, int m0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Pz = rad.n;
     double2* a = reinterpret_cast<double2*>(smem_raw);
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256) k_zinv(const double2* __restrict__ u, dou
     const int g = blockIdx.x % groups;
     const int rm = blockIdx.x / groups;
     const int r = rm % N_r;        // r fastest: blocks sharing stencil rows run together
-    const int m = rm / N_r;
+    const int m = m0 + rm / N_r;
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
     const size_t colstride = (size_t)(M + 1) * nk;
@@ -181,14 +181,15 @@ __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __re
 // ---------------------------------------------------------------- forward z-pass
 __global__ void __launch_bounds__(256) k_zfwd(const double2* __restrict__ H2, double2* __restrict__ N,
                                               int N_r, int M, int K, double scale,
-                                              const double2* __restrict__ tw, Radices rad, int Lf) {
+                                              const double2* __restrict__ tw, Radices rad, int Lf,
+                                              int m0, int mcnt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Pz = rad.n;
     double2* a = reinterpret_cast<double2*>(smem_raw);
     double2* b = a + (size_t)Lf * Pz;
     const int cg = blockIdx.x % (3 / Lf);     // component group (Lf = 3: all three)
-    const int m = (blockIdx.x / (3 / Lf)) % (M + 1);
-    const int r = (blockIdx.x / (3 / Lf)) / (M + 1);
+    const int m = m0 + (blockIdx.x / (3 / Lf)) % mcnt;
+    const int r = (blockIdx.x / (3 / Lf)) / mcnt;
     const size_t fstride = (size_t)N_r * (M + 1) * Pz;
     const double2* h = H2 + ((size_t)r * (M + 1) + m) * Pz;
     const int nk = 2 * K + 1;
@@ -239,7 +240,8 @@ __device__ __forceinline__ double2 zinv_value(const double2* __restrict__ u, con
 template <int PZ, int L, int NT>
 __global__ void __launch_bounds__(NT, 2) k_zinv_s64(const double2* __restrict__ u, double2* __restrict__ H1,
                                                     const double* __restrict__ w1, const int* __restrict__ col0,
-                                                    int N_r, int M, int K, double kz, const double2* __restrict__ tw) {
+                                                    int N_r, int M, int K, double kz, const double2* __restrict__ tw,
+                                                    int m0) {
     constexpr int LP = cft::padded<PZ>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* a = reinterpret_cast<double2*>(smem_raw);
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(NT, 2) k_zinv_s64(const double2* __restrict__ 
     const int g = blockIdx.x % groups;
     const int rm = blockIdx.x / groups;
     const int r = rm % N_r;
-    const int m = rm / N_r;
+    const int m = m0 + rm / N_r;
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
     const size_t colstride = (size_t)(M + 1) * nk;
@@ -272,15 +274,15 @@ __global__ void __launch_bounds__(NT, 2) k_zinv_s64(const double2* __restrict__ 
 template <int PZ, int LF, int NT>
 __global__ void __launch_bounds__(NT, 2) k_zfwd_s64(const double2* __restrict__ H2, double2* __restrict__ N,
                                                     int N_r, int M, int K, double scale,
-                                                    const double2* __restrict__ tw) {
+                                                    const double2* __restrict__ tw, int m0, int mcnt) {
     constexpr int LP = cft::padded<PZ>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* a = reinterpret_cast<double2*>(smem_raw);
     double2* b = a + LF * LP;
     constexpr int groups = 3 / LF;
     const int cg = blockIdx.x % groups;
-    const int m = (blockIdx.x / groups) % (M + 1);
-    const int r = (blockIdx.x / groups) / (M + 1);
+    const int m = m0 + (blockIdx.x / groups) % mcnt;
+    const int r = (blockIdx.x / groups) / mcnt;
     const size_t fstride = (size_t)N_r * (M + 1) * PZ;
     const double2* h = H2 + ((size_t)r * (M + 1) + m) * PZ;
     const int nk = 2 * K + 1;
@@ -306,14 +308,15 @@ namespace {
 
 template <int PZ, int L, int LF, int NT>
 tc_status zpass64(tc_plan* p, const double2* u, double2* H1, const double2* H2, double2* N, cudaStream_t s,
-                  bool inverse) {
+                  bool inverse, int ma, int mb) {
     constexpr int LP = cft::padded<PZ>();
+    const int mc = mb - ma;
     if (inverse) {
         const size_t sm = (size_t)2 * L * LP * sizeof(double2);
         TC_CUDA(p, cudaFuncSetAttribute(k_zinv_s64<PZ, L, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int slot = prof_begin(p, kKZinv, s);
-        k_zinv_s64<PZ, L, NT><<<p->N_r * (p->M + 1) * (9 / L), NT, sm, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M,
-                                                                           p->K, p->k_z, p->d_tw_z);
+        k_zinv_s64<PZ, L, NT><<<p->N_r * mc * (9 / L), NT, sm, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M,
+                                                                   p->K, p->k_z, p->d_tw_z, ma);
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_zinv_s64");
     } else {
@@ -321,29 +324,29 @@ tc_status zpass64(tc_plan* p, const double2* u, double2* H1, const double2* H2, 
         TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_s64<PZ, LF, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const double scale = 1.0 / ((double)p->P_t * (double)p->P_z);
         const int slot = prof_begin(p, kKZfwd, s);
-        k_zfwd_s64<PZ, LF, NT><<<p->N_r * (p->M + 1) * (3 / LF), NT, sm, s>>>(H2, N, p->N_r, p->M, p->K, scale,
-                                                                             p->d_tw_z);
+        k_zfwd_s64<PZ, LF, NT><<<p->N_r * mc * (3 / LF), NT, sm, s>>>(H2, N, p->N_r, p->M, p->K, scale,
+                                                                     p->d_tw_z, ma, mc);
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_zfwd_s64");
     }
     return TC_OK;
 }
 
-// length-specialised FP64 z passes; TC_ERR_ARG if P_z has no compile-time plan
+// length-specialised FP64 z passes over m in [ma, mb); TC_ERR_ARG if P_z has no compile-time plan
 tc_status zpass64_s(tc_plan* p, const double2* u, double2* H1, const double2* H2, double2* N, cudaStream_t s,
-                    bool inverse) {
+                    bool inverse, int ma, int mb) {
     switch (p->P_z) {
-        case 12: return zpass64<12, 9, 3, 64>(p, u, H1, H2, N, s, inverse);
-        case 24: return zpass64<24, 9, 3, 64>(p, u, H1, H2, N, s, inverse);
-        case 48: return zpass64<48, 9, 3, 128>(p, u, H1, H2, N, s, inverse);
-        case 96: return zpass64<96, 9, 3, 128>(p, u, H1, H2, N, s, inverse);
-        case 192: return zpass64<192, 9, 3, 256>(p, u, H1, H2, N, s, inverse);
-        case 384: return zpass64<384, 3, 3, 128>(p, u, H1, H2, N, s, inverse);
+        case 12: return zpass64<12, 9, 3, 64>(p, u, H1, H2, N, s, inverse, ma, mb);
+        case 24: return zpass64<24, 9, 3, 64>(p, u, H1, H2, N, s, inverse, ma, mb);
+        case 48: return zpass64<48, 9, 3, 128>(p, u, H1, H2, N, s, inverse, ma, mb);
+        case 96: return zpass64<96, 9, 3, 128>(p, u, H1, H2, N, s, inverse, ma, mb);
+        case 192: return zpass64<192, 9, 3, 256>(p, u, H1, H2, N, s, inverse, ma, mb);
+        case 384: return zpass64<384, 3, 3, 128>(p, u, H1, H2, N, s, inverse, ma, mb);
         // one line per block from 768 on: three FP64 lines would take 76 KB and more
-        case 768: return zpass64<768, 3, 1, 256>(p, u, H1, H2, N, s, inverse);
-        case 1152: return zpass64<1152, 1, 1, 128>(p, u, H1, H2, N, s, inverse);
-        case 1536: return zpass64<1536, 1, 1, 256>(p, u, H1, H2, N, s, inverse);
-        case 2304: return zpass64<2304, 1, 1, 256>(p, u, H1, H2, N, s, inverse);
+        case 768: return zpass64<768, 3, 1, 256>(p, u, H1, H2, N, s, inverse, ma, mb);
+        case 1152: return zpass64<1152, 1, 1, 128>(p, u, H1, H2, N, s, inverse, ma, mb);
+        case 1536: return zpass64<1536, 1, 1, 256>(p, u, H1, H2, N, s, inverse, ma, mb);
+        case 2304: return zpass64<2304, 1, 1, 256>(p, u, H1, H2, N, s, inverse, ma, mb);
     }
     return TC_ERR_ARG;
 }
@@ -358,50 +361,53 @@ bool zpass64_ok(const tc_plan* p) {
 
 }  // namespace
 
-static tc_status run_nonlinear(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s) {
-    double2* H1 = reinterpret_cast<double2*>(ws + p->ws.H1);
-    double2* H2 = reinterpret_cast<double2*>(ws + p->ws.H2);
-    TC_TRY_STATUS(launch_zinv_fp64(p, u, H1, s));
-    const int zt = p->zt;
-    const size_t sm2 = (size_t)2 * 6 * zt * p->P_t * sizeof(double2);
-    const int Lf = p->zfwd_lines;
-    const size_t sm3 = (size_t)2 * Lf * p->P_z * sizeof(double2);
-    TC_CUDA(p, cudaFuncSetAttribute(k_theta<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    TC_CUDA(p, cudaFuncSetAttribute(k_zfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-    int slot;
-    if (p->theta_zt_forced == 0 && theta_s_zt(p, true) > 0) {
-        TC_TRY_STATUS(launch_theta_s64(p, H1, H2, s));   // length-specialised, streamed products
-    } else {
-        slot = prof_begin(p, kKTheta, s);
-        k_theta<double2><<<p->N_r * (p->P_z / zt), p->thr_theta, sm2, s>>>(H1, H2, p->d_r, p->N_r, p->M, p->P_z,
-                                                                          (double)p->m_p, zt, p->d_tw_t, p->rad_t);
-        prof_end(p, slot, s);
-        TC_LAUNCHED(p, "k_theta");
-    }
-    if (zpass64_ok(p)) return zpass64_s(p, u, H1, H2, N, s, false);
-    const double scale = 1.0 / ((double)p->P_t * (double)p->P_z);
-    slot = prof_begin(p, kKZfwd, s);
-    k_zfwd<<<p->N_r * (p->M + 1) * (3 / Lf), p->thr_zfwd, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, p->d_tw_z,
-                                                                    p->rad_z, Lf);
-    prof_end(p, slot, s);
-    TC_LAUNCHED(p, "k_zfwd");
-    return TC_OK;
-}
-
-tc_status launch_zinv_fp64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s) {
-    if (zpass64_ok(p)) return zpass64_s(p, u, H1, nullptr, nullptr, s, true);
+// inverse z pass (with the radial stencil) of the lines of m in [ma, mb)
+static tc_status zinv64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s, int ma, int mb) {
+    if (zpass64_ok(p)) return zpass64_s(p, u, H1, nullptr, nullptr, s, true, ma, mb);
     const int L = p->zinv_lines;
     const size_t sm1 = (size_t)2 * L * p->P_z * sizeof(double2);
     TC_CUDA(p, cudaFuncSetAttribute(k_zinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
     const int slot = prof_begin(p, kKZinv, s);
-    k_zinv<<<p->N_r * (p->M + 1) * (9 / L), p->thr_zinv, sm1, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M, p->K,
-                                                                   p->k_z, L, p->d_tw_z, p->rad_z);
+    k_zinv<<<p->N_r * (mb - ma) * (9 / L), p->thr_zinv, sm1, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M, p->K,
+                                                                  p->k_z, L, p->d_tw_z, p->rad_z, ma);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_zinv");
     return TC_OK;
 }
 
-// theta pass of the mixed form: FP32 lines (H1, H2 in float2)
+// forward z pass of the lines of m in [ma, mb) into N
+static tc_status zfwd64(tc_plan* p, const double2* H2, double2* N, cudaStream_t s, int ma, int mb) {
+    if (zpass64_ok(p)) return zpass64_s(p, nullptr, nullptr, H2, N, s, false, ma, mb);
+    const int Lf = p->zfwd_lines;
+    const size_t sm3 = (size_t)2 * Lf * p->P_z * sizeof(double2);
+    TC_CUDA(p, cudaFuncSetAttribute(k_zfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+    const double scale = 1.0 / ((double)p->P_t * (double)p->P_z);
+    const int slot = prof_begin(p, kKZfwd, s);
+    k_zfwd<<<p->N_r * (mb - ma) * (3 / Lf), p->thr_zfwd, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, p->d_tw_z,
+                                                                   p->rad_z, Lf, ma, mb - ma);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_zfwd");
+    return TC_OK;
+}
+
+static tc_status theta64(tc_plan* p, const double2* H1, double2* H2, cudaStream_t s) {
+    if (p->theta_zt_forced == 0 && theta_s_zt(p, true) > 0) return launch_theta_s64(p, H1, H2, s);
+    const int zt = p->zt;
+    const size_t sm2 = (size_t)2 * 6 * zt * p->P_t * sizeof(double2);
+    TC_CUDA(p, cudaFuncSetAttribute(k_theta<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    const int slot = prof_begin(p, kKTheta, s);
+    k_theta<double2><<<p->N_r * (p->P_z / zt), p->thr_theta, sm2, s>>>(H1, H2, p->d_r, p->N_r, p->M, p->P_z,
+                                                                      (double)p->m_p, zt, p->d_tw_t, p->rad_t);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_theta");
+    return TC_OK;
+}
+
+tc_status launch_zinv_fp64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s) {
+    return zinv64(p, u, H1, s, 0, p->M + 1);
+}
+
+// theta pass of the mixed form with the generic kernel: FP32 lines (H1, H2 in float2)
 tc_status launch_theta32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t s) {
     const int zt = p->zt32;
     const size_t sm2 = (size_t)2 * 6 * zt * p->P_t * sizeof(float2);
@@ -414,9 +420,27 @@ tc_status launch_theta32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t 
     return TC_OK;
 }
 
+// The nonlinear term in three parts: before the theta pass (per m: the z-inverse lines and,
+// in the mixed form, the FP32 split), the theta pass (all m), after it (per m: z-forward into N)
+tc_status launch_nl_pre(tc_plan* p, const double2* u, char* ws, cudaStream_t s, int ma, int mb) {
+    if (p->precision == TC_MIXED) return launch_nl_pre32(p, u, ws, s, ma, mb);
+    return zinv64(p, u, reinterpret_cast<double2*>(ws + p->ws.H1), s, ma, mb);
+}
+
+tc_status launch_nl_theta(tc_plan* p, char* ws, cudaStream_t s) {
+    if (p->precision == TC_MIXED) return launch_nl_theta32(p, ws, s);
+    return theta64(p, reinterpret_cast<const double2*>(ws + p->ws.H1), reinterpret_cast<double2*>(ws + p->ws.H2), s);
+}
+
+tc_status launch_nl_post(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s, int ma, int mb) {
+    if (p->precision == TC_MIXED) return launch_nl_post32(p, u, N, ws, s, ma, mb);
+    return zfwd64(p, reinterpret_cast<const double2*>(ws + p->ws.H2), N, s, ma, mb);
+}
+
 tc_status launch_nonlinear(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s) {
-    if (p->precision == TC_MIXED) return launch_nonlinear_mixed(p, u, N, ws, s);
-    return run_nonlinear(p, u, N, ws, s);
+    TC_TRY_STATUS(launch_nl_pre(p, u, ws, s, 0, p->M + 1));
+    TC_TRY_STATUS(launch_nl_theta(p, ws, s));
+    return launch_nl_post(p, u, N, ws, s, 0, p->M + 1);
 }
 
 }  // namespace tc

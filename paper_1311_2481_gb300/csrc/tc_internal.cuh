@@ -30,7 +30,7 @@ struct Radices {
 struct Workspace {
     size_t H1;      // inverse z-pass output: 9 fields x N_r x (M+1) x P_z complex
     size_t H2;      // theta-pass output: 3 fields x N_r x (M+1) x P_z complex
-    size_t P32;     // mixed form: u', d_r u' in FP32, 6 x S float2 (aliases H2, dead before it)
+    size_t P32;     // mixed form: u', d_r u' in FP32, 6 x S float2
     size_t Ncur;    // N^i: vector field
     size_t uE;      // start-up Euler result: vector field
     size_t pstar;   // split path only: p* (scalar), u* (vector), phi (scalar)
@@ -62,6 +62,9 @@ struct tc_plan {
     int zt, zt32;                  // z values per theta-pass block (FP64 / FP32 lines)
     int theta_zt_forced;           // tc_options.theta_zt (> 0: generic transform kernels)
     int theta_variant;             // tc_options.theta_variant (launch shape of the FP32 streamed theta pass)
+    int pipeline;                  // m-chunks of the overlapped step (1: sequential)
+    cudaStream_t aux[2] = {nullptr, nullptr};   // solve and pre-theta streams of the overlapped step
+    std::vector<cudaEvent_t> pev;               // its events: fork, join, pre-done, then Z[c], P[c]
     int pc_modes;                  // modes per block of the fused steps-2-5 kernel (0: auto)
     int thr_zinv, thr_theta, thr_zfwd;  // block sizes of the FP64 transform kernels
     bool pc_split;                      // steps 2-5 as separate kernels (large N_r)
@@ -157,11 +160,16 @@ tc_status launch_theta32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t 
 int theta_s_zt(const tc_plan* p, bool fp64);
 tc_status launch_theta_s(tc_plan* p, const float2* H1, float2* H2, cudaStream_t s);
 tc_status launch_theta_s64(tc_plan* p, const double2* H1, double2* H2, cudaStream_t s);
-tc_status launch_nonlinear_mixed(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s);
+tc_status launch_nl_pre(tc_plan* p, const double2* u, char* ws, cudaStream_t s, int ma, int mb);
+tc_status launch_nl_theta(tc_plan* p, char* ws, cudaStream_t s);
+tc_status launch_nl_post(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s, int ma, int mb);
+tc_status launch_nl_pre32(tc_plan* p, const double2* u, char* ws, cudaStream_t s, int ma, int mb);
+tc_status launch_nl_theta32(tc_plan* p, char* ws, cudaStream_t s);
+tc_status launch_nl_post32(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s, int ma, int mb);
 tc_status launch_solve(tc_plan* p, int set, double2* x, int nfields, cudaStream_t s);
 tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const double2* Ncur,
                          double2* N_prev, double2* p_out, double2* u_out, char* ws,
-                         bool commit, cudaStream_t s);
+                         bool commit, cudaStream_t s, int ma = 0, int mb = -1);
 tc_status launch_axpby(tc_plan* p, double2* y, const double2* a, double ca, const double2* b,
                        double cb, size_t n, cudaStream_t s);
 tc_status launch_diagnostics(tc_plan* p, const double2* u, double* red, cudaStream_t s);

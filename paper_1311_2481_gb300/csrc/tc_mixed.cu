@@ -120,7 +120,7 @@ constexpr int kPrepWin = kPrepR + kStencil - 1;
 // P[(d * 3 + c) * S + (r (M+1) + m) nk + kk], d = 0: u', d = 1: d_r u'.
 __global__ void __launch_bounds__(256) k_prep32(const double2* __restrict__ u, float2* __restrict__ P,
                                                 const float* __restrict__ w1f, const int* __restrict__ col0,
-                                                int N_r, int M, int K, int nkt, int nrc) {
+                                                int N_r, int M, int K, int nkt, int nrc, int m0, int mcnt) {
     __shared__ float4 win[kPrepWin * kPrepK];
     __shared__ float sw[kPrepR * kStencil];
     int b = blockIdx.x;
@@ -128,8 +128,8 @@ __global__ void __launch_bounds__(256) k_prep32(const double2* __restrict__ u, f
     b /= nkt;
     const int rc = b % nrc;
     b /= nrc;
-    const int m = b % (M + 1);
-    const int c = b / (M + 1);
+    const int m = m0 + b % mcnt;
+    const int c = b / mcnt;
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
     const size_t colstride = (size_t)(M + 1) * nk;
@@ -195,7 +195,7 @@ __device__ __forceinline__ float2 zinv_input(const float2* __restrict__ P, size_
 // generic length: runtime radices, L lines per block
 __global__ void __launch_bounds__(256) k_zinv_p32(const float2* __restrict__ P, float2* __restrict__ H1,
                                                   int N_r, int M, int K, float kzf, int L,
-                                                  const float2* __restrict__ tw, Radices rad) {
+                                                  const float2* __restrict__ tw, Radices rad, int m0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Pz = rad.n;
     float2* a = reinterpret_cast<float2*>(smem_raw);
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) k_zinv_p32(const float2* __restrict__ P, 
     const int g = blockIdx.x % groups;
     const int rm = blockIdx.x / groups;
     const int r = rm % N_r;
-    const int m = rm / N_r;
+    const int m = m0 + rm / N_r;
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
     const size_t line = ((size_t)r * (M + 1) + m) * nk + K;
@@ -226,7 +226,8 @@ __global__ void __launch_bounds__(256) k_zinv_p32(const float2* __restrict__ P, 
 // compile-time length PZ, L lines per block
 template <int PZ, int L, int NT>
 __global__ void __launch_bounds__(NT) k_zinv_s(const float2* __restrict__ P, float2* __restrict__ H1,
-                                               int N_r, int M, int K, float kzf, const float2* __restrict__ tw) {
+                                               int N_r, int M, int K, float kzf, const float2* __restrict__ tw,
+                                               int m0) {
     constexpr int LP = cft::padded<PZ>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* a = reinterpret_cast<float2*>(smem_raw);
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(NT) k_zinv_s(const float2* __restrict__ P, flo
     const int g = blockIdx.x % groups;
     const int rm = blockIdx.x / groups;
     const int r = rm % N_r;
-    const int m = rm / N_r;
+    const int m = m0 + rm / N_r;
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
     const size_t line = ((size_t)r * (M + 1) + m) * nk + K;
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(256) k_zfwd32(const float2* __restrict__ H2, d
                                                 const float2* __restrict__ tw, Radices rad,
                                                 const double2* __restrict__ u, const double* __restrict__ rnodes,
                                                 const double* __restrict__ w1, const int* __restrict__ col0,
-                                                double mp, int Lf) {
+                                                double mp, int Lf, int m0, int mcnt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float s_cf[8];    // A, B, C, t as (hi, lo)
     __shared__ double s_mf[3];   // U/r, q, U (the (0,0) mode is assembled in FP64)
@@ -355,8 +356,8 @@ __global__ void __launch_bounds__(256) k_zfwd32(const float2* __restrict__ H2, d
     float2* a = reinterpret_cast<float2*>(smem_raw);
     float2* b = a + (size_t)Lf * Pz;
     const int cg = blockIdx.x % (3 / Lf);
-    const int m = (blockIdx.x / (3 / Lf)) % (M + 1);
-    const int r = (blockIdx.x / (3 / Lf)) / (M + 1);
+    const int m = m0 + (blockIdx.x / (3 / Lf)) % mcnt;
+    const int r = (blockIdx.x / (3 / Lf)) / mcnt;
     const size_t fstride = (size_t)N_r * (M + 1) * Pz;
     const float2* h = H2 + ((size_t)r * (M + 1) + m) * Pz;
     const int nk = 2 * K + 1;
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(NT) k_zfwd_s(const float2* __restrict__ H2, do
                                                int N_r, int M, int K, float scale, const float2* __restrict__ tw,
                                                const double2* __restrict__ u, const double* __restrict__ rnodes,
                                                const double* __restrict__ w1, const int* __restrict__ col0,
-                                               double mp) {
+                                               double mp, int m0, int mcnt) {
     constexpr int LP = cft::padded<PZ>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float s_cf[8];
@@ -394,8 +395,8 @@ __global__ void __launch_bounds__(NT) k_zfwd_s(const float2* __restrict__ H2, do
     float2* b = a + LF * LP;
     constexpr int groups = 3 / LF;
     const int cg = blockIdx.x % groups;
-    const int m = (blockIdx.x / groups) % (M + 1);
-    const int r = (blockIdx.x / groups) / (M + 1);
+    const int m = m0 + (blockIdx.x / groups) % mcnt;
+    const int r = (blockIdx.x / groups) / mcnt;
     const size_t fstride = (size_t)N_r * (M + 1) * PZ;
     const float2* h = H2 + ((size_t)r * (M + 1) + m) * PZ;
     const int nk = 2 * K + 1;
@@ -438,14 +439,15 @@ namespace {
 
 template <int PZ, int L, int LF, int NT>
 tc_status run_zpasses_s(tc_plan* p, const float2* P, float2* H1, const float2* H2, const double2* u, double2* N,
-                        cudaStream_t s, bool inverse) {
+                        cudaStream_t s, bool inverse, int ma, int mb) {
     constexpr int LP = cft::padded<PZ>();
+    const int mc = mb - ma;
     if (inverse) {
         const size_t sm = (size_t)2 * L * LP * sizeof(float2);
         TC_CUDA(p, cudaFuncSetAttribute(k_zinv_s<PZ, L, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int slot = prof_begin(p, kKZinv32, s);
-        k_zinv_s<PZ, L, NT><<<p->N_r * (p->M + 1) * (9 / L), NT, sm, s>>>(P, H1, p->N_r, p->M, p->K, (float)p->k_z,
-                                                                         p->d_tw_z32);
+        k_zinv_s<PZ, L, NT><<<p->N_r * mc * (9 / L), NT, sm, s>>>(P, H1, p->N_r, p->M, p->K, (float)p->k_z,
+                                                                 p->d_tw_z32, ma);
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_zinv_s");
     } else {
@@ -453,30 +455,30 @@ tc_status run_zpasses_s(tc_plan* p, const float2* P, float2* H1, const float2* H
         TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_s<PZ, LF, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const float scale = (float)(1.0 / ((double)p->P_t * (double)p->P_z));
         const int slot = prof_begin(p, kKZfwd32, s);
-        k_zfwd_s<PZ, LF, NT><<<p->N_r * (p->M + 1) * (3 / LF), NT, sm, s>>>(H2, N, p->N_r, p->M, p->K, scale,
-                                                                           p->d_tw_z32, u, p->d_r, p->d_w1,
-                                                                           p->d_col0, (double)p->m_p);
+        k_zfwd_s<PZ, LF, NT><<<p->N_r * mc * (3 / LF), NT, sm, s>>>(H2, N, p->N_r, p->M, p->K, scale,
+                                                                   p->d_tw_z32, u, p->d_r, p->d_w1,
+                                                                   p->d_col0, (double)p->m_p, ma, mc);
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_zfwd_s");
     }
     return TC_OK;
 }
 
-// length-specialised z passes; TC_ERR_ARG if P_z has no compile-time plan
+// length-specialised z passes over m in [ma, mb); TC_ERR_ARG if P_z has no compile-time plan
 tc_status zpass_s(tc_plan* p, const float2* P, float2* H1, const float2* H2, const double2* u, double2* N,
-                  cudaStream_t s, bool inverse) {
+                  cudaStream_t s, bool inverse, int ma, int mb) {
     switch (p->P_z) {
-        case 12: return run_zpasses_s<12, 9, 3, 64>(p, P, H1, H2, u, N, s, inverse);
-        case 24: return run_zpasses_s<24, 9, 3, 64>(p, P, H1, H2, u, N, s, inverse);
-        case 48: return run_zpasses_s<48, 9, 3, 128>(p, P, H1, H2, u, N, s, inverse);
-        case 96: return run_zpasses_s<96, 9, 3, 128>(p, P, H1, H2, u, N, s, inverse);
-        case 192: return run_zpasses_s<192, 9, 3, 256>(p, P, H1, H2, u, N, s, inverse);
-        case 384: return run_zpasses_s<384, 3, 3, 128>(p, P, H1, H2, u, N, s, inverse);
-        case 768: return run_zpasses_s<768, 3, 3, 256>(p, P, H1, H2, u, N, s, inverse);
-        case 1152: return run_zpasses_s<1152, 3, 3, 256>(p, P, H1, H2, u, N, s, inverse);
-        case 1536: return run_zpasses_s<1536, 3, 3, 256>(p, P, H1, H2, u, N, s, inverse);
-        case 2304: return run_zpasses_s<2304, 1, 1, 256>(p, P, H1, H2, u, N, s, inverse);
-        case 3072: return run_zpasses_s<3072, 1, 1, 256>(p, P, H1, H2, u, N, s, inverse);
+        case 12: return run_zpasses_s<12, 9, 3, 64>(p, P, H1, H2, u, N, s, inverse, ma, mb);
+        case 24: return run_zpasses_s<24, 9, 3, 64>(p, P, H1, H2, u, N, s, inverse, ma, mb);
+        case 48: return run_zpasses_s<48, 9, 3, 128>(p, P, H1, H2, u, N, s, inverse, ma, mb);
+        case 96: return run_zpasses_s<96, 9, 3, 128>(p, P, H1, H2, u, N, s, inverse, ma, mb);
+        case 192: return run_zpasses_s<192, 9, 3, 256>(p, P, H1, H2, u, N, s, inverse, ma, mb);
+        case 384: return run_zpasses_s<384, 3, 3, 128>(p, P, H1, H2, u, N, s, inverse, ma, mb);
+        case 768: return run_zpasses_s<768, 3, 3, 256>(p, P, H1, H2, u, N, s, inverse, ma, mb);
+        case 1152: return run_zpasses_s<1152, 3, 3, 256>(p, P, H1, H2, u, N, s, inverse, ma, mb);
+        case 1536: return run_zpasses_s<1536, 3, 3, 256>(p, P, H1, H2, u, N, s, inverse, ma, mb);
+        case 2304: return run_zpasses_s<2304, 1, 1, 256>(p, P, H1, H2, u, N, s, inverse, ma, mb);
+        case 3072: return run_zpasses_s<3072, 1, 1, 256>(p, P, H1, H2, u, N, s, inverse, ma, mb);
     }
     return TC_ERR_ARG;
 }
@@ -491,44 +493,52 @@ bool zpass_s_ok(const tc_plan* p) {
 
 }  // namespace
 
-tc_status launch_nonlinear_mixed(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s) {
-    float2* P = reinterpret_cast<float2*>(ws + p->ws.P32);   // aliases H2: dead before the theta pass
+// before the theta pass, for m in [ma, mb): FP32 split and radial derivative, inverse z pass
+tc_status launch_nl_pre32(tc_plan* p, const double2* u, char* ws, cudaStream_t s, int ma, int mb) {
+    float2* P = reinterpret_cast<float2*>(ws + p->ws.P32);
     float2* H1 = reinterpret_cast<float2*>(ws + p->ws.H1);
-    float2* H2 = reinterpret_cast<float2*>(ws + p->ws.H2);
+    const int mc = mb - ma;
     const int nk = 2 * p->K + 1;
     const int nkt = (nk + kPrepK - 1) / kPrepK;
     const int nrc = (p->N_r + kPrepR - 1) / kPrepR;
     int slot = prof_begin(p, kKPrep32, s);
-    k_prep32<<<(unsigned)(nkt * nrc * (p->M + 1) * 3), dim3(kPrepK, 8), 0, s>>>(u, P, p->d_w1f, p->d_col0, p->N_r,
-                                                                             p->M, p->K, nkt, nrc);
+    k_prep32<<<(unsigned)(nkt * nrc * mc * 3), dim3(kPrepK, 8), 0, s>>>(u, P, p->d_w1f, p->d_col0, p->N_r, p->M, p->K,
+                                                                      nkt, nrc, ma, mc);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_prep32");
     // length-specialised kernels where the plan's lengths have compile-time radix plans, unless
     // the plan fixed the generic theta kernel's z tile (tc_options.theta_zt)
-    const bool zs = zpass_s_ok(p);
-    if (zs) {
-        TC_TRY_STATUS(zpass_s(p, P, H1, H2, u, N, s, true));
-    } else {
-        const int L = p->zinv_lines32;
-        const size_t sm1 = (size_t)2 * L * p->P_z * sizeof(float2);
-        TC_CUDA(p, cudaFuncSetAttribute(k_zinv_p32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
-        slot = prof_begin(p, kKZinv32, s);
-        k_zinv_p32<<<p->N_r * (p->M + 1) * (9 / L), 256, sm1, s>>>(P, H1, p->N_r, p->M, p->K, (float)p->k_z, L,
-                                                                    p->d_tw_z32, p->rad_z);
-        prof_end(p, slot, s);
-        TC_LAUNCHED(p, "k_zinv_p32");
-    }
-    if (p->theta_zt_forced == 0 && theta_s_zt(p, false) > 0) TC_TRY_STATUS(launch_theta_s(p, H1, H2, s));
-    else TC_TRY_STATUS(launch_theta32(p, H1, H2, s));
-    if (zs) return zpass_s(p, P, H1, H2, u, N, s, false);
+    if (zpass_s_ok(p)) return zpass_s(p, P, H1, nullptr, nullptr, nullptr, s, true, ma, mb);
+    const int L = p->zinv_lines32;
+    const size_t sm1 = (size_t)2 * L * p->P_z * sizeof(float2);
+    TC_CUDA(p, cudaFuncSetAttribute(k_zinv_p32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+    slot = prof_begin(p, kKZinv32, s);
+    k_zinv_p32<<<p->N_r * mc * (9 / L), 256, sm1, s>>>(P, H1, p->N_r, p->M, p->K, (float)p->k_z, L,
+                                                        p->d_tw_z32, p->rad_z, ma);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_zinv_p32");
+    return TC_OK;
+}
+
+tc_status launch_nl_theta32(tc_plan* p, char* ws, cudaStream_t s) {
+    const float2* H1 = reinterpret_cast<const float2*>(ws + p->ws.H1);
+    float2* H2 = reinterpret_cast<float2*>(ws + p->ws.H2);
+    if (p->theta_zt_forced == 0 && theta_s_zt(p, false) > 0) return launch_theta_s(p, H1, H2, s);
+    return launch_theta32(p, H1, H2, s);
+}
+
+// after the theta pass, for m in [ma, mb): forward z pass, mean-flow terms, N in FP64
+tc_status launch_nl_post32(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s, int ma, int mb) {
+    const float2* H2 = reinterpret_cast<const float2*>(ws + p->ws.H2);
+    if (zpass_s_ok(p)) return zpass_s(p, nullptr, nullptr, H2, u, N, s, false, ma, mb);
     const int Lf = p->zfwd_lines32;
     const size_t sm3 = (size_t)2 * Lf * p->P_z * sizeof(float2);
     TC_CUDA(p, cudaFuncSetAttribute(k_zfwd32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
     const float scale = (float)(1.0 / ((double)p->P_t * (double)p->P_z));
-    slot = prof_begin(p, kKZfwd32, s);
-    k_zfwd32<<<p->N_r * (p->M + 1) * (3 / Lf), 256, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, p->d_tw_z32,
-                                                               p->rad_z, u, p->d_r, p->d_w1, p->d_col0,
-                                                               (double)p->m_p, Lf);
+    const int slot = prof_begin(p, kKZfwd32, s);
+    k_zfwd32<<<p->N_r * (mb - ma) * (3 / Lf), 256, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, p->d_tw_z32,
+                                                              p->rad_z, u, p->d_r, p->d_w1, p->d_col0,
+                                                              (double)p->m_p, Lf, ma, mb - ma);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_zfwd32");
     return TC_OK;

@@ -247,6 +247,14 @@ static tc_status upload(tc_plan* p) {
     TC_CUDA(p, put((void**)&p->d_tw_z32, f.data(), f.size() * sizeof(float)));
     f.assign(p->tw_t.begin(), p->tw_t.end());
     TC_CUDA(p, put((void**)&p->d_tw_t32, f.data(), f.size() * sizeof(float)));
+    if (p->pipeline > 1) {
+        for (int i = 0; i < 2; ++i) TC_CUDA(p, cudaStreamCreateWithFlags(&p->aux[i], cudaStreamNonBlocking));
+        for (int i = 0; i < 3 + 2 * p->pipeline; ++i) {
+            cudaEvent_t e;
+            TC_CUDA(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            p->pev.push_back(e);
+        }
+    }
     return TC_OK;
 }
 
@@ -281,6 +289,13 @@ void prof_end(tc_plan* p, int slot, cudaStream_t s) {
 static void free_device(tc_plan* p) {
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     p->prof_ev.clear();
+    for (cudaEvent_t e : p->pev) cudaEventDestroy(e);
+    p->pev.clear();
+    for (cudaStream_t& q : p->aux)
+        if (q) {
+            cudaStreamDestroy(q);
+            q = nullptr;
+        }
     void* ptrs[] = {p->d_r, p->d_ir, p->d_w1, p->d_w1f, p->d_w2, p->d_col0, p->d_d1t_row, p->d_d1t_w, p->d_fac, p->d_piv,
                     p->d_tw_z, p->d_tw_t, p->d_tw_z32, p->d_tw_t32};
     for (void* q : ptrs)
@@ -429,11 +444,12 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     p->pc_modes = o.pc_modes;
     p->theta_zt_forced = o.theta_zt;
     p->theta_variant = o.theta_variant;
+    p->pipeline = o.pipeline == 0 ? 1 : std::min(o.pipeline, std::min(16, M + 1));
     p->thr_zinv = choose_threads(rz, p->zinv_lines, 0);
     p->thr_theta = choose_threads(rt, 6 * p->zt, p->zt + (p->zt + 1) / 2);
     p->thr_zfwd = choose_threads(rz, p->zfwd_lines, 0);
     if (o.theta_zt < 0 || o.theta_zt > 64 || o.pc_modes < 0 || o.pc_modes > 32 || o.pc_split < -1 || o.pc_split > 1 ||
-        o.theta_variant < 0 || o.theta_variant > 3) {
+        o.theta_variant < 0 || o.theta_variant > 3 || o.pipeline < 0) {
         delete p;
         return TC_ERR_ARG;
     }
@@ -452,11 +468,10 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     p->adjoint = o.no_adjoint == 0;
     const size_t lane = (p->precision == TC_MIXED && !p->adjoint) ? sizeof(float2) : cplx;
     p->ws.H1 = take(9 * p->Hfield * lane);
-    // the mixed form's FP32 u', d_r u' live between k_prep32 and k_zinv_p32, before k_theta
-    // writes H2, so they share its region
-    const size_t p32 = p->precision == TC_MIXED ? 6 * p->S * sizeof(float2) : 0;
-    p->ws.H2 = take(std::max(3 * p->Hfield * lane, p32));
-    p->ws.P32 = p->ws.H2;
+    p->ws.H2 = take(3 * p->Hfield * lane);
+    // the mixed form's FP32 u', d_r u' (its own region: with the overlapped step the split of
+    // one m-chunk runs while the forward z pass of another still reads H2)
+    p->ws.P32 = take(p->precision == TC_MIXED ? 6 * p->S * sizeof(float2) : 0);
     p->ws.Ncur = take(3 * p->S * cplx);
     p->ws.uE = take(3 * p->S * cplx);
     // steps 2-5: fused kernel while 8 modes' four columns fit in 96 KB of shared memory,

@@ -41,8 +41,8 @@ __global__ void __launch_bounds__(kPCThreads) k_pc(PCArgs a, Geo g, int T) {
     double2* C1 = sm + items;
     double2* C2 = C1 + items;
     double2* C3 = C2 + items;
-    const int mode0 = blockIdx.x * T;
-    const int nT = min(T, g.nmode - mode0);
+    const int mode0 = g.mlo + blockIdx.x * T;
+    const int nT = min(T, g.mhi - mode0);
     const size_t per_set = (size_t)N * kBands * g.M1K1;
     const double c1 = 1.0 / (2.0 * g.dt);
 
@@ -254,8 +254,8 @@ __global__ void __launch_bounds__(kPCThreads) k_pc(PCArgs a, Geo g, int T) {
 // X = (2N - N_prev)_r = ((2N - N_prev)_+ + (2N - N_prev)_-) / 2, once per element (the
 // pressure right-hand side applies the radial stencil to it).
 __global__ void k_nn_r(const double2* __restrict__ Nc, const double2* __restrict__ Np, double2* __restrict__ X, Geo g) {
-    const int mode = blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
-    if (mode >= g.nmode) return;
+    const int mode = g.mlo + blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
+    if (mode >= g.mhi) return;
     const size_t e = (size_t)blockIdx.x * g.nmode + mode;
     const double2 n1 = Nc[e], n0 = Np[e], m1 = Nc[g.S + e], m0 = Np[g.S + e];
     X[e] = make_double2(0.5 * ((2.0 * n1.x - n0.x) + (2.0 * m1.x - m0.x)),
@@ -272,8 +272,8 @@ __global__ void k_rhs_pressure(const double2* __restrict__ u, const double2* __r
                                const int* __restrict__ col0, Geo g) {
     // grid: x = radial row (fastest, so neighbouring rows of a mode range run together and
     // the stencil's rows stay in cache), y over modes
-    const int mode = blockIdx.y * blockDim.x + threadIdx.x;
-    if (mode >= g.nmode) return;
+    const int mode = g.mlo + blockIdx.y * blockDim.x + threadIdx.x;
+    if (mode >= g.mhi) return;
     const int j = blockIdx.x;
     const size_t e = (size_t)j * g.nmode + mode;
     const int m = mode / g.nk;
@@ -312,8 +312,8 @@ __global__ void k_rhs_velocity(const double2* __restrict__ u, const double2* __r
                                double2* __restrict__ p_out, const double* __restrict__ irn,
                                const double* __restrict__ w1, const int* __restrict__ col0,
                                double Re_i, double Re_o, Geo g) {
-    const int mode = blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
-    if (mode >= g.nmode) return;
+    const int mode = g.mlo + blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
+    if (mode >= g.mhi) return;
     const int j = blockIdx.x;
     const size_t e = (size_t)j * g.nmode + mode;
     const int m = mode / g.nk;
@@ -345,8 +345,8 @@ __global__ void k_rhs_velocity(const double2* __restrict__ u, const double2* __r
 __global__ void k_rhs_div(const double2* __restrict__ us, double2* __restrict__ b,
                           const double* __restrict__ irn, const double* __restrict__ w1,
                           const int* __restrict__ col0, Geo g) {
-    const int mode = blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
-    if (mode >= g.nmode) return;
+    const int mode = g.mlo + blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
+    if (mode >= g.mhi) return;
     const int j = blockIdx.x;
     const size_t e = (size_t)j * g.nmode + mode;
     if (j == 0 || j == g.N - 1) { b[e] = make_double2(0.0, 0.0); return; }
@@ -375,8 +375,8 @@ __global__ void k_update(double2* u, double2* up, const double2* Nc, double2* Np
                          const double2* __restrict__ us, const double2* __restrict__ phi,
                          double2* __restrict__ u_out, const double* __restrict__ irn,
                          const double* __restrict__ w1, const int* __restrict__ col0, int commit, Geo g) {
-    const int mode = blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
-    if (mode >= g.nmode) return;
+    const int mode = g.mlo + blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
+    if (mode >= g.mhi) return;
     const int j = blockIdx.x;
     const size_t e = (size_t)j * g.nmode + mode;
     const int m = mode / g.nk;
@@ -412,9 +412,9 @@ __global__ void k_update(double2* u, double2* up, const double2* Nc, double2* Np
 __global__ void k_band_solve_g(double2* __restrict__ x, const double* __restrict__ fac,
                                const uint8_t* __restrict__ piv, int set0, int nfields, Geo g) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;   // (mode, part); y = field
-    if (t >= 2 * g.nmode) return;
+    if (t >= 2 * (g.mhi - g.mlo)) return;
     const int part = t & 1;
-    const int mode = t >> 1;
+    const int mode = g.mlo + (t >> 1);
     const int fld = blockIdx.y;
     const int m = mode / g.nk;
     const int k = mode - m * g.nk - g.K;
@@ -431,8 +431,8 @@ __global__ void __launch_bounds__(256) k_band_solve_s(double2* __restrict__ x, c
                                                       const uint8_t* __restrict__ piv, int set, Geo g, int T) {
     extern __shared__ double2 sm[];
     const int N = g.N;
-    const int mode0 = blockIdx.x * T;
-    const int nT = min(T, g.nmode - mode0);
+    const int mode0 = g.mlo + blockIdx.x * T;
+    const int nT = min(T, g.mhi - mode0);
     for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
         const int j = idx / T, t = idx - (idx / T) * T;
         sm[idx] = t < nT ? x[(size_t)j * g.nmode + mode0 + t] : make_double2(0.0, 0.0);
@@ -552,13 +552,16 @@ tc_status launch_solve(tc_plan* p, int set, double2* x, int nfields, cudaStream_
 
 static tc_status launch_advance_split(tc_plan* p, const double2* u, double2* u_prev, const double2* Ncur,
                                       double2* N_prev, double2* p_out, double2* u_out, char* ws, bool commit,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, int ma, int mb) {
     Geo g = geo(p);
+    g.mlo = ma * g.nk;
+    g.mhi = mb * g.nk;
+    const int nm = g.mhi - g.mlo;
     double2* ps = reinterpret_cast<double2*>(ws + p->ws.pstar);
     double2* us = reinterpret_cast<double2*>(ws + p->ws.ustar);
     double2* phi = reinterpret_cast<double2*>(ws + p->ws.phi);   // also holds X before phi
-    const dim3 g1(g.N, blocks_for(g.nmode, 128));
-    auto sgrid = [&](int nf) { return dim3(blocks_for((size_t)2 * g.nmode, 128), nf); };
+    const dim3 g1(g.N, blocks_for(nm, 128));
+    auto sgrid = [&](int nf) { return dim3(blocks_for((size_t)2 * nm, 128), nf); };
     int slot = prof_begin(p, kKRhsPressure, s);
     k_nn_r<<<g1, 128, 0, s>>>(Ncur, N_prev, phi, g);
     k_rhs_pressure<<<g1, 128, 0, s>>>(u, u_prev, Ncur, N_prev, phi, ps, p->d_r, p->d_ir, p->d_w1, p->d_w2, p->d_col0, g);
@@ -595,9 +598,12 @@ static tc_status launch_advance_split(tc_plan* p, const double2* u, double2* u_p
 
 tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const double2* Ncur,
                          double2* N_prev, double2* p_out, double2* u_out, char* ws, bool commit,
-                         cudaStream_t s) {
-    if (p->pc_split) return launch_advance_split(p, u, u_prev, Ncur, N_prev, p_out, u_out, ws, commit, s);
+                         cudaStream_t s, int ma, int mb) {
+    if (mb < 0) mb = p->M + 1;
+    if (p->pc_split) return launch_advance_split(p, u, u_prev, Ncur, N_prev, p_out, u_out, ws, commit, s, ma, mb);
     Geo g = geo(p);
+    g.mlo = ma * g.nk;
+    g.mhi = mb * g.nk;
     const int T = pc_modes(p);
     PCArgs a;
     a.u = u; a.up = u_prev; a.Nc = Ncur; a.Np = N_prev;
@@ -613,7 +619,7 @@ tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const do
     const int threads = kPCThreads;   // T <= 16 keeps the 6T substitution threads within the block
     TC_CUDA(p, cudaFuncSetAttribute(k_pc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int slot = prof_begin(p, kKPC, s);
-    k_pc<<<blocks_for(g.nmode, T), threads, sm, s>>>(a, g, T);
+    k_pc<<<blocks_for(g.mhi - g.mlo, T), threads, sm, s>>>(a, g, T);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_pc");
     return TC_OK;

@@ -31,7 +31,7 @@ class tc_options(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("P_theta", ctypes.c_int), ("P_z", ctypes.c_int),
                 ("precision", ctypes.c_int), ("host_only", ctypes.c_int), ("theta_zt", ctypes.c_int),
                 ("pc_modes", ctypes.c_int), ("no_adjoint", ctypes.c_int), ("pc_split", ctypes.c_int),
-                ("theta_variant", ctypes.c_int)]
+                ("theta_variant", ctypes.c_int), ("pipeline", ctypes.c_int)]
 
 
 class tc_state(ctypes.Structure):
@@ -182,9 +182,9 @@ class Plan:
 
     def __init__(self, N_r, M, K, m_p, eta, Re_i, Re_o, L_z, dt, fd_order=8, alpha=0.5,
                  P_theta=0, P_z=0, precision=TC_FP64, host_only=False, device=None, theta_zt=0,
-                 pc_modes=0, no_adjoint=False, pc_split=0, theta_variant=0):
+                 pc_modes=0, no_adjoint=False, pc_split=0, theta_variant=0, pipeline=0):
         opt = tc_options(alpha if alpha != 0.0 else -1.0, P_theta, P_z, precision, int(host_only),
-                         theta_zt, pc_modes, int(no_adjoint), pc_split, theta_variant)
+                         theta_zt, pc_modes, int(no_adjoint), pc_split, theta_variant, pipeline)
         self.N_r, self.M, self.K = N_r, M, K
         self.handle = None
         torch = _torch()
