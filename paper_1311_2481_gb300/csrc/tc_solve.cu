@@ -33,7 +33,8 @@ struct PCArgs {
 // Steps 2-5 of Sec. 3.2 for the T modes of this block: pressure prediction (Eq. pressure
 // with the Neumann rows of Eq. ppBC), velocity prediction (Eq. vel), correction potential
 // (Eq. correction) and update (Eq. update).
-__global__ void __launch_bounds__(kPCThreads) k_pc(PCArgs a, Geo g, int T) {
+template <int NTH>
+__global__ void __launch_bounds__(NTH) k_pc(PCArgs a, Geo g, int T) {
     extern __shared__ double2 sm[];
     const int N = g.N;
     const int items = N * T;
@@ -616,10 +617,15 @@ tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const do
     a.Re_i = p->Re_i; a.Re_o = p->Re_o;
     a.commit = commit ? 1 : 0;
     const size_t sm = (size_t)4 * p->N_r * T * sizeof(double2);
-    const int threads = kPCThreads;   // T <= 16 keeps the 6T substitution threads within the block
-    TC_CUDA(p, cudaFuncSetAttribute(k_pc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    // 128 threads up to 8 modes per block, 256 beyond (6T substitution threads plus helpers)
     const int slot = prof_begin(p, kKPC, s);
-    k_pc<<<blocks_for(g.mhi - g.mlo, T), threads, sm, s>>>(a, g, T);
+    if (T <= 8) {
+        TC_CUDA(p, cudaFuncSetAttribute(k_pc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_pc<128><<<blocks_for(g.mhi - g.mlo, T), 128, sm, s>>>(a, g, T);
+    } else {
+        TC_CUDA(p, cudaFuncSetAttribute(k_pc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_pc<256><<<blocks_for(g.mhi - g.mlo, T), 256, sm, s>>>(a, g, T);
+    }
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_pc");
     return TC_OK;

@@ -287,3 +287,20 @@ def test_overlapped_twenty_steps_match_oracle():
     st = tc.State(plan, dev(u0))
     plan.step(st, 20)
     assert rel(host(st.u), ref.u) <= 1e-10
+
+
+@pytest.mark.parametrize("T", [4, 16])
+def test_pc_modes_bit_identical(T):
+    """The fused steps-2-5 kernel with 4 or 16 modes per block (128 or 256 threads) gives the
+    same state as the default 8, bit for bit: each mode's arithmetic is the same."""
+    cfg = dict(N_r=32, M=12, K=16, m_p=1, eta=0.5, Re_i=100.0, Re_o=0.0, L_z=LZ, dt=1e-4)
+    ops = O.Operators(O.Params(**cfg))
+    u0 = init(ops, kind="broadband", amp=1e-2, seed=10)
+    out = []
+    for modes in (8, T):
+        plan = tc.Plan(**cfg, pc_modes=modes)
+        st = tc.State(plan, dev(u0))
+        plan.step(st, 5)
+        out.append([host(getattr(st, k)) for k in ("u", "u_prev", "N_prev", "p")])
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
