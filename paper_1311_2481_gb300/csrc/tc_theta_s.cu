@@ -82,20 +82,60 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, 
 #pragma unroll 1
     for (int phase = 0; phase < 3; ++phase) {
         // spectra of the two lines of each z (lines 2 zi and 2 zi + 1)
-        for (int m = (int)threadIdx.x / ZT; m <= M; m += mstep) {
-            const size_t o = (size_t)m * Pz + zi;
-            const T mm = mpf * (T)m;
+        if constexpr (sizeof(V) == 16) {
+            // FP64 lines: the four fields of the phase for two m values per thread loaded
+            // before they are placed (measured faster; 2M+1 <= PT bounds the m values)
+            const int fa = phase == 0 ? 0 : phase == 1 ? 3 : 6;
+            const int fc = phase == 0 ? 2 : phase == 1 ? 0 : 2;
+            const int fd = phase == 0 ? 5 : phase == 1 ? 1 : 8;
+            constexpr int MI = (PT / 2 + 1 + NT / ZT - 1) / (NT / ZT);
+            constexpr int G = 2;
             V* L0 = A + (2 * zi) * LP;
             V* L1 = L0 + LP;
-            if (phase == 0) {
-                put_pair(L0, PT, m, h[0 * fstride + o], h[1 * fstride + o]);
-                put_real2(L1, PT, m, h[2 * fstride + o], h[5 * fstride + o]);
-            } else if (phase == 1) {
-                put_pair(L0, PT, m, h[3 * fstride + o], h[4 * fstride + o]);
-                put_pair(L1, PT, m, imul(h[0 * fstride + o], mm), imul(h[1 * fstride + o], mm));
-            } else {
-                put_pair(L0, PT, m, h[6 * fstride + o], h[7 * fstride + o]);
-                put_real2(L1, PT, m, imul(h[2 * fstride + o], mm), h[8 * fstride + o]);
+#pragma unroll
+            for (int i0 = 0; i0 < MI; i0 += G) {
+                V va[G], vb[G], vc[G], vd[G];
+#pragma unroll
+                for (int i = 0; i < G; ++i) {
+                    const int m = (int)threadIdx.x / ZT + (i0 + i) * mstep;
+                    if (i0 + i < MI && m <= M) {
+                        const size_t o = (size_t)m * Pz + zi;
+                        va[i] = h[fa * fstride + o];
+                        vb[i] = h[(fa + 1) * fstride + o];
+                        vc[i] = h[fc * fstride + o];
+                        vd[i] = h[fd * fstride + o];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < G; ++i) {
+                    const int m = (int)threadIdx.x / ZT + (i0 + i) * mstep;
+                    if (i0 + i < MI && m <= M) {
+                        const T mm = mpf * (T)m;
+                        put_pair(L0, PT, m, va[i], vb[i]);
+                        if (phase == 0) put_real2(L1, PT, m, vc[i], vd[i]);
+                        else if (phase == 1) put_pair(L1, PT, m, imul(vc[i], mm), imul(vd[i], mm));
+                        else put_real2(L1, PT, m, imul(vc[i], mm), vd[i]);
+                    }
+                }
+            }
+        } else {
+            // FP32 lines: one m value at a time (the extra registers of batched loads cost
+            // more than the latency they hide here)
+            for (int m = (int)threadIdx.x / ZT; m <= M; m += mstep) {
+                const size_t o = (size_t)m * Pz + zi;
+                const T mm = mpf * (T)m;
+                V* L0 = A + (2 * zi) * LP;
+                V* L1 = L0 + LP;
+                if (phase == 0) {
+                    put_pair(L0, PT, m, h[0 * fstride + o], h[1 * fstride + o]);
+                    put_real2(L1, PT, m, h[2 * fstride + o], h[5 * fstride + o]);
+                } else if (phase == 1) {
+                    put_pair(L0, PT, m, h[3 * fstride + o], h[4 * fstride + o]);
+                    put_pair(L1, PT, m, imul(h[0 * fstride + o], mm), imul(h[1 * fstride + o], mm));
+                } else {
+                    put_pair(L0, PT, m, h[6 * fstride + o], h[7 * fstride + o]);
+                    put_real2(L1, PT, m, imul(h[2 * fstride + o], mm), h[8 * fstride + o]);
+                }
             }
         }
         // zero band M < p < PT - M of every line
