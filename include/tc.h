@@ -151,6 +151,17 @@ tc_status tc_helmholtz_solve(tc_plan* plan, int which, const void* rhs, void* x,
  * that history. */
 tc_status tc_step(tc_plan* plan, tc_state* st, int nsteps, void* ws, void* stream);
 
+/* tc_step with the state in host memory.  host_in: host copies of u, u_prev, N_prev, p (all
+ * four required) and its started flag; dev: caller-owned device buffers of the same shapes,
+ * used as the working state; host_out: each non-null field receives the device result after
+ * the steps (u, u_prev, N_prev, p; host_out->started is set).  Host buffers may be pinned or
+ * pageable; pinned ones let the copies run at full link speed.  The copies and the steps are
+ * enqueued on `stream`, which is synchronised before the call returns, so host_out is valid
+ * on return.  host_out fields may alias host_in fields.  Errors: TC_ERR_ARG if a pointer of
+ * dev is not device memory, a host pointer is device memory, or dev fields coincide. */
+tc_status tc_step_host(tc_plan* plan, const tc_state* host_in, tc_state* host_out, tc_state* dev,
+                       int nsteps, void* ws, void* stream);
+
 /* Diagnostics of the velocity field u (device vector field); synchronises the stream and
  * writes *out (host).  Returns TC_ERR_NONFINITE if u holds a NaN/Inf. */
 tc_status tc_diagnostics(tc_plan* plan, const void* u, tc_diag* out, void* ws, void* stream);

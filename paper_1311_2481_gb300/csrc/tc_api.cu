@@ -150,6 +150,37 @@ tc_status tc_step(tc_plan* plan, tc_state* st, int nsteps, void* ws, void* strea
     return TC_OK;
 }
 
+tc_status tc_step_host(tc_plan* plan, const tc_state* host_in, tc_state* host_out, tc_state* dev,
+                       int nsteps, void* ws, void* stream) {
+    TC_TRY(ready(plan));
+    if (!host_in || !host_out || !dev) return TC_ERR_ARG;
+    const void* hin[4] = {host_in->u, host_in->u_prev, host_in->N_prev, host_in->p};
+    for (int i = 0; i < 4; ++i) {
+        if (!hin[i]) return TC_ERR_ARG;
+        cudaPointerAttributes at;
+        TC_CUDA(plan, cudaPointerGetAttributes(&at, hin[i]));
+        if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+            snprintf(plan->err, sizeof(plan->err), "tc_step_host: host_in field %d is device memory", i);
+            return TC_ERR_ARG;
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t vb = 3 * plan->S * sizeof(double2), sb = plan->S * sizeof(double2);
+    void* dptr[4] = {dev->u, dev->u_prev, dev->N_prev, dev->p};
+    const size_t bytes[4] = {vb, vb, vb, sb};
+    for (int i = 0; i < 4; ++i) TC_TRY(check_device_ptr(plan, dptr[i], "dev state"));
+    for (int i = 0; i < 4; ++i)
+        TC_CUDA(plan, cudaMemcpyAsync(dptr[i], hin[i], bytes[i], cudaMemcpyHostToDevice, s));
+    dev->started = host_in->started;
+    TC_TRY(tc_step(plan, dev, nsteps, ws, stream));
+    void* hout[4] = {host_out->u, host_out->u_prev, host_out->N_prev, host_out->p};
+    for (int i = 0; i < 4; ++i)
+        if (hout[i]) TC_CUDA(plan, cudaMemcpyAsync(hout[i], dptr[i], bytes[i], cudaMemcpyDeviceToHost, s));
+    TC_CUDA(plan, cudaStreamSynchronize(s));
+    host_out->started = dev->started;
+    return TC_OK;
+}
+
 tc_status tc_diagnostics(tc_plan* plan, const void* u, tc_diag* out, void* ws, void* stream) {
     TC_TRY(ready(plan));
     if (!out) return TC_ERR_ARG;

@@ -224,8 +224,17 @@ __global__ void __launch_bounds__(256) k_zinv_p32(const float2* __restrict__ P, 
 }
 
 // compile-time length PZ, L lines per block
+// blocks per SM the shared memory of L padded FP32 line pairs allows, at most 1024 threads
 template <int PZ, int L, int NT>
-__global__ void __launch_bounds__(NT) k_zinv_s(const float2* __restrict__ P, float2* __restrict__ H1,
+constexpr int zinv_minb() {
+    constexpr int sm = 2 * L * cft::padded<PZ>() * 8 + 1024;
+    constexpr int by_smem = (227 * 1024) / sm;
+    constexpr int by_threads = 1024 / NT;
+    return by_smem < by_threads ? (by_smem > 0 ? by_smem : 1) : by_threads;
+}
+
+template <int PZ, int L, int NT>
+__global__ void __launch_bounds__(NT, zinv_minb<PZ, L, NT>()) k_zinv_s(const float2* __restrict__ P, float2* __restrict__ H1,
                                                int N_r, int M, int K, float kzf, const float2* __restrict__ tw,
                                                int m0) {
     constexpr int LP = cft::padded<PZ>();

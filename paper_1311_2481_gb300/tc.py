@@ -21,7 +21,7 @@ TC_FP64, TC_MIXED = 0, 1
 SYMBOLS = [
     "tc_plan_create", "tc_plan_create_ex", "tc_plan_destroy", "tc_plan_workspace_bytes",
     "tc_plan_nodes", "tc_plan_fd_weights", "tc_plan_last_error", "tc_status_string",
-    "tc_nonlinear", "tc_helmholtz_solve", "tc_step", "tc_diagnostics",
+    "tc_nonlinear", "tc_helmholtz_solve", "tc_step", "tc_step_host", "tc_diagnostics",
     "tc_adjoint_step", "tc_adjoint_start", "tc_energy_gradient",
     "tc_nonlinear_noalloc", "tc_profile_enable", "tc_profile_read",
 ]
@@ -80,6 +80,8 @@ def load_library(path: str = LIB_PATH):
         "tc_nonlinear": (I, [P, P, P, P, P]),
         "tc_helmholtz_solve": (I, [P, I, P, P, P, P]),
         "tc_step": (I, [P, ctypes.POINTER(tc_state), I, P, P]),
+        "tc_step_host": (I, [P, ctypes.POINTER(tc_state), ctypes.POINTER(tc_state), ctypes.POINTER(tc_state),
+                             I, P, P]),
         "tc_diagnostics": (I, [P, P, ctypes.POINTER(tc_diag), P, P]),
         "tc_adjoint_step": (I, [P, ctypes.POINTER(tc_state), ctypes.POINTER(tc_state_bar), P, P]),
         "tc_adjoint_start": (I, [P, P, ctypes.POINTER(tc_state_bar), P, P, P]),
@@ -146,6 +148,11 @@ def tc_helmholtz_solve(h, which, rhs_ptr, x_ptr, ws_ptr, stream_ptr):
 
 def tc_step(h, state: tc_state, nsteps, ws_ptr, stream_ptr):
     _check(load_library().tc_step(h, ctypes.byref(state), nsteps, ws_ptr, stream_ptr), h)
+
+
+def tc_step_host(h, host_in: tc_state, host_out: tc_state, dev: tc_state, nsteps, ws_ptr, stream_ptr):
+    _check(load_library().tc_step_host(h, ctypes.byref(host_in), ctypes.byref(host_out), ctypes.byref(dev),
+                                       nsteps, ws_ptr, stream_ptr), h)
 
 
 def tc_diagnostics(h, u_ptr, ws_ptr, stream_ptr):
@@ -244,6 +251,19 @@ class Plan:
         tc_step(self.handle, cs, nsteps, self._ws(), _stream_ptr(stream))
         state.started = bool(cs.started)
         return state
+
+    def step_host(self, dev: "State", host_in: dict, host_out: dict, nsteps=1, stream=None):
+        """tc_step_host: host_in / host_out map 'u', 'u_prev', 'N_prev', 'p' to CPU tensors
+        (pinned for full-speed copies; host_out may omit fields); dev is the device working
+        state.  Returns when host_out holds the result."""
+        def hstate(d, started):
+            return tc_state(*[d[k].data_ptr() if k in d else None for k in ("u", "u_prev", "N_prev", "p")],
+                            int(started))
+        hin, hout = hstate(host_in, host_in.get("started", dev.started)), hstate(host_out, 0)
+        cs = dev.c_struct()
+        tc_step_host(self.handle, hin, hout, cs, nsteps, self._ws(), _stream_ptr(stream))
+        dev.started = bool(cs.started)
+        return dev
 
     def diagnostics(self, u, stream=None):
         return tc_diagnostics(self.handle, _ptr(u), self._ws(), _stream_ptr(stream))

@@ -304,3 +304,29 @@ def test_pc_modes_bit_identical(T):
         out.append([host(getattr(st, k)) for k in ("u", "u_prev", "N_prev", "p")])
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+def test_step_host_matches_device_step():
+    """tc_step_host (state in host memory, pinned or pageable) gives the device tc_step's
+    result, and refuses device pointers where host memory is expected."""
+    ops = O.Operators(O.Params(**CFG1))
+    u0 = init(ops)
+    plan = tc.Plan(**CFG1)
+    ref = tc.State(plan, dev(u0))
+    plan.step(ref, 3)
+    want = {k: host(getattr(ref, k)) for k in ("u", "u_prev", "N_prev", "p")}
+    plan.step(ref, 2)
+    want2 = {k: host(getattr(ref, k)) for k in ("u", "p")}
+    for pin in (True, False):
+        h_in = {k: torch.from_numpy(v.copy()) for k, v in want.items()}
+        if pin:
+            h_in = {k: v.pin_memory() for k, v in h_in.items()}
+        h_in["started"] = True
+        h_out = {"u": torch.empty_like(h_in["u"]), "p": torch.empty_like(h_in["p"])}
+        work = tc.State(plan, dev(u0))
+        plan.step_host(work, h_in, h_out, 2)
+        assert np.array_equal(h_out["u"].numpy(), want2["u"])
+        assert np.array_equal(h_out["p"].numpy(), want2["p"])
+    bad = {k: getattr(ref, k) for k in ("u", "u_prev", "N_prev", "p")}   # device tensors
+    with pytest.raises(tc.TCError):
+        plan.step_host(tc.State(plan, dev(u0)), bad, {}, 1)
