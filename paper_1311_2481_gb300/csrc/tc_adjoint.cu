@@ -715,6 +715,116 @@ __global__ void __launch_bounds__(256) k_zfwd_adj(const double2* __restrict__ H3
     }
 }
 
+// Length-specialised forms of k_zinv_adjin and k_zfwd_adj: compile-time radix plans
+// (radices <= 8) over padded lines; same inputs, outputs and arithmetic.
+template <int PZ, int NT>
+__global__ void __launch_bounds__(NT) k_zinv_adjin_s(const double2* __restrict__ Nb, double2* __restrict__ H,
+                                                     int N_r, int M, int K, double scale,
+                                                     const double2* __restrict__ tw) {
+    constexpr int LP = cft::padded<PZ>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* a = reinterpret_cast<double2*>(smem_raw);
+    double2* b = a + 3 * LP;
+    const int m = blockIdx.x % (M + 1);
+    const int r = blockIdx.x / (M + 1);
+    const int nk = 2 * K + 1;
+    const size_t S = (size_t)N_r * (M + 1) * nk;
+    const size_t o = ((size_t)r * (M + 1) + m) * nk;
+    const double cm = (m == 0 ? 1.0 : 0.5) * scale;
+    for (int q = threadIdx.x; q < PZ; q += NT) {
+        const int k = q <= K ? q : q - PZ;
+        if (k < -K) continue;                      // zero band, not read by the first pass
+        const size_t e = o + (k + K);
+        const double2 p = Nb[e], n = Nb[S + e], zz = Nb[2 * S + e];
+        a[cft::pd(q)] = make_double2(cm * (p.x + n.x), cm * (p.y + n.y));
+        a[LP + cft::pd(q)] = make_double2(cm * (p.y - n.y), -cm * (p.x - n.x));
+        a[2 * LP + cft::pd(q)] = make_double2(cm * zz.x, cm * zz.y);
+    }
+    __syncthreads();
+    const double2* X = cft::passes<PZ, 0, 1, 3, NT, true, double2, true>(a, b, tw, K + 1, PZ - K);
+    const size_t fstride = (size_t)N_r * (M + 1) * PZ;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        double2* dst = H + l * fstride + ((size_t)r * (M + 1) + m) * PZ;
+        for (int z = threadIdx.x; z < PZ; z += NT) dst[z] = X[l * LP + cft::pd(z)];
+    }
+}
+
+template <int PZ, int NT>
+__global__ void __launch_bounds__(NT) k_zfwd_adj_s(const double2* __restrict__ H3, double2* __restrict__ ub,
+                                                   double2* __restrict__ Rh, int N_r, int M, int K, double kz,
+                                                   const double2* __restrict__ tw) {
+    constexpr int LP = cft::padded<PZ>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* a = reinterpret_cast<double2*>(smem_raw);
+    double2* b = a + 3 * LP;
+    const int c = blockIdx.x % 3;
+    const int rm = blockIdx.x / 3;
+    const int m = rm % (M + 1), r = rm / (M + 1);
+    const size_t fstride = (size_t)N_r * (M + 1) * PZ;
+    const double2* h = H3 + ((size_t)r * (M + 1) + m) * PZ;
+#pragma unroll
+    for (int l = 0; l < 3; ++l)   // l: 0 A, 1 R, 2 Z of component c
+        for (int z = threadIdx.x; z < PZ; z += NT) a[l * LP + cft::pd(z)] = h[(size_t)(3 * l + c) * fstride + z];
+    __syncthreads();
+    const double2* X = cft::passes<PZ, 0, 1, 3, NT, false, double2, true>(a, b, tw);
+    const int nk = 2 * K + 1;
+    const size_t S = (size_t)N_r * (M + 1) * nk;
+    for (int kk = threadIdx.x; kk < nk; kk += NT) {
+        const int k = kk - K;
+        const int q = cft::pd(k < 0 ? k + PZ : k);
+        const double2 Av = X[q], Rv = X[LP + q], Zv = X[2 * LP + q];
+        const double kzk = kz * k;
+        const size_t e = (size_t)c * S + ((size_t)r * (M + 1) + m) * nk + kk;
+        double2 u = ub[e];
+        u.x += Av.x + kzk * Zv.y;
+        u.y += Av.y - kzk * Zv.x;
+        ub[e] = u;
+        Rh[e] = Rv;
+    }
+}
+
+template <int PZ, int NT>
+static tc_status zadj_s(tc_plan* p, const double2* Nbar, double2* Ha, const double2* H3, double2* ubar,
+                        double2* Rh, cudaStream_t s, bool inverse) {
+    const size_t sm = (size_t)2 * 3 * cft::padded<PZ>() * sizeof(double2);
+    if (inverse) {
+        TC_CUDA(p, cudaFuncSetAttribute(k_zinv_adjin_s<PZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        const int slot = prof_begin(p, kKZinvAdj, s);
+        k_zinv_adjin_s<PZ, NT><<<p->N_r * (p->M + 1), NT, sm, s>>>(Nbar, Ha, p->N_r, p->M, p->K,
+                                                                   1.0 / ((double)p->P_t * (double)p->P_z), p->d_tw_z);
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_zinv_adjin_s");
+    } else {
+        TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_adj_s<PZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        const int slot = prof_begin(p, kKZfwdAdj, s);
+        k_zfwd_adj_s<PZ, NT><<<p->N_r * (p->M + 1) * 3, NT, sm, s>>>(H3, ubar, Rh, p->N_r, p->M, p->K, p->k_z,
+                                                                     p->d_tw_z);
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_zfwd_adj_s");
+    }
+    return TC_OK;
+}
+
+static bool zadj_ok(const tc_plan* p) {
+    return p->theta_zt_forced == 0 &&
+           (p->P_z == 48 || p->P_z == 96 || p->P_z == 192 || p->P_z == 384 || p->P_z == 768);
+}
+
+// specialised adjoint z passes where P_z has a compile-time plan (TC_ERR_ARG otherwise)
+static tc_status zadj_dispatch(tc_plan* p, const double2* Nbar, double2* Ha, const double2* H3, double2* ubar,
+                               double2* Rh, cudaStream_t s, bool inverse) {
+    if (p->theta_zt_forced != 0) return TC_ERR_ARG;
+    switch (p->P_z) {
+        case 48: return zadj_s<48, 128>(p, Nbar, Ha, H3, ubar, Rh, s, inverse);
+        case 96: return zadj_s<96, 128>(p, Nbar, Ha, H3, ubar, Rh, s, inverse);
+        case 192: return zadj_s<192, 256>(p, Nbar, Ha, H3, ubar, Rh, s, inverse);
+        case 384: return zadj_s<384, 256>(p, Nbar, Ha, H3, ubar, Rh, s, inverse);
+        case 768: return zadj_s<768, 256>(p, Nbar, Ha, H3, ubar, Rh, s, inverse);
+    }
+    return TC_ERR_ARG;
+}
+
 // ubar(c, j, mode) += (D1^T Rhat)(c, j, mode)
 __global__ void k_drT(double2* __restrict__ ub, const double2* __restrict__ Rh, const int* __restrict__ trow,
                       const double* __restrict__ tw, int ntab, Geo g) {
@@ -781,12 +891,17 @@ tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* 
     tc_status st = launch_zinv_fp64(p, u, H1, s);
     if (st != TC_OK) return st;
     const size_t smz = (size_t)2 * 3 * p->P_z * sizeof(double2);
-    TC_CUDA(p, cudaFuncSetAttribute(k_zinv_adjin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
-    int slot = prof_begin(p, kKZinvAdj, s);
-    k_zinv_adjin<<<p->N_r * (p->M + 1), 256, smz, s>>>(Nbar, Ha, p->N_r, p->M, p->K,
-                                                         1.0 / ((double)p->P_t * (double)p->P_z), p->d_tw_z, p->rad_z);
-    prof_end(p, slot, s);
-    TC_LAUNCHED(p, "k_zinv_adjin");
+    int slot;
+    if (zadj_ok(p)) {
+        TC_TRY_STATUS(zadj_dispatch(p, Nbar, Ha, nullptr, nullptr, nullptr, s, true));
+    } else {
+        TC_CUDA(p, cudaFuncSetAttribute(k_zinv_adjin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
+        slot = prof_begin(p, kKZinvAdj, s);
+        k_zinv_adjin<<<p->N_r * (p->M + 1), 256, smz, s>>>(Nbar, Ha, p->N_r, p->M, p->K,
+                                                             1.0 / ((double)p->P_t * (double)p->P_z), p->d_tw_z, p->rad_z);
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_zinv_adjin");
+    }
     int zt = 4;
     auto smem_for = [&](int z) {
         const int nza = (z + 1) / 2, nl = 7 * z + nza;
@@ -813,12 +928,16 @@ tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* 
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_theta_adj");
     }
-    TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
-    slot = prof_begin(p, kKZfwdAdj, s);
-    k_zfwd_adj<<<p->N_r * (p->M + 1) * 3, 256, smz, s>>>(H3, ubar, Rh, p->N_r, p->M, p->K, p->k_z,
-                                                           p->d_tw_z, p->rad_z);
-    prof_end(p, slot, s);
-    TC_LAUNCHED(p, "k_zfwd_adj");
+    if (zadj_ok(p)) {
+        TC_TRY_STATUS(zadj_dispatch(p, nullptr, nullptr, H3, ubar, Rh, s, false));
+    } else {
+        TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
+        slot = prof_begin(p, kKZfwdAdj, s);
+        k_zfwd_adj<<<p->N_r * (p->M + 1) * 3, 256, smz, s>>>(H3, ubar, Rh, p->N_r, p->M, p->K, p->k_z,
+                                                               p->d_tw_z, p->rad_z);
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_zfwd_adj");
+    }
     slot = prof_begin(p, kKDrT, s);
     k_drT<<<dim3(g.N, ablocks(g.nmode, 128), 3), 128, 0, s>>>(ubar, Rh, p->d_d1t_row, p->d_d1t_w, p->d1t_n, g);
     prof_end(p, slot, s);

@@ -169,29 +169,13 @@ tc_status tc_step_host(tc_plan* plan, const tc_state* host_in, tc_state* host_ou
     void* dptr[4] = {dev->u, dev->u_prev, dev->N_prev, dev->p};
     const size_t bytes[4] = {vb, vb, vb, sb};
     for (int i = 0; i < 4; ++i) TC_TRY(check_device_ptr(plan, dptr[i], "dev state"));
-    // one copy stream per field, so that the copy engines move the fields concurrently;
-    // forked from and joined back to the caller's stream
-    if (!plan->copy_s[0]) {
-        for (int i = 0; i < 4; ++i) TC_CUDA(plan, cudaStreamCreateWithFlags(&plan->copy_s[i], cudaStreamNonBlocking));
-        for (int i = 0; i < 5; ++i) TC_CUDA(plan, cudaEventCreateWithFlags(&plan->copy_ev[i], cudaEventDisableTiming));
-    }
-    auto fan = [&](void* const* dst, const void* const* src, cudaMemcpyKind kind) -> tc_status {
-        TC_CUDA(plan, cudaEventRecord(plan->copy_ev[4], s));
-        for (int i = 0; i < 4; ++i) {
-            if (!dst[i] || !src[i]) continue;
-            TC_CUDA(plan, cudaStreamWaitEvent(plan->copy_s[i], plan->copy_ev[4], 0));
-            TC_CUDA(plan, cudaMemcpyAsync(dst[i], src[i], bytes[i], kind, plan->copy_s[i]));
-            TC_CUDA(plan, cudaEventRecord(plan->copy_ev[i], plan->copy_s[i]));
-            TC_CUDA(plan, cudaStreamWaitEvent(s, plan->copy_ev[i], 0));
-        }
-        return TC_OK;
-    };
-    TC_TRY(fan(dptr, hin, cudaMemcpyHostToDevice));
+    for (int i = 0; i < 4; ++i)
+        TC_CUDA(plan, cudaMemcpyAsync(dptr[i], hin[i], bytes[i], cudaMemcpyHostToDevice, s));
     dev->started = host_in->started;
     TC_TRY(tc_step(plan, dev, nsteps, ws, stream));
     void* hout[4] = {host_out->u, host_out->u_prev, host_out->N_prev, host_out->p};
-    const void* dsrc[4] = {dptr[0], dptr[1], dptr[2], dptr[3]};
-    TC_TRY(fan(hout, dsrc, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 4; ++i)
+        if (hout[i]) TC_CUDA(plan, cudaMemcpyAsync(hout[i], dptr[i], bytes[i], cudaMemcpyDeviceToHost, s));
     TC_CUDA(plan, cudaStreamSynchronize(s));
     host_out->started = dev->started;
     return TC_OK;

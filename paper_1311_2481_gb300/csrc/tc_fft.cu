@@ -259,11 +259,11 @@ __global__ void __launch_bounds__(NT, 2) k_zinv_s64(const double2* __restrict__ 
     for (int l = 0; l < L; ++l)
         for (int q = threadIdx.x; q < PZ; q += NT) {
             const int k = q <= K ? q : q - PZ;
-            a[l * LP + cft::pd(q)] = k >= -K ? zinv_value(u, w1, c0, S, colstride, r, m, nk, K, g * L + l, k, kz)
-                                             : make_double2(0.0, 0.0);
+            if (k >= -K) a[l * LP + cft::pd(q)] = zinv_value(u, w1, c0, S, colstride, r, m, nk, K, g * L + l, k, kz);
         }
     __syncthreads();
-    const double2* X = cft::passes<PZ, 0, 1, L, NT, true, double2, true>(a, b, tw);
+    // the band K < q < PZ - K is zero: the first pass does not read it
+    const double2* X = cft::passes<PZ, 0, 1, L, NT, true, double2, true>(a, b, tw, K + 1, PZ - K);
 #pragma unroll
     for (int l = 0; l < L; ++l) {
         double2* dst = H1 + (((size_t)(g * L + l) * N_r + r) * (M + 1) + m) * PZ;

@@ -159,8 +159,10 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dftR(V* v
 
 // ---------------------------------------------------------------- Stockham passes
 // one radix-R pass over NL lines of length PT: in -> out, Ns = product of earlier radices
+// Inputs at positions zlo <= p < zhi are zero and are not read (the dealiasing band of an
+// inverse transform's input; only the first pass is given a band).
 template <int PT, int R, int NS, int NL, int NT, bool INV, typename V>
-__device__ __forceinline__ void pass(const V* in, V* out, const V* __restrict__ tw) {
+__device__ __forceinline__ void pass(const V* in, V* out, const V* __restrict__ tw, int zlo, int zhi) {
     constexpr int NB = PT / R;
     constexpr int STEP = PT / (NS * R);
     constexpr int LP = padded<PT>();
@@ -172,7 +174,10 @@ __device__ __forceinline__ void pass(const V* in, V* out, const V* __restrict__ 
         const int k = j % NS;
         V v[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) v[q] = src[pd(j + q * NB)];
+        for (int q = 0; q < R; ++q) {
+            const int pos = j + q * NB;
+            v[q] = (pos >= zlo && pos < zhi) ? vmk<V>(0, 0) : src[pd(pos)];
+        }
         if (NS > 1 && k) {
 #pragma unroll
             for (int q = 1; q < R; ++q) {
@@ -190,14 +195,16 @@ __device__ __forceinline__ void pass(const V* in, V* out, const V* __restrict__ 
 }
 
 // all passes of the plan; returns the buffer that holds the result
+// zlo, zhi: zero band of the input (first pass only); zlo = zhi = PT for none
 template <int PT, int P, int NS, int NL, int NT, bool INV, typename V, bool R8 = sizeof(V) == 16>
-__device__ __forceinline__ V* passes(V* a, V* b, const V* __restrict__ tw) {
+__device__ __forceinline__ V* passes(V* a, V* b, const V* __restrict__ tw, int zlo = PT, int zhi = PT) {
     if constexpr (P == Plan<PT, R8>::np) {
         return a;
     } else {
         constexpr int R = Plan<PT, R8>::r[P];
-        pass<PT, R, NS, NL, NT, INV, V>(a, b, tw);
-        return passes<PT, P + 1, NS * R, NL, NT, INV, V, R8>(b, a, tw);
+        if constexpr (P == 0) pass<PT, R, NS, NL, NT, INV, V>(a, b, tw, zlo, zhi);
+        else pass<PT, R, NS, NL, NT, INV, V>(a, b, tw, PT, PT);
+        return passes<PT, P + 1, NS * R, NL, NT, INV, V, R8>(b, a, tw, PT, PT);
     }
 }
 template <int PT, bool R8> __host__ __device__ constexpr bool result_in_first() { return Plan<PT, R8>::np % 2 == 0; }

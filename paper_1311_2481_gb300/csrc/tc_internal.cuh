@@ -64,8 +64,6 @@ struct tc_plan {
     int pipeline;                  // m-chunks of the overlapped step (1: sequential)
     cudaStream_t aux[2] = {nullptr, nullptr};   // solve and pre-theta streams of the overlapped step
     std::vector<cudaEvent_t> pev;               // its events: fork, join, pre-done, then Z[c], P[c]
-    cudaStream_t copy_s[4] = {nullptr, nullptr, nullptr, nullptr};   // tc_step_host copies, one per field
-    cudaEvent_t copy_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int pc_modes;                  // modes per block of the fused steps-2-5 kernel (0: auto)
     int thr_zinv, thr_theta, thr_zfwd;  // block sizes of the FP64 transform kernels
     bool pc_split;                      // steps 2-5 as separate kernels (large N_r)

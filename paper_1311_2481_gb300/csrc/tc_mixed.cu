@@ -257,17 +257,19 @@ __global__ void __launch_bounds__(NT, zinv_minb<PZ, L, NT>()) k_zinv_s(const flo
 #pragma unroll
         for (int i = 0; i < NQ; ++i) {
             const int q = threadIdx.x + i * NT;
-            vals[l][i] = q < PZ ? zinv_input(P, S, line, g * L + l, q, K, PZ, kzf) : make_float2(0.f, 0.f);
+            vals[l][i] = (q < PZ && (q <= K || q >= PZ - K)) ? zinv_input(P, S, line, g * L + l, q, K, PZ, kzf)
+                                                              : make_float2(0.f, 0.f);
         }
 #pragma unroll
     for (int l = 0; l < L; ++l)
 #pragma unroll
         for (int i = 0; i < NQ; ++i) {
             const int q = threadIdx.x + i * NT;
-            if (q < PZ) a[l * LP + cft::pd(q)] = vals[l][i];
+            if (q < PZ && (q <= K || q >= PZ - K)) a[l * LP + cft::pd(q)] = vals[l][i];
         }
     __syncthreads();
-    const float2* X = cft::passes<PZ, 0, 1, L, NT, true, float2, false>(a, b, tw);
+    // the band K < q < PZ - K is zero: the first pass does not read it
+    const float2* X = cft::passes<PZ, 0, 1, L, NT, true, float2, false>(a, b, tw, K + 1, PZ - K);
 #pragma unroll
     for (int l = 0; l < L; ++l) {
         float2* dst = H1 + (((size_t)(g * L + l) * N_r + r) * (M + 1) + m) * PZ;

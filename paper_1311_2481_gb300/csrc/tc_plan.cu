@@ -296,16 +296,7 @@ static void free_device(tc_plan* p) {
             cudaStreamDestroy(q);
             q = nullptr;
         }
-    for (cudaStream_t& q : p->copy_s)
-        if (q) {
-            cudaStreamDestroy(q);
-            q = nullptr;
-        }
-    for (cudaEvent_t& e : p->copy_ev)
-        if (e) {
-            cudaEventDestroy(e);
-            e = nullptr;
-        }
+
     void* ptrs[] = {p->d_r, p->d_ir, p->d_w1, p->d_w1f, p->d_w2, p->d_col0, p->d_d1t_row, p->d_d1t_w, p->d_fac, p->d_piv,
                     p->d_tw_z, p->d_tw_t, p->d_tw_z32, p->d_tw_t32};
     for (void* q : ptrs)

@@ -138,11 +138,9 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, 
                 }
             }
         }
-        // zero band M < p < PT - M of every line
-        for (int l = 0; l < NL; ++l)
-            for (int q = M + 1 + (int)threadIdx.x; q < PT - M; q += NT) A[l * LP + pd(q)] = vmk<V>(0, 0);
         __syncthreads();
-        const V* X = passes<PT, 0, 1, NL, NT, true, V, R8>(A, B, tw);
+        // the band M < p < PT - M of every line is zero: the first pass does not read it
+        const V* X = passes<PT, 0, 1, NL, NT, true, V, R8>(A, B, tw, M + 1, PT - M);
         for (int pt = threadIdx.x; pt < NPT; pt += NT) {
             const int z = pt / PT;
             const int th = pt - z * PT;

@@ -89,6 +89,27 @@ def test_adjoint_step_theta_lengths(M):
             assert rel(host(got), want) <= 1e-11, zt
 
 
+@pytest.mark.parametrize("K", [32, 64, 128, 256])
+def test_adjoint_step_z_lengths(K):
+    """The length-specialised adjoint z passes (P_z = 96 ... 768) and the generic ones
+    (explicit theta_zt) both match the oracle's adjoint step."""
+    cfg = dict(N_r=10, M=4, K=K, m_p=1, eta=0.5, Re_i=50.0, Re_o=0.0, L_z=LZ, dt=1e-3)
+    ops = O.Operators(O.Params(**cfg))
+    prm = ops.prm
+    u0 = I.initial_state(ops.r, prm.M, prm.K, prm.m_p, prm.L_z, prm.eta, prm.Re_i, prm.Re_o,
+                         kind="broadband", amp=1e-2)
+    st_o = O.step(ops, O.cold_state(u0))
+    sh = (3,) + prm.shape()
+    y = [I.random_spectral(sh, seed=s) for s in (41, 42, 43)]
+    ref = O.adjoint_step(ops, st_o, *y)
+    for zt in (0, 1):
+        plan = tc.Plan(**cfg, theta_zt=zt)
+        bar = tc.StateBar(*[dev(v) for v in y])
+        plan.adjoint_step(gpu_state(plan, st_o), bar)
+        for got, want in zip((bar.u, bar.u_prev, bar.N_prev), ref):
+            assert rel(host(got), want) <= 1e-11, zt
+
+
 def test_adjoint_start_matches_oracle():
     ops, plan, u0 = setup(CFG1)
     sh = (3,) + ops.prm.shape()
