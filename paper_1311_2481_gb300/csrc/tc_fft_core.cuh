@@ -95,7 +95,4 @@ __device__ V* smem_fft(V* a, V* b, int nlines, const V* __restrict__ tw, bool in
     return a;
 }
 
-template <typename V>
-__device__ __forceinline__ V from_d2(double2 a) { V v; v.x = (typename Real<V>::type)a.x; v.y = (typename Real<V>::type)a.y; return v; }
-
 }  // namespace tc

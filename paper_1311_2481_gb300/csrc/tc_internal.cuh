@@ -106,19 +106,12 @@ struct tc_plan {
 namespace tc {
 
 // ------------------------------------------------------------------ complex helpers
-template <typename T> struct C2;
-template <> struct C2<double> { using type = double2; };
-template <> struct C2<float> { using type = float2; };
-
-__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
-__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
 template <typename V> __host__ __device__ __forceinline__ V cadd(V a, V b) { V c; c.x = a.x + b.x; c.y = a.y + b.y; return c; }
 template <typename V> __host__ __device__ __forceinline__ V csub(V a, V b) { V c; c.x = a.x - b.x; c.y = a.y - b.y; return c; }
 template <typename V> __host__ __device__ __forceinline__ V cmul(V a, V b) {
     V c; c.x = a.x * b.x - a.y * b.y; c.y = a.x * b.y + a.y * b.x; return c;
 }
 template <typename V> __host__ __device__ __forceinline__ V cconj(V a) { a.y = -a.y; return a; }
-template <typename V, typename T> __host__ __device__ __forceinline__ V cscale(V a, T s) { a.x *= s; a.y *= s; return a; }
 // i * a
 template <typename V> __host__ __device__ __forceinline__ V cmuli(V a) { V c; c.x = -a.y; c.y = a.x; return c; }
 
@@ -145,7 +138,7 @@ tc_status check_device_ptr(tc_plan* p, const void* ptr, const char* name);
 // ------------------------------------------------------------------ tracing
 enum KernelId {
     kKZinv = 0, kKTheta, kKZfwd, kKRhsPressure, kKSolveP, kKRhsVelocity, kKSolveH, kKRhsDiv,
-    kKUpdate, kKAxpby, kKDiag, kKZinv32, kKTheta32, kKZfwd32, kKMeanFlow, kKPC, kKPCAdj,
+    kKUpdate, kKAxpby, kKDiag, kKZinv32, kKTheta32, kKZfwd32, kKPC, kKPCAdj,
     kKZinvAdj, kKThetaAdj, kKZfwdAdj, kKDrT, kKPrep32, kNumKernels
 };
 extern const char* const kKernelNames[kNumKernels];

@@ -261,7 +261,7 @@ static tc_status upload(tc_plan* p) {
 const char* const kKernelNames[kNumKernels] = {
     "k_zinv", "k_theta", "k_zfwd", "k_rhs_pressure", "k_band_solve_P", "k_rhs_velocity",
     "k_band_solve_H", "k_rhs_div", "k_update", "k_axpby", "k_diag", "k_zinv_f32",
-    "k_theta_f32", "k_zfwd_f32", "k_mean_flow", "k_pc", "k_pc_adj", "k_zinv_adjin",
+    "k_theta_f32", "k_zfwd_f32", "k_pc", "k_pc_adj", "k_zinv_adjin",
     "k_theta_adj", "k_zfwd_adj", "k_drT", "k_prep_f32"};
 
 int prof_begin(tc_plan* p, int kid, cudaStream_t s) {
