@@ -139,7 +139,6 @@ __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __re
     V* phys = smem_fft(a, b, nl, tw, true, rad);
     V* fw = phys == a ? b : a;
     const int nzl = (zt + 1) / 2;
-    const T rr = (T)rnodes[r];
     const T ir = (T)(1.0 / rnodes[r]);
     for (int idx = threadIdx.x; idx < zt * Pt; idx += blockDim.x) {
         const int zi = idx / Pt;
@@ -157,7 +156,6 @@ __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __re
         if (zi & 1) zl->y = Nz;
         else { zl->x = Nz; if (zi + 1 == zt) zl->y = 0; }
     }
-    (void)rr;
     __syncthreads();
     V* other = fw == a ? b : a;
     V* spec = smem_fft(fw, other, zt + nzl, tw, false, rad);
