@@ -16,9 +16,12 @@ static int ablocks(size_t n, int bs) { return (int)((n + bs - 1) / bs); }
 // x <- A^{-T} x on one real part of column t of a [N][T] smem array, for A = P L U stored
 // as in smem_band_solve: first U^T y = x (forward), then for j = N-1..0 the transposed
 // elimination x_j -= sum_q l_q(j) x_{j+q} followed by the row interchange j <-> j + piv_j.
+// The factors of the next kPCDepth rows are kept in flight in a register ring (as in
+// smem_band_solve).
 __device__ __forceinline__ void smem_band_solve_T(double2* col, int T, int t, int part, int N,
                                                   const double* __restrict__ F,
                                                   const uint8_t* __restrict__ P, int M1K1) {
+    constexpr int D = kPCDepth;
     double* x = reinterpret_cast<double*>(col) + 2 * t + part;
     const int st = 2 * T;
     // U^T y = b: y_j = (b_j - sum_{q=1..8} U(j-q, j) y_{j-q}) / U_jj, column-oriented: p0..p7
@@ -30,46 +33,74 @@ __device__ __forceinline__ void smem_band_solve_T(double2* col, int T, int t, in
     double p3 = N > 3 ? x[(size_t)3 * st] : 0.0, p4 = N > 4 ? x[(size_t)4 * st] : 0.0;
     double p5 = N > 5 ? x[(size_t)5 * st] : 0.0, p6 = N > 6 ? x[(size_t)6 * st] : 0.0;
     double p7 = N > 7 ? x[(size_t)7 * st] : 0.0;
-    double un[9];
+    double ur[D][9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) un[q] = N > 0 ? __ldg(&F[(size_t)(4 + q) * M1K1]) : 0.0;
-    for (int j = 0; j < N; ++j) {
-        double u[9];
+    for (int d = 0; d < D; ++d)
 #pragma unroll
-        for (int q = 0; q < 9; ++q) u[q] = un[q];
-        if (j + 1 < N) {
+        for (int q = 0; q < 9; ++q) ur[d][q] = d < N ? __ldg(&F[(size_t)d * rs + (size_t)(4 + q) * M1K1]) : 0.0;
+    for (int j0 = 0; j0 < N; j0 += D) {
 #pragma unroll
-            for (int q = 0; q < 9; ++q) un[q] = __ldg(&F[(size_t)(j + 1) * rs + (size_t)(4 + q) * M1K1]);
+        for (int d = 0; d < D; ++d) {
+            const int j = j0 + d;
+            if (j < N) {
+                double u[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) u[q] = ur[d][q];
+                if (j + D < N) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) ur[d][q] = __ldg(&F[(size_t)(j + D) * rs + (size_t)(4 + q) * M1K1]);
+                }
+                const double yj = p0 * u[0];
+                x[(size_t)j * st] = yj;
+                const double p8 = j + 8 < N ? x[(size_t)(j + 8) * st] : 0.0;
+                p0 = fma(-u[1], yj, p1);
+                p1 = fma(-u[2], yj, p2);
+                p2 = fma(-u[3], yj, p3);
+                p3 = fma(-u[4], yj, p4);
+                p4 = fma(-u[5], yj, p5);
+                p5 = fma(-u[6], yj, p6);
+                p6 = fma(-u[7], yj, p7);
+                p7 = fma(-u[8], yj, p8);
+            }
         }
-        const double yj = p0 * u[0];
-        x[(size_t)j * st] = yj;
-        const double p8 = j + 8 < N ? x[(size_t)(j + 8) * st] : 0.0;
-        p0 = fma(-u[1], yj, p1);
-        p1 = fma(-u[2], yj, p2);
-        p2 = fma(-u[3], yj, p3);
-        p3 = fma(-u[4], yj, p4);
-        p4 = fma(-u[5], yj, p5);
-        p5 = fma(-u[6], yj, p6);
-        p6 = fma(-u[7], yj, p7);
-        p7 = fma(-u[8], yj, p8);
     }
     // transposed eliminations and interchanges, j = N-1 .. 0; w1..w4 hold x_{j+1..j+4}
     double w1 = 0.0, w2 = 0.0, w3 = 0.0, w4 = 0.0;
-    for (int j = N - 1; j >= 0; --j) {
-        const double* Fj = F + (size_t)j * kBands * M1K1;
-        double w0 = x[(size_t)j * st];
-        // oldest values first: without an interchange at row j+1 only w1 is new
-        w0 = fma(-__ldg(&Fj[(size_t)3 * M1K1]), w4, w0);
-        w0 = fma(-__ldg(&Fj[(size_t)2 * M1K1]), w3, w0);
-        w0 = fma(-__ldg(&Fj[(size_t)M1K1]), w2, w0);
-        w0 = fma(-__ldg(&Fj[0]), w1, w0);
-        const int pj = P[(size_t)j * M1K1];
-        if (pj == 1) { double q = w0; w0 = w1; w1 = q; }
-        else if (pj == 2) { double q = w0; w0 = w2; w2 = q; }
-        else if (pj == 3) { double q = w0; w0 = w3; w3 = q; }
-        else if (pj == 4) { double q = w0; w0 = w4; w4 = q; }
-        if (j + 4 < N) x[(size_t)(j + 4) * st] = w4;   // x_{j+4} is final
-        w4 = w3; w3 = w2; w2 = w1; w1 = w0;
+    double lr[D][4];
+    int pr[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const int j = N - 1 - d;
+        pr[d] = j >= 0 ? P[(size_t)j * M1K1] : 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) lr[d][q] = j >= 0 ? __ldg(&F[(size_t)j * rs + (size_t)q * M1K1]) : 0.0;
+    }
+    for (int j0 = N - 1; j0 >= 0; j0 -= D) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int j = j0 - d;
+            if (j >= 0) {
+                const double l1 = lr[d][0], l2 = lr[d][1], l3 = lr[d][2], l4 = lr[d][3];
+                const int pj = pr[d];
+                if (j - D >= 0) {
+                    pr[d] = P[(size_t)(j - D) * M1K1];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) lr[d][q] = __ldg(&F[(size_t)(j - D) * rs + (size_t)q * M1K1]);
+                }
+                double w0 = x[(size_t)j * st];
+                // oldest values first: without an interchange at row j+1 only w1 is new
+                w0 = fma(-l4, w4, w0);
+                w0 = fma(-l3, w3, w0);
+                w0 = fma(-l2, w2, w0);
+                w0 = fma(-l1, w1, w0);
+                if (pj == 1) { double q = w0; w0 = w1; w1 = q; }
+                else if (pj == 2) { double q = w0; w0 = w2; w2 = q; }
+                else if (pj == 3) { double q = w0; w0 = w3; w3 = q; }
+                else if (pj == 4) { double q = w0; w0 = w4; w4 = q; }
+                if (j + 4 < N) x[(size_t)(j + 4) * st] = w4;   // x_{j+4} is final
+                w4 = w3; w3 = w2; w2 = w1; w1 = w0;
+            }
+        }
     }
     // flush the window: x_0..x_3
     if (N > 0) x[0] = w1;

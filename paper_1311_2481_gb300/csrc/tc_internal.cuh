@@ -14,7 +14,8 @@ namespace tc {
 constexpr int kMaxRadix = 16;   // passes of a mixed-radix 2^a 3^b transform
 constexpr int kStencil = 9;     // padded FD stencil width (fd_order <= 8)
 constexpr int kBands = 13;      // stored doubles per LU row: 4 L multipliers, 1/U_jj, 8 U
-constexpr int kKl = 4;          // sub/super diagonals of the mode matrices (fd_order/2 <= 4)
+constexpr int kKl = 4;
+constexpr int kPCDepth = 4;              // rows of LU factors in flight per substitution chain          // sub/super diagonals of the mode matrices (fd_order/2 <= 4)
 
 // Factor sets of Sec. 3.2: Poisson (p*, phi), Helmholtz for u_+, u_-, u_z.
 enum FactorSet { kSetP = 0, kSetHp = 1, kSetHm = 2, kSetHz = 3, kNumSets = 4 };

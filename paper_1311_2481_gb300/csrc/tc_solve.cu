@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(NTH) k_pc(PCArgs a, Geo g, int T) {
         const int t = threadIdx.x >> 1, part = threadIdx.x & 1;
         const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
         const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
-        smem_band_solve(C0, T, t, part, N, a.fac + (size_t)kSetP * per_set + mk,
+        smem_band_solve<kPCDepth>(C0, T, t, part, N, a.fac + (size_t)kSetP * per_set + mk,
                         a.piv + (size_t)kSetP * N * g.M1K1 + mk, g.M1K1);
     }
     // (with no spare warp the whole block does this after the substitution)
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(NTH) k_pc(PCArgs a, Geo g, int T) {
         const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
         const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
         const int set = kSetHp + c;
-        smem_band_solve(C1 + (size_t)c * items, T, t, part, N, a.fac + (size_t)set * per_set + mk,
+        smem_band_solve<kPCDepth>(C1 + (size_t)c * items, T, t, part, N, a.fac + (size_t)set * per_set + mk,
                         a.piv + (size_t)set * N * g.M1K1 + mk, g.M1K1);
     } else if (a.commit && threadIdx.x >= helper1) {
         for (int idx = threadIdx.x - helper1; idx < 3 * items; idx += blockDim.x - helper1) {
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(NTH) k_pc(PCArgs a, Geo g, int T) {
         const int t = threadIdx.x >> 1, part = threadIdx.x & 1;
         const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
         const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
-        smem_band_solve(C0, T, t, part, N, a.fac + (size_t)kSetP * per_set + mk,
+        smem_band_solve<kPCDepth>(C0, T, t, part, N, a.fac + (size_t)kSetP * per_set + mk,
                         a.piv + (size_t)kSetP * N * g.M1K1 + mk, g.M1K1);
     }
     __syncthreads();
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(256) k_band_solve_s(double2* __restrict__ x, c
         const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
         const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
         const size_t per_set = (size_t)N * kBands * g.M1K1;
-        smem_band_solve(sm, T, t, part, N, fac + (size_t)set * per_set + mk, piv + (size_t)set * N * g.M1K1 + mk, g.M1K1);
+        smem_band_solve<kPCDepth>(sm, T, t, part, N, fac + (size_t)set * per_set + mk, piv + (size_t)set * N * g.M1K1 + mk, g.M1K1);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {

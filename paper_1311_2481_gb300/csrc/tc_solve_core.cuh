@@ -66,73 +66,97 @@ static __device__ double2 lap_r(const double2* __restrict__ u, const double* __r
 
 // In-place banded substitution on one real part (part = 0: re, 1: im) of column t of a
 // [N][T] complex smem array, with the pivoted LU of Sec. 3.2 stored for (set, m, |k|).
+// The factors of the next D rows are kept in flight in a register ring: the few long
+// substitution chains of a block wait on each row's factors otherwise (they come from DRAM:
+// a step streams more than L2 holds between two uses), and one row of arithmetic does not
+// cover that latency.
+template <int D = 1>
 __device__ __forceinline__ void smem_band_solve(double2* col, int T, int t, int part, int N,
                                                 const double* __restrict__ F, const uint8_t* __restrict__ P,
                                                 int M1K1) {
     double* x = reinterpret_cast<double*>(col) + 2 * t + part;   // x[j] at x[2 T j]
     const int st = 2 * T;
+    const size_t rs = (size_t)kBands * M1K1;                      // one row of factors
     // forward: rows j .. j+4 live in w0..w4
     double w0 = x[0], w1 = N > 1 ? x[st] : 0.0, w2 = N > 2 ? x[2 * st] : 0.0,
            w3 = N > 3 ? x[3 * st] : 0.0, w4 = N > 4 ? x[4 * st] : 0.0;
-    // factors of the next row are loaded one row ahead
-    int pn = P[0];
-    double l1n = __ldg(&F[0]), l2n = __ldg(&F[(size_t)M1K1]), l3n = __ldg(&F[(size_t)2 * M1K1]),
-           l4n = __ldg(&F[(size_t)3 * M1K1]);
-    for (int j = 0; j < N; ++j) {
-        const int pj = pn;
-        const double l1 = l1n, l2 = l2n, l3 = l3n, l4 = l4n;
-        if (j + 1 < N) {
-            const double* Fn = F + (size_t)(j + 1) * kBands * M1K1;
-            pn = P[(size_t)(j + 1) * M1K1];
-            l1n = __ldg(&Fn[0]);
-            l2n = __ldg(&Fn[(size_t)M1K1]);
-            l3n = __ldg(&Fn[(size_t)2 * M1K1]);
-            l4n = __ldg(&Fn[(size_t)3 * M1K1]);
+    double lr[D][4];
+    int pr[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        pr[d] = 0;
+        lr[d][0] = lr[d][1] = lr[d][2] = lr[d][3] = 0.0;
+        if (d < N) {
+            const double* Fr = F + (size_t)d * rs;
+            pr[d] = P[(size_t)d * M1K1];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) lr[d][q] = __ldg(&Fr[(size_t)q * M1K1]);
         }
-        if (pj == 1) { double q = w0; w0 = w1; w1 = q; }
-        else if (pj == 2) { double q = w0; w0 = w2; w2 = q; }
-        else if (pj == 3) { double q = w0; w0 = w3; w3 = q; }
-        else if (pj == 4) { double q = w0; w0 = w4; w4 = q; }
-        x[(size_t)j * st] = w0;
-        w1 = fma(-l1, w0, w1);
-        w2 = fma(-l2, w0, w2);
-        w3 = fma(-l3, w0, w3);
-        w4 = fma(-l4, w0, w4);
-        w0 = w1; w1 = w2; w2 = w3; w3 = w4;
-        w4 = (j + 5 < N) ? x[(size_t)(j + 5) * st] : 0.0;
+    }
+    for (int j0 = 0; j0 < N; j0 += D) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int j = j0 + d;
+            if (j < N) {
+                const int pj = pr[d];
+                const double l1 = lr[d][0], l2 = lr[d][1], l3 = lr[d][2], l4 = lr[d][3];
+                if (j + D < N) {   // refill this slot with row j + D
+                    const double* Fr = F + (size_t)(j + D) * rs;
+                    pr[d] = P[(size_t)(j + D) * M1K1];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) lr[d][q] = __ldg(&Fr[(size_t)q * M1K1]);
+                }
+                if (pj == 1) { double q = w0; w0 = w1; w1 = q; }
+                else if (pj == 2) { double q = w0; w0 = w2; w2 = q; }
+                else if (pj == 3) { double q = w0; w0 = w3; w3 = q; }
+                else if (pj == 4) { double q = w0; w0 = w4; w4 = q; }
+                x[(size_t)j * st] = w0;
+                w1 = fma(-l1, w0, w1);
+                w2 = fma(-l2, w0, w2);
+                w3 = fma(-l3, w0, w3);
+                w4 = fma(-l4, w0, w4);
+                w0 = w1; w1 = w2; w2 = w3; w3 = w4;
+                w4 = (j + 5 < N) ? x[(size_t)(j + 5) * st] : 0.0;
+            }
+        }
     }
     // backward: x_{j+1..j+8} in v1..v8.  Row-oriented; a column-oriented variant (each x_j
     // taken out of the rows above at once: two dependent operations per row instead of nine)
-    // measured slower on GB300 in k_pc and k_band_solve_g (0.400 vs 0.364 ms at N_r = 64):
-    // the substitutions are bound by FP64 issue, not by the dependency chain
+    // measured slower on GB300 in k_pc and k_band_solve_g (0.400 vs 0.364 ms at N_r = 64)
     double v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0, v5 = 0.0, v6 = 0.0, v7 = 0.0, v8 = 0.0;
-    double un[9];
-    {
-        const double* Fl = F + (size_t)(N - 1) * kBands * M1K1;
+    double ur[D][9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) un[q] = __ldg(&Fl[(size_t)(4 + q) * M1K1]);
+    for (int d = 0; d < D; ++d) {
+        const int j = N - 1 - d;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) ur[d][q] = j >= 0 ? __ldg(&F[(size_t)j * rs + (size_t)(4 + q) * M1K1]) : 0.0;
     }
-    for (int j = N - 1; j >= 0; --j) {
-        double uc[9];
+    for (int j0 = N - 1; j0 >= 0; j0 -= D) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) uc[q] = un[q];
-        if (j > 0) {
-            const double* Fp = F + (size_t)(j - 1) * kBands * M1K1;
+        for (int d = 0; d < D; ++d) {
+            const int j = j0 - d;
+            if (j >= 0) {
+                double uc[9];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) un[q] = __ldg(&Fp[(size_t)(4 + q) * M1K1]);
+                for (int q = 0; q < 9; ++q) uc[q] = ur[d][q];
+                if (j - D >= 0) {   // refill this slot with row j - D
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) ur[d][q] = __ldg(&F[(size_t)(j - D) * rs + (size_t)(4 + q) * M1K1]);
+                }
+                double s = x[(size_t)j * st];
+                s = fma(-uc[8], v8, s);
+                s = fma(-uc[7], v7, s);
+                s = fma(-uc[6], v6, s);
+                s = fma(-uc[5], v5, s);
+                s = fma(-uc[4], v4, s);
+                s = fma(-uc[3], v3, s);
+                s = fma(-uc[2], v2, s);
+                s = fma(-uc[1], v1, s);
+                const double xj = s * uc[0];
+                x[(size_t)j * st] = xj;
+                v8 = v7; v7 = v6; v6 = v5; v5 = v4; v4 = v3; v3 = v2; v2 = v1; v1 = xj;
+            }
         }
-        double s = x[(size_t)j * st];
-        s = fma(-uc[8], v8, s);
-        s = fma(-uc[7], v7, s);
-        s = fma(-uc[6], v6, s);
-        s = fma(-uc[5], v5, s);
-        s = fma(-uc[4], v4, s);
-        s = fma(-uc[3], v3, s);
-        s = fma(-uc[2], v2, s);
-        s = fma(-uc[1], v1, s);
-        const double xj = s * uc[0];
-        x[(size_t)j * st] = xj;
-        v8 = v7; v7 = v6; v6 = v5; v5 = v4; v4 = v3; v3 = v2; v2 = v1; v1 = xj;
     }
 }
 
