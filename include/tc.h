@@ -82,6 +82,11 @@ typedef struct {
                          the forward z pass, steps 2-5 and the next inverse z pass of different
                          chunks run concurrently on two internal streams (forked from and
                          joined back to the caller's stream).  0 or 1: sequential */
+    int pc_partitions; /* the fused steps-2-5 kernel solves each banded system (Sec. 3.2) as
+                         two partitions, rows [0, N_r/2) and [N_r/2, N_r), each with its own
+                         pivoted LU factors, coupled through an 8 x 8 reduced system (SPIKE
+                         form; the two halves run on separate lanes).  0 or 2: when N_r >= 16
+                         and the fused kernel runs; 1: one pivoted banded LU per system */
 } tc_options;
 
 /* Step state (Sec. 3.2): u = u^i, u_prev = u^{i-1}, N_prev = N^{i-1} (vector fields), p = p^i
@@ -126,6 +131,13 @@ tc_status tc_plan_nodes(const tc_plan* plan, double* r_host);
 /* FD weights into host memory: w[N_r][fd_order+1] applied to nodes col0[j] + t
  * (zero-padded), deriv = 1 or 2. */
 tc_status tc_plan_fd_weights(const tc_plan* plan, int deriv, double* w_host, int* col0_host);
+/* Inspection of the stored factors (host_only plans): x = A^{-1} b on the host for the system
+ * `which` of mode (m, |k| = ka), b and x real host arrays of N_r values, with the pivoted
+ * banded LU factors (partitions = 1) or the two-partition form the fused steps-2-5 kernel
+ * uses (partitions = 2: TC_ERR_STATE if the plan has none).  TC_ERR_STATE on a plan with
+ * device memory (its host factors are released after upload). */
+tc_status tc_plan_solve_host(const tc_plan* plan, int which, int m, int ka, int partitions, const double* b,
+                             double* x);
 /* Text of the last CUDA error seen by this plan (static storage inside the plan). */
 const char* tc_plan_last_error(const tc_plan* plan);
 const char* tc_status_string(tc_status s);

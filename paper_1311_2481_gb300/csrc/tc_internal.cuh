@@ -66,8 +66,10 @@ struct tc_plan {
     cudaStream_t aux[2] = {nullptr, nullptr};   // solve and pre-theta streams of the overlapped step
     std::vector<cudaEvent_t> pev;               // its events: fork, join, pre-done, then Z[c], P[c]
     int pc_modes;                  // modes per block of the fused steps-2-5 kernel (0: auto)
+    int num_sms = 152;             // multiprocessors of the plan's device
     int thr_zinv, thr_theta, thr_zfwd;  // block sizes of the FP64 transform kernels
     bool pc_split;                      // steps 2-5 as separate kernels (large N_r)
+    int part_h = 0;                     // fused kernel: systems cut into rows [0, h), [h, N_r) (0: uncut)
     int zinv_lines, zinv_lines32;  // lines per inverse z-pass block (FP64 / FP32 lines)
     int zfwd_lines, zfwd_lines32;  // lines per forward z-pass block (3 or 1)
     tc::Workspace ws;
@@ -79,6 +81,11 @@ struct tc_plan {
     std::vector<double> d1t_w;       // [N_r][d1t_n] matching weights D1[j][col] (0 padding)
     std::vector<double> fac;         // [set][j][band][m][ka]
     std::vector<uint8_t> piv;        // [set][j][m][ka] pivot offset 0..4
+    // two-partition form (part_h > 0): LU factors of the diagonal blocks at their global
+    // rows (layout of fac / piv), spikes [set][j][q][m][ka] (q < 4: V = A1^{-1} B for j < h,
+    // W = A2^{-1} C for j >= h) and the inverse reduced matrix [set][8 i + l][m][ka]
+    std::vector<double> fac2, spk, rinv;
+    std::vector<uint8_t> piv2;
     std::vector<double> tw_z, tw_t;  // interleaved complex exp(+2 pi i j / n)
     // device plan
     double* d_r = nullptr;
@@ -91,6 +98,10 @@ struct tc_plan {
     double* d_d1t_w = nullptr;
     double* d_fac = nullptr;
     uint8_t* d_piv = nullptr;
+    double* d_fac2 = nullptr;
+    uint8_t* d_piv2 = nullptr;
+    double* d_spk = nullptr;
+    double* d_rinv = nullptr;
     double2* d_tw_z = nullptr;
     double2* d_tw_t = nullptr;
     float2* d_tw_z32 = nullptr;

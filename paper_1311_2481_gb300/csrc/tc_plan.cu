@@ -221,8 +221,133 @@ static bool build_factors(tc_plan* p) {
     return ok;
 }
 
+// Solve with the factors band_lu leaves in W (row swap and column-j elimination in the
+// order of the factorisation, then back substitution), in place.
+static void band_lu_solve(int n, const double* W, const uint8_t* piv, double* b) {
+    const int kl = kKl, w = 3 * kKl + 1;
+    auto at = [&](int i, int c) { return W[(size_t)i * w + (c - i + kl)]; };
+    for (int j = 0; j < n; ++j) {
+        const int pj = j + piv[j];
+        if (pj != j) std::swap(b[j], b[pj]);
+        for (int q = 1; q <= kl && j + q < n; ++q) b[j + q] -= at(j + q, j) * b[j];
+    }
+    for (int j = n - 1; j >= 0; --j) {
+        double s = b[j];
+        for (int q = 1; q <= 2 * kl && j + q < n; ++q) s -= at(j, j + q) * b[j + q];
+        b[j] = s / at(j, j);
+    }
+}
+
+// Store the factors of an n-row block whose first row is global row r0 (layout of fac).
+static void store_lu(const tc_plan* p, std::vector<double>& fac, std::vector<uint8_t>& piv, int set, int m,
+                     int ka, int r0, int n, const double* W, const uint8_t* pv) {
+    const int N = p->N_r, M1 = p->M + 1, K1 = p->K + 1, w = 3 * kKl + 1;
+    const size_t per_set = (size_t)N * kBands * M1 * K1;
+    for (int i = 0; i < n; ++i) {
+        const int j = r0 + i;
+        auto dst = [&](int q) -> double& { return fac[(size_t)set * per_set + (((size_t)j * kBands + q) * M1 + m) * K1 + ka]; };
+        const double* row = &W[(size_t)i * w];
+        for (int q = 1; q <= kKl; ++q) dst(q - 1) = (i + q < n) ? W[(size_t)(i + q) * w + (kKl - q)] : 0.0;
+        dst(4) = 1.0 / row[kKl];
+        for (int q = 1; q <= 2 * kKl; ++q) dst(4 + q) = (i + q < n) ? row[kKl + q] : 0.0;
+        piv[(((size_t)set * N + j) * M1 + m) * K1 + ka] = pv[i];
+    }
+}
+
+// Two-partition (SPIKE) form of every system: A = [A1 B; C A2] cut at row h.  A1 and A2 are
+// factored like A; with kl = ku = 4, B has its non-zeros in rows h-4..h-1 of columns h..h+3
+// and C in rows h..h+3 of columns h-4..h-1.  The spikes V = A1^{-1} B and W = A2^{-1} C give
+// x1 = g1 - V x2[0..3] and x2 = g2 - W x1[h-4..h-1] (g_i = A_i^{-1} b_i), and the eight
+// interface unknowns x[h-4..h+3] solve R t = g[h-4..h+3] with R = [I V_b; W_t I] (V_b: rows
+// h-4..h-1 of V, W_t: rows 0..3 of W), whose inverse is stored.  Returns false if a block or
+// R is singular (the plan then keeps one partition).
+static bool build_partitions(tc_plan* p, int h) {
+    const int N = p->N_r, M1 = p->M + 1, K1 = p->K + 1, w = 3 * kKl + 1, n2 = N - h;
+    const size_t per_set = (size_t)N * kBands * M1 * K1;
+    p->fac2.assign((size_t)kNumSets * per_set, 0.0);
+    p->piv2.assign((size_t)kNumSets * N * M1 * K1, 0);
+    p->spk.assign((size_t)kNumSets * N * 4 * M1 * K1, 0.0);
+    p->rinv.assign((size_t)kNumSets * 64 * M1 * K1, 0.0);
+    unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    std::vector<char> good(nth, 1);
+    for (unsigned t = 0; t < nth; ++t) {
+        th.emplace_back([&, t]() {
+            std::vector<double> W((size_t)N * w), W1((size_t)h * w), W2((size_t)n2 * w), col(N);
+            std::vector<uint8_t> pv1(h), pv2(n2);
+            double Bm[4][4], Cm[4][4];   // B[h-4+i][h+q], C[h+i][h-4+q]
+            for (int job = t; job < kNumSets * M1; job += nth) {
+                const int set = job / M1, m = job % M1;
+                for (int ka = 0; ka < K1; ++ka) {
+                    assemble(p, set, m, ka, W.data());
+                    auto A = [&](int i, int c) -> double {
+                        const int d = c - i + kKl;
+                        return (d >= 0 && d < w) ? W[(size_t)i * w + d] : 0.0;
+                    };
+                    std::fill(W1.begin(), W1.end(), 0.0);
+                    std::fill(W2.begin(), W2.end(), 0.0);
+                    for (int i = 0; i < h; ++i)
+                        for (int c = std::max(0, i - kKl); c <= std::min(h - 1, i + kKl); ++c)
+                            W1[(size_t)i * w + (c - i + kKl)] = A(i, c);
+                    for (int i = 0; i < n2; ++i)
+                        for (int c = std::max(0, i - kKl); c <= std::min(n2 - 1, i + kKl); ++c)
+                            W2[(size_t)i * w + (c - i + kKl)] = A(h + i, h + c);
+                    for (int i = 0; i < 4; ++i)
+                        for (int q = 0; q < 4; ++q) {
+                            Bm[i][q] = A(h - 4 + i, h + q);
+                            Cm[i][q] = A(h + i, h - 4 + q);
+                        }
+                    if (!band_lu(h, W1.data(), pv1.data()) || !band_lu(n2, W2.data(), pv2.data())) { good[t] = 0; return; }
+                    store_lu(p, p->fac2, p->piv2, set, m, ka, 0, h, W1.data(), pv1.data());
+                    store_lu(p, p->fac2, p->piv2, set, m, ka, h, n2, W2.data(), pv2.data());
+                    long double R[8][16];
+                    for (int i = 0; i < 8; ++i)
+                        for (int c = 0; c < 16; ++c) R[i][c] = (c == i || c == i + 8) ? 1.0L : 0.0L;
+                    auto spk = [&](int j, int q) -> double& { return p->spk[((((size_t)set * N + j) * 4 + q) * M1 + m) * K1 + ka]; };
+                    for (int q = 0; q < 4; ++q) {
+                        std::fill(col.begin(), col.end(), 0.0);
+                        for (int i = 0; i < 4; ++i) col[h - 4 + i] = Bm[i][q];
+                        band_lu_solve(h, W1.data(), pv1.data(), col.data());
+                        for (int j = 0; j < h; ++j) spk(j, q) = col[j];
+                        for (int i = 0; i < 4; ++i) R[i][4 + q] = col[h - 4 + i];
+                        std::fill(col.begin(), col.end(), 0.0);
+                        for (int i = 0; i < 4; ++i) col[i] = Cm[i][q];
+                        band_lu_solve(n2, W2.data(), pv2.data(), col.data());
+                        for (int i = 0; i < n2; ++i) spk(h + i, q) = col[i];
+                        for (int i = 0; i < 4; ++i) R[4 + i][q] = col[i];
+                    }
+                    // Gauss-Jordan with partial pivoting on [R | I]
+                    for (int c = 0; c < 8; ++c) {
+                        int piv = c;
+                        for (int i = c + 1; i < 8; ++i)
+                            if (std::fabs((double)R[i][c]) > std::fabs((double)R[piv][c])) piv = i;
+                        if (R[piv][c] == 0.0L) { good[t] = 0; return; }
+                        if (piv != c)
+                            for (int e = 0; e < 16; ++e) std::swap(R[c][e], R[piv][e]);
+                        const long double d = R[c][c];
+                        for (int e = 0; e < 16; ++e) R[c][e] /= d;
+                        for (int i = 0; i < 8; ++i) {
+                            if (i == c || R[i][c] == 0.0L) continue;
+                            const long double f = R[i][c];
+                            for (int e = 0; e < 16; ++e) R[i][e] -= f * R[c][e];
+                        }
+                    }
+                    for (int i = 0; i < 8; ++i)
+                        for (int l = 0; l < 8; ++l)
+                            p->rinv[(((size_t)set * 64 + i * 8 + l) * M1 + m) * K1 + ka] = (double)R[i][8 + l];
+                }
+            }
+        });
+    }
+    for (auto& x : th) x.join();
+    for (char g : good)
+        if (!g) return false;
+    return true;
+}
+
 static tc_status upload(tc_plan* p) {
     TC_CUDA(p, cudaGetDevice(&p->device));
+    TC_CUDA(p, cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
     auto put = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
         cudaError_t e = cudaMalloc(dst, bytes);
         if (e != cudaSuccess) return e;
@@ -241,6 +366,12 @@ static tc_status upload(tc_plan* p) {
     TC_CUDA(p, put((void**)&p->d_d1t_w, p->d1t_w.data(), p->d1t_w.size() * sizeof(double)));
     TC_CUDA(p, put((void**)&p->d_fac, p->fac.data(), p->fac.size() * sizeof(double)));
     TC_CUDA(p, put((void**)&p->d_piv, p->piv.data(), p->piv.size()));
+    if (p->part_h > 0) {
+        TC_CUDA(p, put((void**)&p->d_fac2, p->fac2.data(), p->fac2.size() * sizeof(double)));
+        TC_CUDA(p, put((void**)&p->d_piv2, p->piv2.data(), p->piv2.size()));
+        TC_CUDA(p, put((void**)&p->d_spk, p->spk.data(), p->spk.size() * sizeof(double)));
+        TC_CUDA(p, put((void**)&p->d_rinv, p->rinv.data(), p->rinv.size() * sizeof(double)));
+    }
     TC_CUDA(p, put((void**)&p->d_tw_z, p->tw_z.data(), p->tw_z.size() * sizeof(double)));
     TC_CUDA(p, put((void**)&p->d_tw_t, p->tw_t.data(), p->tw_t.size() * sizeof(double)));
     std::vector<float> f(p->tw_z.begin(), p->tw_z.end());
@@ -298,7 +429,7 @@ static void free_device(tc_plan* p) {
         }
 
     void* ptrs[] = {p->d_r, p->d_ir, p->d_w1, p->d_w1f, p->d_w2, p->d_col0, p->d_d1t_row, p->d_d1t_w, p->d_fac, p->d_piv,
-                    p->d_tw_z, p->d_tw_t, p->d_tw_z32, p->d_tw_t32};
+                    p->d_fac2, p->d_piv2, p->d_spk, p->d_rinv, p->d_tw_z, p->d_tw_t, p->d_tw_z32, p->d_tw_t32};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -450,7 +581,7 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     p->thr_theta = choose_threads(rt, 6 * p->zt, p->zt + (p->zt + 1) / 2);
     p->thr_zfwd = choose_threads(rz, p->zfwd_lines, 0);
     if (o.theta_zt < 0 || o.theta_zt > 64 || o.pc_modes < 0 || o.pc_modes > 32 || o.pc_split < -1 || o.pc_split > 1 ||
-        o.theta_variant < 0 || o.theta_variant > 3 || o.pipeline < 0) {
+        o.theta_variant < 0 || o.theta_variant > 3 || o.pipeline < 0 || o.pc_partitions < 0 || o.pc_partitions > 2) {
         delete p;
         return TC_ERR_ARG;
     }
@@ -478,6 +609,16 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     // steps 2-5: fused kernel while 8 modes' four columns fit in 96 KB of shared memory,
     // split kernels beyond (tc_options.pc_split forces either)
     p->pc_split = o.pc_split == 1 || (o.pc_split == 0 && (size_t)4 * N_r * 8 * cplx > 96 * 1024);
+    // two partitions per system in the fused kernel (a singular diagonal block or reduced
+    // matrix keeps one)
+    if (!p->pc_split && o.pc_partitions != 1 && N_r >= 16)
+        p->part_h = build_partitions(p, N_r / 2) ? N_r / 2 : 0;
+    if (p->part_h == 0) {
+        std::vector<double>().swap(p->fac2);
+        std::vector<double>().swap(p->spk);
+        std::vector<double>().swap(p->rinv);
+        std::vector<uint8_t>().swap(p->piv2);
+    }
     if (p->pc_split) {
         p->ws.pstar = take(p->S * cplx);
         p->ws.ustar = take(3 * p->S * cplx);
@@ -501,6 +642,10 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
         // the device holds the factors now; release the host copy (tens of GB at N_r = 384)
         std::vector<double>().swap(p->fac);
         std::vector<uint8_t>().swap(p->piv);
+        std::vector<double>().swap(p->fac2);
+        std::vector<double>().swap(p->spk);
+        std::vector<double>().swap(p->rinv);
+        std::vector<uint8_t>().swap(p->piv2);
     }
     *out = p;
     return TC_OK;
@@ -562,6 +707,54 @@ tc_status tc_plan_fd_weights(const tc_plan* plan, int deriv, double* w_host, int
     const std::vector<double>& w = deriv == 1 ? plan->w1 : plan->w2;
     memcpy(w_host, w.data(), w.size() * sizeof(double));
     if (col0_host) memcpy(col0_host, plan->col0.data(), plan->col0.size() * sizeof(int));
+    return TC_OK;
+}
+
+tc_status tc_plan_solve_host(const tc_plan* plan, int which, int m, int ka, int partitions, const double* b,
+                             double* x) {
+    if (!plan || !b || !x || which < TC_P_STAR || which > TC_PHI || m < 0 || m > plan->M || ka < 0 ||
+        ka > plan->K || (partitions != 1 && partitions != 2))
+        return TC_ERR_ARG;
+    if (!plan->host_only || (partitions == 2 && plan->part_h == 0)) return TC_ERR_STATE;
+    const int N = plan->N_r, M1 = plan->M + 1, K1 = plan->K + 1;
+    const int set = which == TC_PHI ? kSetP : which;
+    const size_t per_set = (size_t)N * kBands * M1 * K1;
+    const std::vector<double>& fac = partitions == 2 ? plan->fac2 : plan->fac;
+    const std::vector<uint8_t>& piv = partitions == 2 ? plan->piv2 : plan->piv;
+    auto F = [&](int j, int q) { return fac[(size_t)set * per_set + (((size_t)j * kBands + q) * M1 + m) * K1 + ka]; };
+    auto Pv = [&](int j) { return (int)piv[(((size_t)set * N + j) * M1 + m) * K1 + ka]; };
+    for (int j = 0; j < N; ++j) x[j] = b[j];
+    // rows [r0, r0 + n) with the stored factors, in the order the device substitution uses
+    auto solve_rows = [&](int r0, int n) {
+        for (int i = 0; i < n; ++i) {
+            const int j = r0 + i, pj = j + Pv(j);
+            if (pj != j) std::swap(x[j], x[pj]);
+            for (int q = 1; q <= kKl && i + q < n; ++q) x[j + q] -= F(j, q - 1) * x[j];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            const int j = r0 + i;
+            double s = x[j];
+            for (int q = 2 * kKl; q >= 1; --q)
+                if (i + q < n) s -= F(j, 4 + q) * x[j + q];
+            x[j] = s * F(j, 4);
+        }
+    };
+    if (partitions == 1) {
+        solve_rows(0, N);
+        return TC_OK;
+    }
+    const int h = plan->part_h;
+    solve_rows(0, h);
+    solve_rows(h, N - h);
+    double t[8];
+    for (int i = 0; i < 8; ++i) {
+        double acc = 0.0;
+        for (int l = 0; l < 8; ++l) acc += plan->rinv[(((size_t)set * 64 + i * 8 + l) * M1 + m) * K1 + ka] * x[h - 4 + l];
+        t[i] = acc;
+    }
+    for (int j = 0; j < N; ++j)
+        for (int q = 0; q < 4; ++q)
+            x[j] -= plan->spk[((((size_t)set * N + j) * 4 + q) * M1 + m) * K1 + ka] * (j < h ? t[4 + q] : t[q]);
     return TC_OK;
 }
 

@@ -26,15 +26,76 @@ struct PCArgs {
     const int* col0;
     const double* fac;
     const uint8_t* piv;
+    const double* fac2;   // two-partition form (g.sh > 0): factors of the diagonal blocks,
+    const uint8_t* piv2;  // spikes [set][j][q][m][ka] and inverse reduced matrices
+    const double* spk;    // [set][8 i + l][m][ka]
+    const double* rinv;
     double Re_i, Re_o;
     int commit;
 };
+
+// Thread lt of the 4 nT threads of one system solves one half of it for one (mode, part):
+// threads [0, 2nT) rows [0, sh), threads [2nT, 4nT) rows [sh, N), each with the pivoted LU
+// factors of its diagonal block; the column then holds g = (A1^{-1} b1, A2^{-1} b2).
+__device__ __forceinline__ void half_solve(const PCArgs& a, const Geo& g, double2* X, int set, int T, int nT,
+                                           int mode0, int lt) {
+    const int half = lt >= 2 * nT ? 1 : 0;
+    const int r = lt - half * 2 * nT;
+    const int t = r >> 1, part = r & 1;
+    const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
+    const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+    const size_t per_set = (size_t)g.N * kBands * g.M1K1;
+    const int r0 = half ? g.sh : 0, n = half ? g.N - g.sh : g.sh;
+    smem_band_solve<kPCDepth>(X + (size_t)r0 * T, T, t, part, n,
+                              a.fac2 + (size_t)set * per_set + (size_t)r0 * kBands * g.M1K1 + mk,
+                              a.piv2 + ((size_t)set * g.N + r0) * g.M1K1 + mk, g.M1K1);
+}
+
+// Couple the halves of nsys systems (columns X0 + s N T, factor sets set0 + s), block-wide:
+// the interface unknowns x[sh-4 .. sh+3] = R^{-1} g[sh-4 .. sh+3] per (mode, part) into Xr,
+// then x = g - V x[sh .. sh+3] on rows < sh and x = g - W x[sh-4 .. sh-1] on rows >= sh.
+// Starts after a barrier that follows the half solves; ends with one.
+__device__ __forceinline__ void spike_combine(const PCArgs& a, const Geo& g, double2* X0, int nsys, int set0,
+                                              int T, int nT, int mode0, double* Xr) {
+    const int N = g.N, h = g.sh, items = N * T, st = 2 * T;
+    for (int task = threadIdx.x; task < nsys * nT * 16; task += blockDim.x) {
+        const int s = task / (nT * 16), rem = task - s * nT * 16;
+        const int t = rem >> 4, part = (rem >> 3) & 1, i = rem & 7;
+        const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
+        const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+        const double* x = reinterpret_cast<const double*>(X0 + (size_t)s * items) + 2 * t + part;
+        const double* R = a.rinv + ((size_t)(set0 + s) * 64 + 8 * i) * g.M1K1 + mk;
+        double acc = 0.0;
+#pragma unroll
+        for (int l = 0; l < 8; ++l) acc = fma(__ldg(&R[(size_t)l * g.M1K1]), x[(size_t)(h - 4 + l) * st], acc);
+        Xr[(s * T + t) * 16 + part * 8 + i] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nsys * items; idx += blockDim.x) {
+        const int s = idx / items, rem = idx - s * items;
+        const int j = rem / T, t = rem - j * T;
+        if (t >= nT) continue;
+        const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
+        const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+        const double* V = a.spk + ((size_t)((set0 + s) * N + j) * 4) * g.M1K1 + mk;
+        const double* xr = Xr + (s * T + t) * 16 + (j < h ? 4 : 0);
+        double2 v = X0[idx];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double w = __ldg(&V[(size_t)q * g.M1K1]);
+            v.x = fma(-w, xr[q], v.x);
+            v.y = fma(-w, xr[8 + q], v.y);
+        }
+        X0[idx] = v;
+    }
+    __syncthreads();
+}
 
 // Steps 2-5 of Sec. 3.2 for the T modes of this block: pressure prediction (Eq. pressure
 // with the Neumann rows of Eq. ppBC), velocity prediction (Eq. vel), correction potential
 // (Eq. correction) and update (Eq. update).
 template <int NTH>
-__global__ void __launch_bounds__(NTH) k_pc(PCArgs a, Geo g, int T) {
+__global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     extern __shared__ double2 sm[];
     const int N = g.N;
     const int items = N * T;
@@ -97,13 +158,21 @@ __global__ void __launch_bounds__(NTH) k_pc(PCArgs a, Geo g, int T) {
     // B: p* = P^{-1} b_p (real and imaginary parts by separate threads).  Meanwhile the
     // warps without a substitution precompute the part of the velocity right-hand sides that
     // does not depend on p*: (4u - u_prev)/(2dt) - (2N - N_prev), and the Dirichlet rows.
-    const int helper0 = ((2 * nT + 31) / 32) * 32;
-    if (threadIdx.x < 2 * nT) {
-        const int t = threadIdx.x >> 1, part = threadIdx.x & 1;
-        const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
-        const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
-        smem_band_solve<kPCDepth>(C0, T, t, part, N, a.fac + (size_t)kSetP * per_set + mk,
-                        a.piv + (size_t)kSetP * N * g.M1K1 + mk, g.M1K1);
+    // With two partitions (g.sh > 0) 4 nT threads solve, two per (mode, part).
+    const bool sp = g.sh > 0;
+    double* Xr = reinterpret_cast<double*>(C3 + items);
+    const int nsolve = (sp ? 4 : 2) * nT;
+    const int helper0 = ((nsolve + 31) / 32) * 32;
+    if (threadIdx.x < nsolve) {
+        if (sp) {
+            half_solve(a, g, C0, kSetP, T, nT, mode0, threadIdx.x);
+        } else {
+            const int t = threadIdx.x >> 1, part = threadIdx.x & 1;
+            const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
+            const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+            smem_band_solve<kPCDepth>(C0, T, t, part, N, a.fac + (size_t)kSetP * per_set + mk,
+                            a.piv + (size_t)kSetP * N * g.M1K1 + mk, g.M1K1);
+        }
     }
     // (with no spare warp the whole block does this after the substitution)
     const bool spare0 = helper0 < (int)blockDim.x;
@@ -140,6 +209,7 @@ __global__ void __launch_bounds__(NTH) k_pc(PCArgs a, Geo g, int T) {
         }
     }
     __syncthreads();
+    if (sp) spike_combine(a, g, C0, 1, kSetP, T, nT, mode0, Xr);
     // C: velocity right-hand sides: subtract grad_h p* on interior rows; p <- p* (commit)
     for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
         const int j = idx / T, t = idx - (idx / T) * T;
@@ -161,15 +231,21 @@ __global__ void __launch_bounds__(NTH) k_pc(PCArgs a, Geo g, int T) {
     __syncthreads();
     // D: the three Helmholtz solves.  Meanwhile the other warps rotate the history (nothing
     // reads u_prev or N_prev after C): u_prev <- u^i, N_prev <- N^i (commit).
-    const int helper1 = ((6 * nT + 31) / 32) * 32;
-    if (threadIdx.x < 6 * nT) {
-        const int c = threadIdx.x / (2 * nT), rem = threadIdx.x - c * 2 * nT;
-        const int t = rem >> 1, part = rem & 1;
-        const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
-        const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
-        const int set = kSetHp + c;
-        smem_band_solve<kPCDepth>(C1 + (size_t)c * items, T, t, part, N, a.fac + (size_t)set * per_set + mk,
-                        a.piv + (size_t)set * N * g.M1K1 + mk, g.M1K1);
+    const int nsolve1 = (sp ? 12 : 6) * nT;
+    const int helper1 = ((nsolve1 + 31) / 32) * 32;
+    if (threadIdx.x < nsolve1) {
+        if (sp) {
+            const int c = threadIdx.x / (4 * nT);
+            half_solve(a, g, C1 + (size_t)c * items, kSetHp + c, T, nT, mode0, threadIdx.x - c * 4 * nT);
+        } else {
+            const int c = threadIdx.x / (2 * nT), rem = threadIdx.x - c * 2 * nT;
+            const int t = rem >> 1, part = rem & 1;
+            const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
+            const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+            const int set = kSetHp + c;
+            smem_band_solve<kPCDepth>(C1 + (size_t)c * items, T, t, part, N, a.fac + (size_t)set * per_set + mk,
+                            a.piv + (size_t)set * N * g.M1K1 + mk, g.M1K1);
+        }
     } else if (a.commit && threadIdx.x >= helper1) {
         for (int idx = threadIdx.x - helper1; idx < 3 * items; idx += blockDim.x - helper1) {
             const int c = idx / items, rem = idx - c * items;
@@ -181,6 +257,7 @@ __global__ void __launch_bounds__(NTH) k_pc(PCArgs a, Geo g, int T) {
         }
     }
     __syncthreads();
+    if (sp) spike_combine(a, g, C1, 3, kSetHp, T, nT, mode0, Xr);
     if (a.commit && helper1 >= (int)blockDim.x) {   // no spare warp: rotate here
         for (int idx = threadIdx.x; idx < 3 * items; idx += blockDim.x) {
             const int c = idx / items, rem = idx - c * items;
@@ -209,14 +286,19 @@ __global__ void __launch_bounds__(NTH) k_pc(PCArgs a, Geo g, int T) {
     }
     __syncthreads();
     // F: phi = P^{-1} div_h u*
-    if (threadIdx.x < 2 * nT) {
-        const int t = threadIdx.x >> 1, part = threadIdx.x & 1;
-        const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
-        const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
-        smem_band_solve<kPCDepth>(C0, T, t, part, N, a.fac + (size_t)kSetP * per_set + mk,
-                        a.piv + (size_t)kSetP * N * g.M1K1 + mk, g.M1K1);
+    if (threadIdx.x < nsolve) {
+        if (sp) {
+            half_solve(a, g, C0, kSetP, T, nT, mode0, threadIdx.x);
+        } else {
+            const int t = threadIdx.x >> 1, part = threadIdx.x & 1;
+            const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
+            const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+            smem_band_solve<kPCDepth>(C0, T, t, part, N, a.fac + (size_t)kSetP * per_set + mk,
+                            a.piv + (size_t)kSetP * N * g.M1K1 + mk, g.M1K1);
+        }
     }
     __syncthreads();
+    if (sp) spike_combine(a, g, C0, 1, kSetP, T, nT, mode0, Xr);
     // G: u^{i+1} = u* - grad_h phi, p^{i+1} = p* + 3 phi / (2 dt), history rotation
     for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
         const int j = idx / T, t = idx - (idx / T) * T;
@@ -530,8 +612,14 @@ __global__ void k_diag(const double2* __restrict__ u, double* __restrict__ red,
 static int blocks_for(size_t n, int bs) { return (int)((n + bs - 1) / bs); }
 
 // modes per block of the fused kernel: four complex columns of N_r rows in shared memory
-static int pc_modes(const tc_plan* p) {
-    int T = p->pc_modes > 0 ? std::min(p->pc_modes, 16) : 8;
+// Modes per block of the fused kernel: the most (up to 16) that still give every SM a block,
+// within 96 KB of shared memory for the four columns.  Each block's time is its substitution
+// chain, so more modes per block cost little while the blocks fit one wave.
+static int pc_modes(const tc_plan* p, int nmode) {
+    int T = 16;
+    if (p->pc_modes > 0) T = std::min(p->pc_modes, 16);
+    else
+        while (T > 4 && (nmode + T - 1) / T < p->num_sms) T /= 2;
     while (T > 1 && (size_t)4 * p->N_r * T * sizeof(double2) > 96 * 1024) T /= 2;
     return T;
 }
@@ -605,7 +693,7 @@ tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const do
     Geo g = geo(p);
     g.mlo = ma * g.nk;
     g.mhi = mb * g.nk;
-    const int T = pc_modes(p);
+    const int T = pc_modes(p, g.mhi - g.mlo);
     PCArgs a;
     a.u = u; a.up = u_prev; a.Nc = Ncur; a.Np = N_prev;
     a.u_out = commit ? const_cast<double2*>(u) : u_out;
@@ -614,9 +702,12 @@ tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const do
     a.p = commit ? p_out : nullptr;
     a.rn = p->d_r; a.ir = p->d_ir; a.w1 = p->d_w1; a.w2 = p->d_w2; a.col0 = p->d_col0;
     a.fac = p->d_fac; a.piv = p->d_piv;
+    a.fac2 = p->d_fac2; a.piv2 = p->d_piv2; a.spk = p->d_spk; a.rinv = p->d_rinv;
     a.Re_i = p->Re_i; a.Re_o = p->Re_o;
     a.commit = commit ? 1 : 0;
-    const size_t sm = (size_t)4 * p->N_r * T * sizeof(double2);
+    // two partitions while the 12 T substitution threads of the Helmholtz phase fit the block
+    g.sh = (p->part_h > 0 && 12 * T <= (T <= 8 ? 128 : 256)) ? p->part_h : 0;
+    const size_t sm = (size_t)4 * p->N_r * T * sizeof(double2) + (size_t)3 * T * 16 * sizeof(double);
     // 128 threads up to 8 modes per block, 256 beyond (6T substitution threads plus helpers)
     const int slot = prof_begin(p, kKPC, s);
     if (T <= 8) {

@@ -10,6 +10,7 @@ namespace tc {
 struct Geo {
     int N, M, K, nk, nmode, K1, M1K1;
     int mlo, mhi;            // modes [mlo, mhi) handled by a launch (default: all)
+    int sh;                  // fused steps 2-5: systems cut at row sh into two partitions (0: uncut)
     size_t S;
     double mp, kz, dt, c1;   // c1 = 1 / (2 dt)
 };
@@ -19,6 +20,7 @@ static inline Geo geo(const tc_plan* p) {
     g.N = p->N_r; g.M = p->M; g.K = p->K; g.nk = 2 * p->K + 1; g.nmode = p->nmode;
     g.K1 = p->K + 1; g.M1K1 = (p->M + 1) * (p->K + 1); g.S = p->S;
     g.mlo = 0; g.mhi = g.nmode;
+    g.sh = 0;
     g.mp = (double)p->m_p; g.kz = p->k_z; g.dt = p->dt; g.c1 = 1.0 / (2.0 * p->dt);
     return g;
 }

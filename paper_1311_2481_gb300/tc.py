@@ -20,7 +20,7 @@ TC_FP64, TC_MIXED = 0, 1
 # every symbol include/tc.h declares, in declaration order
 SYMBOLS = [
     "tc_plan_create", "tc_plan_create_ex", "tc_plan_destroy", "tc_plan_workspace_bytes",
-    "tc_plan_nodes", "tc_plan_fd_weights", "tc_plan_last_error", "tc_status_string",
+    "tc_plan_nodes", "tc_plan_fd_weights", "tc_plan_solve_host", "tc_plan_last_error", "tc_status_string",
     "tc_nonlinear", "tc_helmholtz_solve", "tc_step", "tc_step_host", "tc_diagnostics",
     "tc_adjoint_step", "tc_adjoint_start", "tc_energy_gradient",
     "tc_nonlinear_noalloc", "tc_profile_enable", "tc_profile_read",
@@ -31,7 +31,8 @@ class tc_options(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("P_theta", ctypes.c_int), ("P_z", ctypes.c_int),
                 ("precision", ctypes.c_int), ("host_only", ctypes.c_int), ("theta_zt", ctypes.c_int),
                 ("pc_modes", ctypes.c_int), ("no_adjoint", ctypes.c_int), ("pc_split", ctypes.c_int),
-                ("theta_variant", ctypes.c_int), ("pipeline", ctypes.c_int)]
+                ("theta_variant", ctypes.c_int), ("pipeline", ctypes.c_int),
+                ("pc_partitions", ctypes.c_int)]
 
 
 class tc_state(ctypes.Structure):
@@ -75,6 +76,7 @@ def load_library(path: str = LIB_PATH):
         "tc_plan_workspace_bytes": (I, [P, ctypes.POINTER(S)]),
         "tc_plan_nodes": (I, [P, ctypes.POINTER(D)]),
         "tc_plan_fd_weights": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(I)]),
+        "tc_plan_solve_host": (I, [P, I, I, I, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "tc_plan_last_error": (ctypes.c_char_p, [P]),
         "tc_status_string": (ctypes.c_char_p, [I]),
         "tc_nonlinear": (I, [P, P, P, P, P]),
@@ -189,9 +191,11 @@ class Plan:
 
     def __init__(self, N_r, M, K, m_p, eta, Re_i, Re_o, L_z, dt, fd_order=8, alpha=0.5,
                  P_theta=0, P_z=0, precision=TC_FP64, host_only=False, device=None, theta_zt=0,
-                 pc_modes=0, no_adjoint=False, pc_split=0, theta_variant=0, pipeline=0):
+                 pc_modes=0, no_adjoint=False, pc_split=0, theta_variant=0, pipeline=0,
+                 pc_partitions=0):
         opt = tc_options(alpha if alpha != 0.0 else -1.0, P_theta, P_z, precision, int(host_only),
-                         theta_zt, pc_modes, int(no_adjoint), pc_split, theta_variant, pipeline)
+                         theta_zt, pc_modes, int(no_adjoint), pc_split, theta_variant, pipeline,
+                         pc_partitions)
         self.N_r, self.M, self.K = N_r, M, K
         self.handle = None
         torch = _torch()
@@ -231,6 +235,16 @@ class Plan:
                                                  w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                  c.ctypes.data_as(ctypes.POINTER(ctypes.c_int))), self.handle)
         return w, c
+
+    def solve_host(self, which, m, ka, b, partitions=1):
+        """Host solve with the stored factors of a host_only plan (inspection)."""
+        import numpy as np
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(self.N_r)
+        _check(load_library().tc_plan_solve_host(self.handle, which, m, ka, partitions,
+                                                 b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                 x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), self.handle)
+        return x
 
     def nonlinear(self, u, N=None, stream=None):
         torch = _torch()

@@ -72,3 +72,35 @@ def test_host_plan_matches_oracle_nodes_and_weights(lib):
             for j in range(N):
                 D[j, c[j]:c[j] + 9] = w[j]
             assert np.abs(D - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("N", [15, 16, 25, 48])
+def test_host_factors_solve_the_mode_systems(lib, N):
+    """The stored pivoted banded LU factors of every system (Sec. 3.2: Eq. pressure, Eq. vel,
+    Eq. correction) and their two-partition form (the diagonal blocks' own LU factors, the
+    spikes and the inverse 8 x 8 reduced matrix) solve the oracle's mode matrices: against
+    the dense solve, on random right-hand sides.  N_r = 15 has no two-partition form."""
+    import oracle as O
+    L = 2 * math.pi / 3.16
+    cfg = (N, 6, 8, 1, 0.5, 300.0, 0.0, L, 1e-3)
+    p = tc.Plan(*cfg, host_only=True)
+    ops = O.Operators(O.Params(*cfg))
+    rng = np.random.default_rng(3)
+    names = {tc.TC_P_STAR: "P", tc.TC_U_PLUS: "Hp", tc.TC_U_MINUS: "Hm", tc.TC_U_Z: "Hz", tc.TC_PHI: "P"}
+    worst = 0.0
+    for which, name in names.items():
+        for (m, ka) in ((0, 0), (0, 3), (1, 0), (6, 8), (3, 5)):
+            A = ops.mats[name][m, ka]
+            b = rng.standard_normal(N)
+            ref = np.linalg.solve(A, b)
+            for parts in (1, 2):
+                if parts == 2 and N < 16:
+                    with pytest.raises(tc.TCError) as e:
+                        p.solve_host(which, m, ka, b, parts)
+                    assert e.value.status == tc.TC_ERR_STATE
+                    continue
+                x = p.solve_host(which, m, ka, b, parts)
+                err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
+                worst = max(worst, err)
+                assert err <= 1e-11, (which, m, ka, parts, err)
+    print("worst", worst)

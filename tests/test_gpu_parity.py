@@ -129,6 +129,29 @@ def test_step_full_size_config2(pc_split):
     assert rel(host(st.p), st_o.p) <= 1e-10
 
 
+@pytest.mark.parametrize("N_r", [15, 16, 17, 33])
+def test_partitioned_solves_match_oracle(N_r):
+    """The fused kernel's two-partition (SPIKE) form of the banded systems, with even, odd and
+    ragged cuts (N_r = 15 keeps one partition): 20 steps against the oracle, and against the
+    one-partition form of the same kernel to rounding (the forms differ in rounding order, so
+    a cut plan's state is not bit-identical to the uncut one)."""
+    cfg = dict(CFG1, N_r=N_r)
+    ops = O.Operators(O.Params(**cfg))
+    u0 = init(ops, kind="broadband", amp=1e-2, seed=12)
+    ref = O.run(ops, O.cold_state(u0), 20)
+    out = {}
+    for parts in (1, 2):
+        plan = tc.Plan(**cfg, pc_split=-1, pc_partitions=parts)
+        st = tc.State(plan, dev(u0))
+        plan.step(st, 20)
+        out[parts] = {k: host(getattr(st, k)) for k in ("u", "p")}
+        for k in ("u", "p"):
+            assert rel(out[parts][k], getattr(ref, k)) <= 1e-10, (parts, k, rel(out[parts][k], getattr(ref, k)))
+    for k in ("u", "p"):
+        assert rel(out[2][k], out[1][k]) <= 1e-12, (k, rel(out[2][k], out[1][k]))
+    assert np.array_equal(out[2]["u"], out[1]["u"]) == (N_r < 16)
+
+
 def test_diagnostics_match_oracle():
     ops, plan = pair(CFG1)
     u = O.run(ops, O.cold_state(init(ops)), 3).u
