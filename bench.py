@@ -358,6 +358,44 @@ def large_mixed(tc, torch, I, dev, steps=4):
     return out
 
 
+# the paper's SMALL timing grid (n_r, n_theta, n_z) = (32, 384, 640): m = -192..192,
+# k = -320..320; P_z = 972 = 2^2 3^5 >= 3K + 1 (the 3/2 grid 960 has a factor 5)
+CFG_SMALL = dict(N_r=32, M=192, K=320, m_p=1, eta=0.5, Re_i=1e3, Re_o=0.0, L_z=2 * math.pi / 3.16,
+                 dt=5e-4, P_theta=576, P_z=972)
+# its best time in the paper: 0.104 s per step on 32 x 20 Xeon cores (Table of the SMALL run)
+PAPER_SMALL_S_PER_STEP = 0.104
+
+
+def paper_small(tc, torch, I, dev, steps=10):
+    """FP64 and mixed step at the paper's SMALL grid, beside its best CPU time (context)."""
+    cfg = {**CFG_SMALL, "dt": cfl_dt(CFG_SMALL)}
+    out = {"workload": "paper SMALL grid: N_r=32, m=-192..192, k=-320..320, phys 32x576x972, eta=0.5, "
+                       "Re_i=1000, broadband amp 0.01 (seed 42)",
+           "gdof": gdof(cfg), "dt": cfg["dt"],
+           "paper_best_s_per_step": PAPER_SMALL_S_PER_STEP, "paper_cores": 640}
+    for name, prec in (("fp64", tc.TC_FP64), ("mixed", tc.TC_MIXED)):
+        plan = tc.Plan(**cfg, precision=prec, no_adjoint=True, device=dev)
+        r = plan.nodes()
+        u0 = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"],
+                                              cfg["Re_o"], kind="broadband", amp=0.01, seed=42)).to(dev)
+        st = tc.State(plan, u0)
+        del u0
+        plan.step(st, 3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.step(st, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        d = plan.diagnostics(st.u)
+        out[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "gdof_steps_per_s": gdof(cfg) / ms / 1e6,
+                     "vs_paper_best": PAPER_SMALL_S_PER_STEP * 1e3 / ms, "state_finite": bool(d.finite)}
+        del plan, st
+        torch.cuda.empty_cache()
+    return out
+
+
 # largest single-GPU workload: N_r = 384, m = -384..384, k = -768..768, grid 384 x 1152 x 2304
 CFG5 = dict(N_r=384, M=384, K=768, m_p=1, eta=0.5, Re_i=3e4, Re_o=math.sqrt(0.5) * 3e4,
             L_z=2 * math.pi / 3.16, dt=5e-5)
@@ -613,7 +651,8 @@ def run_ours(args):
                                                       "ours_fp64_nonlinear_ms": nl64,
                                                       "ours_fp32_nonlinear_ms": nl32}),
                         ("adjoint", lambda: adjoint_ratio(tc, torch, I, f"cuda:{local}")),
-                        ("large_same_size", lambda: large_mixed(tc, torch, I, f"cuda:{local}"))):
+                        ("large_same_size", lambda: large_mixed(tc, torch, I, f"cuda:{local}")),
+                        ("paper_small", lambda: paper_small(tc, torch, I, f"cuda:{local}"))):
             try:
                 out[key] = fn()
             except Exception as exc:  # keep the main line even if an extra measurement fails
