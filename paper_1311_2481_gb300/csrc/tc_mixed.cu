@@ -539,9 +539,42 @@ tc_status launch_nl_theta32(tc_plan* p, char* ws, cudaStream_t s) {
 }
 
 // after the theta pass, for m in [ma, mb): forward z pass, mean-flow terms, N in FP64
+// The m = 0 line of a real field satisfies N_+(0,k) = conj N_-(0,-k) and N_z(0,k) = conj N_z(0,-k).
+// The FP32 products keep this only to rounding (about 1e-8 of N); the FP64 mean-flow terms of
+// the next evaluation act on the non-real part of u that such a defect seeds, and above the
+// Taylor-vortex onset they amplify it, while nothing saturates it (the transforms read only the
+// real part of the m = 0 line).  Projecting N's m = 0 line onto the symmetry leaves that part of
+// u to decay under the Stokes operator.  One thread per (r, k >= 0).
+__global__ void k_sym_m0(double2* __restrict__ N, int N_r, int M, int K, size_t S) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N_r * (K + 1)) return;
+    const int r = idx / (K + 1), k = idx - r * (K + 1);
+    const size_t line = (size_t)r * (M + 1) * (2 * K + 1);
+    const size_t ep = line + K + k, em = line + K - k;
+    auto pair = [&](size_t ia, size_t ib) {   // a <- (a + conj b) / 2, b <- conj a
+        const double2 a = N[ia], b = N[ib];
+        const double2 v = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+        N[ia] = v;
+        N[ib] = make_double2(v.x, -v.y);
+    };
+    pair(ep, S + em);                          // N_+(k), N_-(-k)
+    if (k > 0) pair(em, S + ep);               // N_+(-k), N_-(k)
+    pair(2 * S + ep, 2 * S + em);              // N_z(k), N_z(-k)
+}
+
+static tc_status launch_sym_m0(tc_plan* p, double2* N, cudaStream_t s) {
+    const int n = p->N_r * (p->K + 1);
+    k_sym_m0<<<(n + 127) / 128, 128, 0, s>>>(N, p->N_r, p->M, p->K, p->S);
+    TC_LAUNCHED(p, "k_sym_m0");
+    return TC_OK;
+}
+
 tc_status launch_nl_post32(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s, int ma, int mb) {
     const float2* H2 = reinterpret_cast<const float2*>(ws + p->ws.H2);
-    if (zpass_s_ok(p)) return zpass_s(p, nullptr, nullptr, H2, u, N, s, false, ma, mb);
+    if (zpass_s_ok(p)) {
+        TC_TRY_STATUS(zpass_s(p, nullptr, nullptr, H2, u, N, s, false, ma, mb));
+        return ma == 0 ? launch_sym_m0(p, N, s) : TC_OK;
+    }
     const int Lf = p->zfwd_lines32;
     const size_t sm3 = (size_t)2 * Lf * p->P_z * sizeof(float2);
     TC_CUDA(p, cudaFuncSetAttribute(k_zfwd32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
@@ -552,7 +585,7 @@ tc_status launch_nl_post32(tc_plan* p, const double2* u, double2* N, char* ws, c
                                                               (double)p->m_p, Lf, ma, mb - ma);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_zfwd32");
-    return TC_OK;
+    return ma == 0 ? launch_sym_m0(p, N, s) : TC_OK;
 }
 
 }  // namespace tc

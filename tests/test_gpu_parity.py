@@ -206,6 +206,22 @@ def test_mixed_nonlinear_error_is_fp32_level_of_the_perturbation_part(cfg):
     assert err <= 1e-8 * np.linalg.norm(ref)
 
 
+def test_mixed_nonlinear_m0_line_is_a_real_field():
+    """The mixed form's N keeps the m = 0 symmetry of a real field exactly:
+    N_+(0,k) = conj N_-(0,-k) and N_z(0,k) = conj N_z(0,-k)."""
+    cfg = dict(CFG1, m_p=6, eta=0.868, Re_i=458.1, L_z=2.4, dt=2e-5)
+    ops, plan = pair(cfg, precision=tc.TC_MIXED)
+    u0 = init(ops, kind="taylor", amp=1e-2, seed=7)
+    N = host(plan.nonlinear(dev(u0)))
+    K = ops.prm.K
+    Np, Nm, Nz = N[0, :, 0, :], N[1, :, 0, :], N[2, :, 0, :]
+    assert np.array_equal(Np, np.conj(Nm[:, ::-1]))
+    assert np.array_equal(Nz, np.conj(Nz[:, ::-1]))
+    assert np.all(Nz[:, K].imag == 0)
+    ref = O.nonlinear(ops, u0)
+    assert rel(N, ref) <= 2e-6
+
+
 @pytest.mark.parametrize("M,K", [(16, 8), (32, 8), (64, 8), (128, 8), (256, 4), (384, 4), (512, 4)])
 def test_mixed_theta_pass_lengths(M, K):
     """Every length-specialised theta pass (P_theta = 48 ... 1536) against the oracle and
