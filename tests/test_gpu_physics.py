@@ -90,3 +90,56 @@ def test_wavy_vortex_wave_speed_mixed():
     assert e_ratio > 1e-3, "no saturated wavy mode"
     assert residual <= 1e-5, residual
     assert abs(c / GOLD["c"] - 1) <= 1e-4, (c, steps)
+
+
+ONSET = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "wavy_vortex_onset.json")))
+
+
+def n1_growth_rate(Re, u_tvf=None, Re_prev=None):
+    """Growth rate of an n = 1 disturbance on saturated Taylor vortices.  In the linear regime
+    only the axisymmetric base (m = 0) and the disturbance (m = 1) interact, so M = 1 gives the
+    paper's azimuthal resolution's answer; N_r = 64 and |k| <= 64 are its radial and axial
+    resolution ((n_r, n_z) = (64, 128) = (M, 2L+1) in its notation)."""
+    eta, L_z, dt = ONSET["eta"], ONSET["Gamma"], ONSET["dt"]
+    N_r, M, K = 64, 1, 64
+    plan = tc.Plan(N_r, M, K, ONSET["k_theta"], eta, Re, ONSET["Re_o"], L_z, dt, no_adjoint=True)
+    r = plan.nodes()
+    base = torch.from_numpy(I.base_state(r, M, K, eta, Re, 0.0)).cuda()
+    if u_tvf is None:
+        u0 = torch.from_numpy(I.initial_state(r, M, K, 1, L_z, eta, Re, 0.0, kind="taylor", amp=0.02, seed=3)).cuda()
+        u0[:, :, 1, :] = 0
+    else:   # the previous Reynolds number's vortices on this Reynolds number's Couette flow
+        u0 = u_tvf - torch.from_numpy(I.base_state(r, M, K, eta, Re_prev, 0.0)).cuda() + base
+    st = tc.State(plan, u0)
+    prev = None
+    for _ in range(60):
+        plan.step(st, 5000)
+        e0 = float((st.u[:, :, 0, :].abs() ** 2).sum())
+        if prev is not None and abs(e0 / prev - 1) < 1e-12:
+            break
+        prev = e0
+    u_tvf = st.u.clone()
+    pert = torch.from_numpy(I.initial_state(r, M, K, 1, L_z, eta, Re, 0.0, kind="box", amp=1e-7, seed=5)).cuda() - base
+    u1 = u_tvf.clone()
+    u1[:, :, 1, :] = pert[:, :, 1, :]
+    st = tc.State(plan, u1)
+    span, logs, rates = 5000, [], []
+    for _ in range(60):
+        plan.step(st, span)
+        logs.append(math.log(float((st.u[:, :, 1, :].abs() ** 2).sum())))
+        if len(logs) >= 2:
+            rates.append((logs[-1] - logs[-2]) / (2 * span * dt))   # energy ~ exp(2 sigma t)
+        if len(rates) >= 3 and abs(rates[-1] - rates[-3]) < 1e-7:
+            break
+    return rates[-1], u_tvf
+
+
+def test_wavy_vortex_onset():
+    lo, hi = 407.6, 408.6
+    s_lo, u_tvf = n1_growth_rate(lo)
+    s_hi, _ = n1_growth_rate(hi, u_tvf, lo)
+    Re_c = lo - s_lo * (hi - lo) / (s_hi - s_lo)
+    print(f"sigma({lo}) = {s_lo:.6e}, sigma({hi}) = {s_hi:.6e}, Re_c = {Re_c:.4f}")
+    assert s_lo < 0 < s_hi
+    a, b = ONSET["Re_c_bracket"]
+    assert a - 0.05 <= Re_c <= b + 0.05, Re_c
