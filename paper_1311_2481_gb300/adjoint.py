@@ -68,3 +68,67 @@ class FinalEnergy(torch.autograd.Function):
 def final_energy(u0, plan, nsteps, checkpoint=20):
     """Differentiable J(u0); u0 is a complex128 CUDA tensor of the plan's vector shape."""
     return FinalEnergy.apply(u0, plan, nsteps, checkpoint)
+
+
+def energy_weights(plan, like):
+    """W with J(u) = 1/2 sum W |u - U|^2 over the stored coefficients, so that dJ/du = W (u - U):
+    taken from the library's gradient kernel as W = g(u + 1) - g(u)."""
+    z = torch.zeros_like(like)
+    return (plan.energy_gradient(z + 1) - plan.energy_gradient(z)).real.contiguous()
+
+
+def _real_field_m0(d):
+    """Project the m = 0 line onto the symmetry of a real field: d_+(0,k) = conj d_-(0,-k),
+    d_z(0,k) = conj d_z(0,-k)."""
+    line = d[:, :, 0, :]
+    p, m, z = line[0], line[1], line[2]
+    pm = 0.5 * (p + torch.conj(torch.flip(m, dims=[-1])))
+    zz = 0.5 * (z + torch.conj(torch.flip(z, dims=[-1])))
+    d = d.clone()
+    d[0, :, 0, :] = pm
+    d[1, :, 0, :] = torch.conj(torch.flip(pm, dims=[-1]))
+    d[2, :, 0, :] = zz
+    return d
+
+
+def _grad_and_value(u, plan, nsteps, checkpoint):
+    x = u.detach().clone().requires_grad_(True)
+    J = final_energy(x, plan, nsteps, checkpoint)
+    J.backward()
+    return float(J.detach()), x.grad.detach()
+
+
+def optimal_perturbation(plan, u_base, nsteps, delta0, energy=1e-6, iters=10, checkpoint=20):
+    """Largest energy gain over nsteps steps of a perturbation of the state u_base, and the
+    perturbation that attains it (the optimal initial perturbation from which transition
+    studies start), by power iteration in the energy inner product of tc_diag:
+
+        delta <- W^{-1} (dJ(u_base + delta) - dJ(u_base)),  rescaled to E(delta) = energy,
+
+    with the gradients from the hand-written adjoint (final_energy), the wall rows held at
+    zero and the m = 0 line kept that of a real field.  For small `energy` the iteration
+    converges to the leading right singular vector of the step map's linearisation about
+    u_base in the energy norm.  The gain of each iterate is the second-order part of J,
+    (J(u_base + delta) - J(u_base) - <dJ(u_base), delta>) / E(delta), which is insensitive to
+    a slow drift of the base state itself.  Returns (delta, gains)."""
+    W = energy_weights(plan, u_base)
+
+    def E(d):
+        return 0.5 * float((W * d.abs() ** 2).sum())
+
+    def admissible(d):
+        d = _real_field_m0(d)
+        d[:, 0] = 0
+        d[:, -1] = 0
+        return d
+
+    J0, g0 = _grad_and_value(u_base, plan, nsteps, checkpoint)
+    d = admissible(delta0.to(u_base.device, torch.complex128))
+    gains = []
+    for _ in range(iters):
+        d = d * (energy / E(d)) ** 0.5
+        J, g = _grad_and_value(u_base + d, plan, nsteps, checkpoint)
+        lin = float(torch.sum(torch.view_as_real(g0) * torch.view_as_real(d)))
+        gains.append((J - J0 - lin) / energy)
+        d = admissible((g - g0) / W)
+    return d * (energy / E(d)) ** 0.5, gains
