@@ -122,9 +122,11 @@ __device__ __forceinline__ void smem_band_solve(double2* col, int T, int t, int 
             }
         }
     }
-    // backward: x_{j+1..j+8} in v1..v8.  Row-oriented; a column-oriented variant (each x_j
-    // taken out of the rows above at once: two dependent operations per row instead of nine)
-    // measured slower on GB300 in k_pc and k_band_solve_g (0.400 vs 0.364 ms at N_r = 64)
+    // backward: x_{j+1..j+8} in v1..v8.  Row-oriented.  A column-oriented variant (each x_j
+    // taken out of the rows above at once: two dependent operations per row instead of nine,
+    // same results bit for bit) measured slower on GB300 (k_pc 0.547 against 0.286 ms at
+    // N_r = 64): each FP64 instruction costs its warp the same issue time whatever the chain,
+    // so the substitution is bound by the count of FP64 instructions, not by their latency
     double v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0, v5 = 0.0, v6 = 0.0, v7 = 0.0, v8 = 0.0;
     double ur[D][9];
 #pragma unroll
