@@ -43,7 +43,8 @@ typedef enum {
     TC_ERR_ARG = 1,       /* invalid argument (checked on the host before any launch) */
     TC_ERR_CUDA = 2,      /* a CUDA runtime call failed (see tc_plan_last_error) */
     TC_ERR_OOM = 3,       /* device or host allocation failed */
-    TC_ERR_NONFINITE = 4, /* a NaN/Inf was found in the state (tc_diagnostics) */
+    TC_ERR_NONFINITE = 4, /* a NaN/Inf was found in the state (tc_diagnostics), or an earlier
+                             step wrote one (tc_step, tc_step_host) */
     TC_ERR_TIMEOUT = 5,   /* reserved: a bounded device wait gave up (no such wait exists yet) */
     TC_ERR_STATE = 6      /* call not allowed in this plan state (e.g. host-only plan) */
 } tc_status;
@@ -160,7 +161,11 @@ tc_status tc_helmholtz_solve(tc_plan* plan, int which, const void* rhs, void* x,
  * (started == 0) first gets its history: one implicit Euler step of size 2dt/3 (the scheme
  * with u^{-1} = u^0, N^{-1} = N^0, same factors), u^{-1} = u^0 - 1.5 (u_E - u^0),
  * N^{-1} = N(u^{-1}); started is then set to 1.  nsteps = 0 on a cold state builds only
- * that history. */
+ * that history.  The update kernel raises a flag (in mapped host memory, no synchronisation)
+ * when it writes a NaN/Inf into the state; the first tc_step call that finds the flag set
+ * returns TC_ERR_NONFINITE before launching anything and clears it, so the caller can
+ * restore a state and continue.  Steps still in flight are not waited for: a blow-up is
+ * reported by a later call. */
 tc_status tc_step(tc_plan* plan, tc_state* st, int nsteps, void* ws, void* stream);
 
 /* tc_step with the state in host memory.  host_in: host copies of u, u_prev, N_prev, p (all
@@ -170,7 +175,8 @@ tc_status tc_step(tc_plan* plan, tc_state* st, int nsteps, void* ws, void* strea
  * pageable; pinned ones let the copies run at full link speed.  The copies and the steps are
  * enqueued on `stream`, which is synchronised before the call returns, so host_out is valid
  * on return.  host_out fields may alias host_in fields.  Errors: TC_ERR_ARG if a pointer of
- * dev is not device memory, a host pointer is device memory, or dev fields coincide. */
+ * dev is not device memory, a host pointer is device memory, or dev fields coincide;
+ * TC_ERR_NONFINITE if these steps wrote a NaN/Inf into the state (host_out is written). */
 tc_status tc_step_host(tc_plan* plan, const tc_state* host_in, tc_state* host_out, tc_state* dev,
                        int nsteps, void* ws, void* stream);
 

@@ -32,6 +32,18 @@ tc_status check_ws(tc_plan* p, void* ws) {
     return check_device_ptr(p, ws, "ws");
 }
 
+// An update kernel of an earlier step wrote a NaN/Inf into the state (flag in mapped host
+// memory, read without synchronising): report it once and clear it.
+tc_status take_nonfinite(tc_plan* p) {
+    volatile int* f = p->h_nonfinite;
+    if (f && *f) {
+        *f = 0;
+        snprintf(p->err, sizeof(p->err), "an earlier step wrote a non-finite value into the state");
+        return TC_ERR_NONFINITE;
+    }
+    return TC_OK;
+}
+
 #define TC_TRY(x)                       \
     do {                                \
         tc_status s_ = (x);             \
@@ -125,6 +137,7 @@ tc_status tc_step(tc_plan* plan, tc_state* st, int nsteps, void* ws, void* strea
     for (int i = 0; i < 4; ++i)
         for (int j = i + 1; j < 4; ++j)
             if (ptrs[i] == ptrs[j]) return TC_ERR_ARG;
+    TC_TRY(take_nonfinite(plan));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
     double2* u = static_cast<double2*>(st->u);
@@ -178,7 +191,7 @@ tc_status tc_step_host(tc_plan* plan, const tc_state* host_in, tc_state* host_ou
         if (hout[i]) TC_CUDA(plan, cudaMemcpyAsync(hout[i], dptr[i], bytes[i], cudaMemcpyDeviceToHost, s));
     TC_CUDA(plan, cudaStreamSynchronize(s));
     host_out->started = dev->started;
-    return TC_OK;
+    return take_nonfinite(plan);   // this call's own steps (it has synchronised)
 }
 
 tc_status tc_diagnostics(tc_plan* plan, const void* u, tc_diag* out, void* ws, void* stream) {

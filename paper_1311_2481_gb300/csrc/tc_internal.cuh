@@ -106,6 +106,10 @@ struct tc_plan {
     double2* d_tw_t = nullptr;
     float2* d_tw_z32 = nullptr;
     float2* d_tw_t32 = nullptr;
+    // non-finite flag: mapped pinned host memory that the update kernels set when they write
+    // a NaN/Inf into the state; tc_step reports and clears it
+    int* h_nonfinite = nullptr;
+    int* d_nonfinite = nullptr;
     int device = -1;
     char err[512];
     // per-kernel CUDA-event tracing
@@ -126,6 +130,12 @@ template <typename V> __host__ __device__ __forceinline__ V cmul(V a, V b) {
 template <typename V> __host__ __device__ __forceinline__ V cconj(V a) { a.y = -a.y; return a; }
 // i * a
 template <typename V> __host__ __device__ __forceinline__ V cmuli(V a) { V c; c.x = -a.y; c.y = a.x; return c; }
+
+// true if either part of v is a NaN or an Inf: exponent bits all set (integer test, no FP64
+// instruction)
+__device__ __forceinline__ bool nonfinite2(double2 v) {
+    return ((__double2hiint(v.x) & 0x7ff00000) == 0x7ff00000) | ((__double2hiint(v.y) & 0x7ff00000) == 0x7ff00000);
+}
 
 // ------------------------------------------------------------------ error helpers
 tc_status cuda_fail(tc_plan* p, cudaError_t e, const char* where);

@@ -348,6 +348,9 @@ static bool build_partitions(tc_plan* p, int h) {
 static tc_status upload(tc_plan* p) {
     TC_CUDA(p, cudaGetDevice(&p->device));
     TC_CUDA(p, cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    TC_CUDA(p, cudaHostAlloc((void**)&p->h_nonfinite, sizeof(int), cudaHostAllocMapped));
+    *p->h_nonfinite = 0;
+    TC_CUDA(p, cudaHostGetDevicePointer((void**)&p->d_nonfinite, p->h_nonfinite, 0));
     auto put = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
         cudaError_t e = cudaMalloc(dst, bytes);
         if (e != cudaSuccess) return e;
@@ -432,6 +435,8 @@ static void free_device(tc_plan* p) {
                     p->d_fac2, p->d_piv2, p->d_spk, p->d_rinv, p->d_tw_z, p->d_tw_t, p->d_tw_z32, p->d_tw_t32};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    if (p->h_nonfinite) cudaFreeHost(p->h_nonfinite);
+    p->h_nonfinite = p->d_nonfinite = nullptr;
 }
 
 }  // namespace tc

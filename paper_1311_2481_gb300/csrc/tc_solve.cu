@@ -30,6 +30,7 @@ struct PCArgs {
     const uint8_t* piv2;  // spikes [set][j][q][m][ka] and inverse reduced matrices
     const double* spk;    // [set][8 i + l][m][ka]
     const double* rinv;
+    int* nonfinite;       // set to 1 when a NaN/Inf is written into the state
     double Re_i, Re_o;
     int commit;
 };
@@ -300,6 +301,7 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     __syncthreads();
     if (sp) spike_combine(a, g, C0, 1, kSetP, T, nT, mode0, Xr);
     // G: u^{i+1} = u* - grad_h phi, p^{i+1} = p* + 3 phi / (2 dt), history rotation
+    bool bad = false;
     for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
         const int j = idx / T, t = idx - (idx / T) * T;
         if (t >= nT) continue;
@@ -318,7 +320,9 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t ec = (size_t)c * g.S + e;
-            a.u_out[ec] = make_double2(us[c].x - gph[c].x, us[c].y - gph[c].y);
+            const double2 un = make_double2(us[c].x - gph[c].x, us[c].y - gph[c].y);
+            a.u_out[ec] = un;
+            bad |= nonfinite2(un);
         }
         if (a.commit) {
             const double q = 3.0 * c1;   // 3 / (2 dt)
@@ -326,6 +330,7 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
             a.p[e] = make_double2(ps.x + q * f.x, ps.y + q * f.y);
         }
     }
+    if (bad && a.nonfinite) *a.nonfinite = 1;
 }
 
 // ---------------------------------------------------------------- split path (large N_r)
@@ -457,7 +462,8 @@ __global__ void k_rhs_div(const double2* __restrict__ us, double2* __restrict__ 
 __global__ void k_update(double2* u, double2* up, const double2* Nc, double2* Np, double2* p,
                          const double2* __restrict__ us, const double2* __restrict__ phi,
                          double2* __restrict__ u_out, const double* __restrict__ irn,
-                         const double* __restrict__ w1, const int* __restrict__ col0, int commit, Geo g) {
+                         const double* __restrict__ w1, const int* __restrict__ col0, int commit,
+                         int* __restrict__ nonfinite, Geo g) {
     const int mode = g.mlo + blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
     if (mode >= g.mhi) return;
     const int j = blockIdx.x;
@@ -475,6 +481,7 @@ __global__ void k_update(double2* u, double2* up, const double2* Nc, double2* Np
         const size_t ec = (size_t)c * g.S + e;
         const double2 s = us[ec];
         const double2 un = make_double2(s.x - gph[c].x, s.y - gph[c].y);
+        if (nonfinite2(un) && nonfinite) *nonfinite = 1;
         if (commit) {
             up[ec] = u[ec];
             u[ec] = un;
@@ -679,7 +686,7 @@ static tc_status launch_advance_split(tc_plan* p, const double2* u, double2* u_p
     TC_LAUNCHED(p, "k_band_solve_g");
     slot = prof_begin(p, kKUpdate, s);
     k_update<<<g1, 128, 0, s>>>(const_cast<double2*>(u), u_prev, Ncur, N_prev, p_out, us, phi, u_out, p->d_ir,
-                                p->d_w1, p->d_col0, commit ? 1 : 0, g);
+                                p->d_w1, p->d_col0, commit ? 1 : 0, p->d_nonfinite, g);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_update");
     return TC_OK;
@@ -703,6 +710,7 @@ tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const do
     a.rn = p->d_r; a.ir = p->d_ir; a.w1 = p->d_w1; a.w2 = p->d_w2; a.col0 = p->d_col0;
     a.fac = p->d_fac; a.piv = p->d_piv;
     a.fac2 = p->d_fac2; a.piv2 = p->d_piv2; a.spk = p->d_spk; a.rinv = p->d_rinv;
+    a.nonfinite = p->d_nonfinite;
     a.Re_i = p->Re_i; a.Re_o = p->Re_o;
     a.commit = commit ? 1 : 0;
     // two partitions while the 12 T substitution threads of the Helmholtz phase fit the block

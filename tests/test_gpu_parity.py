@@ -152,6 +152,37 @@ def test_partitioned_solves_match_oracle(N_r):
     assert np.array_equal(out[2]["u"], out[1]["u"]) == (N_r < 16)
 
 
+@pytest.mark.parametrize("pc_split", [-1, 1])
+def test_nonfinite_state_is_reported_by_the_next_step(pc_split):
+    """A step that writes a NaN into the state raises the plan's flag (mapped host memory):
+    the next tc_step returns TC_ERR_NONFINITE before launching and clears it; tc_step_host
+    reports its own steps."""
+    ops, plan = pair(CFG1, pc_split=pc_split)
+    u0 = init(ops)
+    st = tc.State(plan, dev(u0))
+    plan.step(st, 2)
+    bad = host(st.u).copy()
+    bad[0, 5, 1, ops.prm.K] = np.nan
+    st.u.copy_(dev(bad))
+    plan.step(st, 1)
+    torch.cuda.synchronize()
+    with pytest.raises(tc.TCError) as e:
+        plan.step(st, 1)
+    assert e.value.status == tc.TC_ERR_NONFINITE
+    st2 = tc.State(plan, dev(u0))
+    plan.step(st2, 3)                               # cleared: a finite state steps on
+    assert plan.diagnostics(st2.u).finite
+    hin = {k: torch.from_numpy(host(getattr(st2, k))).pin_memory() for k in ("u", "u_prev", "N_prev", "p")}
+    hin["u"][0, 5, 1, ops.prm.K] = complex("nan")
+    hin["started"] = True
+    hout = {"u": torch.empty_like(hin["u"]).pin_memory()}
+    with pytest.raises(tc.TCError) as e:
+        plan.step_host(st2, hin, hout, 1)
+    assert e.value.status == tc.TC_ERR_NONFINITE
+    hin["u"][0, 5, 1, ops.prm.K] = complex(0.0)
+    plan.step_host(st2, hin, hout, 1)               # cleared again
+
+
 def test_diagnostics_match_oracle():
     ops, plan = pair(CFG1)
     u = O.run(ops, O.cold_state(init(ops)), 3).u
