@@ -131,7 +131,7 @@ struct PCAdjArgs {
     double2* up_out;           // adjoint of u^{i-1}
     double2* N_out;            // total adjoint of N^i (input of the transposed nonlinear term)
     double2* Np_out;           // adjoint of N^{i-1}
-    const double* rn;
+    const double* ir;   // 1 / r_j
     const double* w1;
     const double* w2;
     const int* col0;
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_pc_adj(PCAdjArgs a, Geo g, int T) {
         const double2 dp = sdrowT(C1, a.trow, a.tw, a.ntab, j, T, t);
         const double2 dm = sdrowT(C2, a.trow, a.tw, a.ntab, j, T, t);
         const double2 gp = C1[j * T + t], gm = C2[j * T + t], gz = C3[j * T + t];
-        const double mm = g.mp * m / a.rn[j], kk = g.kz * k;
+        const double mm = g.mp * m * a.ir[j], kk = g.kz * k;
         double2 o;
         o.x = dp.x + dm.x - mm * (gp.x - gm.x) + kk * gz.y;
         o.y = dp.y + dm.y - mm * (gp.y - gm.y) - kk * gz.x;
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256) k_pc_adj(PCAdjArgs a, Geo g, int T) {
         if (t >= nT) continue;
         int m, k;
         minfo(t, m, k);
-        const double ir = 1.0 / a.rn[j];
+        const double ir = a.ir[j];
         const double2 d = sdrowT(C0, a.trow, a.tw, a.ntab, j, T, t);
         const double2 b = C0[idx];
         const double2 tt = make_double2(d.x + b.x * ir, d.y + b.y * ir);
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(256) k_pc_adj(PCAdjArgs a, Geo g, int T) {
         if (t >= nT) continue;
         int m, k;
         minfo(t, m, k);
-        const double ir = 1.0 / a.rn[j];
+        const double ir = a.ir[j];
         // v = -bpbar on interior rows, 0 on wall rows
         double2 d = make_double2(0.0, 0.0);
         for (int e = 0; e < a.ntab; ++e) {
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256) k_pc_adj(PCAdjArgs a, Geo g, int T) {
         const int jw = side == 0 ? 0 : N - 1;
         if (jw == N - 1 && m == 0 && k == 0) continue;
         const int c = a.col0[jw] + q;
-        const double r = a.rn[jw], ir = 1.0 / r, ir2 = ir * ir;
+        const double ir = a.ir[jw], ir2 = ir * ir;
         const double wq = 0.5 * (a.w2[jw * kStencil + q] + ir * a.w1[jw * kStencil + q]);
         const double2 w = C0[jw * T + t];
         const double mm = g.mp * m, kk = g.kz * k;
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256) k_pc_adj(PCAdjArgs a, Geo g, int T) {
             const int jw = N - 1;
             if (m == 0 && k == 0) continue;
             const int c = a.col0[jw] + q;
-            const double r = a.rn[jw], ir = 1.0 / r, ir2 = ir * ir;
+            const double ir = a.ir[jw], ir2 = ir * ir;
             const double wq = 0.5 * (a.w2[jw * kStencil + q] + ir * a.w1[jw * kStencil + q]);
             const double2 w = C0[jw * T + t];
             const double mm = g.mp * m, kk = g.kz * k;
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(256) k_zinv_adjin(const double2* __restrict__ 
 // times c_m) of the 12 adjoint fields as 6 paired lines.  Output per (r, m, z), 9 lines in
 // the (+, -, z) basis: A (u, with -i m m_p d_theta folded in), R (d_r), Z (d_z).
 __global__ void __launch_bounds__(256) k_theta_adj(const double2* __restrict__ H1, const double2* __restrict__ Ha,
-                                                   double2* __restrict__ H3, const double* __restrict__ rnodes,
+                                                   double2* __restrict__ H3, const double* __restrict__ irn,
                                                    int N_r, int M, int Pz, double mp, int zt,
                                                    const double2* __restrict__ tw, Radices rad) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(256) k_theta_adj(const double2* __restrict__ H
     __syncthreads();
     double2* phys = smem_fft(A, B, nl, tw, true, rad);
     double2* out = phys == A ? B : A;
-    const double ir = 1.0 / rnodes[r];
+    const double ir = irn[r];   // 1 / r_j from the plan
     for (int idx = threadIdx.x; idx < zt * Pt; idx += blockDim.x) {
         const int zi = idx / Pt, th = idx - zi * Pt;
         const double2* L0 = phys + (size_t)(zi * 6) * Pt + th;
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(256) k_theta_adj(const double2* __restrict__ H
 // lines; same fields, products and outputs.
 template <int PT, int ZT, int NT>
 __global__ void __launch_bounds__(NT) k_theta_adj_s(const double2* __restrict__ H1, const double2* __restrict__ Ha,
-                                                   double2* __restrict__ H3, const double* __restrict__ rnodes,
+                                                   double2* __restrict__ H3, const double* __restrict__ irn,
                                                    int N_r, int M, int Pz, double mp,
                                                    const double2* __restrict__ tw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(NT) k_theta_adj_s(const double2* __restrict__ 
     __syncthreads();
     const double2* phys = cft::passes<PT, 0, 1, nl, NT, true, double2, true>(A, B, tw);
     double2* out = phys == A ? B : A;
-    const double ir = 1.0 / rnodes[r];
+    const double ir = irn[r];   // 1 / r_j from the plan
     for (int idx = threadIdx.x; idx < zt * Pt; idx += NT) {
         const int zi = idx / Pt, th = idx - zi * Pt;
         const int pth = cft::pd(th);
@@ -883,7 +883,7 @@ tc_status launch_adjoint_advance(tc_plan* p, const double2* ubar_new, const doub
     PCAdjArgs a;
     a.ubar_new = ubar_new; a.ubar_cur = ubar_cur; a.Nbar_cur = Nbar_cur;
     a.u_out = u_out; a.up_out = up_out; a.N_out = N_out; a.Np_out = Np_out;
-    a.rn = p->d_r; a.w1 = p->d_w1; a.w2 = p->d_w2; a.col0 = p->d_col0;
+    a.ir = p->d_ir; a.w1 = p->d_w1; a.w2 = p->d_w2; a.col0 = p->d_col0;
     a.trow = p->d_d1t_row; a.tw = p->d_d1t_w; a.ntab = p->d1t_n;
     a.fac = p->d_fac; a.piv = p->d_piv;
     const size_t sm = (size_t)4 * p->N_r * T * sizeof(double2);
@@ -904,7 +904,7 @@ static tc_status theta_adj_s(tc_plan* p, const double2* H1, const double2* Ha, d
     const size_t sm = (size_t)2 * nl * cft::padded<PT>() * sizeof(double2);
     TC_CUDA(p, cudaFuncSetAttribute(k_theta_adj_s<PT, ZT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int slot = prof_begin(p, kKThetaAdj, s);
-    k_theta_adj_s<PT, ZT, NT><<<p->N_r * (p->P_z / ZT), NT, sm, s>>>(H1, Ha, H3, p->d_r, p->N_r, p->M, p->P_z,
+    k_theta_adj_s<PT, ZT, NT><<<p->N_r * (p->P_z / ZT), NT, sm, s>>>(H1, Ha, H3, p->d_ir, p->N_r, p->M, p->P_z,
                                                                     (double)p->m_p, p->d_tw_t);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_theta_adj_s");
@@ -954,7 +954,7 @@ tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* 
         const size_t smt = smem_for(zt);
         TC_CUDA(p, cudaFuncSetAttribute(k_theta_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt));
         slot = prof_begin(p, kKThetaAdj, s);
-        k_theta_adj<<<p->N_r * (p->P_z / zt), 256, smt, s>>>(H1, Ha, H3, p->d_r, p->N_r, p->M, p->P_z,
+        k_theta_adj<<<p->N_r * (p->P_z / zt), 256, smt, s>>>(H1, Ha, H3, p->d_ir, p->N_r, p->M, p->P_z,
                                                                (double)p->m_p, zt, p->d_tw_t, p->rad_t);
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_theta_adj");

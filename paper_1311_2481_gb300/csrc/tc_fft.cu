@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_zinv(const double2* __restrict__ u, dou
 //                                 3 (d_z u_r, d_z u_t)  4 (u_z, d_r u_z)  5 (d_t u_z, d_z u_z)
 template <typename V>
 __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __restrict__ H2,
-                                               const double* __restrict__ rnodes, int N_r, int M,
+                                               const double* __restrict__ irn, int N_r, int M,
                                                int Pz, double mp, int zt,
                                                const V* __restrict__ tw, Radices rad) {
     using T = typename Real<V>::type;
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __re
     V* phys = smem_fft(a, b, nl, tw, true, rad);
     V* fw = phys == a ? b : a;
     const int nzl = (zt + 1) / 2;
-    const T ir = (T)(1.0 / rnodes[r]);
+    const T ir = (T)irn[r];   // 1 / r_j from the plan
     for (int idx = threadIdx.x; idx < zt * Pt; idx += blockDim.x) {
         const int zi = idx / Pt;
         const int th = idx - zi * Pt;
@@ -394,7 +394,7 @@ static tc_status theta64(tc_plan* p, const double2* H1, double2* H2, cudaStream_
     const size_t sm2 = (size_t)2 * 6 * zt * p->P_t * sizeof(double2);
     TC_CUDA(p, cudaFuncSetAttribute(k_theta<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     const int slot = prof_begin(p, kKTheta, s);
-    k_theta<double2><<<p->N_r * (p->P_z / zt), p->thr_theta, sm2, s>>>(H1, H2, p->d_r, p->N_r, p->M, p->P_z,
+    k_theta<double2><<<p->N_r * (p->P_z / zt), p->thr_theta, sm2, s>>>(H1, H2, p->d_ir, p->N_r, p->M, p->P_z,
                                                                       (double)p->m_p, zt, p->d_tw_t, p->rad_t);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_theta");
@@ -411,7 +411,7 @@ tc_status launch_theta32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t 
     const size_t sm2 = (size_t)2 * 6 * zt * p->P_t * sizeof(float2);
     TC_CUDA(p, cudaFuncSetAttribute(k_theta<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     const int slot = prof_begin(p, kKTheta32, s);
-    k_theta<float2><<<p->N_r * (p->P_z / zt), 256, sm2, s>>>(H1, H2, p->d_r, p->N_r, p->M, p->P_z, (double)p->m_p,
+    k_theta<float2><<<p->N_r * (p->P_z / zt), 256, sm2, s>>>(H1, H2, p->d_ir, p->N_r, p->M, p->P_z, (double)p->m_p,
                                                              zt, p->d_tw_t32, p->rad_t);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_theta");

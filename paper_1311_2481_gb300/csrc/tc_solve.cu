@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     const int mode0 = g.mlo + blockIdx.x * T;
     const int nT = min(T, g.mhi - mode0);
     const size_t per_set = (size_t)N * kBands * g.M1K1;
-    const double c1 = 1.0 / (2.0 * g.dt);
+    const double c1 = g.c1;   // 1 / (2 dt)
 
     // A1: X = (2N - N_prev)_r into C1
     for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {

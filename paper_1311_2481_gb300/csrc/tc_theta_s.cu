@@ -54,7 +54,7 @@ __device__ __forceinline__ V imul(V a, typename Elem<V>::T s) { return vmk<V>(-s
 // transform of N_r + i N_t (one line per z) and of N_z (two z per line).
 template <typename V, int PT, int ZT, int NT, int MINB, bool R8>
 __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, V* __restrict__ H2,
-                                                      const double* __restrict__ rnodes, int N_r, int M, int Pz,
+                                                      const double* __restrict__ irn, int N_r, int M, int Pz,
                                                       double mp, const V* __restrict__ tw) {
     using T = typename Elem<V>::T;
     constexpr int LP = padded<PT>();
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, 
     const int z0 = (blockIdx.x % tiles) * ZT;
     const size_t fstride = (size_t)N_r * (M + 1) * Pz;
     const V* h = H1 + (size_t)r * (M + 1) * Pz + z0;
-    const T ir = (T)(1.0 / rnodes[r]);
+    const T ir = (T)irn[r];   // 1 / r_j from the plan
     const T mpf = (T)mp;
     const int zi = threadIdx.x % ZT;        // z of this thread in the load and store loops
     const int mstep = NT / ZT;
@@ -214,7 +214,7 @@ tc_status run_theta_s(tc_plan* p, const V* H1, V* H2, const V* tw, cudaStream_t 
     auto kern = k_theta_s<V, PT, ZT, NT, MINB, R8>;
     TC_CUDA(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int slot = prof_begin(p, sizeof(V) == 8 ? kKTheta32 : kKTheta, s);
-    kern<<<p->N_r * (p->P_z / ZT), NT, sm, s>>>(H1, H2, p->d_r, p->N_r, p->M, p->P_z, (double)p->m_p, tw);
+    kern<<<p->N_r * (p->P_z / ZT), NT, sm, s>>>(H1, H2, p->d_ir, p->N_r, p->M, p->P_z, (double)p->m_p, tw);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_theta_s");
     return TC_OK;
