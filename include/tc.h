@@ -71,7 +71,8 @@ typedef struct {
     int theta_zt;     /* launch tuning: z values per theta-pass block (0: automatic); in the
                          mixed form a value > 0 also selects the generic theta kernel over the
                          length-specialised one */
-    int pc_modes;     /* launch tuning: modes per block of the steps-2-5 kernel (0: automatic) */
+    int pc_modes;     /* launch tuning: modes per block of the steps-2-5 kernel, rounded down to
+                         a power of two, at most 16 (0: automatic) */
     int no_adjoint;   /* 1: size the workspace without the adjoint regions (tc_adjoint_* then
                          return TC_ERR_STATE); a TC_MIXED plan also stages its transforms in FP32 */
     int pc_split;     /* steps 2-5 as one fused kernel (-1) or as separate kernels (1);

@@ -108,10 +108,20 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     const int nT = min(T, g.mhi - mode0);
     const size_t per_set = (size_t)N * kBands * g.M1K1;
     const double c1 = g.c1;   // 1 / (2 dt)
+    // T divides the block size, so every element a thread visits in the element loops below
+    // belongs to the same mode t = threadIdx.x % T: its row index steps by blockDim / T, and
+    // m, k and the FP64 factors m m_p, k k_z are computed once (an int -> double conversion
+    // takes the FP64 pipe like an arithmetic instruction)
+    const int tq = threadIdx.x % T;
+    const int jstep = blockDim.x / T;
+    const int modeq = mode0 + tq;
+    const int mq = modeq / g.nk;
+    const int kq = modeq - mq * g.nk - g.K;
+    const double mmq = g.mp * mq, kkq = g.kz * kq;
 
     // A1: X = (2N - N_prev)_r into C1
-    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
-        const int j = idx / T, t = idx - (idx / T) * T;
+    for (int j = threadIdx.x / T; j < N; j += jstep) {
+        const int idx = j * T + tq, t = tq;
         double2 x = make_double2(0.0, 0.0);
         if (t < nT) {
             const size_t e = (size_t)j * g.nmode + mode0 + t;
@@ -123,14 +133,12 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     }
     __syncthreads();
     // A2: pressure right-hand side into C0
-    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
-        const int j = idx / T, t = idx - (idx / T) * T;
+    for (int j = threadIdx.x / T; j < N; j += jstep) {
+        const int idx = j * T + tq, t = tq;
         double2 out = make_double2(0.0, 0.0);
         if (t < nT) {
-            const int mode = mode0 + t;
-            const int m = mode / g.nk;
-            const int k = mode - m * g.nk - g.K;
-            const double mm = g.mp * m, kk = g.kz * k;
+            const int mode = modeq, m = mq, k = kq;
+            const double mm = mmq, kk = kkq;
             const double r = a.rn[j], ir = a.ir[j];
             const size_t e = (size_t)j * g.nmode + mode;
             if (j == 0 || j == N - 1) {
@@ -179,14 +187,12 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     const bool spare0 = helper0 < (int)blockDim.x;
     if (!spare0) __syncthreads();
     if (spare0 ? threadIdx.x >= helper0 : true) {
-        const int first = spare0 ? helper0 : 0;
-        for (int idx = threadIdx.x - first; idx < items; idx += blockDim.x - first) {
-            const int j = idx / T, t = idx - (idx / T) * T;
+        const int first = spare0 ? helper0 : 0;   // a multiple of 32: (threadIdx.x - first) % T == tq
+        for (int j = (threadIdx.x - first) / T; j < N; j += ((int)blockDim.x - first) / T) {
+            const int idx = j * T + tq, t = tq;
             double2 o[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
             if (t < nT) {
-                const int mode = mode0 + t;
-                const int m = mode / g.nk;
-                const int k = mode - m * g.nk - g.K;
+                const int mode = modeq, m = mq, k = kq;
                 if (j == 0 || j == N - 1) {
                     if (m == 0 && k == 0) {
                         const double Re = j == 0 ? a.Re_i : a.Re_o;
@@ -212,18 +218,15 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     __syncthreads();
     if (sp) spike_combine(a, g, C0, 1, kSetP, T, nT, mode0, Xr);
     // C: velocity right-hand sides: subtract grad_h p* on interior rows; p <- p* (commit)
-    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
-        const int j = idx / T, t = idx - (idx / T) * T;
-        if (t >= nT) continue;
-        const int mode = mode0 + t;
-        const int m = mode / g.nk;
-        const int k = mode - m * g.nk - g.K;
+    for (int j = threadIdx.x / T; j < N && tq < nT; j += jstep) {
+        const int idx = j * T + tq, t = tq;
+        const int mode = modeq;
         const double2 pv = C0[idx];
         if (a.commit) a.p[(size_t)j * g.nmode + mode] = pv;
         if (j == 0 || j == N - 1) continue;
         const double2 d = sdrow(C0, a.w1, a.col0, j, T, t);
-        const double tt = g.mp * m * a.ir[j];
-        const double kk = g.kz * k;
+        const double tt = mmq * a.ir[j];
+        const double kk = kkq;
         double2 v;
         v = C1[idx]; v.x -= d.x - tt * pv.x; v.y -= d.y - tt * pv.y; C1[idx] = v;
         v = C2[idx]; v.x -= d.x + tt * pv.x; v.y -= d.y + tt * pv.y; C2[idx] = v;
@@ -270,14 +273,11 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
         }
     }
     // E: div_h u* into C0 (homogeneous Neumann / Dirichlet rows)
-    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
-        const int j = idx / T, t = idx - (idx / T) * T;
+    for (int j = threadIdx.x / T; j < N; j += jstep) {
+        const int idx = j * T + tq, t = tq;
         double2 out = make_double2(0.0, 0.0);
         if (t < nT && j > 0 && j < N - 1) {
-            const int mode = mode0 + t;
-            const int m = mode / g.nk;
-            const int k = mode - m * g.nk - g.K;
-            const double mm = g.mp * m, kk = g.kz * k, ir = a.ir[j];
+            const double mm = mmq, kk = kkq, ir = a.ir[j];
             const double2 dp = sdrow(C1, a.w1, a.col0, j, T, t), dm = sdrow(C2, a.w1, a.col0, j, T, t);
             const double2 vp = C1[idx], vm = C2[idx], vz = C3[idx];
             out.x = 0.5 * (dp.x + dm.x) + 0.5 * (vp.x + vm.x) * ir + 0.5 * mm * ir * (vp.x - vm.x) - kk * vz.y;
@@ -302,17 +302,13 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     if (sp) spike_combine(a, g, C0, 1, kSetP, T, nT, mode0, Xr);
     // G: u^{i+1} = u* - grad_h phi, p^{i+1} = p* + 3 phi / (2 dt), history rotation
     bool bad = false;
-    for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
-        const int j = idx / T, t = idx - (idx / T) * T;
-        if (t >= nT) continue;
-        const int mode = mode0 + t;
-        const int m = mode / g.nk;
-        const int k = mode - m * g.nk - g.K;
-        const size_t e = (size_t)j * g.nmode + mode;
+    for (int j = threadIdx.x / T; j < N && tq < nT; j += jstep) {
+        const int idx = j * T + tq, t = tq;
+        const size_t e = (size_t)j * g.nmode + modeq;
         const double2 f = C0[idx];
         const double2 d = sdrow(C0, a.w1, a.col0, j, T, t);
-        const double tt = g.mp * m * a.ir[j];
-        const double kk = g.kz * k;
+        const double tt = mmq * a.ir[j];
+        const double kk = kkq;
         const double2 gph[3] = {make_double2(d.x - tt * f.x, d.y - tt * f.y),
                                 make_double2(d.x + tt * f.x, d.y + tt * f.y),
                                 make_double2(-kk * f.y, kk * f.x)};
@@ -619,12 +615,13 @@ __global__ void k_diag(const double2* __restrict__ u, double* __restrict__ red,
 static int blocks_for(size_t n, int bs) { return (int)((n + bs - 1) / bs); }
 
 // modes per block of the fused kernel: four complex columns of N_r rows in shared memory
-// Modes per block of the fused kernel: the most (up to 16) that still give every SM a block,
+// Modes per block of the fused kernel (a power of two): the most (up to 16) that still give every SM a block,
 // within 96 KB of shared memory for the four columns.  Each block's time is its substitution
 // chain, so more modes per block cost little while the blocks fit one wave.
 static int pc_modes(const tc_plan* p, int nmode) {
     int T = 16;
-    if (p->pc_modes > 0) T = std::min(p->pc_modes, 16);
+    if (p->pc_modes > 0)
+        while (T > p->pc_modes) T /= 2;   // a power of two: it divides the block size
     else
         while (T > 4 && (nmode + T - 1) / T < p->num_sms) T /= 2;
     while (T > 1 && (size_t)4 * p->N_r * T * sizeof(double2) > 96 * 1024) T /= 2;
