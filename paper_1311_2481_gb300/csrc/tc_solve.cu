@@ -72,22 +72,31 @@ __device__ __forceinline__ void spike_combine(const PCArgs& a, const Geo& g, dou
         Xr[(s * T + t) * 16 + part * 8 + i] = acc;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nsys * items; idx += blockDim.x) {
-        const int s = idx / items, rem = idx - s * items;
-        const int j = rem / T, t = rem - j * T;
-        if (t >= nT) continue;
+    // fix-up: T divides the block size, so a thread's elements all belong to mode t = tid % T;
+    // rows step by blockDim / T, four in flight per iteration
+    const int t = threadIdx.x % T;
+    if (t < nT) {
         const int mode = mode0 + t, m = mode / g.nk, k = mode - m * g.nk - g.K;
         const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
-        const double* V = a.spk + ((size_t)((set0 + s) * N + j) * 4) * g.M1K1 + mk;
-        const double* xr = Xr + (s * T + t) * 16 + (j < h ? 4 : 0);
-        double2 v = X0[idx];
+        const int jstep = blockDim.x / T;
+        for (int s = 0; s < nsys; ++s) {
+            const double* Vs = a.spk + (size_t)(set0 + s) * N * 4 * g.M1K1 + mk;
+            const double* xs = Xr + (s * T + t) * 16;
+            double2* Xs = X0 + (size_t)s * items + t;
+#pragma unroll 4
+            for (int j = threadIdx.x / T; j < N; j += jstep) {
+                const double* V = Vs + (size_t)j * 4 * g.M1K1;
+                const double* xr = xs + (j < h ? 4 : 0);
+                double2 v = Xs[(size_t)j * T];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const double w = __ldg(&V[(size_t)q * g.M1K1]);
-            v.x = fma(-w, xr[q], v.x);
-            v.y = fma(-w, xr[8 + q], v.y);
+                for (int q = 0; q < 4; ++q) {
+                    const double w = __ldg(&V[(size_t)q * g.M1K1]);
+                    v.x = fma(-w, xr[q], v.x);
+                    v.y = fma(-w, xr[8 + q], v.y);
+                }
+                Xs[(size_t)j * T] = v;
+            }
         }
-        X0[idx] = v;
     }
     __syncthreads();
 }
