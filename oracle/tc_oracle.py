@@ -230,25 +230,36 @@ def _dr(ops, a):
     return np.tensordot(ops.D1, a, axes=(1, 0))
 
 
-def physical_fields(ops, u_hat):
+def physical_fields(ops, u_hat, rows=None):
     """The twelve physical fields of step 1 of Sec. 3.2: for c in (r, theta, z):
-    u_c, d_r u_c, d_theta u_c, d_z u_c (d_theta is the angle derivative)."""
-    up, um, uz = u_hat
+    u_c, d_r u_c, d_theta u_c, d_z u_c (d_theta is the angle derivative).
+
+    rows: radial rows to evaluate (default all).  Each row's fields need only that row and,
+    for d_r, the rows of its stencil, so the others are not touched (the same arithmetic)."""
+    if rows is None:
+        sub, D, sel = u_hat, ops.D1, slice(None)
+    else:
+        rows = np.atleast_1d(rows)
+        need = np.unique(np.concatenate([rows, np.nonzero(np.any(ops.D1[rows] != 0, axis=0))[0]]))
+        sub, D, sel = u_hat[:, need], ops.D1[np.ix_(rows, need)], np.searchsorted(need, rows)
+    up, um, uz = sub
     comps = [(up + um) / 2.0, (up - um) / 2j, uz]
     im = 1j * ops.mm[None, :, None]
     ik = 1j * ops.kk[None, None, :]
     out = []
     for a in comps:
-        out.append([to_physical(ops, a), to_physical(ops, _dr(ops, a)),
-                    to_physical(ops, im * a), to_physical(ops, ik * a)])
+        ar = a[sel]
+        out.append([to_physical(ops, ar), to_physical(ops, np.tensordot(D, a, axes=(1, 0))),
+                    to_physical(ops, im * ar), to_physical(ops, ik * ar)])
     return out
 
 
-def nonlinear(ops, u_hat):
+def nonlinear(ops, u_hat, rows=None):
     """N(u) = u . grad u with the curvature terms of Eq. NS_cyl, dealiased; returned as
-    (N_+, N_-, N_z) coefficients with N_pm = N_r +- i N_theta."""
-    (ur, ur_r, ur_t, ur_z), (ut, ut_r, ut_t, ut_z), (uz, uz_r, uz_t, uz_z) = physical_fields(ops, u_hat)
-    r = ops.r[:, None, None]
+    (N_+, N_-, N_z) coefficients with N_pm = N_r +- i N_theta.  rows: radial rows to evaluate
+    (default all); the result then has those rows only."""
+    (ur, ur_r, ur_t, ur_z), (ut, ut_r, ut_t, ut_z), (uz, uz_r, uz_t, uz_z) = physical_fields(ops, u_hat, rows)
+    r = (ops.r if rows is None else ops.r[np.atleast_1d(rows)])[:, None, None]
 
     def adv(f_r, f_t, f_z):
         return ur * f_r + (ut / r) * f_t + uz * f_z

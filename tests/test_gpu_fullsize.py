@@ -1,0 +1,80 @@
+"""Parity of the nonlinear term at the two largest workloads, on sampled outputs: the oracle
+evaluates N(u) one radial row at a time with its own DFT matrices (a whole evaluation at
+these sizes would take hours on the host), and the CUDA path runs the whole field.
+
+* N_r = 256, m = -256..256, k = -512..512 (grid 256 x 768 x 1536), FP64: wall rows, the first
+  interior row and a middle row, relative error <= 1e-12;
+* N_r = 384, m = -384..384, k = -768..768 (grid 384 x 1152 x 2304), mixed form as bench.py
+  runs it there (FP32 staging, no adjoint workspace): error <= 2e-6 of the perturbation
+  part N(u') on the sampled rows, as for the mixed form at small sizes, plus FP64 rounding
+  of the whole N (the wall rows' N(u') is zero).
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+from paper_1311_2481_gb300 import build as B  # noqa: E402
+from paper_1311_2481_gb300 import inputs as I  # noqa: E402
+from paper_1311_2481_gb300 import tc  # noqa: E402
+
+B.build()
+LZ = 2 * math.pi / 3.16
+# quasi-Keplerian workloads (Re_o = sqrt(eta) Re_i); dt does not enter N(u)
+CFG4 = dict(N_r=256, M=256, K=512, m_p=1, eta=0.5, Re_i=1e4, Re_o=math.sqrt(0.5) * 1e4, L_z=LZ, dt=1e-4)
+CFG5 = dict(N_r=384, M=384, K=768, m_p=1, eta=0.5, Re_i=3e4, Re_o=math.sqrt(0.5) * 3e4, L_z=LZ, dt=5e-5)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _state(ops, cfg):
+    return I.initial_state(ops.r, cfg["M"], cfg["K"], cfg["m_p"], cfg["L_z"], cfg["eta"], cfg["Re_i"],
+                           cfg["Re_o"], kind="broadband", amp=0.05, seed=42)
+
+
+def test_fp64_nonlinear_sampled_rows_at_N_r_256():
+    ops = O.Operators(O.Params(**CFG4))
+    u = _state(ops, CFG4)
+    plan = tc.Plan(**CFG4, no_adjoint=True)
+    rows = [0, 1, 128, 255]
+    N = plan.nonlinear(torch.from_numpy(u).cuda())
+    got = N[:, rows].cpu().numpy()
+    del N, plan
+    torch.cuda.empty_cache()
+    ref = O.nonlinear(ops, u, rows=rows)
+    for i, j in enumerate(rows):
+        assert rel(got[:, i], ref[:, i]) <= 1e-12, (j, rel(got[:, i], ref[:, i]))
+
+
+def test_mixed_nonlinear_sampled_rows_at_N_r_384():
+    ops = O.Operators(O.Params(**CFG5))
+    u = _state(ops, CFG5)
+    plan = tc.Plan(**CFG5, precision=tc.TC_MIXED, no_adjoint=True)
+    rows = [0, 191, 383]
+    N = plan.nonlinear(torch.from_numpy(u).cuda())
+    got = N[:, rows].cpu().numpy()
+    del N, plan
+    torch.cuda.empty_cache()
+    ref = O.nonlinear(ops, u, rows=rows)
+    # the perturbation part: the mean azimuthal flow U = Re u_theta^(0,0) removed (in place;
+    # u is not used after this)
+    K = CFG5["K"]
+    U = np.imag(u[0, :, 0, K] - u[1, :, 0, K]) / 2
+    u[0, :, 0, K] -= 1j * U
+    u[1, :, 0, K] += 1j * U
+    ref_pert = O.nonlinear(ops, u, rows=rows)
+    for i, j in enumerate(rows):
+        err = np.linalg.norm(got[:, i] - ref[:, i])
+        # FP32 roundings of N(u') plus FP64 roundings of the whole N (at a wall row u' = 0, so
+        # N(u') vanishes and only the FP64 mean-flow term -U^2/r is left)
+        bound = 2e-6 * np.linalg.norm(ref_pert[:, i]) + 1e-13 * np.linalg.norm(ref[:, i])
+        assert err <= bound, (j, err, np.linalg.norm(ref_pert[:, i]), np.linalg.norm(ref[:, i]))

@@ -232,6 +232,12 @@ def test_nonlinear_manufactured_against_analytic_derivatives():
     ref = np.stack([Nr_h + 1j * Nt_h, Nr_h - 1j * Nt_h, Nz_h])
     got = O.nonlinear(ops, u_hat)
     assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+    # the row-restricted evaluation (wall rows, a stencil-edge row, an interior row)
+    rows = [0, 3, 7, prm.N_r - 1]
+    got_rows = O.nonlinear(ops, u_hat, rows=rows)
+    assert got_rows.shape == (3, len(rows), M + 1, 2 * K + 1)
+    assert np.linalg.norm(got_rows - ref[:, rows]) <= 1e-12 * np.linalg.norm(ref[:, rows])
+    assert np.linalg.norm(got_rows - got[:, rows]) <= 1e-14 * np.linalg.norm(got[:, rows])
 
 
 def test_nonlinear_closed_forms():
