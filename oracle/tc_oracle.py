@@ -275,15 +275,18 @@ def nonlinear(ops, u_hat, rows=None):
 # Per-mode operators (Eq. modalNSdecoup) and the five systems of Sec. 3.2
 # ----------------------------------------------------------------------------------------
 
-def mode_matrices(ops):
+def mode_matrices(ops, m=None, ka=None):
     """Dense real matrices indexed [m, |k|]: 'P' Poisson with Neumann wall rows (Dirichlet
-    at r_o for (0,0)); 'Hp', 'Hm', 'Hz' = 3/(2 dt) I - L_c with Dirichlet wall rows."""
+    at r_o for (0,0)); 'Hp', 'Hm', 'Hz' = 3/(2 dt) I - L_c with Dirichlet wall rows.
+    m, ka: one mode (m, |k|) only (the result then has leading shape (1, 1)); default all."""
     prm = ops.prm
     N, M, K = prm.N_r, prm.M, prm.K
     r = ops.r
     I = np.eye(N)
-    mm = ops.mm[:, None, None, None]
-    ka = (prm.k_z * np.arange(K + 1))[None, :, None, None]
+    ms = np.arange(M + 1) if m is None else np.array([m])
+    kas = np.arange(K + 1) if ka is None else np.array([ka])
+    mm = ops.mm[ms][:, None, None, None]
+    ka = (prm.k_z * kas)[None, :, None, None]
     D1, D2 = ops.D1, ops.D2
     inv_r = (1.0 / r)[:, None]
     inv_r2 = (1.0 / r ** 2)[:, None]
@@ -292,7 +295,8 @@ def mode_matrices(ops):
     P = Lh.copy()
     P[:, :, 0, :] = D1[0]
     P[:, :, -1, :] = D1[-1]
-    P[0, 0, -1, :] = I[-1]
+    if ms[0] == 0 and kas[0] == 0:
+        P[0, 0, -1, :] = I[-1]
     c = 3.0 / (2.0 * prm.dt)
     Lp = Lh - inv_r2 * I - 2.0 * mm * inv_r2 * I
     Lm = Lh - inv_r2 * I + 2.0 * mm * inv_r2 * I

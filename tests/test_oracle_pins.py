@@ -361,6 +361,8 @@ def test_mode_matrices_are_banded_and_match_library_banded_solve():
             rhs[:, m, k + prm.K] = b
             got = O.solve_modes(ops, ops.mats[name], rhs)[:, m, k + prm.K]
             np.testing.assert_allclose(got.real, x, rtol=1e-10, atol=1e-12 * np.abs(x).max())
+            # the single-mode form builds the same matrix
+            assert np.array_equal(O.mode_matrices(ops, m, k)[name][0, 0], A)
 
 
 # ---------------------------------------------------------------- P8 divergence
