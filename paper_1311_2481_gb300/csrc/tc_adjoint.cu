@@ -1022,7 +1022,7 @@ tc_status adj_ready(tc_plan* p, void* ws) {
     TC_CUDA(p, cudaGetDevice(&dev));
     if (dev != p->device) return TC_ERR_STATE;
     if (!ws || reinterpret_cast<uintptr_t>(ws) % 256 != 0) return TC_ERR_ARG;
-    return check_device_ptr(p, ws, "ws");
+    return check_device_ptr(p, ws, "ws", p->ws.total);
 }
 
 #define TC_TRY2(x)                   \
@@ -1042,10 +1042,11 @@ tc_status tc_adjoint_step(tc_plan* plan, const tc_state* fwd, tc_state_bar* bar,
         snprintf(plan->err, sizeof(plan->err), "tc_adjoint_step needs a started forward state (use tc_adjoint_start for the cold start)");
         return TC_ERR_STATE;
     }
-    TC_TRY2(check_device_ptr(plan, fwd->u, "fwd->u"));
-    TC_TRY2(check_device_ptr(plan, bar->u, "bar->u"));
-    TC_TRY2(check_device_ptr(plan, bar->u_prev, "bar->u_prev"));
-    TC_TRY2(check_device_ptr(plan, bar->N_prev, "bar->N_prev"));
+    const size_t vb = 3 * plan->S * sizeof(double2);
+    TC_TRY2(check_device_ptr(plan, fwd->u, "fwd->u", vb));
+    TC_TRY2(check_device_ptr(plan, bar->u, "bar->u", vb));
+    TC_TRY2(check_device_ptr(plan, bar->u_prev, "bar->u_prev", vb));
+    TC_TRY2(check_device_ptr(plan, bar->N_prev, "bar->N_prev", vb));
     if (bar->u == bar->u_prev || bar->u == bar->N_prev || bar->u_prev == bar->N_prev) return TC_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
@@ -1061,11 +1062,12 @@ tc_status tc_adjoint_start(tc_plan* plan, const void* u0, const tc_state_bar* ba
                            void* ws, void* stream) {
     TC_TRY2(adj_ready(plan, ws));
     if (!bar) return TC_ERR_ARG;
-    TC_TRY2(check_device_ptr(plan, u0, "u0"));
-    TC_TRY2(check_device_ptr(plan, u0_bar, "u0_bar"));
-    TC_TRY2(check_device_ptr(plan, bar->u, "bar->u"));
-    TC_TRY2(check_device_ptr(plan, bar->u_prev, "bar->u_prev"));
-    TC_TRY2(check_device_ptr(plan, bar->N_prev, "bar->N_prev"));
+    const size_t vb = 3 * plan->S * sizeof(double2);
+    TC_TRY2(check_device_ptr(plan, u0, "u0", vb));
+    TC_TRY2(check_device_ptr(plan, u0_bar, "u0_bar", vb));
+    TC_TRY2(check_device_ptr(plan, bar->u, "bar->u", vb));
+    TC_TRY2(check_device_ptr(plan, bar->u_prev, "bar->u_prev", vb));
+    TC_TRY2(check_device_ptr(plan, bar->N_prev, "bar->N_prev", vb));
     if (u0_bar == u0 || u0_bar == bar->u_prev || u0_bar == bar->N_prev) return TC_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
@@ -1103,8 +1105,8 @@ tc_status tc_adjoint_start(tc_plan* plan, const void* u0, const tc_state_bar* ba
 tc_status tc_energy_gradient(tc_plan* plan, const void* u, void* g, void* stream) {
     if (!plan) return TC_ERR_ARG;
     if (plan->host_only) return TC_ERR_STATE;
-    TC_TRY2(check_device_ptr(plan, u, "u"));
-    TC_TRY2(check_device_ptr(plan, g, "g"));
+    TC_TRY2(check_device_ptr(plan, u, "u", 3 * plan->S * sizeof(double2)));
+    TC_TRY2(check_device_ptr(plan, g, "g", 3 * plan->S * sizeof(double2)));
     return launch_energy_gradient(plan, static_cast<const double2*>(u), static_cast<double2*>(g),
                                   static_cast<cudaStream_t>(stream));
 }

@@ -29,7 +29,7 @@ tc_status check_ws(tc_plan* p, void* ws) {
         snprintf(p->err, sizeof(p->err), "workspace must be a 256-byte aligned device pointer");
         return TC_ERR_ARG;
     }
-    return check_device_ptr(p, ws, "ws");
+    return check_device_ptr(p, ws, "ws", p->ws.total);
 }
 
 // An update kernel of an earlier step wrote a NaN/Inf into the state (flag in mapped host
@@ -103,8 +103,9 @@ extern "C" {
 
 tc_status tc_nonlinear(tc_plan* plan, const void* u_hat, void* N_hat, void* ws, void* stream) {
     TC_TRY(ready(plan));
-    TC_TRY(check_device_ptr(plan, u_hat, "u_hat"));
-    TC_TRY(check_device_ptr(plan, N_hat, "N_hat"));
+    const size_t vb = 3 * plan->S * sizeof(double2);
+    TC_TRY(check_device_ptr(plan, u_hat, "u_hat", vb));
+    TC_TRY(check_device_ptr(plan, N_hat, "N_hat", vb));
     TC_TRY(check_ws(plan, ws));
     if (u_hat == N_hat) return TC_ERR_ARG;
     return launch_nonlinear(plan, static_cast<const double2*>(u_hat), static_cast<double2*>(N_hat),
@@ -114,8 +115,8 @@ tc_status tc_nonlinear(tc_plan* plan, const void* u_hat, void* N_hat, void* ws, 
 tc_status tc_helmholtz_solve(tc_plan* plan, int which, const void* rhs, void* x, void* ws, void* stream) {
     TC_TRY(ready(plan));
     if (which < TC_P_STAR || which > TC_PHI) return TC_ERR_ARG;
-    TC_TRY(check_device_ptr(plan, rhs, "rhs"));
-    TC_TRY(check_device_ptr(plan, x, "x"));
+    TC_TRY(check_device_ptr(plan, rhs, "rhs", plan->S * sizeof(double2)));
+    TC_TRY(check_device_ptr(plan, x, "x", plan->S * sizeof(double2)));
     TC_TRY(check_ws(plan, ws));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (rhs != x)
@@ -128,10 +129,11 @@ tc_status tc_helmholtz_solve(tc_plan* plan, int which, const void* rhs, void* x,
 tc_status tc_step(tc_plan* plan, tc_state* st, int nsteps, void* ws, void* stream) {
     TC_TRY(ready(plan));
     if (!st || nsteps < 0) return TC_ERR_ARG;
-    TC_TRY(check_device_ptr(plan, st->u, "u"));
-    TC_TRY(check_device_ptr(plan, st->u_prev, "u_prev"));
-    TC_TRY(check_device_ptr(plan, st->N_prev, "N_prev"));
-    TC_TRY(check_device_ptr(plan, st->p, "p"));
+    const size_t vb = 3 * plan->S * sizeof(double2), sb = plan->S * sizeof(double2);
+    TC_TRY(check_device_ptr(plan, st->u, "u", vb));
+    TC_TRY(check_device_ptr(plan, st->u_prev, "u_prev", vb));
+    TC_TRY(check_device_ptr(plan, st->N_prev, "N_prev", vb));
+    TC_TRY(check_device_ptr(plan, st->p, "p", sb));
     TC_TRY(check_ws(plan, ws));
     const void* ptrs[4] = {st->u, st->u_prev, st->N_prev, st->p};
     for (int i = 0; i < 4; ++i)
@@ -181,7 +183,7 @@ tc_status tc_step_host(tc_plan* plan, const tc_state* host_in, tc_state* host_ou
     const size_t vb = 3 * plan->S * sizeof(double2), sb = plan->S * sizeof(double2);
     void* dptr[4] = {dev->u, dev->u_prev, dev->N_prev, dev->p};
     const size_t bytes[4] = {vb, vb, vb, sb};
-    for (int i = 0; i < 4; ++i) TC_TRY(check_device_ptr(plan, dptr[i], "dev state"));
+    for (int i = 0; i < 4; ++i) TC_TRY(check_device_ptr(plan, dptr[i], "dev state", bytes[i]));
     for (int i = 0; i < 4; ++i)
         TC_CUDA(plan, cudaMemcpyAsync(dptr[i], hin[i], bytes[i], cudaMemcpyHostToDevice, s));
     dev->started = host_in->started;
@@ -197,7 +199,7 @@ tc_status tc_step_host(tc_plan* plan, const tc_state* host_in, tc_state* host_ou
 tc_status tc_diagnostics(tc_plan* plan, const void* u, tc_diag* out, void* ws, void* stream) {
     TC_TRY(ready(plan));
     if (!out) return TC_ERR_ARG;
-    TC_TRY(check_device_ptr(plan, u, "u"));
+    TC_TRY(check_device_ptr(plan, u, "u", 3 * plan->S * sizeof(double2)));
     TC_TRY(check_ws(plan, ws));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double* red = reinterpret_cast<double*>(static_cast<char*>(ws) + plan->ws.red);

@@ -72,9 +72,9 @@ extern "C" tc_status tc_nonlinear_noalloc(tc_plan* plan, const void* u_hat, void
         snprintf(plan->err, sizeof(plan->err), "current device %d differs from the plan's device %d", dev, plan->device);
         return TC_ERR_STATE;
     }
-    tc_status st = tc::check_device_ptr(plan, u_hat, "u_hat");
+    tc_status st = tc::check_device_ptr(plan, u_hat, "u_hat", 3 * plan->S * sizeof(double2));
     if (st != TC_OK) return st;
-    st = tc::check_device_ptr(plan, N_hat, "N_hat");
+    st = tc::check_device_ptr(plan, N_hat, "N_hat", 3 * plan->S * sizeof(double2));
     if (st != TC_OK) return st;
     if (u_hat == N_hat) return TC_ERR_ARG;
     void* scratch = nullptr;

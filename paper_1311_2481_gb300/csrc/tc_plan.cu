@@ -7,6 +7,8 @@
 #include <new>
 #include <thread>
 
+#include <cuda.h>
+
 #include "tc_internal.cuh"
 
 namespace tc {
@@ -19,7 +21,31 @@ tc_status cuda_fail(tc_plan* p, cudaError_t e, const char* where) {
     return TC_ERR_CUDA;
 }
 
-tc_status check_device_ptr(tc_plan* p, const void* ptr, const char* name) {
+// The allocation that contains ptr (base, size), from cuMemGetAddressRange fetched through the
+// runtime, so that the library needs no link against the driver library.  False if the query
+// is unavailable or fails.
+static bool alloc_range(const void* ptr, unsigned long long* base, size_t* size) {
+    using Fn = CUresult (*)(CUdeviceptr*, size_t*, CUdeviceptr);
+    static const Fn fn = []() -> Fn {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<Fn>(f);
+    }();
+    if (!fn) return false;
+    CUdeviceptr b = 0;
+    size_t s = 0;
+    if (fn(&b, &s, (CUdeviceptr)(uintptr_t)ptr) != CUDA_SUCCESS) return false;
+    *base = (unsigned long long)b;
+    *size = s;
+    return true;
+}
+
+tc_status check_device_ptr(tc_plan* p, const void* ptr, const char* name, size_t bytes) {
     if (!ptr) {
         snprintf(p->err, sizeof(p->err), "%s is NULL", name);
         return TC_ERR_ARG;
@@ -38,6 +64,16 @@ tc_status check_device_ptr(tc_plan* p, const void* ptr, const char* name) {
     if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
         snprintf(p->err, sizeof(p->err), "%s is not device memory", name);
         return TC_ERR_ARG;
+    }
+    unsigned long long base = 0;
+    size_t size = 0;
+    if (bytes > 0 && alloc_range(ptr, &base, &size)) {
+        const unsigned long long q = (unsigned long long)(uintptr_t)ptr;
+        if (q + bytes > base + size) {
+            snprintf(p->err, sizeof(p->err), "%s: its allocation holds %llu bytes from this pointer, %zu needed", name,
+                     base + size - q, bytes);
+            return TC_ERR_ARG;
+        }
     }
     return TC_OK;
 }

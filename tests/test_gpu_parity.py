@@ -183,6 +183,31 @@ def test_nonfinite_state_is_reported_by_the_next_step(pc_split):
     plan.step_host(st2, hin, hout, 1)               # cleared again
 
 
+def test_undersized_buffers_rejected_before_launch():
+    """Allocations too short for the plan are rejected on the host (the driver's address-range
+    query).  Every call here is tc_step with nsteps = 0 on a started state, which launches
+    nothing even when the arguments pass, so a failing check cannot touch device memory.
+    Large torch tensors sit in allocations rounded up to 2 MiB, so a pointer 2 MiB into one
+    has fewer bytes left than the tensor holds."""
+    import ctypes
+    ops, plan = pair(CFG2)           # a vector field is 13.1 MB, the workspace 0.2 GB
+    lib = tc.load_library()
+    st = tc.State(plan, dev(init(ops)))
+    plan.step(st, 0)
+    assert st.started
+
+    def call(u_ptr, ws_ptr):
+        cs = tc.tc_state(u_ptr, st.u_prev.data_ptr(), st.N_prev.data_ptr(), st.p.data_ptr(), 1)
+        return lib.tc_step(plan.handle, ctypes.byref(cs), 0, ws_ptr, None)
+
+    ws = plan._ws()
+    assert call(st.u.data_ptr(), ws) == tc.TC_OK
+    assert call(st.u.data_ptr() + (2 << 20), ws) == tc.TC_ERR_ARG
+    assert b"allocation holds" in lib.tc_plan_last_error(plan.handle)
+    assert call(st.u.data_ptr(), ctypes.c_void_p(ws.value + (4 << 20))) == tc.TC_ERR_ARG
+    assert call(st.u.data_ptr(), ws) == tc.TC_OK
+
+
 def test_diagnostics_match_oracle():
     ops, plan = pair(CFG1)
     u = O.run(ops, O.cold_state(init(ops)), 3).u
