@@ -19,10 +19,9 @@
  *  - Physical grid for the nonlinear term: P_theta x P_z points per radial node (default
  *    3M x 3K, the 3/2 rule of Sec. 3.1 / Sec. 3.2 step 1).
  *  - Every call validates its arguments on the host before any launch and returns a
- *    tc_status; nothing aborts.  Device pointers must be 16-byte aligned device memory whose
- *    allocation extends at least the array's size past the pointer (TC_ERR_ARG otherwise;
- *    the allocation range comes from the driver, so a sub-allocation of a larger pool block
- *    is checked against the block).  Kernels are enqueued on the caller's stream (cudaStream_t
+ *    tc_status; nothing aborts.  Device pointers must be 16-byte aligned device memory, and
+ *    the array's bytes from the pointer must be mapped without a gap (TC_ERR_ARG otherwise;
+ *    a short buffer followed by another allocation cannot be detected).  Kernels are enqueued on the caller's stream (cudaStream_t
  *    passed as void*; NULL = legacy default stream); calls return before the GPU finishes.
  *    Asynchronous CUDA errors surface as TC_ERR_CUDA on a later call.
  *  - ws is caller-owned device scratch of at least tc_plan_workspace_bytes() bytes, 256-byte

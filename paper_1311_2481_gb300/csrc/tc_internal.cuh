@@ -155,9 +155,9 @@ tc_status cuda_fail(tc_plan* p, cudaError_t e, const char* where);
         if (e_ != cudaSuccess) return tc::cuda_fail(plan, e_, what);   \
     } while (0)
 
-// ptr must be 16-byte aligned device memory; with bytes > 0, the allocation that holds it must
-// extend at least bytes past it (checked through the driver's address-range query when the
-// driver provides it; a sub-allocation of a larger pool block is checked against the block)
+// ptr must be 16-byte aligned device memory; with bytes > 0, the bytes from ptr must be mapped
+// without a gap (checked through the driver's address-range query when the driver provides
+// it; the check cannot tell a short buffer followed by another allocation from a long one)
 tc_status check_device_ptr(tc_plan* p, const void* ptr, const char* name, size_t bytes = 0);
 
 // ------------------------------------------------------------------ tracing

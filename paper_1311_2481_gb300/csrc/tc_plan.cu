@@ -65,14 +65,21 @@ tc_status check_device_ptr(tc_plan* p, const void* ptr, const char* name, size_t
         snprintf(p->err, sizeof(p->err), "%s is not device memory", name);
         return TC_ERR_ARG;
     }
+    // the bytes from ptr must be mapped without a gap: walk the allocations that cover them
+    // (contiguous mappings, as in virtual-memory pools, count as one buffer; a buffer that
+    // runs into a neighbouring allocation cannot be told from one that does not)
     unsigned long long base = 0;
     size_t size = 0;
     if (bytes > 0 && alloc_range(ptr, &base, &size)) {
-        const unsigned long long q = (unsigned long long)(uintptr_t)ptr;
-        if (q + bytes > base + size) {
-            snprintf(p->err, sizeof(p->err), "%s: its allocation holds %llu bytes from this pointer, %zu needed", name,
-                     base + size - q, bytes);
-            return TC_ERR_ARG;
+        const unsigned long long q = (unsigned long long)(uintptr_t)ptr, end = q + bytes;
+        unsigned long long cur = base + size;
+        for (int i = 0; i < 4096 && cur < end; ++i) {
+            if (!alloc_range(reinterpret_cast<const void*>((uintptr_t)cur), &base, &size) || base != cur) {
+                snprintf(p->err, sizeof(p->err), "%s: only %llu of the %zu bytes from this pointer are mapped", name,
+                         cur - q, bytes);
+                return TC_ERR_ARG;
+            }
+            cur = base + size;
         }
     }
     return TC_OK;

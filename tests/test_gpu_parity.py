@@ -183,14 +183,23 @@ def test_nonfinite_state_is_reported_by_the_next_step(pc_split):
     plan.step_host(st2, hin, hout, 1)               # cleared again
 
 
-def test_undersized_buffers_rejected_before_launch():
-    """Allocations too short for the plan are rejected on the host (the driver's address-range
-    query).  Every call here is tc_step with nsteps = 0 on a started state, which launches
-    nothing even when the arguments pass, so a failing check cannot touch device memory.
-    Large torch tensors sit in allocations rounded up to 2 MiB, so a pointer 2 MiB into one
-    has fewer bytes left than the tensor holds."""
+def test_unmapped_buffer_tails_rejected_before_launch():
+    """A buffer whose bytes run past mapped device memory is rejected on the host (the
+    driver's address-range query, walked over contiguous mappings).  Every call here is
+    tc_step with nsteps = 0 on a started state, which launches nothing even when the
+    arguments pass, so the test cannot touch device memory either way.  The bogus workspace
+    starts on the last 256-byte boundary at least 256 bytes before the end of the mapped run
+    that holds the state's u (found with the same driver query), so the 0.2 GB it must hold
+    cross into unmapped memory."""
     import ctypes
-    ops, plan = pair(CFG2)           # a vector field is 13.1 MB, the workspace 0.2 GB
+    try:
+        cuda = ctypes.CDLL("libcuda.so.1")
+    except OSError:
+        pytest.skip("no driver library to locate the end of the mapping")
+    get_range = cuda.cuMemGetAddressRange_v2
+    get_range.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_size_t), ctypes.c_uint64]
+    get_range.restype = ctypes.c_int
+    ops, plan = pair(CFG2)
     lib = tc.load_library()
     st = tc.State(plan, dev(init(ops)))
     plan.step(st, 0)
@@ -200,11 +209,16 @@ def test_undersized_buffers_rejected_before_launch():
         cs = tc.tc_state(u_ptr, st.u_prev.data_ptr(), st.N_prev.data_ptr(), st.p.data_ptr(), 1)
         return lib.tc_step(plan.handle, ctypes.byref(cs), 0, ws_ptr, None)
 
+    base, size = ctypes.c_uint64(0), ctypes.c_size_t(0)
+    end = st.u.data_ptr()
+    for _ in range(100000):   # to the end of the contiguous run of mappings
+        if get_range(ctypes.byref(base), ctypes.byref(size), ctypes.c_uint64(end)) != 0 or base.value > end:
+            break
+        end = base.value + size.value
     ws = plan._ws()
     assert call(st.u.data_ptr(), ws) == tc.TC_OK
-    assert call(st.u.data_ptr() + (2 << 20), ws) == tc.TC_ERR_ARG
-    assert b"allocation holds" in lib.tc_plan_last_error(plan.handle)
-    assert call(st.u.data_ptr(), ctypes.c_void_p(ws.value + (4 << 20))) == tc.TC_ERR_ARG
+    assert call(st.u.data_ptr(), ctypes.c_void_p((end - 256) & ~255)) == tc.TC_ERR_ARG
+    assert b"are mapped" in lib.tc_plan_last_error(plan.handle)
     assert call(st.u.data_ptr(), ws) == tc.TC_OK
 
 
