@@ -118,8 +118,8 @@ typedef struct {
 /* Create a plan: nodes (Eq. nodeDist, paper's M = N_r - 1), FD weights of fd_order + 1 points
  * (Sec. 3.1; shortened centred stencils near the walls, one-sided fd_order/2 + 1 points on
  * the wall rows), twiddles, and the banded LU factors with partial pivoting of the Poisson
- * and three Helmholtz matrices of every mode (m, |k|) (Sec. 3.2, "precomputed at the
- * beginning").  Requires fd_order + 1 <= N_r <= 2048, M >= 1, K >= 1, m_p >= 1, 0 < eta < 1,
+ * and three Helmholtz matrices of every mode (m, |k|), factored once before any step
+ * (Sec. 3.2).  Requires fd_order + 1 <= N_r <= 2048, M >= 1, K >= 1, m_p >= 1, 0 < eta < 1,
  * L_z > 0, dt > 0, fd_order in {2, 4, 6, 8}.  *out receives the plan or NULL on error. */
 tc_status tc_plan_create(tc_plan** out, int N_r, int M, int K, int m_p, double eta,
                          double Re_i, double Re_o, double L_z, double dt, int fd_order);

@@ -79,7 +79,7 @@ def test_wavy_vortex_wave_speed_fp64():
     assert e_ratio > 1e-3, "no saturated wavy mode"
     assert residual <= 1e-6, residual
     assert abs(c / GOLD["c"] - 1) <= 1e-4, (c, steps)
-    # "about 1e-6" at this resolution and time step (Sec. 5.3): within a decade either way
+    # roughly 1e-6 at this resolution and time step (Sec. 5.3): within a decade either way
     assert GOLD["relative_slip_about"] / 10 <= slip <= GOLD["relative_slip_about"] * 10, slip
 
 
