@@ -104,3 +104,22 @@ def test_host_factors_solve_the_mode_systems(lib, N):
                 worst = max(worst, err)
                 assert err <= 1e-11, (which, m, ka, parts, err)
     print("worst", worst)
+
+
+def test_plan_options_validated(lib):
+    """Out-of-range launch options are rejected at plan creation; pc_partitions = 1 leaves
+    the plan without the two-partition form (its host solve then reports TC_ERR_STATE)."""
+    L = 2 * math.pi / 3.16
+    args = (24, 4, 4, 1, 0.5, 50.0, 0.0, L, 1e-3)
+    for kw in (dict(pc_partitions=3), dict(pc_partitions=-1), dict(pc_split=2), dict(theta_variant=4),
+               dict(pipeline=-1), dict(pc_modes=33)):
+        with pytest.raises(tc.TCError) as e:
+            tc.Plan(*args, host_only=True, **kw)
+        assert e.value.status == tc.TC_ERR_ARG, kw
+    b = np.linspace(0.0, 1.0, 24)
+    p2 = tc.Plan(*args, host_only=True)
+    p1 = tc.Plan(*args, host_only=True, pc_partitions=1)
+    assert np.allclose(p2.solve_host(tc.TC_U_Z, 2, 3, b, 2), p1.solve_host(tc.TC_U_Z, 2, 3, b, 1), rtol=1e-12)
+    with pytest.raises(tc.TCError) as e:
+        p1.solve_host(tc.TC_U_Z, 2, 3, b, 2)
+    assert e.value.status == tc.TC_ERR_STATE
