@@ -1,6 +1,8 @@
 // Host plan of libtc: radial nodes (Eq. nodeDist), finite-difference weights (Sec. 3.1,
 // Fornberg's recursion in long double), twiddle tables, and the banded LU factors with partial
-// pivoting of the per-mode Poisson / Helmholtz matrices (Sec. 3.2, precomputed once).
+// pivoting of the per-mode Poisson / Helmholtz matrices (Sec. 3.2, factored once), plus their
+// two-partition form for the fused steps-2-5 kernel; argument checks shared by the entry
+// points.
 #include <algorithm>
 #include <cmath>
 #include <cstring>

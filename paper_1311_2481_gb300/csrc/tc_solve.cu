@@ -1,8 +1,17 @@
 // Linear part of the AB2BD2 step (Sec. 3.2 steps 2-5): right-hand sides, the five banded
 // solves per Fourier mode with precomputed LU factors (forward / backward substitution,
-// O(N_r) per system), and the update.  One thread per (m, k) system; threads of a warp own
-// consecutive k, so every access to a field [r][m][k] or to the factors [j][band][m][|k|]
-// is coalesced.
+// O(N_r) per system), and the update.  Two paths:
+//
+//   k_pc     (N_r up to 192) one block per T consecutive modes, all five solves and their
+//            right-hand sides in shared memory.  Each system is solved in two partitions
+//            (rows [0, N_r/2) and [N_r/2, N_r), each with its own pivoted LU factors, on
+//            separate threads), coupled through an 8 x 8 reduced system and a fix-up; one
+//            real part per thread, consecutive modes on consecutive threads.
+//   split    (larger N_r) one kernel per stage; the solves walk one column per thread in
+//            global memory with the full-system factors.
+//
+// Threads of a warp own consecutive k, so every access to a field [r][m][k] or to the
+// factors [j][band][m][|k|] is coalesced.
 #include <algorithm>
 
 #include "tc_internal.cuh"
