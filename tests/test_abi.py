@@ -74,7 +74,7 @@ def test_host_plan_matches_oracle_nodes_and_weights(lib):
             assert np.abs(D - ref).max() <= 1e-13 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("N", [15, 16, 25, 48])
+@pytest.mark.parametrize("N", [15, 16, 25, 48, 96, 128])
 def test_host_factors_solve_the_mode_systems(lib, N):
     """The stored pivoted banded LU factors of every system (Sec. 3.2: Eq. pressure, Eq. vel,
     Eq. correction) and their two-partition form (the diagonal blocks' own LU factors, the
