@@ -18,8 +18,9 @@ for pseudospectral simulations with application to Taylor–Couette flow"):
 * diagnostics: perturbation energy, torque (Sec. 5.4 quasi-Nusselt number), divergence.
 
 Everything is written from the definitions: transforms are explicit DFT matrices applied
-by matrix products, the five linear systems per Fourier mode are dense matrices solved
-with ``numpy.linalg.solve``.  Angles, nodes and finite-difference weights are computed in
+by matrix products, the five linear systems per Fourier mode are assembled as dense
+matrices and solved by the oracle's own Gaussian elimination with partial pivoting over
+their band (``gauss_banded``).  Angles, nodes and finite-difference weights are computed in
 long double and rounded once to float64.
 
 Readings where the paper is silent (the same readings bind the CUDA path):
@@ -46,10 +47,10 @@ __all__ = [
     "Params", "Operators", "State", "radial_nodes", "fd_weights", "stencil_nodes",
     "derivative_matrices", "build_operators", "to_physical", "to_spectral",
     "physical_fields", "nonlinear", "mode_matrices", "div_h", "grad_h", "vector_laplacian_r",
-    "solve_modes", "advance", "start_up", "step", "run", "couette_state", "perturbation_energy", "torque",
-    "max_divergence", "cold_state", "nonlinear_tangent", "tangent_step", "nonlinear_adjoint",
-    "adjoint_step", "adjoint_advance", "adjoint_start_up", "energy_gradient",
-    "gradient_final_energy", "inner",
+    "gauss_banded", "solve_modes", "advance", "start_up", "step", "run", "couette_state",
+    "perturbation_energy", "torque", "max_divergence", "cold_state", "nonlinear_tangent",
+    "tangent_step", "nonlinear_adjoint", "adjoint_step", "adjoint_advance", "adjoint_start_up",
+    "energy_gradient", "gradient_final_energy", "inner",
 ]
 
 LD = np.longdouble
@@ -310,15 +311,59 @@ def mode_matrices(ops, m=None, ka=None):
     return out
 
 
+def gauss_banded(A, B, kl=4, ku=4):
+    """Solve A x = B by Gaussian elimination with partial pivoting (row interchanges), for
+    a batch of real matrices A[..., N, N] with A[i, j] = 0 unless -kl <= j - i <= ku, and
+    right-hand sides B[..., N, nrhs].  The paper solves each mode's banded system once per
+    step with precomputed LU factors and row interchanges (Sec. 3.2); this is the same
+    elimination done afresh, with B carried along.
+
+    Column c: the pivot is the largest |A[i, c]| over rows i = c..c+kl (the rows below
+    hold zeros there); rows c and p are interchanged; rows c+1..c+kl subtract multiples of
+    row c.  The rows in the active window hold non-zeros only up to column c+kl+ku (row c+kl
+    starts with its band edge there, and the pivot row never reaches further), so the
+    interchange and the elimination touch columns c..c+kl+ku only.  Back substitution then
+    runs over the kl+ku super-diagonals of the triangular result."""
+    A = np.array(A, dtype=np.float64)
+    B = np.array(B, dtype=np.float64)
+    N = A.shape[-1]
+    lead = A.shape[:-2]
+    A = A.reshape((-1, N, N))
+    B = B.reshape((-1, N, B.shape[-1]))
+    ib = np.arange(A.shape[0])
+    for c in range(N):
+        last = min(c + kl, N - 1)
+        hi = min(c + kl + ku, N - 1) + 1
+        p = c + np.argmax(np.abs(A[:, c:last + 1, c]), axis=1)
+        row_c, row_p = A[ib, c, c:hi].copy(), A[ib, p, c:hi].copy()
+        A[ib, c, c:hi], A[ib, p, c:hi] = row_p, row_c
+        b_c, b_p = B[ib, c].copy(), B[ib, p].copy()
+        B[ib, c], B[ib, p] = b_p, b_c
+        f = A[:, c + 1:last + 1, c] / A[:, c, c][:, None]
+        A[:, c + 1:last + 1, c + 1:hi] -= f[:, :, None] * A[:, c, None, c + 1:hi]
+        A[:, c + 1:last + 1, c] = 0.0
+        B[:, c + 1:last + 1] -= f[:, :, None] * B[:, c, None, :]
+    x = np.zeros_like(B)
+    for i in range(N - 1, -1, -1):
+        hi = min(i + kl + ku, N - 1) + 1
+        s = B[:, i] - np.einsum("bj,bjr->br", A[:, i, i + 1:hi], x[:, i + 1:hi])
+        x[:, i] = s / A[:, i, i][:, None]
+    return x.reshape(lead + (N, x.shape[-1]))
+
+
 def solve_modes(ops, A, rhs):
-    """Solve A[m, |k|] x[:, m, k] = rhs[:, m, k] for every stored mode (dense solves)."""
+    """Solve A[m, |k|] x[:, m, k] = rhs[:, m, k] for every stored mode: the matrices are
+    real, so the real and imaginary parts of the right-hand sides of k = +|k| and -|k| are
+    four right-hand sides of one elimination (`gauss_banded`)."""
     K = ops.prm.K
-    kabs = np.abs(np.arange(-K, K + 1))
-    Af = A[:, kabs]                                        # (M+1, 2K+1, N, N)
     b = np.moveaxis(rhs, 0, -1)                            # (M+1, 2K+1, N)
-    br = np.stack([b.real, b.imag], axis=-1)               # (M+1, 2K+1, N, 2)
-    x = np.linalg.solve(Af, br)
-    return np.moveaxis(x[..., 0] + 1j * x[..., 1], -1, 0)
+    bp, bm = b[:, K:], b[:, K::-1]                         # k = +|k| and k = -|k|
+    B = np.stack([bp.real, bp.imag, bm.real, bm.imag], axis=-1)
+    x = gauss_banded(A, B)                                 # (M+1, K+1, N, 4)
+    out = np.empty(b.shape, np.complex128)
+    out[:, K:] = x[..., 0] + 1j * x[..., 1]
+    out[:, K::-1] = x[..., 2] + 1j * x[..., 3]
+    return np.moveaxis(out, -1, 0)
 
 
 def div_h(ops, v):

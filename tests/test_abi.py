@@ -79,7 +79,8 @@ def test_host_factors_solve_the_mode_systems(lib, N):
     """The stored pivoted banded LU factors of every system (Sec. 3.2: Eq. pressure, Eq. vel,
     Eq. correction) and their two-partition form (the diagonal blocks' own LU factors, the
     spikes and the inverse 8 x 8 reduced matrix) solve the oracle's mode matrices: against
-    the dense solve, on random right-hand sides.  N_r = 15 has no two-partition form."""
+    the oracle's own banded elimination, on random right-hand sides.  N_r = 15 has no
+    two-partition form."""
     import oracle as O
     L = 2 * math.pi / 3.16
     cfg = (N, 6, 8, 1, 0.5, 300.0, 0.0, L, 1e-3)
@@ -92,7 +93,10 @@ def test_host_factors_solve_the_mode_systems(lib, N):
         for (m, ka) in ((0, 0), (0, 3), (1, 0), (6, 8), (3, 5)):
             A = ops.mats[name][m, ka]
             b = rng.standard_normal(N)
-            ref = np.linalg.solve(A, b)
+            ref = O.gauss_banded(A, b[:, None])[:, 0]
+            # two backward-stable pivoted eliminations in different rounding order differ by
+            # at most about eps * cond(A); the bound asked for is 5e-4 of that
+            tol = 1e-13 + 1e-19 * np.linalg.cond(A)
             for parts in (1, 2):
                 if parts == 2 and N < 16:
                     with pytest.raises(tc.TCError) as e:
@@ -101,9 +105,9 @@ def test_host_factors_solve_the_mode_systems(lib, N):
                     continue
                 x = p.solve_host(which, m, ka, b, parts)
                 err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
-                worst = max(worst, err)
-                assert err <= 1e-11, (which, m, ka, parts, err)
-    print("worst", worst)
+                worst = max(worst, err / tol)
+                assert err <= tol, (which, m, ka, parts, err, tol)
+    print("worst fraction of the bound", worst)
 
 
 def test_plan_options_validated(lib):

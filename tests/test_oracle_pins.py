@@ -195,8 +195,9 @@ def test_dealiased_product_equals_truncated_convolution():
 
 # ---------------------------------------------------------------- P5 nonlinear term
 
-def test_nonlinear_manufactured_against_analytic_derivatives():
-    prm = _prm(N_r=16, M=8, K=8)
+@pytest.mark.parametrize("m_p", [1, 6])
+def test_nonlinear_manufactured_against_analytic_derivatives(m_p):
+    prm = _prm(N_r=16, M=8, K=8, m_p=m_p)
     ops = O.Operators(prm)
     r = ops.r
     M, K = prm.M, prm.K
@@ -302,43 +303,87 @@ def test_couette_steady_state_pressure_and_torque():
 
 # ---------------------------------------------------------------- P7 solves
 
-def test_helmholtz_and_poisson_manufactured():
-    m, k = 3, 2
-    errs = {"Hp": [], "P": [], "P00": []}
+def _solve_one_mode(ops, name, m, k, f):
+    """The oracle's solve of system `name` for the single mode (m, k), through solve_modes
+    (a right-hand side that is zero on every other mode)."""
+    prm = ops.prm
+    rhs = np.zeros(prm.shape(), np.complex128)
+    rhs[:, m, k + prm.K] = f
+    x = O.solve_modes(ops, ops.mats[name], rhs)
+    others = np.ones(prm.shape(), bool)
+    others[:, m, k + prm.K] = False
+    assert not np.any(x[others])
+    return x[:, m, k + prm.K]
+
+
+@pytest.mark.parametrize("m_p", [1, 6])
+def test_helmholtz_and_poisson_manufactured(m_p):
+    """Each of the four matrices of Sec. 3.2 against its own analytic operator
+    (Eq. modalNSdecoup: L_pm = Lap_h - 1/r^2 -+ 2 m m_p / r^2, L_z = Lap_h with
+    Lap_h = d_rr + d_r / r - (m m_p)^2 / r^2 - (k k_z)^2), on a mode with m > 0, for k = +2
+    and k = -2, with FD-order convergence in N_r."""
+    m = 3
+    errs = {}
     for N in (32, 64):
-        prm = _prm(N_r=N, M=4, K=4, dt=1e-3)
+        prm = _prm(N_r=N, M=4, K=4, dt=1e-3, m_p=m_p)
         ops = O.Operators(prm)
-        mats = ops.mats
         r = ops.r
         x = r - prm.r_i
-        mmp, kkz = m * prm.m_p, k * prm.k_z
-        # Helmholtz (u_+ operator): u = sin(pi x) e^r, Dirichlet zero at both walls
-        u = np.sin(np.pi * x) * np.exp(r)
-        du = (np.pi * np.cos(np.pi * x) + np.sin(np.pi * x)) * np.exp(r)
-        d2u = (2 * np.pi * np.cos(np.pi * x) + (1 - np.pi ** 2) * np.sin(np.pi * x)) * np.exp(r)
-        lap = d2u + du / r - mmp ** 2 * u / r ** 2 - kkz ** 2 * u
-        Lp = lap - u / r ** 2 - 2 * mmp * u / r ** 2
-        f = 1.5 / prm.dt * u - Lp
-        f[0] = f[-1] = 0.0
-        sol = np.linalg.solve(mats["Hp"][m, k], f)
-        errs["Hp"].append(np.abs(sol - u).max() / np.abs(u).max())
-        # Poisson with Neumann rows: phi = cos(pi x) (zero slope at both walls)
-        phi = np.cos(np.pi * x)
-        lap = -np.pi ** 2 * phi - np.pi * np.sin(np.pi * x) / r - mmp ** 2 * phi / r ** 2 - kkz ** 2 * phi
-        f = lap.copy()
-        f[0] = f[-1] = 0.0
-        sol = np.linalg.solve(mats["P"][m, k], f)
-        errs["P"].append(np.abs(sol - phi).max())
+        mmp = m * prm.m_p
+        for k in (2, -2):
+            kkz = k * prm.k_z
+            # Helmholtz: u = sin(pi x) e^r (complex amplitude), Dirichlet zero at both walls
+            u = np.sin(np.pi * x) * np.exp(r) * (1.0 + 0.5j)
+            du = (np.pi * np.cos(np.pi * x) + np.sin(np.pi * x)) * np.exp(r) * (1.0 + 0.5j)
+            d2u = (2 * np.pi * np.cos(np.pi * x) + (1 - np.pi ** 2) * np.sin(np.pi * x)) * np.exp(r) * (1.0 + 0.5j)
+            lap = d2u + du / r - mmp ** 2 * u / r ** 2 - kkz ** 2 * u
+            ops_c = {"Hp": lap - u / r ** 2 - 2 * mmp * u / r ** 2,
+                     "Hm": lap - u / r ** 2 + 2 * mmp * u / r ** 2,
+                     "Hz": lap}
+            for name, Lu in ops_c.items():
+                f = 1.5 / prm.dt * u - Lu
+                f[0] = f[-1] = 0.0
+                sol = _solve_one_mode(ops, name, m, k, f)
+                errs.setdefault((name, k), []).append(np.abs(sol - u).max() / np.abs(u).max())
+            # Poisson with Neumann rows: phi = cos(pi x) (zero slope at both walls)
+            phi = np.cos(np.pi * x) * (0.5 - 1.0j)
+            lap = (-np.pi ** 2 * np.cos(np.pi * x) - np.pi * np.sin(np.pi * x) / r) * (0.5 - 1.0j) \
+                - mmp ** 2 * phi / r ** 2 - kkz ** 2 * phi
+            f = lap.copy()
+            f[0] = f[-1] = 0.0
+            sol = _solve_one_mode(ops, "P", m, k, f)
+            errs.setdefault(("P", k), []).append(np.abs(sol - phi).max())
         # (0,0): Neumann at r_i, Dirichlet at r_o: phi = cos(pi x) + 1
         phi = np.cos(np.pi * x) + 1.0
         f = -np.pi ** 2 * np.cos(np.pi * x) - np.pi * np.sin(np.pi * x) / r
         f[0] = 0.0
         f[-1] = 0.0
-        sol = np.linalg.solve(mats["P"][0, 0], f)
-        errs["P00"].append(np.abs(sol - phi).max())
+        sol = _solve_one_mode(ops, "P", 0, 0, f)
+        errs.setdefault(("P00", 0), []).append(np.abs(sol - phi).max())
     for key, e in errs.items():
         assert e[1] < 1e-7, (key, e)
         assert math.log(e[0] / e[1], 2) > 5.0, (key, e)
+
+
+def test_gauss_banded_against_library_dense_solve():
+    """The oracle's banded elimination against LAPACK's dense LU (numpy.linalg.solve) on
+    random matrices with kl = ku = 4, half of them with a zero diagonal so that every column
+    needs a row interchange, and with a band that reaches the last row."""
+    rng = np.random.default_rng(8)
+    for N in (5, 9, 20, 33):
+        A = np.zeros((6, N, N))
+        for b in range(6):
+            for i in range(N):
+                lo, hi = max(0, i - 4), min(N, i + 5)
+                A[b, i, lo:hi] = rng.standard_normal(hi - lo)
+            if b % 2 == 0:
+                A[b][np.arange(N), np.arange(N)] = 0.0
+        B = rng.standard_normal((6, N, 3))
+        x = O.gauss_banded(A, B)
+        ref = np.linalg.solve(A, B)
+        for b in range(6):
+            cond = np.linalg.cond(A[b])
+            assert np.abs(x[b] - ref[b]).max() <= 1e-14 * cond * np.abs(ref[b]).max(), (N, b)
 
 
 def test_mode_matrices_are_banded_and_match_library_banded_solve():
@@ -367,10 +412,11 @@ def test_mode_matrices_are_banded_and_match_library_banded_solve():
 
 # ---------------------------------------------------------------- P8 divergence
 
-def test_projection_reduces_divergence_and_converges():
+@pytest.mark.parametrize("m_p", [1, 6])
+def test_projection_reduces_divergence_and_converges(m_p):
     vals = {}
     for N in (48, 96):
-        prm = _prm(N_r=N, M=4, K=4)
+        prm = _prm(N_r=N, M=4, K=4, m_p=m_p)
         ops = O.Operators(prm)
         u0 = I.initial_state(ops.r, prm.M, prm.K, prm.m_p, prm.L_z, prm.eta, prm.Re_i,
                              prm.Re_o, kind="box", amp=1e-3)
@@ -379,6 +425,26 @@ def test_projection_reduces_divergence_and_converges():
         vals[N] = (O.max_divergence(ops, parts["u_star"]), O.max_divergence(ops, st.u))
     assert vals[96][1] < 0.05 * vals[96][0]
     assert vals[48][1] / vals[96][1] > 8.0, vals
+
+
+@pytest.mark.parametrize("m_p", [1, 6])
+def test_divergence_of_analytic_solenoidal_field(m_p):
+    """The seeded perturbation is the curl of an analytic vector potential (its curl is
+    written out per mode, independently of the oracle), so its divergence vanishes; the
+    oracle's div_h of it is FD truncation error only.  On the rows with the full 9-point
+    stencil (4 <= j <= N_r - 5) that error falls at the stencil order (2^8 per halving)."""
+    errs = []
+    for N in (48, 96):
+        prm = _prm(N_r=N, M=4, K=4, m_p=m_p)
+        ops = O.Operators(prm)
+        base = I.base_state(ops.r, prm.M, prm.K, prm.eta, prm.Re_i, prm.Re_o)
+        u0 = I.initial_state(ops.r, prm.M, prm.K, prm.m_p, prm.L_z, prm.eta, prm.Re_i,
+                             prm.Re_o, kind="box", amp=1e-1)
+        scale = np.abs(ops.mm[None, :, None] * (u0 - base)[0]).max() / prm.r_i
+        d = np.abs(O.div_h(ops, u0))[4:N - 4]
+        errs.append(d.max() / scale)
+    assert errs[1] < 1e-12, errs
+    assert errs[0] / errs[1] > 100.0, errs
 
 
 # ---------------------------------------------------------------- P10 onset
