@@ -323,32 +323,40 @@ def gauss_banded(A, B, kl=4, ku=4):
     row c.  The rows in the active window hold non-zeros only up to column c+kl+ku (row c+kl
     starts with its band edge there, and the pivot row never reaches further), so the
     interchange and the elimination touch columns c..c+kl+ku only.  Back substitution then
-    runs over the kl+ku super-diagonals of the triangular result."""
-    A = np.array(A, dtype=np.float64)
-    B = np.array(B, dtype=np.float64)
+    runs over the kl+ku super-diagonals of the triangular result.  The batch is held as the
+    last axis so that each step is one array operation over all systems; only the band of
+    the input is copied into that layout (an entry outside it raises ValueError)."""
     N = A.shape[-1]
     lead = A.shape[:-2]
-    A = A.reshape((-1, N, N))
-    B = B.reshape((-1, N, B.shape[-1]))
-    ib = np.arange(A.shape[0])
+    A_in = np.asarray(A, dtype=np.float64).reshape((-1, N, N))
+    ii, jj = np.nonzero(np.abs(np.subtract.outer(np.arange(N), np.arange(N))) <= max(kl, ku))
+    band = (jj - ii >= -kl) & (jj - ii <= ku)
+    ii, jj = ii[band], jj[band]
+    A = np.zeros((N, N, A_in.shape[0]))                                 # (N, N, nb)
+    A[ii, jj] = A_in[:, ii, jj].T
+    if np.count_nonzero(A) != np.count_nonzero(A_in):
+        raise ValueError("matrix has entries outside the band")
+    B = np.moveaxis(np.array(B, dtype=np.float64).reshape((-1, N, B.shape[-1])), 0, -1).copy()
+    ib = np.arange(A.shape[-1])
     for c in range(N):
         last = min(c + kl, N - 1)
         hi = min(c + kl + ku, N - 1) + 1
-        p = c + np.argmax(np.abs(A[:, c:last + 1, c]), axis=1)
-        row_c, row_p = A[ib, c, c:hi].copy(), A[ib, p, c:hi].copy()
-        A[ib, c, c:hi], A[ib, p, c:hi] = row_p, row_c
-        b_c, b_p = B[ib, c].copy(), B[ib, p].copy()
-        B[ib, c], B[ib, p] = b_p, b_c
-        f = A[:, c + 1:last + 1, c] / A[:, c, c][:, None]
-        A[:, c + 1:last + 1, c + 1:hi] -= f[:, :, None] * A[:, c, None, c + 1:hi]
-        A[:, c + 1:last + 1, c] = 0.0
-        B[:, c + 1:last + 1] -= f[:, :, None] * B[:, c, None, :]
+        p = c + np.argmax(np.abs(A[c:last + 1, c]), axis=0)          # pivot row per system
+        cols = np.arange(c, hi)[:, None]
+        row_c, row_p = A[c, c:hi].copy(), A[p, cols, ib].copy()
+        A[c, c:hi], A[p, cols, ib] = row_p, row_c
+        b_c, b_p = B[c].copy(), B[p, :, ib].T.copy()
+        B[c], B[p, :, ib] = b_p, b_c.T
+        f = A[c + 1:last + 1, c] / A[c, c]                           # (rows, nb)
+        A[c + 1:last + 1, c + 1:hi] -= f[:, None] * A[c, None, c + 1:hi]
+        A[c + 1:last + 1, c] = 0.0
+        B[c + 1:last + 1] -= f[:, None] * B[c, None]
     x = np.zeros_like(B)
     for i in range(N - 1, -1, -1):
         hi = min(i + kl + ku, N - 1) + 1
-        s = B[:, i] - np.einsum("bj,bjr->br", A[:, i, i + 1:hi], x[:, i + 1:hi])
-        x[:, i] = s / A[:, i, i][:, None]
-    return x.reshape(lead + (N, x.shape[-1]))
+        s = B[i] - np.sum(A[i, i + 1:hi, None] * x[i + 1:hi], axis=0)
+        x[i] = s / A[i, i]
+    return np.moveaxis(x, -1, 0).reshape(lead + (N, x.shape[1]))
 
 
 def solve_modes(ops, A, rhs):

@@ -30,11 +30,11 @@ MUTATIONS = {
     "L_- coupling sign": ("Lm = Lh - inv_r2 * I + 2.0 * mm * inv_r2 * I", "Lm = Lh - inv_r2 * I - 2.0 * mm * inv_r2 * I"),
     "m_p dropped from m m_p": ("self.mm = prm.m_p * m.astype(np.float64)", "self.mm = m.astype(np.float64)"),
     "H_z takes the 1/r^2 term": ('("Hz", Lh)):', '("Hz", Lh - inv_r2 * I)):'),
-    "no row interchange": ("p = c + np.argmax(np.abs(A[:, c:last + 1, c]), axis=1)",
-                           "p = np.full(A.shape[0], c)"),
+    "no row interchange": ("p = c + np.argmax(np.abs(A[c:last + 1, c]), axis=0)",
+                           "p = np.full(A.shape[-1], c)"),
     "back substitution over ku super-diagonals": (
-        "        hi = min(i + kl + ku, N - 1) + 1\n        s = B[:, i]",
-        "        hi = min(i + ku, N - 1) + 1\n        s = B[:, i]"),
+        "        hi = min(i + kl + ku, N - 1) + 1\n        s = B[i]",
+        "        hi = min(i + ku, N - 1) + 1\n        s = B[i]"),
     "k = -|k| solved with the k = +|k| right-hand side": ("bp, bm = b[:, K:], b[:, K::-1]", "bp, bm = b[:, K:], b[:, K:]"),
     "adjoint transposed solve": ("return solve_modes(ops, np.swapaxes(A, -1, -2), rhs)", "return solve_modes(ops, A, rhs)"),
     "adjoint of theta-derivative": ("+ np.conj(im) * _to_physical_T(ops, bar[(\"t\", c)])", "+ im * _to_physical_T(ops, bar[(\"t\", c)])"),

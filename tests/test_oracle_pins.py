@@ -384,6 +384,10 @@ def test_gauss_banded_against_library_dense_solve():
         for b in range(6):
             cond = np.linalg.cond(A[b])
             assert np.abs(x[b] - ref[b]).max() <= 1e-14 * cond * np.abs(ref[b]).max(), (N, b)
+    A = np.eye(9)
+    A[0, 5] = 1.0
+    with pytest.raises(ValueError):
+        O.gauss_banded(A, np.ones((9, 1)))
 
 
 def test_mode_matrices_are_banded_and_match_library_banded_solve():
