@@ -82,16 +82,27 @@ typedef struct {
     int theta_variant; /* launch tuning of the mixed form's length-specialised theta pass:
                          0 or 1: radices <= 16, two blocks per SM; 2 and 3: radices <= 8 with
                          half the z values per block, four / three blocks per SM */
-    int pipeline;     /* tc_step overlap: the modes are cut into this many chunks of m, and
-                         the forward z pass, steps 2-5 and the next inverse z pass of different
-                         chunks run concurrently on two internal streams (forked from and
-                         joined back to the caller's stream).  0 or 1: sequential */
     int pc_partitions; /* the fused steps-2-5 kernel solves each banded system (Sec. 3.2) as
                          two partitions, rows [0, N_r/2) and [N_r/2, N_r), each with its own
                          pivoted LU factors, coupled through an 8 x 8 reduced system (SPIKE
                          form; the two halves run on separate lanes).  0 or 2: when N_r >= 16
                          and the fused kernel runs; 1: one pivoted banded LU per system */
 } tc_options;
+
+/* Keys of tc_plan_set: one per field of tc_options, with the same meaning and range. */
+typedef enum {
+    TC_SET_ALPHA = 0,
+    TC_SET_P_THETA = 1,
+    TC_SET_P_Z = 2,
+    TC_SET_PRECISION = 3,
+    TC_SET_HOST_ONLY = 4,
+    TC_SET_THETA_ZT = 5,
+    TC_SET_PC_MODES = 6,
+    TC_SET_NO_ADJOINT = 7,
+    TC_SET_PC_SPLIT = 8,
+    TC_SET_THETA_VARIANT = 9,
+    TC_SET_PC_PARTITIONS = 10
+} tc_plan_key;
 
 /* Step state (Sec. 3.2): u = u^i, u_prev = u^{i-1}, N_prev = N^{i-1} (vector fields), p = p^i
  * (scalar field), started = 0 for a cold state whose history is built by the first step. */
@@ -105,14 +116,18 @@ typedef struct {
 
 /* Diagnostics of a velocity field (Sec. 5): perturbation energy about analytic Couette flow
  * J = 1/2 sum_j w_j r_j sum_{m,k} c_m |u - U|^2 (trapezoid weights w_j, c_0 = 1, c_m = 2),
- * torque T = r^3 d_r(u_theta^{00} / r) at r_i and r_o (Sec. 5.4 quasi-Nusselt number =
- * T / T_laminar), max |div_h u| over interior rows, and whether every entry is finite. */
+ * torque T = r^3 d_r(u_theta^{00} / r) at r_i and r_o with the wall FD rows, the
+ * quasi-Nusselt number Nu_omega = T / T_lam of Sec. 5.4 at each wall (T_lam = -2 C2 is the
+ * torque of circular Couette flow U = C1 r + C2 / r, Sec. 5.1; NaN when C2 = 0), max
+ * |div_h u| over interior rows, and whether every entry is finite. */
 typedef struct {
     double energy;
     double torque_inner;
     double torque_outer;
     double max_div;
     int finite;
+    double nu_omega_inner;
+    double nu_omega_outer;
 } tc_diag;
 
 /* Create a plan: nodes (Eq. nodeDist, paper's M = N_r - 1), FD weights of fd_order + 1 points
@@ -127,6 +142,17 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
                             double Re_i, double Re_o, double L_z, double dt, int fd_order,
                             const tc_options* opt);
 void tc_plan_destroy(tc_plan* plan);
+/* Change one plan setting after creation and before the plan's first compute call: the
+ * physical grid (P_theta, P_z of the 3/2 rule, Sec. 3.1), the node clustering alpha of
+ * Eq. nodeDist, the precision form, or a launch option (key: tc_plan_key; an integer setting
+ * takes an integral value).  Everything that depends on the setting (nodes, FD weights,
+ * twiddles, the LU factors of Sec. 3.2, the workspace size) is rebuilt as tc_plan_create_ex
+ * would build it; on any error the plan is left unchanged.  The workspace size may change:
+ * query tc_plan_workspace_bytes again.  TC_ERR_ARG for an unknown key or a value out of
+ * range; TC_ERR_STATE once the plan has run a compute call (tc_nonlinear, tc_step, ...) or
+ * when the current device is not the plan's.  While the replacement is built, the device
+ * holds the constants of both (the factors dominate: 13 doubles per row, mode and set). */
+tc_status tc_plan_set(tc_plan* plan, int key, double value);
 
 /* Device scratch needed by every call that takes ws. */
 tc_status tc_plan_workspace_bytes(const tc_plan* plan, size_t* bytes);
@@ -223,6 +249,14 @@ tc_status tc_energy_gradient(tc_plan* plan, const void* u, void* g, void* stream
  * address once (cudaGetSymbolAddress); make it before any stream capture.  All calls share
  * the array: calls whose GPU work overlaps (other streams, unordered plans) race on it. */
 tc_status tc_nonlinear_noalloc(tc_plan* plan, const void* u_hat, void* N_hat, void* stream);
+
+/* FP64 FMA rate probe (no counterpart in the paper: it measures the FP64 pipe that bounds the
+ * FP64 kernels).  Enqueues one kernel of `blocks` x `threads` threads (threads a multiple of 32,
+ * at most 1024), each running 8 independent chains of `iters` dependent FMAs, and writes one
+ * double per thread into the device buffer `sink` (blocks * threads doubles, caller-owned;
+ * only its type is checked).  *flops (host, may be NULL) receives the flops the launch
+ * executes (2 per FMA); time the launch with events on `stream`. */
+tc_status tc_probe_fp64_fma(int blocks, int threads, int iters, void* sink, void* stream, double* flops);
 
 /* Tracing (no counterpart in the paper beyond its per-phase timings, Table efficiency):
  * when enabled, every kernel the plan launches is bracketed by CUDA events recorded on the

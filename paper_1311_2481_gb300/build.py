@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libtc.so")
-SOURCES = ["tc_plan.cu", "tc_fft.cu", "tc_mixed.cu", "tc_theta_s.cu", "tc_solve.cu", "tc_adjoint.cu", "tc_api.cu", "tc_noalloc.cu"]
+SOURCES = ["tc_plan.cu", "tc_fft.cu", "tc_mixed.cu", "tc_theta_s.cu", "tc_solve.cu", "tc_adjoint.cu", "tc_api.cu", "tc_noalloc.cu", "tc_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -21,6 +21,7 @@ tc_status ready(tc_plan* p) {
         snprintf(p->err, sizeof(p->err), "current device %d differs from the plan's device %d", dev, p->device);
         return TC_ERR_STATE;
     }
+    p->used = true;
     return TC_OK;
 }
 
@@ -49,53 +50,6 @@ tc_status take_nonfinite(tc_plan* p) {
         tc_status s_ = (x);             \
         if (s_ != TC_OK) return s_;     \
     } while (0)
-
-// nsteps steps with the modes cut into C chunks of m.  Per step, on the caller's stream s: the
-// theta pass, then the forward z pass of chunks C-1 .. 0 (event Z[c] after each).  On aux[0]:
-// steps 2-5 of chunk c after Z[c] (event P[c]).  On aux[1]: the next step's pre-theta work
-// (FP32 split, inverse z pass) of chunk c after P[c]; the next theta pass waits for all of it.
-// Chunk 0 holds m = 0, whose (0,0) column every forward z pass reads for the mean flow, so
-// it is solved last.  Every kernel of a chunk touches only the modes of its m-range, except
-// that read of the (0,0) column.
-tc_status step_overlapped(tc_plan* plan, double2* u, double2* up, double2* Np, double2* p, double2* Nc,
-                          char* w, int nsteps, cudaStream_t s) {
-    const int C = plan->pipeline;
-    const int M1 = plan->M + 1;
-    cudaStream_t a0 = plan->aux[0], a1 = plan->aux[1];
-    cudaEvent_t fork = plan->pev[0], join = plan->pev[1], pre_done = plan->pev[2];
-    cudaEvent_t* Z = &plan->pev[3];
-    cudaEvent_t* P = &plan->pev[3 + C];
-    auto lo = [&](int c) { return (int)((long long)c * M1 / C); };
-    TC_CUDA(plan, cudaEventRecord(fork, s));
-    TC_CUDA(plan, cudaStreamWaitEvent(a0, fork, 0));
-    TC_CUDA(plan, cudaStreamWaitEvent(a1, fork, 0));
-    TC_TRY(launch_nl_pre(plan, u, w, s, 0, M1));
-    for (int i = 0; i < nsteps; ++i) {
-        TC_TRY(launch_nl_theta(plan, w, s));
-        for (int c = C - 1; c >= 0; --c) {
-            TC_TRY(launch_nl_post(plan, u, Nc, w, s, lo(c), lo(c + 1)));
-            TC_CUDA(plan, cudaEventRecord(Z[c], s));
-        }
-        for (int c = C - 1; c >= 0; --c) {
-            TC_CUDA(plan, cudaStreamWaitEvent(a0, Z[c], 0));
-            TC_TRY(launch_advance(plan, u, up, Nc, Np, p, nullptr, w, true, a0, lo(c), lo(c + 1)));
-            TC_CUDA(plan, cudaEventRecord(P[c], a0));
-        }
-        if (i + 1 < nsteps) {
-            for (int c = C - 1; c >= 0; --c) {
-                TC_CUDA(plan, cudaStreamWaitEvent(a1, P[c], 0));
-                TC_TRY(launch_nl_pre(plan, u, w, a1, lo(c), lo(c + 1)));
-            }
-            TC_CUDA(plan, cudaEventRecord(pre_done, a1));
-            TC_CUDA(plan, cudaStreamWaitEvent(s, pre_done, 0));
-        }
-    }
-    TC_CUDA(plan, cudaEventRecord(join, a0));
-    TC_CUDA(plan, cudaStreamWaitEvent(s, join, 0));
-    TC_CUDA(plan, cudaEventRecord(pre_done, a1));
-    TC_CUDA(plan, cudaStreamWaitEvent(s, pre_done, 0));
-    return TC_OK;
-}
 
 }  // namespace
 
@@ -157,7 +111,6 @@ tc_status tc_step(tc_plan* plan, tc_state* st, int nsteps, void* ws, void* strea
         TC_TRY(launch_nonlinear(plan, up, Np, w, s));
         st->started = 1;
     }
-    if (plan->pipeline > 1 && nsteps > 0) return step_overlapped(plan, u, up, Np, p, Nc, w, nsteps, s);
     for (int i = 0; i < nsteps; ++i) {
         TC_TRY(launch_nonlinear(plan, u, Nc, w, s));
         TC_TRY(launch_advance(plan, u, up, Nc, Np, p, nullptr, w, true, s));
@@ -234,6 +187,12 @@ tc_status tc_diagnostics(tc_plan* plan, const void* u, tc_diag* out, void* ws, v
     };
     out->torque_inner = torque_at(0);
     out->torque_outer = torque_at(N - 1);
+    // laminar torque r^3 d_r(U / r) = -2 C2 of U = C1 r + C2 / r (Sec. 5.1)
+    const double eta = plan->eta;
+    const double C2 = eta * (plan->Re_i - eta * plan->Re_o) / ((1.0 - eta) * (1.0 - eta * eta));
+    const double T_lam = -2.0 * C2;
+    out->nu_omega_inner = T_lam != 0.0 ? out->torque_inner / T_lam : NAN;
+    out->nu_omega_outer = T_lam != 0.0 ? out->torque_outer / T_lam : NAN;
     return out->finite ? TC_OK : TC_ERR_NONFINITE;
 }
 

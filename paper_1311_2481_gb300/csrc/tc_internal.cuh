@@ -14,8 +14,8 @@ namespace tc {
 constexpr int kMaxRadix = 16;   // passes of a mixed-radix 2^a 3^b transform
 constexpr int kStencil = 9;     // padded FD stencil width (fd_order <= 8)
 constexpr int kBands = 13;      // stored doubles per LU row: 4 L multipliers, 1/U_jj, 8 U
-constexpr int kKl = 4;
-constexpr int kPCDepth = 4;              // rows of LU factors in flight per substitution chain          // sub/super diagonals of the mode matrices (fd_order/2 <= 4)
+constexpr int kKl = 4;          // sub/super diagonals of the mode matrices (fd_order/2 <= 4)
+constexpr int kPCDepth = 4;     // rows of LU factors in flight per substitution chain
 
 // Factor sets of Sec. 3.2: Poisson (p*, phi), Helmholtz for u_+, u_-, u_z.
 enum FactorSet { kSetP = 0, kSetHp = 1, kSetHm = 2, kSetHz = 3, kNumSets = 4 };
@@ -53,6 +53,8 @@ struct tc_plan {
     double eta, Re_i, Re_o, L_z, dt, alpha, k_z, r_i, r_o;
     bool host_only;
     bool adjoint;    // workspace holds the adjoint regions
+    tc_options opt;  // the options the plan was built with (tc_plan_set rebuilds from them)
+    bool used = false;  // a compute call has run (tc_plan_set is refused from then on)
     // derived sizes
     size_t S;        // complex entries of a scalar spectral field
     size_t Hfield;   // complex entries of one z-pass line set: N_r (M+1) P_z
@@ -62,9 +64,6 @@ struct tc_plan {
     int zt, zt32;                  // z values per theta-pass block (FP64 / FP32 lines)
     int theta_zt_forced;           // tc_options.theta_zt (> 0: generic transform kernels)
     int theta_variant;             // tc_options.theta_variant (launch shape of the FP32 streamed theta pass)
-    int pipeline;                  // m-chunks of the overlapped step (1: sequential)
-    cudaStream_t aux[2] = {nullptr, nullptr};   // solve and pre-theta streams of the overlapped step
-    std::vector<cudaEvent_t> pev;               // its events: fork, join, pre-done, then Z[c], P[c]
     int pc_modes;                  // modes per block of the fused steps-2-5 kernel (0: auto)
     int num_sms = 152;             // multiprocessors of the plan's device
     int thr_zinv, thr_theta, thr_zfwd;  // block sizes of the FP64 transform kernels

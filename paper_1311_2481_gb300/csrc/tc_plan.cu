@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <thread>
+#include <utility>
 
 #include <cuda.h>
 
@@ -426,14 +427,6 @@ static tc_status upload(tc_plan* p) {
     TC_CUDA(p, put((void**)&p->d_tw_z32, f.data(), f.size() * sizeof(float)));
     f.assign(p->tw_t.begin(), p->tw_t.end());
     TC_CUDA(p, put((void**)&p->d_tw_t32, f.data(), f.size() * sizeof(float)));
-    if (p->pipeline > 1) {
-        for (int i = 0; i < 2; ++i) TC_CUDA(p, cudaStreamCreateWithFlags(&p->aux[i], cudaStreamNonBlocking));
-        for (int i = 0; i < 3 + 2 * p->pipeline; ++i) {
-            cudaEvent_t e;
-            TC_CUDA(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-            p->pev.push_back(e);
-        }
-    }
     return TC_OK;
 }
 
@@ -468,14 +461,6 @@ void prof_end(tc_plan* p, int slot, cudaStream_t s) {
 static void free_device(tc_plan* p) {
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     p->prof_ev.clear();
-    for (cudaEvent_t e : p->pev) cudaEventDestroy(e);
-    p->pev.clear();
-    for (cudaStream_t& q : p->aux)
-        if (q) {
-            cudaStreamDestroy(q);
-            q = nullptr;
-        }
-
     void* ptrs[] = {p->d_r, p->d_ir, p->d_w1, p->d_w1f, p->d_w2, p->d_col0, p->d_d1t_row, p->d_d1t_w, p->d_fac, p->d_piv,
                     p->d_fac2, p->d_piv2, p->d_spk, p->d_rinv, p->d_tw_z, p->d_tw_t, p->d_tw_z32, p->d_tw_t32};
     for (void* q : ptrs)
@@ -538,6 +523,7 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     p->r_i = eta / (1.0 - eta);
     p->r_o = 1.0 / (1.0 - eta);
     p->host_only = o.host_only != 0;
+    p->opt = o;
     p->rad_z = rz;
     p->rad_t = rt;
     p->S = (size_t)N_r * (M + 1) * (2 * K + 1);
@@ -626,12 +612,11 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     p->pc_modes = o.pc_modes;
     p->theta_zt_forced = o.theta_zt;
     p->theta_variant = o.theta_variant;
-    p->pipeline = o.pipeline == 0 ? 1 : std::min(o.pipeline, std::min(16, M + 1));
     p->thr_zinv = choose_threads(rz, p->zinv_lines, 0);
     p->thr_theta = choose_threads(rt, 6 * p->zt, p->zt + (p->zt + 1) / 2);
     p->thr_zfwd = choose_threads(rz, p->zfwd_lines, 0);
     if (o.theta_zt < 0 || o.theta_zt > 64 || o.pc_modes < 0 || o.pc_modes > 32 || o.pc_split < -1 || o.pc_split > 1 ||
-        o.theta_variant < 0 || o.theta_variant > 3 || o.pipeline < 0 || o.pc_partitions < 0 || o.pc_partitions > 2) {
+        o.theta_variant < 0 || o.theta_variant > 3 || o.pc_partitions < 0 || o.pc_partitions > 2) {
         delete p;
         return TC_ERR_ARG;
     }
@@ -704,6 +689,57 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
 tc_status tc_plan_create(tc_plan** out, int N_r, int M, int K, int m_p, double eta, double Re_i,
                          double Re_o, double L_z, double dt, int fd_order) {
     return tc_plan_create_ex(out, N_r, M, K, m_p, eta, Re_i, Re_o, L_z, dt, fd_order, nullptr);
+}
+
+tc_status tc_plan_set(tc_plan* plan, int key, double value) {
+    if (!plan) return TC_ERR_ARG;
+    if (plan->used) {
+        snprintf(plan->err, sizeof(plan->err), "tc_plan_set after the plan's first compute call");
+        return TC_ERR_STATE;
+    }
+    if (!plan->host_only) {
+        int dev = -1;
+        TC_CUDA(plan, cudaGetDevice(&dev));
+        if (dev != plan->device) {
+            snprintf(plan->err, sizeof(plan->err), "tc_plan_set: current device %d is not the plan's device %d",
+                     dev, plan->device);
+            return TC_ERR_STATE;
+        }
+    }
+    tc_options o = plan->opt;
+    if (key == TC_SET_ALPHA) {
+        if (!std::isfinite(value)) return TC_ERR_ARG;
+        o.alpha = value;
+    } else {
+        // every other setting is an integer
+        if (!(value >= -1e9 && value <= 1e9) || value != std::floor(value)) return TC_ERR_ARG;
+        const int v = (int)value;
+        switch (key) {
+            case TC_SET_P_THETA: o.P_theta = v; break;
+            case TC_SET_P_Z: o.P_z = v; break;
+            case TC_SET_PRECISION: o.precision = v; break;
+            case TC_SET_HOST_ONLY: o.host_only = v; break;
+            case TC_SET_THETA_ZT: o.theta_zt = v; break;
+            case TC_SET_PC_MODES: o.pc_modes = v; break;
+            case TC_SET_NO_ADJOINT: o.no_adjoint = v; break;
+            case TC_SET_PC_SPLIT: o.pc_split = v; break;
+            case TC_SET_THETA_VARIANT: o.theta_variant = v; break;
+            case TC_SET_PC_PARTITIONS: o.pc_partitions = v; break;
+            default: return TC_ERR_ARG;
+        }
+    }
+    // build the replacement completely before touching the plan, so an error leaves it as it was
+    tc_plan* np = nullptr;
+    tc_status st = tc_plan_create_ex(&np, plan->N_r, plan->M, plan->K, plan->m_p, plan->eta, plan->Re_i,
+                                     plan->Re_o, plan->L_z, plan->dt, plan->fd_order, &o);
+    if (st != TC_OK) {
+        snprintf(plan->err, sizeof(plan->err), "tc_plan_set: rebuilding the plan failed (status %d)", (int)st);
+        return st;
+    }
+    free_device(plan);
+    *plan = std::move(*np);   // device pointers move with it; np's destructor frees host vectors only
+    delete np;
+    return TC_OK;
 }
 
 void tc_plan_destroy(tc_plan* plan) {

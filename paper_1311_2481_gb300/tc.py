@@ -16,14 +16,16 @@ LIB_PATH = os.path.join(HERE, "_lib", "libtc.so")
 TC_OK, TC_ERR_ARG, TC_ERR_CUDA, TC_ERR_OOM, TC_ERR_NONFINITE, TC_ERR_TIMEOUT, TC_ERR_STATE = range(7)
 TC_P_STAR, TC_U_PLUS, TC_U_MINUS, TC_U_Z, TC_PHI = range(5)
 TC_FP64, TC_MIXED = 0, 1
+(TC_SET_ALPHA, TC_SET_P_THETA, TC_SET_P_Z, TC_SET_PRECISION, TC_SET_HOST_ONLY, TC_SET_THETA_ZT,
+ TC_SET_PC_MODES, TC_SET_NO_ADJOINT, TC_SET_PC_SPLIT, TC_SET_THETA_VARIANT, TC_SET_PC_PARTITIONS) = range(11)
 
 # every symbol include/tc.h declares, in declaration order
 SYMBOLS = [
-    "tc_plan_create", "tc_plan_create_ex", "tc_plan_destroy", "tc_plan_workspace_bytes",
+    "tc_plan_create", "tc_plan_create_ex", "tc_plan_destroy", "tc_plan_set", "tc_plan_workspace_bytes",
     "tc_plan_nodes", "tc_plan_fd_weights", "tc_plan_solve_host", "tc_plan_last_error", "tc_status_string",
     "tc_nonlinear", "tc_helmholtz_solve", "tc_step", "tc_step_host", "tc_diagnostics",
     "tc_adjoint_step", "tc_adjoint_start", "tc_energy_gradient",
-    "tc_nonlinear_noalloc", "tc_profile_enable", "tc_profile_read",
+    "tc_nonlinear_noalloc", "tc_probe_fp64_fma", "tc_profile_enable", "tc_profile_read",
 ]
 
 
@@ -31,8 +33,7 @@ class tc_options(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("P_theta", ctypes.c_int), ("P_z", ctypes.c_int),
                 ("precision", ctypes.c_int), ("host_only", ctypes.c_int), ("theta_zt", ctypes.c_int),
                 ("pc_modes", ctypes.c_int), ("no_adjoint", ctypes.c_int), ("pc_split", ctypes.c_int),
-                ("theta_variant", ctypes.c_int), ("pipeline", ctypes.c_int),
-                ("pc_partitions", ctypes.c_int)]
+                ("theta_variant", ctypes.c_int), ("pc_partitions", ctypes.c_int)]
 
 
 class tc_state(ctypes.Structure):
@@ -47,7 +48,8 @@ class tc_state_bar(ctypes.Structure):
 class tc_diag(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("torque_inner", ctypes.c_double),
                 ("torque_outer", ctypes.c_double), ("max_div", ctypes.c_double),
-                ("finite", ctypes.c_int)]
+                ("finite", ctypes.c_int), ("nu_omega_inner", ctypes.c_double),
+                ("nu_omega_outer", ctypes.c_double)]
 
 
 class TCError(RuntimeError):
@@ -73,6 +75,7 @@ def load_library(path: str = LIB_PATH):
         "tc_plan_create": (I, [ctypes.POINTER(P), I, I, I, I, D, D, D, D, D, I]),
         "tc_plan_create_ex": (I, [ctypes.POINTER(P), I, I, I, I, D, D, D, D, D, I, ctypes.POINTER(tc_options)]),
         "tc_plan_destroy": (None, [P]),
+        "tc_plan_set": (I, [P, I, D]),
         "tc_plan_workspace_bytes": (I, [P, ctypes.POINTER(S)]),
         "tc_plan_nodes": (I, [P, ctypes.POINTER(D)]),
         "tc_plan_fd_weights": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(I)]),
@@ -89,6 +92,7 @@ def load_library(path: str = LIB_PATH):
         "tc_adjoint_start": (I, [P, P, ctypes.POINTER(tc_state_bar), P, P, P]),
         "tc_energy_gradient": (I, [P, P, P, P]),
         "tc_nonlinear_noalloc": (I, [P, P, P, P]),
+        "tc_probe_fp64_fma": (I, [I, I, I, P, P, ctypes.POINTER(D)]),
         "tc_profile_enable": (I, [P, I]),
         "tc_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(D)]),
@@ -134,6 +138,10 @@ def tc_plan_destroy(h):
     load_library().tc_plan_destroy(h)
 
 
+def tc_plan_set(h, key, value):
+    _check(load_library().tc_plan_set(h, key, float(value)), h)
+
+
 def tc_plan_workspace_bytes(h):
     n = ctypes.c_size_t()
     _check(load_library().tc_plan_workspace_bytes(h, ctypes.byref(n)), h)
@@ -167,6 +175,29 @@ def tc_diagnostics(h, u_ptr, ws_ptr, stream_ptr):
 
 # ------------------------------------------------------------------ torch convenience layer
 
+def fp64_fma_rate(blocks=None, threads=256, iters=20000, reps=5):
+    """Measured FP64 FMA rate of the current device (tc_probe_fp64_fma): flop/s of the best
+    of `reps` launches, timed with CUDA events on the current stream."""
+    torch = _torch()
+    if blocks is None:
+        blocks = 8 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    fl = ctypes.c_double()
+    best = None
+    for i in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _check(load_library().tc_probe_fp64_fma(blocks, threads, iters, ctypes.c_void_p(sink.data_ptr()),
+                                                ctypes.c_void_p(stream.cuda_stream), ctypes.byref(fl)))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i:   # the first launch warms up
+            rate = fl.value / (e0.elapsed_time(e1) / 1e3)
+            best = rate if best is None else max(best, rate)
+    return best
+
+
 def _torch():
     import torch
     return torch
@@ -191,11 +222,9 @@ class Plan:
 
     def __init__(self, N_r, M, K, m_p, eta, Re_i, Re_o, L_z, dt, fd_order=8, alpha=0.5,
                  P_theta=0, P_z=0, precision=TC_FP64, host_only=False, device=None, theta_zt=0,
-                 pc_modes=0, no_adjoint=False, pc_split=0, theta_variant=0, pipeline=0,
-                 pc_partitions=0):
+                 pc_modes=0, no_adjoint=False, pc_split=0, theta_variant=0, pc_partitions=0):
         opt = tc_options(alpha if alpha != 0.0 else -1.0, P_theta, P_z, precision, int(host_only),
-                         theta_zt, pc_modes, int(no_adjoint), pc_split, theta_variant, pipeline,
-                         pc_partitions)
+                         theta_zt, pc_modes, int(no_adjoint), pc_split, theta_variant, pc_partitions)
         self.N_r, self.M, self.K = N_r, M, K
         self.handle = None
         torch = _torch()
@@ -206,10 +235,26 @@ class Plan:
             torch.cuda.set_device(dev)
             self.device = dev
         self.handle = tc_plan_create(N_r, M, K, m_p, eta, Re_i, Re_o, L_z, dt, fd_order, opt)
+        self.host_only = bool(host_only)
+        self.ws = None
+        self._alloc_ws()
+
+    def _alloc_ws(self):
         self.ws_bytes = tc_plan_workspace_bytes(self.handle)
         self.ws = None
-        if not host_only:
-            self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        if not self.host_only:
+            self.ws = _torch().empty(self.ws_bytes + 256, dtype=_torch().uint8, device=self.device)
+
+    def set(self, key, value):
+        """tc_plan_set (before the plan's first compute call); the workspace is sized anew."""
+        self.ws = None
+        tc_plan_set(self.handle, key, value)
+        if key == TC_SET_HOST_ONLY:
+            self.host_only = bool(value)
+            if not self.host_only:
+                torch = _torch()
+                self.device = torch.device("cuda", torch.cuda.current_device())
+        self._alloc_ws()
 
     # shapes
     def vector_shape(self):

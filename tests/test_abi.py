@@ -116,7 +116,7 @@ def test_plan_options_validated(lib):
     L = 2 * math.pi / 3.16
     args = (24, 4, 4, 1, 0.5, 50.0, 0.0, L, 1e-3)
     for kw in (dict(pc_partitions=3), dict(pc_partitions=-1), dict(pc_split=2), dict(theta_variant=4),
-               dict(pipeline=-1), dict(pc_modes=33)):
+               dict(pc_modes=33)):
         with pytest.raises(tc.TCError) as e:
             tc.Plan(*args, host_only=True, **kw)
         assert e.value.status == tc.TC_ERR_ARG, kw
@@ -127,3 +127,27 @@ def test_plan_options_validated(lib):
     with pytest.raises(tc.TCError) as e:
         p1.solve_host(tc.TC_U_Z, 2, 3, b, 2)
     assert e.value.status == tc.TC_ERR_STATE
+
+
+def test_plan_set_on_host_plan(lib):
+    """tc_plan_set rebuilds what depends on the setting (here the nodes of Eq. nodeDist and the
+    factors), rejects unknown keys and out-of-range values without changing the plan, and a
+    rebuilt plan equals one created with the setting."""
+    L = 2 * math.pi / 3.16
+    args = (24, 4, 4, 1, 0.5, 50.0, 0.0, L, 1e-3)
+    a = tc.Plan(*args, host_only=True)
+    b = tc.Plan(*args, host_only=True, alpha=0.9)
+    r0 = a.nodes()
+    a.set(tc.TC_SET_ALPHA, 0.9)
+    assert np.array_equal(a.nodes(), b.nodes()) and not np.array_equal(a.nodes(), r0)
+    rhs = np.linspace(-1.0, 2.0, 24)
+    assert np.array_equal(a.solve_host(tc.TC_U_PLUS, 2, 3, rhs), b.solve_host(tc.TC_U_PLUS, 2, 3, rhs))
+    for key, value in ((99, 1.0), (tc.TC_SET_P_THETA, 7.0), (tc.TC_SET_P_THETA, 12.5),
+                       (tc.TC_SET_PRECISION, 5.0), (tc.TC_SET_ALPHA, 2.0), (tc.TC_SET_PC_SPLIT, 3.0)):
+        with pytest.raises(tc.TCError) as e:
+            a.set(key, value)
+        assert e.value.status == tc.TC_ERR_ARG, (key, value)
+    assert np.array_equal(a.nodes(), b.nodes())
+    ws0 = a.ws_bytes
+    a.set(tc.TC_SET_NO_ADJOINT, 1)
+    assert a.ws_bytes < ws0

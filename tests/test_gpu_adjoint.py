@@ -1,7 +1,9 @@
-"""Adjoint of the CUDA step (through the C ABI) against the oracle's adjoint, dot-product
-tests against central differences of the CUDA step itself (exact for the quadratic step up
-to rounding), and the gradient of the final perturbation energy against central finite
-differences (h = 1e-7, 8 directions, <= 1e-6) and against the oracle."""
+"""Adjoint of the CUDA step (through the C ABI) against the oracle's adjoint; dot-product
+tests to 1e-12 against the CUDA step's own tangent (exact central differences of the
+quadratic step) and against the oracle's tangent-linear step; the gradient of the final
+perturbation energy against central finite differences (h = 1e-7, 8 directions, <= 1e-6)
+at the 20-step parity size and at the adjoint workload (N_r = 96, 200 steps, checkpoint
+every 20), and against the oracle."""
 import math
 
 import numpy as np
@@ -23,6 +25,9 @@ B.build()
 LZ = 2 * math.pi / 3.16
 CFG1 = dict(N_r=32, M=8, K=16, m_p=1, eta=0.5, Re_i=50.0, Re_o=0.0, L_z=LZ, dt=1e-3)
 SMALL = dict(N_r=12, M=3, K=4, m_p=1, eta=0.5, Re_i=50.0, Re_o=0.0, L_z=LZ, dt=1e-3)
+# adjoint workload: N_r = 96, m = -32..32, k = -64..64, Re_i = 2000, at the stated dt 5e-4
+# halved until 200 FP64 steps stay bounded (5e-4 / 64)
+CFG3 = dict(N_r=96, M=32, K=64, m_p=1, eta=0.5, Re_i=2000.0, Re_o=0.0, L_z=LZ, dt=5e-4 / 64)
 
 
 def dev(a):
@@ -43,12 +48,12 @@ def _inner(a, b):
     return float(np.real(np.vdot(a, b)))
 
 
-def setup(cfg, amp=1e-2):
+def setup(cfg, amp=1e-2, seed=42):
     ops = O.Operators(O.Params(**cfg))
     plan = tc.Plan(**cfg)
     prm = ops.prm
     u0 = I.initial_state(ops.r, prm.M, prm.K, prm.m_p, prm.L_z, prm.eta, prm.Re_i, prm.Re_o,
-                         kind="box", amp=amp, mbox=min(4, prm.M), kbox=min(4, prm.K))
+                         kind="box", amp=amp, mbox=min(4, prm.M), kbox=min(4, prm.K), seed=seed)
     return ops, plan, u0
 
 
@@ -125,29 +130,49 @@ def test_adjoint_start_matches_oracle():
     assert rel(got, ref) <= 1e-11
 
 
-def test_dot_product_against_gpu_central_differences():
-    """<ybar, dF(s)[x]> = <F^T ybar, x>; F is quadratic so the central difference of the CUDA
-    step with h = 1e-2 gives dF(s)[x] up to rounding."""
-    ops, plan, u0 = setup(CFG1)
-    st_o = O.step(ops, O.cold_state(u0))
-    sh = (3,) + ops.prm.shape()
-    x = [I.random_spectral(sh, seed=s) for s in (31, 32, 33)]
-    y = [I.random_spectral(sh, seed=s) for s in (34, 35, 36)]
-    h = 1e-2
+def _gpu_tangent(plan, st_o, x):
+    """dF(s)[x] of the CUDA step F at the started state s: F is quadratic in (u, u_prev,
+    N_prev) (N(u) is its only nonlinear part; p is not fed back) and its wall values cancel,
+    so (F(s + x) - F(s - x)) / 2 equals dF(s)[x] exactly up to rounding, for any size of x."""
     outs = []
     for sg in (1.0, -1.0):
-        st = tc.State(plan, dev(st_o.u + sg * h * x[0]))
-        st.u_prev.copy_(dev(st_o.u_prev + sg * h * x[1]))
-        st.N_prev.copy_(dev(st_o.N_prev + sg * h * x[2]))
+        st = tc.State(plan, dev(st_o.u + sg * x[0]))
+        st.u_prev.copy_(dev(st_o.u_prev + sg * x[1]))
+        st.N_prev.copy_(dev(st_o.N_prev + sg * x[2]))
         st.started = True
         plan.step(st, 1)
         outs.append([host(st.u), host(st.u_prev), host(st.N_prev)])
-    tl = [(a - b) / (2 * h) for a, b in zip(*outs)]
-    lhs = sum(_inner(a, b) for a, b in zip(y, tl))
+    return [(a - b) / 2.0 for a, b in zip(*outs)]
+
+
+@pytest.mark.parametrize("cfg", [CFG1, "CFG3"])
+def test_dot_product_tests_to_1e_12(cfg):
+    """<ybar, dF(s)[x]> = <F^T ybar, x> to 1e-12 relative, with the CUDA adjoint on the
+    right and, on the left, (a) the CUDA step's own tangent (exact central difference of the
+    quadratic step, directions scaled to the state's norm so that no term is lost to
+    cancellation) and (b) the oracle's tangent-linear step.  Run at the 20-step parity size and
+    at the adjoint workload's size (N_r = 96, m = -32..32, k = -64..64, Re_i = 2000)."""
+    if cfg == "CFG3":
+        cfg = CFG3
+        ops, plan, u0 = setup(cfg, amp=1e-4)
+    else:
+        ops, plan, u0 = setup(cfg)
+    st_o = O.step(ops, O.cold_state(u0))
+    sh = (3,) + ops.prm.shape()
+    fields = (st_o.u, st_o.u_prev, st_o.N_prev)
+    x = [I.random_spectral(sh, seed=s) for s in (31, 32, 33)]
+    x = [v * (np.linalg.norm(f) / np.linalg.norm(v)) for v, f in zip(x, fields)]
+    y = [I.random_spectral(sh, seed=s) for s in (34, 35, 36)]
     bar = tc.StateBar(*[dev(v) for v in y])
     plan.adjoint_step(gpu_state(plan, st_o), bar)
     rhs = sum(_inner(host(a), b) for a, b in zip((bar.u, bar.u_prev, bar.N_prev), x))
-    assert abs(lhs - rhs) <= 1e-10 * abs(lhs), (lhs, rhs)
+    tl_gpu = _gpu_tangent(plan, st_o, x)
+    lhs_gpu = sum(_inner(a, b) for a, b in zip(y, tl_gpu))
+    tl_o = O.tangent_step(ops, st_o, *x)
+    lhs_o = sum(_inner(a, b) for a, b in zip(y, tl_o))
+    print("dot products", lhs_gpu, lhs_o, rhs, abs(lhs_gpu / rhs - 1), abs(lhs_o / rhs - 1))
+    assert abs(lhs_gpu - rhs) <= 1e-12 * abs(rhs), (lhs_gpu, rhs)
+    assert abs(lhs_o - rhs) <= 1e-12 * abs(rhs), (lhs_o, rhs)
 
 
 def test_energy_gradient_kernel_matches_oracle():
@@ -186,6 +211,42 @@ def test_final_energy_gradient_fd_and_oracle():
         fd = (Jp - Jm) / (2 * h)
         ad = _inner(g, d)
         assert abs(fd - ad) <= 1e-6 * abs(fd), (fd, ad)
+
+
+def test_final_energy_gradient_fd_at_adjoint_workload():
+    """The adjoint workload as stated: N_r = 96, m = -32..32, k = -64..64, Re_i = 2000,
+    200 steps with a checkpoint every 20, J = final perturbation energy, seeded initial
+    perturbation of amplitude 1e-4 (seed 42).  The gradient from the checkpointed adjoint
+    against central differences with h = 1e-7 on 8 random directions, <= 1e-6.  Each
+    direction is scaled to the norm of the initial state, so h is a relative step: the state
+    carries the Couette flow at Re_i = 2000 against a perturbation of 0.2 RMS, and a step
+    1e-7 of the perturbation alone would be resolved only to the rounding of the total
+    field (1e-12 of J, i.e. 1e-5 of the difference)."""
+    ops, plan, u0 = setup(CFG3, amp=1e-4, seed=42)
+    n, C = 200, 20
+    u = dev(u0)
+    x = u.clone().requires_grad_(True)
+    J = A.final_energy(x, plan, n, checkpoint=C)
+    J.backward()
+    g = host(x.grad)
+    assert np.isfinite(J.item()) and np.all(np.isfinite(g))
+    rng = np.random.default_rng(7)
+    h = 1e-7
+    worst = 0.0
+    for _ in range(8):
+        d = I.random_spectral((3,) + ops.prm.shape(), seed=int(rng.integers(1 << 30)), hermitian_K=ops.prm.K)
+        d[:, 0] = 0.0
+        d[:, -1] = 0.0
+        d *= np.linalg.norm(u0) / np.linalg.norm(d)
+        dd = dev(d)
+        with torch.no_grad():
+            Jp = A.final_energy(u + h * dd, plan, n, checkpoint=n).item()
+            Jm = A.final_energy(u - h * dd, plan, n, checkpoint=n).item()
+        fd = (Jp - Jm) / (2 * h)
+        ad = _inner(g, d)
+        worst = max(worst, abs(fd - ad) / abs(fd))
+    print("FD vs adjoint, worst relative difference over 8 directions:", worst)
+    assert worst <= 1e-6, worst
 
 
 def _oracle_power_iteration(ops, u_base, delta0, nsteps, energy, iters):

@@ -103,3 +103,42 @@ def test_solves_sampled_modes_at_N_r_256():
             ref = x_ri[:, 0] + 1j * x_ri[:, 1]
             assert rel(got, ref) <= tol, (name, m, k, rel(got, ref))
         del x
+
+
+# the paper's SMALL timing grid (n_r, n_theta, n_z) = (32, 384, 640) as bench.py times it:
+# m = -192..192, k = -320..320 on P_theta x P_z = 576 x 972 (972 = 2^2 3^5 >= 3K + 1, so the
+# z passes take the runtime-length radix kernels; 576 = 2^6 3^2 the runtime theta kernel)
+CFG_SMALL = dict(N_r=32, M=192, K=320, m_p=1, eta=0.5, Re_i=1e3, Re_o=0.0, L_z=LZ, dt=5e-4,
+                 P_theta=576, P_z=972)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_nonlinear_sampled_rows_at_paper_small_grid(precision):
+    """N(u) at the SMALL grid on sampled rows (a wall row, the first interior row, a middle
+    row) against the oracle evaluated on those rows: FP64 <= 1e-12; the mixed form within
+    2e-6 of the row's N(u') plus FP64 rounding of its N, as at the other sizes."""
+    cfg = CFG_SMALL
+    ops = O.Operators(O.Params(**cfg))
+    u = I.initial_state(ops.r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"], cfg["Re_o"],
+                        kind="broadband", amp=0.01, seed=42)
+    prec = tc.TC_MIXED if precision == "mixed" else tc.TC_FP64
+    plan = tc.Plan(**cfg, precision=prec, no_adjoint=True)
+    rows = [0, 1, 16]
+    N = plan.nonlinear(torch.from_numpy(u).cuda())
+    got = N[:, rows].cpu().numpy()
+    del N, plan
+    torch.cuda.empty_cache()
+    ref = O.nonlinear(ops, u, rows=rows)
+    if precision == "fp64":
+        for i, j in enumerate(rows):
+            assert rel(got[:, i], ref[:, i]) <= 1e-12, (j, rel(got[:, i], ref[:, i]))
+        return
+    K = cfg["K"]
+    U = np.imag(u[0, :, 0, K] - u[1, :, 0, K]) / 2
+    u[0, :, 0, K] -= 1j * U
+    u[1, :, 0, K] += 1j * U
+    ref_pert = O.nonlinear(ops, u, rows=rows)
+    for i, j in enumerate(rows):
+        err = np.linalg.norm(got[:, i] - ref[:, i])
+        bound = 2e-6 * np.linalg.norm(ref_pert[:, i]) + 1e-13 * np.linalg.norm(ref[:, i])
+        assert err <= bound, (j, err, np.linalg.norm(ref_pert[:, i]), np.linalg.norm(ref[:, i]))

@@ -369,33 +369,29 @@ def test_mixed_twenty_steps_track_fp64():
     assert rel(got, ref.u) <= 1e-8
 
 
-# ------------------------------------------------------------------ overlapped step
-@pytest.mark.parametrize("precision,split", [(tc.TC_FP64, 0), (tc.TC_FP64, 1), (tc.TC_MIXED, 0)])
-@pytest.mark.parametrize("chunks", [2, 3, 5])
-def test_overlapped_step_is_bit_identical(precision, split, chunks):
-    """tc_step with the modes cut into m-chunks on internal streams gives the same state as
-    the sequential step, bit for bit: every kernel computes the same values per element."""
-    cfg = dict(N_r=24, M=12, K=16, m_p=1, eta=0.5, Re_i=100.0, Re_o=0.0, L_z=LZ, dt=1e-4)
+# ------------------------------------------------------------------ tc_plan_set
+@pytest.mark.parametrize("key,value,kw", [(tc.TC_SET_PRECISION, tc.TC_MIXED, dict(precision=tc.TC_MIXED)),
+                                          (tc.TC_SET_PC_SPLIT, 1, dict(pc_split=1)),
+                                          (tc.TC_SET_ALPHA, 0.7, dict(alpha=0.7)),
+                                          (tc.TC_SET_P_Z, 36, dict(P_z=36))])
+def test_plan_set_gives_the_created_plan(key, value, kw):
+    """A setting changed by tc_plan_set before the first compute call gives the same steps,
+    bit for bit, as a plan created with that setting; after a compute call it is refused."""
+    cfg = dict(N_r=24, M=8, K=12, m_p=1, eta=0.5, Re_i=100.0, Re_o=0.0, L_z=LZ, dt=1e-4)
     ops = O.Operators(O.Params(**cfg))
     u0 = init(ops, kind="broadband", amp=1e-2, seed=9)
     out = []
-    for pipe in (1, chunks):
-        plan = tc.Plan(**cfg, precision=precision, pc_split=split, pipeline=pipe)
+    for plan in (tc.Plan(**cfg, **kw), tc.Plan(**cfg)):
+        if len(out):
+            plan.set(key, value)
         st = tc.State(plan, dev(u0))
-        plan.step(st, 6)
+        plan.step(st, 4)
         out.append([host(getattr(st, k)) for k in ("u", "u_prev", "N_prev", "p")])
+        with pytest.raises(tc.TCError) as e:
+            plan.set(key, value)
+        assert e.value.status == tc.TC_ERR_STATE
     for a, b in zip(*out):
         assert np.array_equal(a, b)
-
-
-def test_overlapped_twenty_steps_match_oracle():
-    ops = O.Operators(O.Params(**CFG1))
-    u0 = init(ops)
-    ref = O.run(ops, O.cold_state(u0), 20)
-    plan = tc.Plan(**CFG1, pipeline=3)
-    st = tc.State(plan, dev(u0))
-    plan.step(st, 20)
-    assert rel(host(st.u), ref.u) <= 1e-10
 
 
 @pytest.mark.parametrize("T", [4, 16])

@@ -1,5 +1,7 @@
-"""End-to-end physics check of the CUDA step against a number the paper prints: the wave speed
-of wavy Taylor vortices (Sec. 5.2, tests/golden/wavy_vortex_wave_speed.json).
+"""End-to-end physics checks of the CUDA step against what the paper prints: the wave speed
+of wavy Taylor vortices (Sec. 5.2, tests/golden/wavy_vortex_wave_speed.json), the slip they
+leave at the inner wall at the largest time step, and how that slip falls with the time step
+(Sec. 5.3).
 
 The paper's resolution (n_r, n_theta, n_z) = (32, 32, 32) is (M, 2N+1, 2L+1) in its notation
 (Sec. 3.1), i.e. N_r = 32 nodes and modes |m| <= 16 (m_p = k_theta = 6), |k| <= 16 here.  The
@@ -30,9 +32,21 @@ B.build()
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "wavy_vortex_wave_speed.json")))
 
 
-def wave_speed_run(precision, max_steps=200_000, chunk=20_000, span=500):
+def inner_wall_slip(u, M, K, Re_i):
+    """Tangential slip at the inner wall (Sec. 5.3): the correction u = u* - grad phi leaves
+    (u_theta - Re_i, u_z) != 0 there; RMS over the wall, relative to Re_i, by Parseval on the
+    stored coefficients (mean of f^2 = sum_k |f_0k|^2 + 2 sum_{m>0,k} |f_mk|^2)."""
+    w = u[:, 0].cpu().numpy()                     # [c][m][k] at r = r_i
+    ut = (w[0] - w[1]) / 2j
+    ut[0, K] -= Re_i
+    cm = np.full((M + 1, 1), 2.0)
+    cm[0] = 1.0
+    return float(np.sqrt(np.sum(cm * (np.abs(ut) ** 2 + np.abs(w[2]) ** 2))) / Re_i)
+
+
+def wave_speed_run(precision, N_r=32, max_steps=200_000, chunk=20_000, span=500):
     eta, Re_i, m_p, L_z, dt = GOLD["eta"], GOLD["Re_i"], GOLD["k_theta"], GOLD["Gamma"], GOLD["dt"]
-    N_r, M, K = 32, 16, 16
+    M, K = 16, 16
     plan = tc.Plan(N_r, M, K, m_p, eta, Re_i, GOLD["Re_o"], L_z, dt, precision=precision, no_adjoint=True)
     r = plan.nodes()
     Om_i = Re_i / (eta / (1.0 - eta))
@@ -61,87 +75,82 @@ def wave_speed_run(precision, max_steps=200_000, chunk=20_000, span=500):
     rot = a * complex(math.cos(-m_p * Om_i * c * span * dt), math.sin(-m_p * Om_i * c * span * dt))
     residual = float(torch.linalg.vector_norm(b - rot) / torch.linalg.vector_norm(b))
     e_ratio = float((b.abs() ** 2).sum() / (st.u[:, :, 0, :].abs() ** 2).sum())
-    # tangential slip at the inner wall (Sec. 5.3): the correction u = u* - grad phi leaves
-    # (u_theta - Re_i, u_z) != 0 there; RMS over the wall, relative to Re_i, by Parseval on the
-    # stored coefficients (mean of f^2 = sum_k |f_0k|^2 + 2 sum_{m>0,k} |f_mk|^2)
-    w = st.u[:, 0].cpu().numpy()                   # [c][m][k] at r = r_i
-    ut = (w[0] - w[1]) / 2j
-    ut[0, K] -= Re_i
-    cm = np.full((M + 1, 1), 2.0)
-    cm[0] = 1.0
-    slip = float(np.sqrt(np.sum(cm * (np.abs(ut) ** 2 + np.abs(w[2]) ** 2))) / Re_i)
-    return c, residual, e_ratio, steps, slip
+    slip = inner_wall_slip(st.u, M, K, Re_i)
+    return c, residual, e_ratio, steps, slip, st.u.clone()
 
 
 def test_wavy_vortex_wave_speed_fp64():
-    c, residual, e_ratio, steps, slip = wave_speed_run(tc.TC_FP64)
+    c, residual, e_ratio, steps, slip, _ = wave_speed_run(tc.TC_FP64)
     print(f"c = {c:.7f} after {steps} steps, rigid-rotation residual {residual:.2e}, relative slip {slip:.2e}")
     assert e_ratio > 1e-3, "no saturated wavy mode"
     assert residual <= 1e-6, residual
     assert abs(c / GOLD["c"] - 1) <= 1e-4, (c, steps)
-    # roughly 1e-6 at this resolution and time step (Sec. 5.3): within a decade either way
-    assert GOLD["relative_slip_about"] / 10 <= slip <= GOLD["relative_slip_about"] * 10, slip
+    # about 1e-6 at this resolution and the largest time step (Sec. 5.3): within a factor 3
+    assert GOLD["relative_slip_about"] / 3 <= slip <= GOLD["relative_slip_about"] * 3, slip
+
+
+def test_slip_falls_with_the_time_step():
+    """Sec. 5.3: the tangential slip left by the projection falls with dt as a power law once
+    the radial resolution is high enough (the paper finds an exponent of about 2.5, against the
+    predicted 3; at n_r = 32 its curve levels off at the spatial error).  The saturated wavy
+    vortices at N_r = 64 are restarted cold at dt = 2e-5, 1e-5, 5e-6 and 2.5e-6 and advanced
+    over the same time (4e-3, a fraction of a rotation); the slip at the end gives the
+    exponent between successive dt."""
+    eta, Re_i, m_p, L_z = GOLD["eta"], GOLD["Re_i"], GOLD["k_theta"], GOLD["Gamma"]
+    M, K, N_r = 16, 16, 64
+    *_, u_sat = wave_speed_run(tc.TC_FP64, N_r=N_r)
+    T = 4e-3
+    slips = []
+    dts = [2e-5, 1e-5, 5e-6, 2.5e-6]
+    for dt in dts:
+        plan = tc.Plan(N_r, M, K, m_p, eta, Re_i, GOLD["Re_o"], L_z, dt, no_adjoint=True)
+        st = tc.State(plan, u_sat)
+        plan.step(st, int(round(T / dt)))
+        slips.append(inner_wall_slip(st.u, M, K, Re_i))
+    slopes = [math.log(a / b) / math.log(2.0) for a, b in zip(slips, slips[1:])]
+    print("dt", dts, "slip", [f"{x:.3e}" for x in slips], "exponents", [f"{x:.2f}" for x in slopes])
+    assert all(b < a for a, b in zip(slips, slips[1:])), slips
+    assert 2.0 <= slopes[0] <= 3.3, slopes
 
 
 def test_wavy_vortex_wave_speed_mixed():
     """The mixed form over the same long run.  Without projecting N's m = 0 line onto the
     real-field symmetry, its FP32 rounding seeded a non-real m = 0 part of u that the FP64
     mean-flow terms amplified until the run overflowed (after about one viscous time)."""
-    c, residual, e_ratio, steps, slip = wave_speed_run(tc.TC_MIXED)
+    c, residual, e_ratio, steps, slip, _ = wave_speed_run(tc.TC_MIXED)
     print(f"mixed: c = {c:.7f} after {steps} steps, rigid-rotation residual {residual:.2e}, relative slip {slip:.2e}")
     assert e_ratio > 1e-3, "no saturated wavy mode"
     assert residual <= 1e-5, residual
     assert abs(c / GOLD["c"] - 1) <= 1e-4, (c, steps)
 
 
-ONSET = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "wavy_vortex_onset.json")))
-
-
-def n1_growth_rate(Re, u_tvf=None, Re_prev=None):
-    """Growth rate of an n = 1 disturbance on saturated Taylor vortices.  In the linear regime
-    only the axisymmetric base (m = 0) and the disturbance (m = 1) interact, so M = 1 gives the
-    paper's azimuthal resolution's answer; N_r = 64 and |k| <= 64 are its radial and axial
-    resolution ((n_r, n_z) = (64, 128) = (M, 2L+1) in its notation)."""
-    eta, L_z, dt = ONSET["eta"], ONSET["Gamma"], ONSET["dt"]
-    N_r, M, K = 64, 1, 64
-    plan = tc.Plan(N_r, M, K, ONSET["k_theta"], eta, Re, ONSET["Re_o"], L_z, dt, no_adjoint=True)
-    r = plan.nodes()
-    base = torch.from_numpy(I.base_state(r, M, K, eta, Re, 0.0)).cuda()
-    if u_tvf is None:
-        u0 = torch.from_numpy(I.initial_state(r, M, K, 1, L_z, eta, Re, 0.0, kind="taylor", amp=0.02, seed=3)).cuda()
-        u0[:, :, 1, :] = 0
-    else:   # the previous Reynolds number's vortices on this Reynolds number's Couette flow
-        u0 = u_tvf - torch.from_numpy(I.base_state(r, M, K, eta, Re_prev, 0.0)).cuda() + base
+def test_quasi_nusselt_number():
+    """Nu_omega = T / T_lam of Sec. 5.4 through tc_diagnostics.  For circular Couette flow it
+    is 1 up to the truncation of the wall FD rows; for saturated axisymmetric Taylor vortices at
+    eta = 0.5, Re_i = 100 (above the onset at 68.2 for k_z = 3.16) it exceeds 1 and is the same
+    at both walls (in a steady state the angular-momentum flux through every cylinder is the
+    same); at both walls it equals the oracle's torque of the same state over T_lam."""
+    import oracle as O
+    LZ = 2 * math.pi / 3.16
+    cfg = dict(N_r=32, M=1, K=16, m_p=1, eta=0.5, Re_i=100.0, Re_o=0.0, L_z=LZ, dt=1e-3)
+    plan = tc.Plan(**cfg, no_adjoint=True)
+    ops = O.Operators(O.Params(**cfg))
+    C2 = 0.5 * 100.0 / (0.5 * 0.75)
+    base = torch.from_numpy(I.base_state(ops.r, 1, 16, 0.5, 100.0, 0.0)).cuda()
+    d0 = plan.diagnostics(base)
+    assert abs(d0.nu_omega_inner - 1) <= 1e-5 and abs(d0.nu_omega_outer - 1) <= 1e-5, (d0.nu_omega_inner, d0.nu_omega_outer)
+    u0 = torch.from_numpy(I.initial_state(ops.r, 1, 16, 1, LZ, 0.5, 100.0, 0.0, kind="taylor", amp=1e-2, seed=3)).cuda()
     st = tc.State(plan, u0)
     prev = None
-    for _ in range(60):
-        plan.step(st, 5000)
-        e0 = float((st.u[:, :, 0, :].abs() ** 2).sum())
-        if prev is not None and abs(e0 / prev - 1) < 1e-12:
+    for _ in range(100):
+        plan.step(st, 2000)
+        d = plan.diagnostics(st.u)
+        if prev is not None and abs(d.energy / prev - 1) < 1e-11:
             break
-        prev = e0
-    u_tvf = st.u.clone()
-    pert = torch.from_numpy(I.initial_state(r, M, K, 1, L_z, eta, Re, 0.0, kind="box", amp=1e-7, seed=5)).cuda() - base
-    u1 = u_tvf.clone()
-    u1[:, :, 1, :] = pert[:, :, 1, :]
-    st = tc.State(plan, u1)
-    span, logs, rates = 5000, [], []
-    for _ in range(60):
-        plan.step(st, span)
-        logs.append(math.log(float((st.u[:, :, 1, :].abs() ** 2).sum())))
-        if len(logs) >= 2:
-            rates.append((logs[-1] - logs[-2]) / (2 * span * dt))   # energy ~ exp(2 sigma t)
-        if len(rates) >= 3 and abs(rates[-1] - rates[-3]) < 1e-7:
-            break
-    return rates[-1], u_tvf
-
-
-def test_wavy_vortex_onset():
-    lo, hi = 407.6, 408.6
-    s_lo, u_tvf = n1_growth_rate(lo)
-    s_hi, _ = n1_growth_rate(hi, u_tvf, lo)
-    Re_c = lo - s_lo * (hi - lo) / (s_hi - s_lo)
-    print(f"sigma({lo}) = {s_lo:.6e}, sigma({hi}) = {s_hi:.6e}, Re_c = {Re_c:.4f}")
-    assert s_lo < 0 < s_hi
-    a, b = ONSET["Re_c_bracket"]
-    assert a - 0.05 <= Re_c <= b + 0.05, Re_c
+        prev = d.energy
+    Ti, To = O.torque(ops, st.u.cpu().numpy())
+    print(f"Taylor vortices at Re_i = 100: Nu_omega = {d.nu_omega_inner:.10f} (inner), {d.nu_omega_outer:.10f} (outer)")
+    assert d.nu_omega_inner > 1.05
+    assert abs(d.nu_omega_inner / d.nu_omega_outer - 1) <= 1e-6, (d.nu_omega_inner, d.nu_omega_outer)
+    assert abs(d.nu_omega_inner / (Ti / (-2 * C2)) - 1) <= 1e-12
+    assert abs(d.nu_omega_outer / (To / (-2 * C2)) - 1) <= 1e-12

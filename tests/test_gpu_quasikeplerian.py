@@ -1,0 +1,89 @@
+"""The quasi-Keplerian workload (eta = 0.5, Re_i = 1e4, Re_o = sqrt(eta) Re_i, N_r = 256,
+broadband perturbation of amplitude 0.05, seed 42) over its 100 steps, with the mode count
+reduced to m = -8..8, k = -16..16 so that the oracle can run it, at the stated dt 1e-4
+halved until 100 oracle steps stay finite with less than 10x energy growth (1e-4 / 64: at
+1e-4 / 32 the energy grows 141x by step 50; at 1e-4 / 64 it grows 1.15x in 100 steps):
+
+* the FP64 CUDA step against the oracle after 100 steps: u, u_prev, N_prev, p;
+* the mixed form (FP32 transforms and products, FP64 mean flow and solves) against the
+  oracle: the errors of the velocity perturbation, the velocity, the two torques and the
+  largest divergence, which is what the precision form states.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+from paper_1311_2481_gb300 import build as B  # noqa: E402
+from paper_1311_2481_gb300 import inputs as I  # noqa: E402
+from paper_1311_2481_gb300 import tc  # noqa: E402
+
+B.build()
+LZ = 2 * math.pi / 3.16
+RE_I = 1e4
+RE_O = math.sqrt(0.5) * RE_I
+M, K = 8, 16
+DT = 1e-4 / 64
+CFG = dict(N_r=256, M=M, K=K, m_p=1, eta=0.5, Re_i=RE_I, Re_o=RE_O, L_z=LZ, dt=DT)
+NSTEPS = 100
+
+_cache = {}
+
+
+def _oracle_run():
+    if "ref" not in _cache:
+        ops = O.Operators(O.Params(**CFG))
+        u0 = I.initial_state(ops.r, M, K, 1, LZ, 0.5, RE_I, RE_O, kind="broadband", amp=0.05, seed=42)
+        st = O.run(ops, O.cold_state(u0), NSTEPS)
+        _cache["ref"] = (ops, u0, st)
+    return _cache["ref"]
+
+
+def _gpu_run(precision, u0):
+    plan = tc.Plan(**CFG, precision=precision)
+    st = tc.State(plan, torch.from_numpy(u0).cuda())
+    plan.step(st, NSTEPS)
+    torch.cuda.synchronize()
+    return plan, st
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_fp64_100_steps_match_oracle():
+    ops, u0, ref = _oracle_run()
+    plan, st = _gpu_run(tc.TC_FP64, u0)
+    base = I.base_state(ops.r, M, K, 0.5, RE_I, RE_O)
+    errs = {"u": rel(st.u.cpu().numpy(), ref.u), "u_prev": rel(st.u_prev.cpu().numpy(), ref.u_prev),
+            "N_prev": rel(st.N_prev.cpu().numpy(), ref.N_prev), "p": rel(st.p.cpu().numpy(), ref.p),
+            "u'": rel(st.u.cpu().numpy() - base, ref.u - base)}
+    print("FP64 vs oracle after 100 steps:", errs)
+    for k, e in errs.items():
+        assert e <= 1e-10, (k, e)
+
+
+def test_mixed_100_steps_error_against_oracle():
+    ops, u0, ref = _oracle_run()
+    plan, st = _gpu_run(tc.TC_MIXED, u0)
+    u = st.u.cpu().numpy()
+    base = I.base_state(ops.r, M, K, 0.5, RE_I, RE_O)
+    Ti, To = O.torque(ops, ref.u)
+    d = plan.diagnostics(st.u)
+    err = {"velocity_perturbation": rel(u - base, ref.u - base), "velocity": rel(u, ref.u),
+           "torque_inner": abs(d.torque_inner / Ti - 1), "torque_outer": abs(d.torque_outer / To - 1),
+           "max_div": abs(d.max_div / O.max_divergence(ops, ref.u) - 1),
+           "energy": abs(d.energy / O.perturbation_energy(ops, ref.u) - 1)}
+    print("mixed vs oracle after 100 steps:", err)
+    assert d.finite
+    assert err["velocity_perturbation"] <= 1e-6, err
+    assert err["velocity"] <= 1e-7, err
+    assert err["torque_inner"] <= 1e-6 and err["torque_outer"] <= 1e-6, err
+    assert err["max_div"] <= 1e-4, err
