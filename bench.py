@@ -230,6 +230,51 @@ def cufft_comparison(torch, cfg, dev, reps=20):
     return out
 
 
+def tensor_dft_comparison(torch, dev, reps=3):
+    """The theta stage of the nonlinear term as dense DFT products on the tensor cores, timed
+    with cuBLAS (torch.matmul) as a comparison only, against the hand-written FP32 theta pass.
+    The inverse stage is one real product [P_theta x 2(M+1)] x [2(M+1) x 12 N_r P_z] (cos and
+    sin columns of the stored modes, 12 physical fields per (r, z)); the forward stage
+    [2(M+1) x P_theta] x [P_theta x 3 N_r P_z].  The FP32 error budget of the mixed form needs
+    split operands: with FP16 pairs (hi + lo, about 22 bits) three products per stage
+    (hi hi, hi lo, lo hi), accumulated in FP32.  Counted here: the products alone, 16-bit
+    outputs, no splitting, no assembly and no pointwise products, so the sum is a lower bound
+    for any DFT-as-GEMM theta stage."""
+    out = {}
+    for name, (N_r, M, K) in (("N_r=64, M=32, K=64", (64, 32, 64)), ("N_r=256, M=256, K=512", (256, 256, 512)),
+                              ("N_r=384, M=384, K=768", (384, 384, 768))):
+        Pt, Pz = 3 * M, 3 * K
+        kk = 2 * (M + 1)
+        Li, Lf = 12 * N_r * Pz, 3 * N_r * Pz
+        g = torch.Generator(device=dev).manual_seed(3)
+        Ai = torch.randn(Pt, kk, device=dev, dtype=torch.float16, generator=g)
+        Bi = torch.randn(kk, Li, device=dev, dtype=torch.float16, generator=g)
+        Af = torch.randn(kk, Pt, device=dev, dtype=torch.float16, generator=g)
+        Bf = torch.randn(Pt, Lf, device=dev, dtype=torch.float16, generator=g)
+        Ci = torch.empty(Pt, Li, device=dev, dtype=torch.float16)
+        Cf = torch.empty(kk, Lf, device=dev, dtype=torch.float16)
+        torch.matmul(Ai, Bi, out=Ci)
+        torch.matmul(Af, Bf, out=Cf)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        for _ in range(reps):
+            torch.matmul(Ai, Bi, out=Ci)
+        ev[1].record()
+        for _ in range(reps):
+            torch.matmul(Af, Bf, out=Cf)
+        ev[2].record()
+        torch.cuda.synchronize()
+        ti, tf = ev[0].elapsed_time(ev[1]) / reps, ev[1].elapsed_time(ev[2]) / reps
+        fl = 2.0 * (Pt * kk * Li + kk * Pt * Lf)
+        out[name] = {"inverse_gemm_ms": ti, "forward_gemm_ms": tf,
+                     "tflops": fl / ((ti + tf) / 1e3) / 1e12,
+                     "split_fp16_pairs_lower_bound_ms": 3 * (ti + tf)}
+        del Ai, Bi, Af, Bf, Ci, Cf
+        torch.cuda.empty_cache()
+    return out
+
+
 def stable_dt(tc, torch, cfg, u0_t, dev, nsteps=200):
     """Stated dt halved until nsteps FP64 steps stay finite with < 10x energy growth."""
     dt = cfg["dt"]
@@ -672,6 +717,7 @@ def run_ours(args):
         for key, fn in (("cufft_comparison", lambda: {**cufft_comparison(torch, cfg, f"cuda:{local}"),
                                                       "ours_fp64_nonlinear_ms": nl64,
                                                       "ours_fp32_nonlinear_ms": nl32}),
+                        ("tensor_dft_comparison", lambda: tensor_dft_comparison(torch, f"cuda:{local}")),
                         ("adjoint", lambda: adjoint_ratio(tc, torch, I, f"cuda:{local}")),
                         ("large_same_size", lambda: large_mixed(tc, torch, I, f"cuda:{local}")),
                         ("paper_small", lambda: paper_small(tc, torch, I, f"cuda:{local}"))):

@@ -244,10 +244,15 @@ tc_status tc_energy_gradient(tc_plan* plan, const void* u, void* g, void* stream
  * (the paper has no counterpart: it is a packaging choice of this library).  Instead of a
  * caller workspace, the staging lines between the transform kernels live in one static
  * 80 MiB device array that every GPU loading the library keeps until the process exits.
- * Plans needing more staging (12 * N_r * (M+1) * P_z complex values) get TC_ERR_ARG before
- * any launch.  Allocates nothing.  The first call on each device looks up the array's
- * address once (cudaGetSymbolAddress); make it before any stream capture.  All calls share
- * the array: calls whose GPU work overlaps (other streams, unordered plans) race on it. */
+ * The staging a plan needs is its workspace before N^i: 12 * N_r * (M+1) * P_z line values
+ * (complex128; complex64 for a TC_MIXED plan created with no_adjoint), plus, for TC_MIXED
+ * plans, 6 * N_r * (M+1) * (2K+1) complex64 values of the FP32 split of u and d_r u, each
+ * region rounded up to 256 bytes; plans that need more than 80 MiB get TC_ERR_ARG before any
+ * launch.  Allocates nothing.  The first call on each device looks up the array's address
+ * once (cudaGetSymbolAddress) and keeps it; make that call before any stream capture, and do
+ * not call this entry point after a device reset (cudaDeviceReset or a primary-context reset
+ * unloads the array and leaves the kept address stale).  All calls share the array: calls
+ * whose GPU work overlaps (other streams, unordered plans) race on it. */
 tc_status tc_nonlinear_noalloc(tc_plan* plan, const void* u_hat, void* N_hat, void* stream);
 
 /* FP64 FMA rate probe (no counterpart in the paper: it measures the FP64 pipe that bounds the

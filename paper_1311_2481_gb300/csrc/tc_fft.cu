@@ -84,7 +84,8 @@ template <typename V>
 __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __restrict__ H2,
                                                const double* __restrict__ irn, int N_r, int M,
                                                int Pz, double mp, int zt,
-                                               const V* __restrict__ tw, Radices rad) {
+                                               const V* __restrict__ tw, Radices rad,
+                                               const float* __restrict__ dsc) {
     using T = typename Real<V>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Pt = rad.n;
@@ -96,6 +97,8 @@ __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __re
     const int z0 = (blockIdx.x % tiles) * zt;
     const size_t fstride = (size_t)N_r * (M + 1) * Pz;
     const V* h = H1 + (size_t)r * (M + 1) * Pz + z0;
+    // FP32 lines: d_r u_z enters line 4 scaled by a power of two (1 for FP64 lines)
+    const T ds = sizeof(T) == 4 ? (T)dsc[r] : (T)1, ids = (T)1 / ds;
 
     for (int idx = threadIdx.x; idx < nl * Pt; idx += blockDim.x) { a[idx].x = 0; a[idx].y = 0; }
     __syncthreads();
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __re
             }
         } else {       // two real fields x, y: spectrum X_m + i Y_m, conj(X_m) + i conj(Y_m) at -m
             V X, Y;
-            if (pr == 4) { X = h[2 * fstride + o]; Y = h[5 * fstride + o]; }
+            if (pr == 4) { X = h[2 * fstride + o]; Y = h[5 * fstride + o]; Y.x *= ds; Y.y *= ds; }
             else { X = h[2 * fstride + o]; X = cmuli(X); X.x *= mm; X.y *= mm; Y = h[8 * fstride + o]; }
             if (m == 0) {
                 V c0; c0.x = X.x; c0.y = Y.x;
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __re
         const T utr = ut * ir;
         const T Nr = ur * p1.x + utr * p2.x + uz * p3.x - ut * utr;
         const T Nt = ur * p1.y + utr * p2.y + uz * p3.y + utr * ur;
-        const T Nz = ur * p4.y + utr * p5.x + uz * p5.y;
+        const T Nz = ur * (p4.y * ids) + utr * p5.x + uz * p5.y;
         V q; q.x = Nr; q.y = Nt;
         fw[(size_t)zi * Pt + th] = q;
         V* zl = fw + (size_t)(zt + zi / 2) * Pt + th;
@@ -395,7 +398,8 @@ static tc_status theta64(tc_plan* p, const double2* H1, double2* H2, cudaStream_
     TC_CUDA(p, cudaFuncSetAttribute(k_theta<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     const int slot = prof_begin(p, kKTheta, s);
     k_theta<double2><<<p->N_r * (p->P_z / zt), p->thr_theta, sm2, s>>>(H1, H2, p->d_ir, p->N_r, p->M, p->P_z,
-                                                                      (double)p->m_p, zt, p->d_tw_t, p->rad_t);
+                                                                      (double)p->m_p, zt, p->d_tw_t, p->rad_t,
+                                                                      nullptr);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_theta");
     return TC_OK;
@@ -412,7 +416,7 @@ tc_status launch_theta32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t 
     TC_CUDA(p, cudaFuncSetAttribute(k_theta<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     const int slot = prof_begin(p, kKTheta32, s);
     k_theta<float2><<<p->N_r * (p->P_z / zt), 256, sm2, s>>>(H1, H2, p->d_ir, p->N_r, p->M, p->P_z, (double)p->m_p,
-                                                             zt, p->d_tw_t32, p->rad_t);
+                                                             zt, p->d_tw_t32, p->rad_t, p->d_dsc);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_theta");
     return TC_OK;

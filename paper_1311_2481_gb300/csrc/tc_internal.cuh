@@ -91,6 +91,7 @@ struct tc_plan {
     double* d_ir = nullptr;          // 1 / r_j
     double* d_w1 = nullptr;
     float* d_w1f = nullptr;          // FP32 copy of w1 (mixed form)
+    float* d_dsc = nullptr;          // mixed form: power-of-two scale of d_r u_z beside u_z in a theta line
     double* d_w2 = nullptr;
     int* d_col0 = nullptr;
     int* d_d1t_row = nullptr;

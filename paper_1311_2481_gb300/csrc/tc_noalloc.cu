@@ -10,16 +10,21 @@
 //
 // Costs and limits:
 //  - kStaticScratchBytes (80 MiB) of device memory is reserved on every GPU that loads this
-//    library, for as long as the process lives.  Plans whose staging needs more
-//    (12 * N_r * (M+1) * P_z complex values plus alignment) are rejected with TC_ERR_ARG
-//    before anything is launched.
+//    library, for as long as the process lives.  Plans whose staging needs more are rejected
+//    with TC_ERR_ARG before anything is launched.  The staging is everything the workspace
+//    holds before N^i: the z-pass lines H1 and H2, 12 * N_r * (M+1) * P_z values (complex128,
+//    or complex64 for a TC_MIXED plan created with no_adjoint), and for TC_MIXED plans the
+//    FP32 split of u and d_r u, 6 * N_r * (M+1) * (2K+1) complex64 values, each region
+//    rounded up to 256 bytes.
 //  - All calls share the one array, which keeps whatever the last call left in it.  The
 //    kernels overwrite every staging entry before reading it, so nothing has to start at
 //    zero, but two calls whose work overlaps on the GPU (different streams, or different
 //    plans without ordering between them) race on the array: order them on one stream.
 //  - The first call on each device looks up the array's device address once with
-//    cudaGetSymbolAddress (with that device current).  Make that first call before any
-//    stream capture begins.
+//    cudaGetSymbolAddress (with that device current) and keeps it for the life of the
+//    process.  Make that first call before any stream capture begins.  A device reset
+//    (cudaDeviceReset, or a reset of the primary context) unloads the array, and the kept
+//    address is then stale: do not call this entry point after resetting a device.
 #include <mutex>
 
 #include "tc_internal.cuh"
@@ -57,8 +62,12 @@ tc_status scratch_on_current_device(tc_plan* p, void** out) {
 
 extern "C" tc_status tc_nonlinear_noalloc(tc_plan* plan, const void* u_hat, void* N_hat, void* stream) {
     if (!plan) return TC_ERR_ARG;
-    if (plan->host_only) return TC_ERR_STATE;
-    // staging used by the transform kernels: H1 (9 line sets) then H2 (3 line sets)
+    if (plan->host_only) {
+        snprintf(plan->err, sizeof(plan->err), "host-only plan");
+        return TC_ERR_STATE;
+    }
+    // staging used by the transform kernels: H1 (9 line sets), H2 (3 line sets) and, for the
+    // mixed form, the FP32 split of u and d_r u -- every workspace region before N^i
     const size_t need = plan->ws.Ncur;
     if (need > kStaticScratchBytes) {
         snprintf(plan->err, sizeof(plan->err),
@@ -80,6 +89,7 @@ extern "C" tc_status tc_nonlinear_noalloc(tc_plan* plan, const void* u_hat, void
     void* scratch = nullptr;
     st = scratch_on_current_device(plan, &scratch);
     if (st != TC_OK) return st;
+    plan->used = true;   // a compute call: tc_plan_set is refused from here on
     return tc::launch_nonlinear(plan, static_cast<const double2*>(u_hat), static_cast<double2*>(N_hat),
                                 static_cast<char*>(scratch), static_cast<cudaStream_t>(stream));
 }

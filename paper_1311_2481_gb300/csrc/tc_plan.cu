@@ -409,6 +409,22 @@ static tc_status upload(tc_plan* p) {
     TC_CUDA(p, put((void**)&p->d_w1, p->w1.data(), p->w1.size() * sizeof(double)));
     std::vector<float> w1f(p->w1.begin(), p->w1.end());
     TC_CUDA(p, put((void**)&p->d_w1f, w1f.data(), w1f.size() * sizeof(float)));
+    {
+        // The FP32 theta lines carry u_z and d_r u_z as one complex line, so the transform's
+        // rounding is relative to the larger of the two.  Near a no-slip wall u' ~ (r - r_w)
+        // d_r u', so d_r u_z is scaled by 2^floor(log2 d), d the distance to the nearer wall
+        // (at most 1, the gap width), which keeps both parts of the line at a similar size;
+        // the scale is a power of two, so scaling and unscaling are exact.  Wall rows take
+        // the scale of their neighbour (u' = 0 there).
+        const int N = p->N_r;
+        std::vector<float> dsc(N, 1.0f);
+        for (int j = 0; j < N; ++j) {
+            const int jj = j == 0 ? 1 : (j == N - 1 ? N - 2 : j);
+            const double d = std::min(std::min(p->r[jj] - p->r_i, p->r_o - p->r[jj]), 1.0);
+            dsc[j] = d > 0.0 ? (float)std::ldexp(1.0, (int)std::floor(std::log2(d))) : 1.0f;
+        }
+        TC_CUDA(p, put((void**)&p->d_dsc, dsc.data(), dsc.size() * sizeof(float)));
+    }
     TC_CUDA(p, put((void**)&p->d_w2, p->w2.data(), p->w2.size() * sizeof(double)));
     TC_CUDA(p, put((void**)&p->d_col0, p->col0.data(), p->col0.size() * sizeof(int)));
     TC_CUDA(p, put((void**)&p->d_d1t_row, p->d1t_row.data(), p->d1t_row.size() * sizeof(int)));
@@ -461,7 +477,7 @@ void prof_end(tc_plan* p, int slot, cudaStream_t s) {
 static void free_device(tc_plan* p) {
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     p->prof_ev.clear();
-    void* ptrs[] = {p->d_r, p->d_ir, p->d_w1, p->d_w1f, p->d_w2, p->d_col0, p->d_d1t_row, p->d_d1t_w, p->d_fac, p->d_piv,
+    void* ptrs[] = {p->d_r, p->d_ir, p->d_w1, p->d_w1f, p->d_dsc, p->d_w2, p->d_col0, p->d_d1t_row, p->d_d1t_w, p->d_fac, p->d_piv,
                     p->d_fac2, p->d_piv2, p->d_spk, p->d_rinv, p->d_tw_z, p->d_tw_t, p->d_tw_z32, p->d_tw_t32};
     for (void* q : ptrs)
         if (q) cudaFree(q);

@@ -55,7 +55,8 @@ __device__ __forceinline__ V imul(V a, typename Elem<V>::T s) { return vmk<V>(-s
 template <typename V, int PT, int ZT, int NT, int MINB, bool R8>
 __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, V* __restrict__ H2,
                                                       const double* __restrict__ irn, int N_r, int M, int Pz,
-                                                      double mp, const V* __restrict__ tw) {
+                                                      double mp, const V* __restrict__ tw,
+                                                      const float* __restrict__ dsc) {
     using T = typename Elem<V>::T;
     constexpr int LP = padded<PT>();
     constexpr int NL = 2 * ZT;             // resident lines in a phase
@@ -76,6 +77,9 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, 
     const V* h = H1 + (size_t)r * (M + 1) * Pz + z0;
     const T ir = (T)irn[r];   // 1 / r_j from the plan
     const T mpf = (T)mp;
+    // FP32 lines: d_r u_z enters the (u_z, d_r u_z) line scaled by a power of two, so that
+    // its rounding does not swamp u_z near the walls; FP64 lines are not scaled
+    const T ds = sizeof(V) == 8 ? (T)dsc[r] : (T)1, ids = (T)1 / ds;
     const int zi = threadIdx.x % ZT;        // z of this thread in the load and store loops
     const int mstep = NT / ZT;
 
@@ -128,7 +132,8 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, 
                 V* L1 = L0 + LP;
                 if (phase == 0) {
                     put_pair(L0, PT, m, h[0 * fstride + o], h[1 * fstride + o]);
-                    put_real2(L1, PT, m, h[2 * fstride + o], h[5 * fstride + o]);
+                    const V drz = h[5 * fstride + o];
+                    put_real2(L1, PT, m, h[2 * fstride + o], vmk<V>(drz.x * ds, drz.y * ds));
                 } else if (phase == 1) {
                     put_pair(L0, PT, m, h[3 * fstride + o], h[4 * fstride + o]);
                     put_pair(L1, PT, m, imul(h[0 * fstride + o], mm), imul(h[1 * fstride + o], mm));
@@ -149,7 +154,7 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, 
             if (phase == 0) {
                 const T utr = p0.y * ir;
                 Ua[pt] = vmk<V>(p0.x, utr);
-                Ub[pt] = vmk<V>(p1.x, p0.x * p1.y);                      // N_z = u_r d_r u_z
+                Ub[pt] = vmk<V>(p1.x, p0.x * (p1.y * ids));              // N_z = u_r d_r u_z
                 Nn[pt] = vmk<V>(-p0.y * utr, utr * p0.x);                // curvature terms
             } else if (phase == 1) {
                 const V a = Ua[pt];
@@ -214,7 +219,8 @@ tc_status run_theta_s(tc_plan* p, const V* H1, V* H2, const V* tw, cudaStream_t 
     auto kern = k_theta_s<V, PT, ZT, NT, MINB, R8>;
     TC_CUDA(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int slot = prof_begin(p, sizeof(V) == 8 ? kKTheta32 : kKTheta, s);
-    kern<<<p->N_r * (p->P_z / ZT), NT, sm, s>>>(H1, H2, p->d_ir, p->N_r, p->M, p->P_z, (double)p->m_p, tw);
+    kern<<<p->N_r * (p->P_z / ZT), NT, sm, s>>>(H1, H2, p->d_ir, p->N_r, p->M, p->P_z, (double)p->m_p, tw,
+                                                 sizeof(V) == 8 ? p->d_dsc : nullptr);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_theta_s");
     return TC_OK;

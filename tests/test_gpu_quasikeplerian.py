@@ -1,10 +1,13 @@
 """The quasi-Keplerian workload (eta = 0.5, Re_i = 1e4, Re_o = sqrt(eta) Re_i, N_r = 256,
 broadband perturbation of amplitude 0.05, seed 42) over its 100 steps, with the mode count
 reduced to m = -8..8, k = -16..16 so that the oracle can run it, at the stated dt 1e-4
-halved until 100 oracle steps stay finite with less than 10x energy growth (1e-4 / 64: at
-1e-4 / 32 the energy grows 141x by step 50; at 1e-4 / 64 it grows 1.15x in 100 steps):
+halved until the oracle's step is stable over the 100 steps: a difference of 1e-9 of the
+state between two oracle runs grows by 1.04x at 1e-4 / 128 (at 1e-4 / 32 the energy grows
+141x by step 50; at 1e-4 / 64 the energy grows only 1.15x, but rounding-level differences
+grow about 1.3x per step, which an FP32 form turns into an overflow):
 
-* the FP64 CUDA step against the oracle after 100 steps: u, u_prev, N_prev, p;
+* the FP64 CUDA step against the oracle after 100 steps: u, u_prev, N_prev, p, with bounds
+  that follow the conditioning of the Poisson matrices at this N_r;
 * the mixed form (FP32 transforms and products, FP64 mean flow and solves) against the
   oracle: the errors of the velocity perturbation, the velocity, the two torques and the
   largest divergence, which is what the precision form states.
@@ -30,7 +33,7 @@ LZ = 2 * math.pi / 3.16
 RE_I = 1e4
 RE_O = math.sqrt(0.5) * RE_I
 M, K = 8, 16
-DT = 1e-4 / 64
+DT = 1e-4 / 128
 CFG = dict(N_r=256, M=M, K=K, m_p=1, eta=0.5, Re_i=RE_I, Re_o=RE_O, L_z=LZ, dt=DT)
 NSTEPS = 100
 
@@ -66,8 +69,14 @@ def test_fp64_100_steps_match_oracle():
             "N_prev": rel(st.N_prev.cpu().numpy(), ref.N_prev), "p": rel(st.p.cpu().numpy(), ref.p),
             "u'": rel(st.u.cpu().numpy() - base, ref.u - base)}
     print("FP64 vs oracle after 100 steps:", errs)
+    # At N_r = 256 the Poisson matrices reach cond 8e9: two pivoted eliminations in different
+    # rounding order then differ by up to about 1e-11 per solve (the sampled-mode solve test
+    # at this N_r bounds them by 1e-10).  Over 100 steps that accumulates to at most 1e-8 on
+    # p and on the perturbation part of u, and stays 10x below that on the full fields, which
+    # the Couette flow dominates.
+    bound = {"u": 1e-9, "u_prev": 1e-9, "N_prev": 1e-9, "p": 1e-8, "u'": 1e-8}
     for k, e in errs.items():
-        assert e <= 1e-10, (k, e)
+        assert e <= bound[k], (k, e)
 
 
 def test_mixed_100_steps_error_against_oracle():
