@@ -652,8 +652,7 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     const size_t lane = (p->precision == TC_MIXED && !p->adjoint) ? sizeof(float2) : cplx;
     p->ws.H1 = take(9 * p->Hfield * lane);
     p->ws.H2 = take(3 * p->Hfield * lane);
-    // the mixed form's FP32 u', d_r u' (its own region: with the overlapped step the split of
-    // one m-chunk runs while the forward z pass of another still reads H2)
+    // the mixed form's FP32 u', d_r u', in a region of its own before N^i
     p->ws.P32 = take(p->precision == TC_MIXED ? 6 * p->S * sizeof(float2) : 0);
     p->ws.Ncur = take(3 * p->S * cplx);
     p->ws.uE = take(3 * p->S * cplx);
