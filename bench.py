@@ -30,6 +30,8 @@ THETA_TRAFFIC = 61.78e6
 CFG2 = dict(N_r=64, M=32, K=64, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)
 # mid-size case for profiling (inputs larger than L2, a few GB on the device)
 CFG_MID = dict(N_r=128, M=128, K=256, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)
+# N_r beyond the fused steps-2-5 kernel's shared memory, for profiling the per-stage kernels
+CFG_SPLIT = dict(N_r=256, M=32, K=64, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)
 # adjoint workload: N_r = 96, m = -32..32, k = -64..64, Re_i = 2000, 200 steps, checkpoint every 20
 CFG3 = dict(N_r=96, M=32, K=64, m_p=1, eta=0.5, Re_i=2000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)
 # mixed vs FP64 at the same size: quasi-Keplerian (Re_o = sqrt(eta) Re_i), 256 x 768 x 1536 grid
@@ -500,7 +502,7 @@ def run_ours(args):
         B.build()
     if dist:
         dist.barrier()
-    cfg = CFG_MID if args.size == "mid" else CFG2
+    cfg = {"mid": CFG_MID, "split": CFG_SPLIT}.get(args.size, CFG2)
     main_is_bench = args.size == "bench" and args.workload == "fp64"
     prec = tc.TC_MIXED if args.workload == "mixed" else tc.TC_FP64
     plan = tc.Plan(**cfg, precision=prec, no_adjoint=True, device=f"cuda:{local}")
@@ -811,8 +813,9 @@ def main():
     ap.add_argument("--largest", action="store_true", help="also time the mixed form at N_r = 384, 384 x 1152 x 2304")
     ap.add_argument("--workload", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the main timed step (the reported metric is the FP64 step)")
-    ap.add_argument("--size", default="bench", choices=["bench", "mid"],
-                    help="bench: N_r=64, M=32, K=64; mid: N_r=128, M=128, K=256 (for profiling)")
+    ap.add_argument("--size", default="bench", choices=["bench", "mid", "split"],
+                    help="bench: N_r=64, M=32, K=64; mid: N_r=128, M=128, K=256; split: N_r=256, M=32, "
+                         "K=64 (the per-stage steps-2-5 kernels) -- the last two for profiling")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -81,7 +81,9 @@ typedef struct {
                          0: fused while N_r <= 192, separate beyond */
     int theta_variant; /* launch tuning of the mixed form's length-specialised theta pass:
                          0 or 1: radices <= 16, two blocks per SM; 2 and 3: radices <= 8 with
-                         half the z values per block, four / three blocks per SM */
+                         half the z values per block, four / three blocks per SM; 4 (lengths
+                         384 and up): variant 1 with the last inverse transform pass and the
+                         first forward pass fused into the products */
     int pc_partitions; /* the fused steps-2-5 kernel solves each banded system (Sec. 3.2) as
                          two partitions, rows [0, N_r/2) and [N_r/2, N_r), each with its own
                          pivoted LU factors, coupled through an 8 x 8 reduced system (SPIKE

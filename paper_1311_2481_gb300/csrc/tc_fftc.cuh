@@ -209,5 +209,26 @@ __device__ __forceinline__ V* passes(V* a, V* b, const V* __restrict__ tw, int z
 }
 template <int PT, bool R8> __host__ __device__ constexpr bool result_in_first() { return Plan<PT, R8>::np % 2 == 0; }
 
+// ---------------------------------------------------------------- partial plans
+// product of the radices before pass P (the NS a pass P starts from)
+template <int PT, int P, bool R8> __host__ __device__ constexpr int ns_before() {
+    int ns = 1;
+    for (int i = 0; i < P; ++i) ns *= Plan<PT, R8>::r[i];
+    return ns;
+}
+// passes P .. PEND - 1 of the plan, ping-pong from a; returns the buffer that holds the result
+// zlo, zhi: zero band of the input of pass P (used only when P == 0)
+template <int PT, int P, int PEND, int NL, int NT, bool INV, typename V, bool R8>
+__device__ __forceinline__ V* passes_range(V* a, V* b, const V* __restrict__ tw, int zlo = PT, int zhi = PT) {
+    if constexpr (P == PEND) {
+        return a;
+    } else {
+        constexpr int R = Plan<PT, R8>::r[P];
+        constexpr int NS = ns_before<PT, P, R8>();
+        pass<PT, R, NS, NL, NT, INV, V>(a, b, tw, P == 0 ? zlo : PT, P == 0 ? zhi : PT);
+        return passes_range<PT, P + 1, PEND, NL, NT, INV, V, R8>(b, a, tw, PT, PT);
+    }
+}
+
 }  // namespace cft
 }  // namespace tc

@@ -233,7 +233,9 @@ constexpr int zinv_minb() {
     return by_smem < by_threads ? (by_smem > 0 ? by_smem : 1) : by_threads;
 }
 
-template <int PZ, int L, int NT>
+// FUSE: the last pass (radix 3, NS = PZ/3) writes its outputs z = j, j + PZ/3, j + 2 PZ/3
+// straight to H1 instead of to shared memory for a separate store loop.
+template <int PZ, int L, int NT, bool FUSE = false>
 __global__ void __launch_bounds__(NT, zinv_minb<PZ, L, NT>()) k_zinv_s(const float2* __restrict__ P, float2* __restrict__ H1,
                                                int N_r, int M, int K, float kzf, const float2* __restrict__ tw,
                                                int m0) {
@@ -269,11 +271,34 @@ __global__ void __launch_bounds__(NT, zinv_minb<PZ, L, NT>()) k_zinv_s(const flo
         }
     __syncthreads();
     // the band K < q < PZ - K is zero: the first pass does not read it
-    const float2* X = cft::passes<PZ, 0, 1, L, NT, true, float2, false>(a, b, tw, K + 1, PZ - K);
+    if constexpr (FUSE) {
+        constexpr int NP = cft::Plan<PZ, false>::np;
+        static_assert(cft::Plan<PZ, false>::r[NP - 1] == 3, "FUSE needs a plan that ends with radix 3");
+        const float2* X = cft::passes_range<PZ, 0, NP - 1, L, NT, true, float2, false>(a, b, tw, K + 1, PZ - K);
+        constexpr int NB3 = PZ / 3;
+        for (int it = threadIdx.x; it < L * NB3; it += NT) {
+            const int l = it / NB3;
+            const int j = it - l * NB3;
+            const float2* src = X + l * LP;
+            float2 v[3];
 #pragma unroll
-    for (int l = 0; l < L; ++l) {
-        float2* dst = H1 + (((size_t)(g * L + l) * N_r + r) * (M + 1) + m) * PZ;
-        for (int z = threadIdx.x; z < PZ; z += NT) dst[z] = X[l * LP + cft::pd(z)];
+            for (int q = 0; q < 3; ++q) v[q] = src[cft::pd(j + q * NB3)];
+            if (j) {
+#pragma unroll
+                for (int q = 1; q < 3; ++q) v[q] = cft::vmul(v[q], __ldg(&tw[q * j]));
+            }
+            cft::dftR<3, true>(v);
+            float2* dst = H1 + (((size_t)(g * L + l) * N_r + r) * (M + 1) + m) * PZ;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) dst[j + q * NB3] = v[q];
+        }
+    } else {
+        const float2* X = cft::passes<PZ, 0, 1, L, NT, true, float2, false>(a, b, tw, K + 1, PZ - K);
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            float2* dst = H1 + (((size_t)(g * L + l) * N_r + r) * (M + 1) + m) * PZ;
+            for (int z = threadIdx.x; z < PZ; z += NT) dst[z] = X[l * LP + cft::pd(z)];
+        }
     }
 }
 
@@ -392,7 +417,9 @@ __global__ void __launch_bounds__(256) k_zfwd32(const float2* __restrict__ H2, d
 }
 
 // compile-time length PZ, LF components per block
-template <int PZ, int LF, int NT>
+// FUSE: the first pass (NS = 1, no twiddles) reads its inputs z = j + q PZ/R straight from H2
+// instead of from a separate load into shared memory.
+template <int PZ, int LF, int NT, bool FUSE = false>
 __global__ void __launch_bounds__(NT) k_zfwd_s(const float2* __restrict__ H2, double2* __restrict__ N,
                                                int N_r, int M, int K, float scale, const float2* __restrict__ tw,
                                                const double2* __restrict__ u, const double* __restrict__ rnodes,
@@ -413,7 +440,26 @@ __global__ void __launch_bounds__(NT) k_zfwd_s(const float2* __restrict__ H2, do
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
     constexpr int NQ = (PZ + NT - 1) / NT;
-    {
+    const float2* X;
+    if constexpr (FUSE) {
+        constexpr int NP = cft::Plan<PZ, false>::np;
+        constexpr int R0 = cft::Plan<PZ, false>::r[0];
+        constexpr int NB0 = PZ / R0;
+        for (int idx = threadIdx.x; idx < LF * NB0; idx += NT) {
+            const int l = idx / NB0;
+            const int j = idx - l * NB0;
+            const float2* src = h + (size_t)(cg * LF + l) * fstride;
+            float2 v[R0];
+#pragma unroll
+            for (int q = 0; q < R0; ++q) v[q] = src[j + q * NB0];
+            cft::dftR<R0, false>(v);
+#pragma unroll
+            for (int q = 0; q < R0; ++q) a[l * LP + cft::pd(j * R0 + q)] = v[q];
+        }
+        if (threadIdx.x == 0) mean_flow_coeffs(u, rnodes, w1, col0, r, m, M, K, S, mp, s_cf, s_mf);
+        __syncthreads();
+        X = cft::passes_range<PZ, 1, NP, LF, NT, false, float2, false>(a, b, tw);
+    } else {
         float2 vals[LF][NQ];
 #pragma unroll
         for (int l = 0; l < LF; ++l)
@@ -429,10 +475,10 @@ __global__ void __launch_bounds__(NT) k_zfwd_s(const float2* __restrict__ H2, do
                 const int z = threadIdx.x + i * NT;
                 if (z < PZ) a[l * LP + cft::pd(z)] = vals[l][i];
             }
+        if (threadIdx.x == 0) mean_flow_coeffs(u, rnodes, w1, col0, r, m, M, K, S, mp, s_cf, s_mf);
+        __syncthreads();
+        X = cft::passes<PZ, 0, 1, LF, NT, false, float2, false>(a, b, tw);
     }
-    if (threadIdx.x == 0) mean_flow_coeffs(u, rnodes, w1, col0, r, m, M, K, S, mp, s_cf, s_mf);
-    __syncthreads();
-    const float2* X = cft::passes<PZ, 0, 1, LF, NT, false, float2, false>(a, b, tw);
     const size_t e0 = ((size_t)r * (M + 1) + m) * nk;
     // one thread per k for all LF components of the block
     for (int kk = threadIdx.x; kk < nk; kk += NT) {
@@ -448,31 +494,43 @@ __global__ void __launch_bounds__(NT) k_zfwd_s(const float2* __restrict__ H2, do
 
 namespace {
 
-template <int PZ, int L, int LF, int NT>
-tc_status run_zpasses_s(tc_plan* p, const float2* P, float2* H1, const float2* H2, const double2* u, double2* N,
+template <int PZ, int L, int LF, int NT, bool FUSE>
+tc_status run_zpasses_f(tc_plan* p, const float2* P, float2* H1, const float2* H2, const double2* u, double2* N,
                         cudaStream_t s, bool inverse, int ma, int mb) {
     constexpr int LP = cft::padded<PZ>();
     const int mc = mb - ma;
     if (inverse) {
         const size_t sm = (size_t)2 * L * LP * sizeof(float2);
-        TC_CUDA(p, cudaFuncSetAttribute(k_zinv_s<PZ, L, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        auto kern = k_zinv_s<PZ, L, NT, FUSE>;
+        TC_CUDA(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int slot = prof_begin(p, kKZinv32, s);
-        k_zinv_s<PZ, L, NT><<<p->N_r * mc * (9 / L), NT, sm, s>>>(P, H1, p->N_r, p->M, p->K, (float)p->k_z,
-                                                                 p->d_tw_z32, ma);
+        kern<<<p->N_r * mc * (9 / L), NT, sm, s>>>(P, H1, p->N_r, p->M, p->K, (float)p->k_z, p->d_tw_z32, ma);
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_zinv_s");
     } else {
         const size_t sm = (size_t)2 * LF * LP * sizeof(float2);
-        TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_s<PZ, LF, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        auto kern = k_zfwd_s<PZ, LF, NT, FUSE>;
+        TC_CUDA(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const float scale = (float)(1.0 / ((double)p->P_t * (double)p->P_z));
         const int slot = prof_begin(p, kKZfwd32, s);
-        k_zfwd_s<PZ, LF, NT><<<p->N_r * mc * (3 / LF), NT, sm, s>>>(H2, N, p->N_r, p->M, p->K, scale,
-                                                                   p->d_tw_z32, u, p->d_r, p->d_w1,
-                                                                   p->d_col0, (double)p->m_p, ma, mc);
+        kern<<<p->N_r * mc * (3 / LF), NT, sm, s>>>(H2, N, p->N_r, p->M, p->K, scale, p->d_tw_z32, u, p->d_r,
+                                                   p->d_w1, p->d_col0, (double)p->m_p, ma, mc);
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_zfwd_s");
     }
     return TC_OK;
+}
+
+// The inverse pass always writes from its fused last pass (measured 4-12% faster at
+// P_z = 384 ... 1536 on GB300, bit-identical).  The forward pass reads through its fused first
+// pass only when that pass keeps every thread busy (LF PZ / R0 >= NT: P_z = 1536, 5% faster);
+// with fewer butterflies than threads it measured 6-8% slower (P_z = 768).
+template <int PZ, int L, int LF, int NT>
+tc_status run_zpasses_s(tc_plan* p, const float2* P, float2* H1, const float2* H2, const double2* u, double2* N,
+                        cudaStream_t s, bool inverse, int ma, int mb) {
+    constexpr bool fuse_fwd = LF * (PZ / cft::Plan<PZ, false>::r[0]) >= NT;
+    if (inverse) return run_zpasses_f<PZ, L, LF, NT, true>(p, P, H1, H2, u, N, s, true, ma, mb);
+    return run_zpasses_f<PZ, L, LF, NT, fuse_fwd>(p, P, H1, H2, u, N, s, false, ma, mb);
 }
 
 // length-specialised z passes over m in [ma, mb); TC_ERR_ARG if P_z has no compile-time plan

@@ -632,7 +632,7 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     p->thr_theta = choose_threads(rt, 6 * p->zt, p->zt + (p->zt + 1) / 2);
     p->thr_zfwd = choose_threads(rz, p->zfwd_lines, 0);
     if (o.theta_zt < 0 || o.theta_zt > 64 || o.pc_modes < 0 || o.pc_modes > 32 || o.pc_split < -1 || o.pc_split > 1 ||
-        o.theta_variant < 0 || o.theta_variant > 3 || o.pc_partitions < 0 || o.pc_partitions > 2) {
+        o.theta_variant < 0 || o.theta_variant > 4 || o.pc_partitions < 0 || o.pc_partitions > 2) {
         delete p;
         return TC_ERR_ARG;
     }

@@ -52,7 +52,12 @@ __device__ __forceinline__ V imul(V a, typename Elem<V>::T s) { return vmk<V>(-s
 // Phase 0: lines (u_r, u_t) and (u_z, d_r u_z); phase 1: (d_r u_r, d_r u_t) and
 // (d_t u_r, d_t u_t); phase 2: (d_z u_r, d_z u_t) and (d_t u_z, d_z u_z); then the forward
 // transform of N_r + i N_t (one line per z) and of N_z (two z per line).
-template <typename V, int PT, int ZT, int NT, int MINB, bool R8>
+// FUSE (plans whose last pass is radix 3): the last inverse pass feeds the products from
+// registers instead of storing its lines and reading them back: a thread takes the radix-3
+// butterfly j of both lines of a z, whose outputs are the points theta = j, j + PT/3,
+// j + 2 PT/3 of that z, and those points are its own in every phase.  Likewise the first
+// forward pass (NS = 1) reads N_r + i N_t and N_z from the per-point arrays directly.
+template <typename V, int PT, int ZT, int NT, int MINB, bool R8, bool FUSE = false>
 __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, V* __restrict__ H2,
                                                       const double* __restrict__ irn, int N_r, int M, int Pz,
                                                       double mp, const V* __restrict__ tw,
@@ -63,6 +68,8 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, 
     constexpr int NLF = ZT + (ZT + 1) / 2;  // lines of the forward transform
     constexpr int NPT = ZT * PT;           // physical points of the block
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NP = Plan<PT, R8>::np;
+    static_assert(!FUSE || Plan<PT, R8>::r[NP - 1] == 3, "FUSE needs a plan that ends with radix 3");
     V* A = reinterpret_cast<V*>(smem_raw);
     V* B = A + NL * LP;
     // per physical point: Ua = (u_r, u_t / r), Ub = (u_z, N_z), Nn = (N_r, N_t); each point is
@@ -82,6 +89,30 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, 
     const T ds = sizeof(V) == 8 ? (T)dsc[r] : (T)1, ids = (T)1 / ds;
     const int zi = threadIdx.x % ZT;        // z of this thread in the load and store loops
     const int mstep = NT / ZT;
+    // one phase's products at point pt from the two physical lines' values p0, p1
+    auto products = [&](int phase, int pt, V p0, V p1) {
+        if (phase == 0) {
+            const T utr = p0.y * ir;
+            Ua[pt] = vmk<V>(p0.x, utr);
+            Ub[pt] = vmk<V>(p1.x, p0.x * (p1.y * ids));              // N_z = u_r d_r u_z
+            Nn[pt] = vmk<V>(-p0.y * utr, utr * p0.x);                // curvature terms
+        } else if (phase == 1) {
+            const V a = Ua[pt];
+            V n = Nn[pt];
+            n.x += a.x * p0.x + a.y * p1.x;
+            n.y += a.x * p0.y + a.y * p1.y;
+            Nn[pt] = n;
+        } else {
+            const V a = Ua[pt];
+            V b = Ub[pt];
+            V n = Nn[pt];
+            n.x += b.x * p0.x;
+            n.y += b.x * p0.y;
+            Nn[pt] = n;
+            b.y += a.y * p1.x + b.x * p1.y;
+            Ub[pt] = b;
+        }
+    };
 
 #pragma unroll 1
     for (int phase = 0; phase < 3; ++phase) {
@@ -145,53 +176,91 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, 
         }
         __syncthreads();
         // the band M < p < PT - M of every line is zero: the first pass does not read it
-        const V* X = passes<PT, 0, 1, NL, NT, true, V, R8>(A, B, tw, M + 1, PT - M);
-        for (int pt = threadIdx.x; pt < NPT; pt += NT) {
-            const int z = pt / PT;
-            const int th = pt - z * PT;
-            const V p0 = X[(2 * z) * LP + pd(th)];
-            const V p1 = X[(2 * z + 1) * LP + pd(th)];
-            if (phase == 0) {
-                const T utr = p0.y * ir;
-                Ua[pt] = vmk<V>(p0.x, utr);
-                Ub[pt] = vmk<V>(p1.x, p0.x * (p1.y * ids));              // N_z = u_r d_r u_z
-                Nn[pt] = vmk<V>(-p0.y * utr, utr * p0.x);                // curvature terms
-            } else if (phase == 1) {
-                const V a = Ua[pt];
-                V n = Nn[pt];
-                n.x += a.x * p0.x + a.y * p1.x;
-                n.y += a.x * p0.y + a.y * p1.y;
-                Nn[pt] = n;
-            } else {
-                const V a = Ua[pt];
-                V b = Ub[pt];
-                V n = Nn[pt];
-                n.x += b.x * p0.x;
-                n.y += b.x * p0.y;
-                Nn[pt] = n;
-                b.y += a.y * p1.x + b.x * p1.y;
-                Ub[pt] = b;
+        if constexpr (FUSE) {
+            // all passes but the last, then the last radix-3 pass (NS = PT/3, unit twiddle
+            // step) on both lines of each z with the products taken from its outputs
+            const V* X = passes_range<PT, 0, NP - 1, NL, NT, true, V, R8>(A, B, tw, M + 1, PT - M);
+            constexpr int NB3 = PT / 3;
+            for (int it = threadIdx.x; it < ZT * NB3; it += NT) {
+                const int z = it / NB3;
+                const int j = it - z * NB3;
+                const V* s0 = X + (2 * z) * LP;
+                const V* s1 = s0 + LP;
+                V a[3], b[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    a[q] = s0[pd(j + q * NB3)];
+                    b[q] = s1[pd(j + q * NB3)];
+                }
+                if (j) {
+#pragma unroll
+                    for (int q = 1; q < 3; ++q) {
+                        const V w = __ldg(&tw[q * j]);
+                        a[q] = vmul(a[q], w);
+                        b[q] = vmul(b[q], w);
+                    }
+                }
+                dftR<3, true>(a);
+                dftR<3, true>(b);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) products(phase, z * PT + j + q * NB3, a[q], b[q]);
             }
+            __syncthreads();   // the next fill overwrites the lines
+        } else {
+            const V* X = passes<PT, 0, 1, NL, NT, true, V, R8>(A, B, tw, M + 1, PT - M);
+            for (int pt = threadIdx.x; pt < NPT; pt += NT) {
+                const int z = pt / PT;
+                const int th = pt - z * PT;
+                products(phase, pt, X[(2 * z) * LP + pd(th)], X[(2 * z + 1) * LP + pd(th)]);
+            }
+            if (result_in_first<PT, R8>()) __syncthreads();   // the next fill overwrites X
         }
-        if (result_in_first<PT, R8>()) __syncthreads();   // the next fill overwrites X
     }
 
     // forward transform: line z holds N_r + i N_t, line ZT + z/2 holds N_z of two z values
-    for (int pt = threadIdx.x; pt < NPT; pt += NT) {
-        const int z = pt / PT;
-        const int th = pt - z * PT;
-        A[z * LP + pd(th)] = Nn[pt];
-        T* zl = reinterpret_cast<T*>(A + (ZT + z / 2) * LP + pd(th));
-        const T nz = Ub[pt].y;
-        if (z & 1) {
-            zl[1] = nz;
-        } else {
-            zl[0] = nz;
-            if (z + 1 == ZT) zl[1] = 0;
+    const V* Y;
+    if constexpr (FUSE) {
+        // first forward pass (NS = 1, no twiddles) straight from the per-point arrays
+        constexpr int R0 = Plan<PT, R8>::r[0];
+        constexpr int NB0 = PT / R0;
+        for (int idx = threadIdx.x; idx < NLF * NB0; idx += NT) {
+            const int line = idx / NB0;
+            const int j = idx - line * NB0;
+            V v[R0];
+#pragma unroll
+            for (int q = 0; q < R0; ++q) {
+                const int th = j + q * NB0;
+                if (line < ZT) {
+                    v[q] = Nn[line * PT + th];
+                } else {
+                    const int z = 2 * (line - ZT);
+                    v[q] = vmk<V>(Ub[z * PT + th].y, z + 1 < ZT ? Ub[(z + 1) * PT + th].y : (T)0);
+                }
+            }
+            dftR<R0, false>(v);
+            V* dst = A + line * LP;
+#pragma unroll
+            for (int q = 0; q < R0; ++q) dst[pd(j * R0 + q)] = v[q];
         }
+        __syncthreads();
+        Y = passes_range<PT, 1, NP, NLF, NT, false, V, R8>(A, B, tw);
+    } else {
+        for (int pt = threadIdx.x; pt < NPT; pt += NT) {
+            const int z = pt / PT;
+            const int th = pt - z * PT;
+            A[z * LP + pd(th)] = Nn[pt];
+            T* zl = reinterpret_cast<T*>(A + (ZT + z / 2) * LP + pd(th));
+            const T nz = Ub[pt].y;
+            if (z & 1) {
+                zl[1] = nz;
+            } else {
+                zl[0] = nz;
+                if (z + 1 == ZT) zl[1] = 0;
+            }
+        }
+        __syncthreads();
+        Y = passes<PT, 0, 1, NLF, NT, false, V, R8>(A, B, tw);
     }
-    __syncthreads();
-    const V* Y = passes<PT, 0, 1, NLF, NT, false, V, R8>(A, B, tw);
     for (int m = (int)threadIdx.x / ZT; m <= M; m += mstep) {
         const int mneg = m ? PT - m : 0;
         const V Q = Y[zi * LP + pd(m)];
@@ -212,11 +281,11 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, 
 
 namespace {
 
-template <typename V, int PT, int ZT, int NT, int MINB, bool R8>
+template <typename V, int PT, int ZT, int NT, int MINB, bool R8, bool FUSE = false>
 tc_status run_theta_s(tc_plan* p, const V* H1, V* H2, const V* tw, cudaStream_t s) {
     constexpr int LP = padded<PT>();
     const size_t sm = ((size_t)2 * 2 * ZT * LP + (size_t)3 * ZT * PT) * sizeof(V);
-    auto kern = k_theta_s<V, PT, ZT, NT, MINB, R8>;
+    auto kern = k_theta_s<V, PT, ZT, NT, MINB, R8, FUSE>;
     TC_CUDA(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int slot = prof_begin(p, sizeof(V) == 8 ? kKTheta32 : kKTheta, s);
     kern<<<p->N_r * (p->P_z / ZT), NT, sm, s>>>(H1, H2, p->d_ir, p->N_r, p->M, p->P_z, (double)p->m_p, tw,
@@ -228,17 +297,24 @@ tc_status run_theta_s(tc_plan* p, const V* H1, V* H2, const V* tw, cudaStream_t 
 
 // FP32 launch shapes per length: variant 1 radices <= 16, Z z values per block, 2 blocks per
 // SM; variants 2 and 3 radices <= 8 (64 / 76 registers), half the z values per block, 4 / 3
-// blocks per SM.  Default (0): variant 2 up to P_theta = 96, where occupancy decides, and
-// variant 1 beyond, where the extra pass of the radix-8 plan costs more (measured on GB300:
-// 0.057 vs 0.082 ms at P_theta = 96; 14.1 vs 18.5 ms at 768)
+// blocks per SM; variant 4 is variant 1 with the last inverse pass and the first forward
+// pass fused into the products (FUSE), for lengths 384 and up.  Default (0): variant 2 up to
+// P_theta = 96, where occupancy decides; variant 1 at 192; variant 4 from 384 on, where the
+// extra pass of the radix-8 plan costs more (0.057 vs 0.082 ms at P_theta = 96; 14.1 vs
+// 18.5 ms at 768) and the fusion saves 4-11% (13.5 -> 12.0 ms at 768, N_r = 256), with
+// bit-identical results.
+
 template <int PT, int Z, int NT>
 tc_status theta_s32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t s) {
     const float2* tw = p->d_tw_t32;
     constexpr int Zh = Z > 1 ? Z / 2 : 1;
-    const int v = p->theta_variant ? p->theta_variant : (PT <= 96 ? 2 : 1);
+    const int v = p->theta_variant ? p->theta_variant : (PT <= 96 ? 2 : PT >= 384 ? 4 : 1);
     switch (v) {
         case 2: return run_theta_s<float2, PT, Zh, NT, (NT > 256 ? 3 : 4), true>(p, H1, H2, tw, s);
         case 3: return run_theta_s<float2, PT, Zh, NT, (NT > 256 ? 2 : 3), true>(p, H1, H2, tw, s);
+        case 4:
+            if constexpr (PT >= 384) return run_theta_s<float2, PT, Z, NT, 2, false, true>(p, H1, H2, tw, s);
+            return run_theta_s<float2, PT, Z, NT, 2, false>(p, H1, H2, tw, s);
         default: return run_theta_s<float2, PT, Z, NT, 2, false>(p, H1, H2, tw, s);
     }
 }
@@ -284,6 +360,8 @@ tc_status launch_theta_s(tc_plan* p, const float2* H1, float2* H2, cudaStream_t 
 tc_status launch_theta_s64(tc_plan* p, const double2* H1, double2* H2, cudaStream_t s) {
     if (theta_s_zt(p, true) == 0) return TC_ERR_ARG;
     const double2* tw = p->d_tw_t;
+    // the FUSE form measured no faster with FP64 lines (0.4425 vs 0.4445 ms at the bench size):
+    // the FP64 pipe, not shared memory, bounds this kernel
     switch (p->P_t) {
         case 96: return run_theta_s<double2, 96, 4, 128, 3, true>(p, H1, H2, tw, s);
         case 192: return run_theta_s<double2, 192, 2, 128, 3, true>(p, H1, H2, tw, s);

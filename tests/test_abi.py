@@ -115,7 +115,7 @@ def test_plan_options_validated(lib):
     the plan without the two-partition form (its host solve then reports TC_ERR_STATE)."""
     L = 2 * math.pi / 3.16
     args = (24, 4, 4, 1, 0.5, 50.0, 0.0, L, 1e-3)
-    for kw in (dict(pc_partitions=3), dict(pc_partitions=-1), dict(pc_split=2), dict(theta_variant=4),
+    for kw in (dict(pc_partitions=3), dict(pc_partitions=-1), dict(pc_split=2), dict(theta_variant=5),
                dict(pc_modes=33)):
         with pytest.raises(tc.TCError) as e:
             tc.Plan(*args, host_only=True, **kw)

@@ -303,7 +303,7 @@ def test_mixed_theta_pass_lengths(M, K):
     ref = O.nonlinear(ops, u)
     nrm = np.linalg.norm(O.nonlinear(ops, _mean_removed(ops, u)))
     got = {}
-    for zt, variant in ((0, 0), (1, 0), (0, 2), (0, 3)):
+    for zt, variant in ((0, 0), (1, 0), (0, 1), (0, 2), (0, 3), (0, 4)):
         plan = tc.Plan(**cfg, precision=tc.TC_MIXED, theta_zt=zt, no_adjoint=True, theta_variant=variant)
         got[zt, variant] = host(plan.nonlinear(dev(u)))
         err = np.linalg.norm(got[zt, variant] - ref)
