@@ -489,6 +489,43 @@ def largest_mixed(tc, torch, I, dev, steps=3):
             "energy_growth": d.energy / e_start}
 
 
+def adjoint_last50(tc, torch, I, dev, n_total=100, n_adj=50, checkpoint=10):
+    """The largest workload's adjoint form at the largest size where it fits one GB300: the
+    quasi-Keplerian flow at N_r = 256, M = 256, K = 512 in the mixed form, n_total steps, and
+    the gradient of the final perturbation energy with respect to the state n_adj steps
+    before the end through the FP64 adjoint, checkpointed (restarted cold at that state)."""
+    from paper_1311_2481_gb300 import adjoint as A
+    cfg = {**CFG4, "dt": cfl_dt(CFG4)}
+    torch.cuda.reset_peak_memory_stats()
+    plan = tc.Plan(**cfg, precision=tc.TC_MIXED, device=dev)
+    r = plan.nodes()
+    u0 = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"],
+                                          cfg["Re_o"], kind="broadband", amp=0.05, seed=42)).to(dev)
+    st = tc.State(plan, u0)
+    del u0
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    plan.step(st, n_total - n_adj)
+    ev[1].record()
+    x = st.u.clone().requires_grad_(True)
+    del st
+    ev[2].record()
+    J = A.final_energy(x, plan, n_adj, checkpoint=checkpoint)
+    J.backward()
+    ev[3].record()
+    torch.cuda.synchronize()
+    t_fwd = ev[0].elapsed_time(ev[1]) / (n_total - n_adj)
+    t_fb = ev[2].elapsed_time(ev[3])
+    back = (t_fb - t_fwd * n_adj) / n_adj
+    return {"workload": f"quasi-Keplerian eta=0.5, Re_i=1e4, Re_o=sqrt(eta) Re_i, N_r=256, m=-256..256, "
+                        f"k=-512..512, mixed form, {n_total} steps, FP64 adjoint of the last {n_adj} "
+                        f"(checkpoint every {checkpoint}, restarted cold {n_adj} steps before the end)",
+            "dt": cfg["dt"], "forward_ms_per_step": t_fwd, "backward_ms_per_step": back,
+            "adjoint_to_forward_ratio": back / t_fwd, "J": float(J),
+            "grad_finite": bool(torch.isfinite(torch.view_as_real(x.grad)).all()),
+            "device_memory_gb": torch.cuda.max_memory_allocated() / 1e9}
+
+
 def run_ours(args):
     import torch
     from paper_1311_2481_gb300 import build as B
@@ -730,11 +767,13 @@ def run_ours(args):
                 out[key] = {"error": repr(exc)[:300]}
             torch.cuda.empty_cache()
     if args.largest:
-        try:
-            out["largest"] = largest_mixed(tc, torch, I, f"cuda:{local}")
-        except Exception as exc:
-            out["largest"] = {"error": repr(exc)[:300]}
-        torch.cuda.empty_cache()
+        for key, fn in (("largest", lambda: largest_mixed(tc, torch, I, f"cuda:{local}")),
+                        ("adjoint_last50", lambda: adjoint_last50(tc, torch, I, f"cuda:{local}"))):
+            try:
+                out[key] = fn()
+            except Exception as exc:
+                out[key] = {"error": repr(exc)[:300]}
+            torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -811,7 +850,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and large-size measurements")
-    ap.add_argument("--largest", action="store_true", help="also time the mixed form at N_r = 384, 384 x 1152 x 2304")
+    ap.add_argument("--largest", action="store_true",
+                    help="also time the mixed form at N_r = 384 (384 x 1152 x 2304) and the mixed form with "
+                         "the FP64 adjoint of its last 50 steps at N_r = 256")
     ap.add_argument("--workload", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the main timed step (the reported metric is the FP64 step)")
     ap.add_argument("--size", default="bench", choices=["bench", "mid", "split"],

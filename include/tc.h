@@ -205,7 +205,10 @@ tc_status tc_step(tc_plan* plan, tc_state* st, int nsteps, void* ws, void* strea
  * the steps (u, u_prev, N_prev, p; host_out->started is set).  Host buffers may be pinned or
  * pageable; pinned ones let the copies run at full link speed.  The copies and the steps are
  * enqueued on `stream`, which is synchronised before the call returns, so host_out is valid
- * on return.  host_out fields may alias host_in fields.  Errors: TC_ERR_ARG if a pointer of
+ * on return.  For a started state and nsteps >= 1, u_prev and N_prev are copied on a second,
+ * plan-owned stream while the first step's nonlinear term runs on u, and p is not copied in:
+ * no step reads p^i (p* is solved afresh and the update writes p^{i+1}).  host_out fields
+ * may alias host_in fields.  Errors: TC_ERR_ARG if a pointer of
  * dev is not device memory, a host pointer is device memory, or dev fields coincide;
  * TC_ERR_NONFINITE if these steps wrote a NaN/Inf into the state (host_out is written). */
 tc_status tc_step_host(tc_plan* plan, const tc_state* host_in, tc_state* host_out, tc_state* dev,

@@ -137,10 +137,36 @@ tc_status tc_step_host(tc_plan* plan, const tc_state* host_in, tc_state* host_ou
     void* dptr[4] = {dev->u, dev->u_prev, dev->N_prev, dev->p};
     const size_t bytes[4] = {vb, vb, vb, sb};
     for (int i = 0; i < 4; ++i) TC_TRY(check_device_ptr(plan, dptr[i], "dev state", bytes[i]));
-    for (int i = 0; i < 4; ++i)
-        TC_CUDA(plan, cudaMemcpyAsync(dptr[i], hin[i], bytes[i], cudaMemcpyHostToDevice, s));
-    dev->started = host_in->started;
-    TC_TRY(tc_step(plan, dev, nsteps, ws, stream));
+    if (host_in->started && nsteps >= 1) {
+        // A started state: the first step's nonlinear term needs u only, so u_prev and N_prev
+        // come in on a second stream while it runs; steps 2-5 wait for them.  p^i is not read
+        // by a step (p* is solved afresh and the update writes p^{i+1}), so it is not copied.
+        TC_TRY(take_nonfinite(plan));
+        TC_CUDA(plan, cudaMemcpyAsync(dptr[0], hin[0], bytes[0], cudaMemcpyHostToDevice, s));
+        if (!plan->copy_stream) {
+            TC_CUDA(plan, cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking));
+            for (cudaEvent_t& e : plan->copy_ev) TC_CUDA(plan, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        TC_CUDA(plan, cudaEventRecord(plan->copy_ev[0], s));           // after earlier work on dev
+        TC_CUDA(plan, cudaStreamWaitEvent(plan->copy_stream, plan->copy_ev[0], 0));
+        for (int i = 1; i < 3; ++i)
+            TC_CUDA(plan, cudaMemcpyAsync(dptr[i], hin[i], bytes[i], cudaMemcpyHostToDevice, plan->copy_stream));
+        TC_CUDA(plan, cudaEventRecord(plan->copy_ev[1], plan->copy_stream));
+        char* w = static_cast<char*>(ws);
+        double2* Nc = reinterpret_cast<double2*>(w + plan->ws.Ncur);
+        double2* u = static_cast<double2*>(dev->u);
+        TC_TRY(launch_nonlinear(plan, u, Nc, w, s));
+        TC_CUDA(plan, cudaStreamWaitEvent(s, plan->copy_ev[1], 0));
+        TC_TRY(launch_advance(plan, u, static_cast<double2*>(dev->u_prev), Nc, static_cast<double2*>(dev->N_prev),
+                              static_cast<double2*>(dev->p), nullptr, w, true, s));
+        dev->started = 1;
+        TC_TRY(tc_step(plan, dev, nsteps - 1, ws, stream));
+    } else {
+        for (int i = 0; i < 4; ++i)
+            TC_CUDA(plan, cudaMemcpyAsync(dptr[i], hin[i], bytes[i], cudaMemcpyHostToDevice, s));
+        dev->started = host_in->started;
+        TC_TRY(tc_step(plan, dev, nsteps, ws, stream));
+    }
     void* hout[4] = {host_out->u, host_out->u_prev, host_out->N_prev, host_out->p};
     for (int i = 0; i < 4; ++i)
         if (hout[i]) TC_CUDA(plan, cudaMemcpyAsync(hout[i], dptr[i], bytes[i], cudaMemcpyDeviceToHost, s));

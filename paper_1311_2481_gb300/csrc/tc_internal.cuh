@@ -112,6 +112,10 @@ struct tc_plan {
     int* d_nonfinite = nullptr;
     int device = -1;
     char err[512];
+    // tc_step_host: a second stream that brings u_prev and N_prev in while the first step's
+    // nonlinear term runs on u, with events for the hand-over (created on first use)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ev[2] = {nullptr, nullptr};
     // per-kernel CUDA-event tracing
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;         // event pool, two per record

@@ -477,6 +477,15 @@ void prof_end(tc_plan* p, int slot, cudaStream_t s) {
 static void free_device(tc_plan* p) {
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     p->prof_ev.clear();
+    for (cudaEvent_t& e : p->copy_ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+    if (p->copy_stream) {
+        cudaStreamDestroy(p->copy_stream);
+        p->copy_stream = nullptr;
+    }
     void* ptrs[] = {p->d_r, p->d_ir, p->d_w1, p->d_w1f, p->d_dsc, p->d_w2, p->d_col0, p->d_d1t_row, p->d_d1t_w, p->d_fac, p->d_piv,
                     p->d_fac2, p->d_piv2, p->d_spk, p->d_rinv, p->d_tw_z, p->d_tw_t, p->d_tw_z32, p->d_tw_t32};
     for (void* q : ptrs)

@@ -118,6 +118,36 @@ def test_twenty_steps_match_oracle(pc_split):
     assert rel(host(st2.u), host(st.u)) <= 1e-14
 
 
+@pytest.mark.parametrize("case", [
+    dict(N_r=20, M=4, K=6, m_p=6, eta=0.868, Re_i=458.1, L_z=2.4, dt=2e-5),   # wavy-vortex parameters
+    dict(N_r=24, M=4, K=6, eta=0.71, Re_i=300.0, Re_o=-150.0, dt=2e-4),        # counter-rotation
+    dict(N_r=12, M=4, K=4, fd_order=4),                                         # 5-point stencils
+    dict(N_r=10, M=3, K=4, fd_order=2),                                         # 3-point stencils
+    dict(N_r=18, M=4, K=6, alpha=0.0),                                          # Chebyshev limit of the nodes
+    dict(N_r=18, M=4, K=6, alpha=1.0),                                          # uniform nodes
+])
+def test_twenty_steps_match_oracle_across_parameters(case):
+    """The whole step against the oracle over 20 steps away from the default parameters:
+    m_p > 1 with the wavy-vortex geometry, a rotating outer cylinder, shorter FD stencils, and
+    both limits of the node clustering of Eq. nodeDist; fused and split steps 2-5.  p carries
+    3 phi / (2 dt), so its bound grows as the time step falls below the 1e-3 of the 20-step
+    gate."""
+    cfg = {**CFG1, **{k: v for k, v in case.items() if k in CFG1 or k == "fd_order"}}
+    opt = {k: v for k, v in case.items() if k == "alpha"}
+    prm = O.Params(**cfg, **opt)
+    ops = O.Operators(prm)
+    u0 = init(ops, amp=1e-2, mbox=min(3, prm.M), kbox=min(3, prm.K))
+    ref = O.run(ops, O.cold_state(u0), 20)
+    for pc_split in (-1, 1):
+        plan = tc.Plan(**cfg, **opt, pc_split=pc_split)
+        st = tc.State(plan, dev(u0))
+        plan.step(st, 20)
+        for name in ("u", "u_prev", "N_prev", "p"):
+            got = host(getattr(st, name))
+            tol = 1e-10 * (max(1.0, 1e-3 / cfg["dt"]) if name == "p" else 1.0)
+            assert rel(got, getattr(ref, name)) <= tol, (pc_split, name, rel(got, getattr(ref, name)))
+
+
 @pytest.mark.parametrize("pc_split", [0, 1])
 def test_step_full_size_config2(pc_split):
     ops, plan = pair(CFG2, pc_split=pc_split)
@@ -369,6 +399,32 @@ def test_mixed_twenty_steps_track_fp64():
     assert rel(got, ref.u) <= 1e-8
 
 
+def test_mixed_at_the_bench_workload_against_oracle():
+    """The mixed form at the bench workload (N_r = 64, m = -32..32, k = -64..64, Re_i = 1000,
+    Taylor-vortex-like start) over 20 steps at the largest stable dt (the stated 5e-4 halved
+    until 200 FP64 steps stay bounded: 1.5625e-5), against the oracle's FP64 steps: the
+    errors of the velocity perturbation, the velocity, the two torques and the largest
+    divergence."""
+    cfg = {**CFG2, "dt": 5e-4 / 32}
+    ops = O.Operators(O.Params(**cfg))
+    u0 = init(ops, kind="taylor", amp=1e-2)
+    ref = O.run(ops, O.cold_state(u0), 20)
+    plan = tc.Plan(**cfg, precision=tc.TC_MIXED)
+    st = tc.State(plan, dev(u0))
+    plan.step(st, 20)
+    got = host(st.u)
+    base = I.base_state(ops.r, ops.prm.M, ops.prm.K, 0.5, 1000.0, 0.0)
+    d = plan.diagnostics(st.u)
+    Ti, To = O.torque(ops, ref.u)
+    err = {"velocity_perturbation": rel(got - base, ref.u - base), "velocity": rel(got, ref.u),
+           "torque_inner": abs(d.torque_inner / Ti - 1), "torque_outer": abs(d.torque_outer / To - 1),
+           "max_div": abs(d.max_div / O.max_divergence(ops, ref.u) - 1)}
+    print("mixed vs oracle, bench workload, 20 steps:", err)
+    assert err["velocity_perturbation"] <= 1e-6 and err["velocity"] <= 1e-8, err
+    assert err["torque_inner"] <= 1e-7 and err["torque_outer"] <= 1e-7, err
+    assert err["max_div"] <= 1e-5, err
+
+
 # ------------------------------------------------------------------ tc_plan_set
 @pytest.mark.parametrize("key,value,kw", [(tc.TC_SET_PRECISION, tc.TC_MIXED, dict(precision=tc.TC_MIXED)),
                                           (tc.TC_SET_PC_SPLIT, 1, dict(pc_split=1)),
@@ -432,6 +488,21 @@ def test_step_host_matches_device_step():
         plan.step_host(work, h_in, h_out, 2)
         assert np.array_equal(h_out["u"].numpy(), want2["u"])
         assert np.array_equal(h_out["p"].numpy(), want2["p"])
+        # a started state's p^i is not read (the update writes p^{i+1}): a NaN there changes nothing
+        h_in["p"].fill_(float("nan"))
+        h_out = {"u": torch.empty_like(h_in["u"]), "p": torch.empty_like(h_in["p"])}
+        plan.step_host(tc.State(plan, dev(u0)), h_in, h_out, 2)
+        assert np.array_equal(h_out["u"].numpy(), want2["u"])
+        assert np.array_equal(h_out["p"].numpy(), want2["p"])
+    # a cold state through host memory: the history is built on the device as tc_step does
+    cold_ref = tc.State(plan, dev(u0))
+    plan.step(cold_ref, 3)
+    h_in = {"u": torch.from_numpy(u0.copy()), "u_prev": torch.zeros_like(torch.from_numpy(u0)),
+            "N_prev": torch.zeros_like(torch.from_numpy(u0)), "p": torch.zeros(plan.scalar_shape(), dtype=torch.complex128),
+            "started": False}
+    h_out = {"u": torch.empty_like(h_in["u"])}
+    plan.step_host(tc.State(plan, dev(u0)), h_in, h_out, 3)
+    assert np.array_equal(h_out["u"].numpy(), host(cold_ref.u))
     bad = {k: getattr(ref, k) for k in ("u", "u_prev", "N_prev", "p")}   # device tensors
     with pytest.raises(tc.TCError):
         plan.step_host(tc.State(plan, dev(u0)), bad, {}, 1)
