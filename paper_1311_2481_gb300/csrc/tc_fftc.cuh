@@ -161,7 +161,14 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dftR(V* v
 // one radix-R pass over NL lines of length PT: in -> out, Ns = product of earlier radices
 // Inputs at positions zlo <= p < zhi are zero and are not read (the dealiasing band of an
 // inverse transform's input; only the first pass is given a band).
-template <int PT, int R, int NS, int NL, int NT, bool INV, typename V>
+// twiddle j of the table: from shared memory (TWS, the caller copied the table there) or
+// through the read-only path from global memory
+template <bool TWS, typename V> __device__ __forceinline__ V twiddle(const V* __restrict__ tw, int j) {
+    if constexpr (TWS) return tw[j];
+    else return __ldg(&tw[j]);
+}
+
+template <int PT, int R, int NS, int NL, int NT, bool INV, typename V, bool TWS = false>
 __device__ __forceinline__ void pass(const V* in, V* out, const V* __restrict__ tw, int zlo, int zhi) {
     constexpr int NB = PT / R;
     constexpr int STEP = PT / (NS * R);
@@ -181,7 +188,7 @@ __device__ __forceinline__ void pass(const V* in, V* out, const V* __restrict__ 
         if (NS > 1 && k) {
 #pragma unroll
             for (int q = 1; q < R; ++q) {
-                V w = __ldg(&tw[q * k * STEP]);
+                V w = twiddle<TWS>(tw, q * k * STEP);
                 if (!INV) w.y = -w.y;
                 v[q] = vmul(v[q], w);
             }
@@ -196,15 +203,15 @@ __device__ __forceinline__ void pass(const V* in, V* out, const V* __restrict__ 
 
 // all passes of the plan; returns the buffer that holds the result
 // zlo, zhi: zero band of the input (first pass only); zlo = zhi = PT for none
-template <int PT, int P, int NS, int NL, int NT, bool INV, typename V, bool R8 = sizeof(V) == 16>
+template <int PT, int P, int NS, int NL, int NT, bool INV, typename V, bool R8 = sizeof(V) == 16, bool TWS = false>
 __device__ __forceinline__ V* passes(V* a, V* b, const V* __restrict__ tw, int zlo = PT, int zhi = PT) {
     if constexpr (P == Plan<PT, R8>::np) {
         return a;
     } else {
         constexpr int R = Plan<PT, R8>::r[P];
-        if constexpr (P == 0) pass<PT, R, NS, NL, NT, INV, V>(a, b, tw, zlo, zhi);
-        else pass<PT, R, NS, NL, NT, INV, V>(a, b, tw, PT, PT);
-        return passes<PT, P + 1, NS * R, NL, NT, INV, V, R8>(b, a, tw, PT, PT);
+        if constexpr (P == 0) pass<PT, R, NS, NL, NT, INV, V, TWS>(a, b, tw, zlo, zhi);
+        else pass<PT, R, NS, NL, NT, INV, V, TWS>(a, b, tw, PT, PT);
+        return passes<PT, P + 1, NS * R, NL, NT, INV, V, R8, TWS>(b, a, tw, PT, PT);
     }
 }
 template <int PT, bool R8> __host__ __device__ constexpr bool result_in_first() { return Plan<PT, R8>::np % 2 == 0; }
@@ -218,15 +225,15 @@ template <int PT, int P, bool R8> __host__ __device__ constexpr int ns_before() 
 }
 // passes P .. PEND - 1 of the plan, ping-pong from a; returns the buffer that holds the result
 // zlo, zhi: zero band of the input of pass P (used only when P == 0)
-template <int PT, int P, int PEND, int NL, int NT, bool INV, typename V, bool R8>
+template <int PT, int P, int PEND, int NL, int NT, bool INV, typename V, bool R8, bool TWS = false>
 __device__ __forceinline__ V* passes_range(V* a, V* b, const V* __restrict__ tw, int zlo = PT, int zhi = PT) {
     if constexpr (P == PEND) {
         return a;
     } else {
         constexpr int R = Plan<PT, R8>::r[P];
         constexpr int NS = ns_before<PT, P, R8>();
-        pass<PT, R, NS, NL, NT, INV, V>(a, b, tw, P == 0 ? zlo : PT, P == 0 ? zhi : PT);
-        return passes_range<PT, P + 1, PEND, NL, NT, INV, V, R8>(b, a, tw, PT, PT);
+        pass<PT, R, NS, NL, NT, INV, V, TWS>(a, b, tw, P == 0 ? zlo : PT, P == 0 ? zhi : PT);
+        return passes_range<PT, P + 1, PEND, NL, NT, INV, V, R8, TWS>(b, a, tw, PT, PT);
     }
 }
 

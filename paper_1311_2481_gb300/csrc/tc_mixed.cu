@@ -235,7 +235,7 @@ constexpr int zinv_minb() {
 
 // FUSE: the last pass (radix 3, NS = PZ/3) writes its outputs z = j, j + PZ/3, j + 2 PZ/3
 // straight to H1 instead of to shared memory for a separate store loop.
-template <int PZ, int L, int NT, bool FUSE = false>
+template <int PZ, int L, int NT, bool FUSE = false, bool TWS = false>
 __global__ void __launch_bounds__(NT, zinv_minb<PZ, L, NT>()) k_zinv_s(const float2* __restrict__ P, float2* __restrict__ H1,
                                                int N_r, int M, int K, float kzf, const float2* __restrict__ tw,
                                                int m0) {
@@ -243,6 +243,12 @@ __global__ void __launch_bounds__(NT, zinv_minb<PZ, L, NT>()) k_zinv_s(const flo
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* a = reinterpret_cast<float2*>(smem_raw);
     float2* b = a + L * LP;
+    // TWS: the twiddle table in shared memory after the two line buffers
+    float2* tws = b + L * LP;
+    if constexpr (TWS) {
+        for (int i = threadIdx.x; i < PZ; i += NT) tws[i] = tw[i];   // visible after the fill's barrier
+    }
+    const float2* twp = TWS ? tws : tw;
     constexpr int groups = 9 / L;
     const int g = blockIdx.x % groups;
     const int rm = blockIdx.x / groups;
@@ -274,7 +280,7 @@ __global__ void __launch_bounds__(NT, zinv_minb<PZ, L, NT>()) k_zinv_s(const flo
     if constexpr (FUSE) {
         constexpr int NP = cft::Plan<PZ, false>::np;
         static_assert(cft::Plan<PZ, false>::r[NP - 1] == 3, "FUSE needs a plan that ends with radix 3");
-        const float2* X = cft::passes_range<PZ, 0, NP - 1, L, NT, true, float2, false>(a, b, tw, K + 1, PZ - K);
+        const float2* X = cft::passes_range<PZ, 0, NP - 1, L, NT, true, float2, false, TWS>(a, b, twp, K + 1, PZ - K);
         constexpr int NB3 = PZ / 3;
         for (int it = threadIdx.x; it < L * NB3; it += NT) {
             const int l = it / NB3;
@@ -285,7 +291,7 @@ __global__ void __launch_bounds__(NT, zinv_minb<PZ, L, NT>()) k_zinv_s(const flo
             for (int q = 0; q < 3; ++q) v[q] = src[cft::pd(j + q * NB3)];
             if (j) {
 #pragma unroll
-                for (int q = 1; q < 3; ++q) v[q] = cft::vmul(v[q], __ldg(&tw[q * j]));
+                for (int q = 1; q < 3; ++q) v[q] = cft::vmul(v[q], cft::twiddle<TWS>(twp, q * j));
             }
             cft::dftR<3, true>(v);
             float2* dst = H1 + (((size_t)(g * L + l) * N_r + r) * (M + 1) + m) * PZ;
@@ -293,7 +299,7 @@ __global__ void __launch_bounds__(NT, zinv_minb<PZ, L, NT>()) k_zinv_s(const flo
             for (int q = 0; q < 3; ++q) dst[j + q * NB3] = v[q];
         }
     } else {
-        const float2* X = cft::passes<PZ, 0, 1, L, NT, true, float2, false>(a, b, tw, K + 1, PZ - K);
+        const float2* X = cft::passes<PZ, 0, 1, L, NT, true, float2, false, TWS>(a, b, twp, K + 1, PZ - K);
 #pragma unroll
         for (int l = 0; l < L; ++l) {
             float2* dst = H1 + (((size_t)(g * L + l) * N_r + r) * (M + 1) + m) * PZ;
@@ -419,7 +425,7 @@ __global__ void __launch_bounds__(256) k_zfwd32(const float2* __restrict__ H2, d
 // compile-time length PZ, LF components per block
 // FUSE: the first pass (NS = 1, no twiddles) reads its inputs z = j + q PZ/R straight from H2
 // instead of from a separate load into shared memory.
-template <int PZ, int LF, int NT, bool FUSE = false>
+template <int PZ, int LF, int NT, bool FUSE = false, bool TWS = false>
 __global__ void __launch_bounds__(NT) k_zfwd_s(const float2* __restrict__ H2, double2* __restrict__ N,
                                                int N_r, int M, int K, float scale, const float2* __restrict__ tw,
                                                const double2* __restrict__ u, const double* __restrict__ rnodes,
@@ -431,6 +437,11 @@ __global__ void __launch_bounds__(NT) k_zfwd_s(const float2* __restrict__ H2, do
     __shared__ double s_mf[3];
     float2* a = reinterpret_cast<float2*>(smem_raw);
     float2* b = a + LF * LP;
+    float2* tws = b + LF * LP;   // TWS: the twiddle table in shared memory
+    if constexpr (TWS) {
+        for (int i = threadIdx.x; i < PZ; i += NT) tws[i] = tw[i];   // visible after the load barrier
+    }
+    const float2* twp = TWS ? tws : tw;
     constexpr int groups = 3 / LF;
     const int cg = blockIdx.x % groups;
     const int m = m0 + (blockIdx.x / groups) % mcnt;
@@ -458,7 +469,7 @@ __global__ void __launch_bounds__(NT) k_zfwd_s(const float2* __restrict__ H2, do
         }
         if (threadIdx.x == 0) mean_flow_coeffs(u, rnodes, w1, col0, r, m, M, K, S, mp, s_cf, s_mf);
         __syncthreads();
-        X = cft::passes_range<PZ, 1, NP, LF, NT, false, float2, false>(a, b, tw);
+        X = cft::passes_range<PZ, 1, NP, LF, NT, false, float2, false, TWS>(a, b, twp);
     } else {
         float2 vals[LF][NQ];
 #pragma unroll
@@ -477,7 +488,7 @@ __global__ void __launch_bounds__(NT) k_zfwd_s(const float2* __restrict__ H2, do
             }
         if (threadIdx.x == 0) mean_flow_coeffs(u, rnodes, w1, col0, r, m, M, K, S, mp, s_cf, s_mf);
         __syncthreads();
-        X = cft::passes<PZ, 0, 1, LF, NT, false, float2, false>(a, b, tw);
+        X = cft::passes<PZ, 0, 1, LF, NT, false, float2, false, TWS>(a, b, twp);
     }
     const size_t e0 = ((size_t)r * (M + 1) + m) * nk;
     // one thread per k for all LF components of the block
@@ -494,22 +505,22 @@ __global__ void __launch_bounds__(NT) k_zfwd_s(const float2* __restrict__ H2, do
 
 namespace {
 
-template <int PZ, int L, int LF, int NT, bool FUSE>
+template <int PZ, int L, int LF, int NT, bool FUSE, bool TWS>
 tc_status run_zpasses_f(tc_plan* p, const float2* P, float2* H1, const float2* H2, const double2* u, double2* N,
                         cudaStream_t s, bool inverse, int ma, int mb) {
     constexpr int LP = cft::padded<PZ>();
     const int mc = mb - ma;
     if (inverse) {
-        const size_t sm = (size_t)2 * L * LP * sizeof(float2);
-        auto kern = k_zinv_s<PZ, L, NT, FUSE>;
+        const size_t sm = ((size_t)2 * L * LP + (TWS ? PZ : 0)) * sizeof(float2);
+        auto kern = k_zinv_s<PZ, L, NT, FUSE, TWS>;
         TC_CUDA(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int slot = prof_begin(p, kKZinv32, s);
         kern<<<p->N_r * mc * (9 / L), NT, sm, s>>>(P, H1, p->N_r, p->M, p->K, (float)p->k_z, p->d_tw_z32, ma);
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_zinv_s");
     } else {
-        const size_t sm = (size_t)2 * LF * LP * sizeof(float2);
-        auto kern = k_zfwd_s<PZ, LF, NT, FUSE>;
+        const size_t sm = ((size_t)2 * LF * LP + (TWS ? PZ : 0)) * sizeof(float2);
+        auto kern = k_zfwd_s<PZ, LF, NT, FUSE, TWS>;
         TC_CUDA(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const float scale = (float)(1.0 / ((double)p->P_t * (double)p->P_z));
         const int slot = prof_begin(p, kKZfwd32, s);
@@ -529,8 +540,11 @@ template <int PZ, int L, int LF, int NT>
 tc_status run_zpasses_s(tc_plan* p, const float2* P, float2* H1, const float2* H2, const double2* u, double2* N,
                         cudaStream_t s, bool inverse, int ma, int mb) {
     constexpr bool fuse_fwd = LF * (PZ / cft::Plan<PZ, false>::r[0]) >= NT;
-    if (inverse) return run_zpasses_f<PZ, L, LF, NT, true>(p, P, H1, H2, u, N, s, true, ma, mb);
-    return run_zpasses_f<PZ, L, LF, NT, fuse_fwd>(p, P, H1, H2, u, N, s, false, ma, mb);
+    // the twiddles stay on the read-only path here: a shared-memory table measured 8% slower at
+    // P_z = 768 and 26-29% slower at 1536
+    constexpr bool tws = false;
+    if (inverse) return run_zpasses_f<PZ, L, LF, NT, true, tws>(p, P, H1, H2, u, N, s, true, ma, mb);
+    return run_zpasses_f<PZ, L, LF, NT, fuse_fwd, tws>(p, P, H1, H2, u, N, s, false, ma, mb);
 }
 
 // length-specialised z passes over m in [ma, mb); TC_ERR_ARG if P_z has no compile-time plan
