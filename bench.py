@@ -489,40 +489,156 @@ def largest_mixed(tc, torch, I, dev, steps=3):
             "energy_growth": d.energy / e_start}
 
 
-def adjoint_last50(tc, torch, I, dev, n_total=100, n_adj=50, checkpoint=10):
-    """The largest workload's adjoint form at the largest size where it fits one GB300: the
-    quasi-Keplerian flow at N_r = 256, M = 256, K = 512 in the mixed form, n_total steps, and
-    the gradient of the final perturbation energy with respect to the state n_adj steps
-    before the end through the FP64 adjoint, checkpointed (restarted cold at that state)."""
-    from paper_1311_2481_gb300 import adjoint as A
-    cfg = {**CFG4, "dt": cfl_dt(CFG4)}
+def _free_device_bytes(torch):
+    """Device memory free for new tensors: the driver's free bytes plus torch's unused cache."""
+    free, _ = torch.cuda.mem_get_info()
+    return free + torch.cuda.memory_reserved() - torch.cuda.memory_allocated()
+
+
+def largest_fp64(tc, torch, I, dev, steps=2):
+    """FP64 step at the largest workload (no adjoint workspace): the transform staging runs
+    slab by slab, so the FP64 lines of 384 rows never coexist."""
+    cfg = {**CFG5, "dt": cfl_dt(CFG5)}
     torch.cuda.reset_peak_memory_stats()
-    plan = tc.Plan(**cfg, precision=tc.TC_MIXED, device=dev)
+    plan = tc.Plan(**cfg, no_adjoint=True, device=dev)
     r = plan.nodes()
     u0 = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"],
                                           cfg["Re_o"], kind="broadband", amp=0.05, seed=42)).to(dev)
     st = tc.State(plan, u0)
     del u0
+    plan.step(st, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.step(st, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": "quasi-Keplerian eta=0.5, Re_i=3e4, N_r=384, m=-384..384, k=-768..768, FP64",
+            "dt": cfg["dt"], "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+            "gdof_steps_per_s": gdof(cfg) / ms / 1e6,
+            "device_memory_gb": torch.cuda.max_memory_allocated() / 1e9,
+            "state_finite": bool(plan.diagnostics(st.u).finite)}
+
+
+def config5_adjoint(tc, torch, I, dev, n_total=100, n_adj=50, checkpoint=17):
+    """The largest workload as stated: the quasi-Keplerian flow at N_r = 384, M = 384,
+    K = 768 in the mixed form for n_total steps, and the gradient of the final perturbation
+    energy with respect to the state (u, u_prev, N_prev) n_adj steps before the end, through
+    the FP64 adjoint (adjoint.state_gradient): checkpoints every `checkpoint` steps in pinned
+    host memory, the segments reversed through as many device copies of u as fit.  Then a
+    central difference of J along the gradient's u part, through the mixed forward."""
+    from paper_1311_2481_gb300 import adjoint as A
+    cfg = {**CFG5, "dt": cfl_dt(CFG5)}
+    torch.cuda.reset_peak_memory_stats()
+    t0 = time.perf_counter()
+    plan = tc.Plan(**cfg, precision=tc.TC_MIXED, device=dev)
+    t_plan = time.perf_counter() - t0
+    r = plan.nodes()
+    u0 = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"],
+                                          cfg["Re_o"], kind="broadband", amp=0.05, seed=42)).to(dev)
+    st = tc.State(plan, u0)
+    del u0
+    field = st.u.numel() * st.u.element_size()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
     plan.step(st, n_total - n_adj)
     ev[1].record()
-    x = st.u.clone().requires_grad_(True)
-    del st
+    torch.cuda.synchronize()
+    # device copies of u for the segment reversal: what is left after the gradient's three fields
+    slots = int(max(1, min(checkpoint, (_free_device_bytes(torch) - 3 * field - (6 << 30)) // field)))
     ev[2].record()
-    J = A.final_energy(x, plan, n_adj, checkpoint=checkpoint)
-    J.backward()
+    J, bar = A.state_gradient(plan, st, n_adj, checkpoint=checkpoint, slots=slots, spill=True)
     ev[3].record()
     torch.cuda.synchronize()
     t_fwd = ev[0].elapsed_time(ev[1]) / (n_total - n_adj)
-    t_fb = ev[2].elapsed_time(ev[3])
-    back = (t_fb - t_fwd * n_adj) / n_adj
-    return {"workload": f"quasi-Keplerian eta=0.5, Re_i=1e4, Re_o=sqrt(eta) Re_i, N_r=256, m=-256..256, "
-                        f"k=-512..512, mixed form, {n_total} steps, FP64 adjoint of the last {n_adj} "
-                        f"(checkpoint every {checkpoint}, restarted cold {n_adj} steps before the end)",
-            "dt": cfg["dt"], "forward_ms_per_step": t_fwd, "backward_ms_per_step": back,
-            "adjoint_to_forward_ratio": back / t_fwd, "J": float(J),
-            "grad_finite": bool(torch.isfinite(torch.view_as_real(x.grad)).all()),
+    t_sg = ev[2].elapsed_time(ev[3])
+    back = (t_sg - t_fwd * n_adj) / n_adj
+    finite = all(bool(torch.isfinite(torch.view_as_real(t)).all()) for t in (bar.u, bar.u_prev, bar.N_prev))
+    mem = torch.cuda.max_memory_allocated() / 1e9
+    # central difference of J(u + h g_u) along g_u = dJ/du, against <g_u, g_u>
+    g = bar.u
+    del bar
+    s_u, s_up, s_N = st.u.clone(), st.u_prev.clone(), st.N_prev.clone()
+    gn2 = float(torch.sum(torch.view_as_real(g) ** 2))
+    h = 1e-2 * J / gn2        # J changes by about 1% of itself: above the mixed form's rounding
+    Js = []
+    for sg in (1.0, -1.0):
+        st.u.copy_(s_u)
+        st.u.add_(g, alpha=sg * h)
+        st.u_prev.copy_(s_up)
+        st.N_prev.copy_(s_N)
+        st.started = True
+        plan.step(st, n_adj)
+        Js.append(plan.diagnostics(st.u).energy)
+    fd = (Js[0] - Js[1]) / (2 * h)
+    return {"workload": f"quasi-Keplerian eta=0.5, Re_i=3e4, Re_o=sqrt(eta) Re_i, N_r=384, m=-384..384, "
+                        f"k=-768..768, broadband amp 0.05 (seed 42), mixed form, {n_total} steps; "
+                        f"FP64 adjoint of the last {n_adj} (gradient w.r.t. the state {n_adj} steps "
+                        f"before the end), checkpoint every {checkpoint} in pinned host memory",
+            "dt_stated": CFG5["dt"], "dt": cfg["dt"], "plan_create_s": t_plan,
+            "forward_ms_per_step": t_fwd, "state_gradient_ms": t_sg, "backward_ms_per_step": back,
+            "adjoint_to_forward_ratio": back / t_fwd, "J": J, "grad_finite": finite,
+            "u_slots": slots, "host_checkpoint_gb": -(-n_adj // checkpoint) * 3 * field / 1e9,
+            "device_memory_gb": mem,
+            "fd_along_grad": fd, "grad_norm_sq": gn2, "fd_rel_diff": abs(fd - gn2) / gn2,
+            "fd_note": "central difference of J through the mixed forward vs <g, g> from the FP64 adjoint"}
+
+
+def config5_dot_product(tc, torch, I, dev, h_scale=1.0):
+    """Dot-product test of the FP64 adjoint step at the largest workload: with s a started
+    FP64 state, x and y seeded directions (x scaled to the state's norms), compares
+    <y, dF(s)[x]> with <F^T y, x>.  dF(s)[x] = (F(s + x) - F(s - x)) / 2 exactly up to
+    rounding, F being quadratic in the state.  s and x are kept in pinned host memory."""
+    cfg = {**CFG5, "dt": cfl_dt(CFG5)}
+    torch.cuda.reset_peak_memory_stats()
+    plan = tc.Plan(**cfg, device=dev)
+    r = plan.nodes()
+    u0 = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"],
+                                          cfg["Re_o"], kind="broadband", amp=0.05, seed=42)).to(dev)
+    st = tc.State(plan, u0)
+    del u0
+    plan.step(st, 1)
+    names = ("u", "u_prev", "N_prev")
+    pin = lambda t: t.to("cpu", non_blocking=False).pin_memory()   # noqa: E731
+    s = [pin(getattr(st, k)) for k in names]
+    gen = torch.Generator(device=dev)
+    x = []
+    for i, k in enumerate(names):
+        gen.manual_seed(1000 + i)
+        v = torch.randn(st.u.shape, dtype=torch.complex128, device=dev, generator=gen)
+        v.mul_(h_scale * float(torch.linalg.vector_norm(getattr(st, k))) / float(torch.linalg.vector_norm(v)))
+        x.append(pin(v))
+        del v
+    # F(s + x) -> kept on the device; F(s - x) in st
+    fp = []
+    for sg in (1.0, -1.0):
+        for k, a, b in zip(names, s, x):
+            t = getattr(st, k)
+            t.copy_(a)
+            t.add_(b.to(dev), alpha=sg)
+        st.started = True
+        plan.step(st, 1)
+        if sg > 0:
+            fp = [getattr(st, k).clone() for k in names]
+    tl = [(a - getattr(st, k)) / 2 for a, k in zip(fp, names)]   # dF(s)[x]
+    del fp
+    ys = []
+    for i in range(3):
+        gen.manual_seed(2000 + i)
+        ys.append(torch.randn(st.u.shape, dtype=torch.complex128, device=dev, generator=gen))
+    lhs = sum(float(torch.sum(torch.view_as_real(a) * torch.view_as_real(b))) for a, b in zip(ys, tl))
+    del tl
+    for k, a in zip(names, s):
+        getattr(st, k).copy_(a)
+    st.started = True
+    bar = tc.StateBar(*ys)
+    plan.adjoint_step(st, bar)
+    rhs = sum(float(torch.sum(torch.view_as_real(getattr(bar, k)) * torch.view_as_real(b.to(dev))))
+              for k, b in zip(names, x))
+    return {"workload": "N_r=384, m=-384..384, k=-768..768, FP64 step and adjoint step at a started "
+                        "state (one step from the broadband initial state)",
+            "lhs": lhs, "rhs": rhs, "rel_diff": abs(lhs - rhs) / abs(rhs),
             "device_memory_gb": torch.cuda.max_memory_allocated() / 1e9}
 
 
@@ -768,7 +884,9 @@ def run_ours(args):
             torch.cuda.empty_cache()
     if args.largest:
         for key, fn in (("largest", lambda: largest_mixed(tc, torch, I, f"cuda:{local}")),
-                        ("adjoint_last50", lambda: adjoint_last50(tc, torch, I, f"cuda:{local}"))):
+                        ("largest_fp64", lambda: largest_fp64(tc, torch, I, f"cuda:{local}")),
+                        ("config5_adjoint", lambda: config5_adjoint(tc, torch, I, f"cuda:{local}")),
+                        ("config5_dot_product", lambda: config5_dot_product(tc, torch, I, f"cuda:{local}"))):
             try:
                 out[key] = fn()
             except Exception as exc:

@@ -89,6 +89,13 @@ typedef struct {
                          pivoted LU factors, coupled through an 8 x 8 reduced system (SPIKE
                          form; the two halves run on separate lanes).  0 or 2: when N_r >= 16
                          and the fused kernel runs; 1: one pivoted banded LU per system */
+    int stage_rows;   /* radial rows per slab of the FP64 transform staging.  The transforms of
+                         the nonlinear term (Sec. 3.2 step 1) and of its adjoint act on each
+                         radial row independently, so they run slab by slab and the workspace
+                         holds the FP64 lines of one slab: 12 line sets of (M+1) P_z values per
+                         row for the FP64 forward term, 21 for the adjoint.  0: all rows while
+                         that staging stays within 4 GiB, else the most rows that do; the
+                         mixed form's FP32 forward lines always cover all rows */
 } tc_options;
 
 /* Keys of tc_plan_set: one per field of tc_options, with the same meaning and range. */
@@ -103,7 +110,8 @@ typedef enum {
     TC_SET_NO_ADJOINT = 7,
     TC_SET_PC_SPLIT = 8,
     TC_SET_THETA_VARIANT = 9,
-    TC_SET_PC_PARTITIONS = 10
+    TC_SET_PC_PARTITIONS = 10,
+    TC_SET_STAGE_ROWS = 11
 } tc_plan_key;
 
 /* Step state (Sec. 3.2): u = u^i, u_prev = u^{i-1}, N_prev = N^{i-1} (vector fields), p = p^i
@@ -232,7 +240,8 @@ typedef struct {
  * (u^i, u^{i-1}, N^{i-1}), in place.  The linear part is the transposed chain of Sec. 3.2
  * steps 2-5 (transposed banded solves and stencils); the nonlinear part is the transposed
  * linearisation of N(u) = u . grad u about fwd->u (recomputed).  Runs in FP64 for every plan
- * precision.  The three bar arrays must be distinct. */
+ * precision.  Of fwd only u and started are read (u_prev, N_prev and p may be NULL).  The
+ * three bar arrays must be distinct. */
 tc_status tc_adjoint_step(tc_plan* plan, const tc_state* fwd, tc_state_bar* bar, void* ws,
                           void* stream);
 /* Adjoint of the cold-start map u^0 -> (u^0, u^{-1}, N^{-1}) that tc_step applies to a state

@@ -4,10 +4,14 @@ tc_adjoint_start) behind a torch.autograd.Function, with checkpointing.
 
 Forward: the cold state u0 gets its AB2BD2 history (tc_step with nsteps = 0) and is
 advanced n steps; the state (u, u_prev, N_prev) is kept every `checkpoint` steps.
-Backward: each segment between checkpoints is recomputed forward from its checkpoint, its
-states kept, and the adjoint steps run backwards through it; the cold start is then
-differentiated by tc_adjoint_start.  All arithmetic runs in libtc's kernels; torch supplies
-device memory only.
+Backward: each segment between checkpoints is recomputed forward from its checkpoint, the
+velocity u of each of its steps kept (the only field an adjoint step reads), and the adjoint
+steps run backwards through it; the cold start is then differentiated by tc_adjoint_start.
+
+`state_gradient` differentiates a run from a started state with respect to that state, with
+its checkpoints in pinned host memory and a bounded number of device copies of u, for
+workloads whose states do not fit the device several times over.  All arithmetic runs in
+libtc's kernels; torch supplies device and host memory only.
 """
 from __future__ import annotations
 
@@ -25,6 +29,17 @@ def _clone_state(plan, st):
 
 def _energy(plan, u):
     return plan.diagnostics(u).energy
+
+
+class _ForwardU:
+    """The forward state an adjoint step reads: u^i only (tc_adjoint_step reads no other
+    field of it)."""
+
+    def __init__(self, u):
+        self.u = u
+
+    def c_struct(self):
+        return tc.tc_state(self.u.data_ptr(), None, None, None, 1)
 
 
 class FinalEnergy(torch.autograd.Function):
@@ -54,12 +69,12 @@ class FinalEnergy(torch.autograd.Function):
             s1 = min(s0 + C, n) if s0 + C <= n else n
             seg_end = min([s for s in starts if s > s0] + [n])
             st = _clone_state(plan, ckpts[s0])
-            states = [_clone_state(plan, st)]
+            us = [st.u.clone()]
             for _ in range(s0, seg_end - 1):
                 plan.step(st, 1)
-                states.append(_clone_state(plan, st))
-            for fwd in reversed(states):
-                plan.adjoint_step(fwd, bar)
+                us.append(st.u.clone())
+            for u in reversed(us):
+                plan.adjoint_step(_ForwardU(u), bar)
             del s1
         g = plan.adjoint_start(u0, bar)
         return g, None, None, None
@@ -68,6 +83,94 @@ class FinalEnergy(torch.autograd.Function):
 def final_energy(u0, plan, nsteps, checkpoint=20):
     """Differentiable J(u0); u0 is a complex128 CUDA tensor of the plan's vector shape."""
     return FinalEnergy.apply(u0, plan, nsteps, checkpoint)
+
+
+def _host_bytes_available():
+    """MemAvailable of this machine in bytes (None where /proc/meminfo is absent)."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        return None
+    return None
+
+
+def state_gradient(plan, st, nsteps, checkpoint=10, slots=None, spill=True, host_fraction=0.6):
+    """Gradient of the final perturbation energy J after `nsteps` steps from the started
+    state st with respect to that state's (u, u_prev, N_prev), by the hand-written adjoint.
+
+    Forward: st is advanced `nsteps` steps; its (u, u_prev, N_prev) is kept every
+    `checkpoint` steps, in pinned host memory when `spill` (else on the device).  Backward:
+    the segments between checkpoints are reversed last first.  A segment is recomputed from
+    its checkpoint with st as the working state, the velocity of its last `slots` steps not
+    yet reversed is copied into device buffers, and the adjoint steps run back through them;
+    this repeats until the segment is reversed (`slots` = None: the whole segment at once).
+    Only u is read by an adjoint step, so a slot holds one vector field.
+
+    st is the working state: on return it holds its initial (u, u_prev, N_prev) again; p is
+    left as the last recomputed step wrote it.  Refuses (ValueError) host checkpoints that
+    would take more than `host_fraction` of the machine's available memory.
+    Returns (J, bar), bar a tc.StateBar of the three gradients."""
+    if not st.started:
+        raise ValueError("state_gradient needs a started state (tc_step has built its history)")
+    C = int(checkpoint)
+    if C < 1 or nsteps < 1:
+        raise ValueError("checkpoint and nsteps must be >= 1")
+    starts = list(range(0, nsteps, C))
+    k = C if slots is None else max(1, min(int(slots), C))
+    field_bytes = st.u.numel() * st.u.element_size()
+    if spill:
+        need = len(starts) * 3 * field_bytes
+        avail = _host_bytes_available()
+        if avail is not None and need > host_fraction * avail:
+            raise ValueError(f"host checkpoints need {need / 1e9:.1f} GB, more than "
+                             f"{host_fraction:.0%} of the {avail / 1e9:.1f} GB available")
+
+    def save():
+        if spill:
+            out = []
+            for t in (st.u, st.u_prev, st.N_prev):
+                h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                h.copy_(t, non_blocking=True)
+                out.append(h)
+            return out
+        return [st.u.clone(), st.u_prev.clone(), st.N_prev.clone()]
+
+    def restore(c):
+        for t, h in zip((st.u, st.u_prev, st.N_prev), c):
+            t.copy_(h, non_blocking=True)
+        st.started = True
+
+    ckpts = {}
+    for i in range(nsteps):
+        if i % C == 0:
+            ckpts[i] = save()
+        plan.step(st, 1)
+    J = _energy(plan, st.u)
+    ub = plan.energy_gradient(st.u)
+    bar = tc.StateBar(ub.contiguous(), torch.zeros_like(ub), torch.zeros_like(ub))
+    buf = [torch.empty_like(st.u) for _ in range(k)]
+    for s0 in reversed(starts):
+        hi = min(s0 + C, nsteps)          # forward states s0 .. hi-1 still to reverse
+        while hi > s0:
+            lo = max(s0, hi - k)
+            restore(ckpts[s0])
+            for j in range(s0, hi):       # st holds the state of step j
+                if j >= lo:
+                    buf[j - lo].copy_(st.u)
+                if j < hi - 1:
+                    plan.step(st, 1)
+            for j in reversed(range(lo, hi)):
+                plan.adjoint_step(_ForwardU(buf[j - lo]), bar)
+            hi = lo
+        if s0 > 0:
+            del ckpts[s0]
+    restore(ckpts[0])
+    torch.cuda.current_stream().synchronize()   # the pinned checkpoints are released after the copies
+    del ckpts
+    return J, bar
 
 
 def energy_weights(plan, like):

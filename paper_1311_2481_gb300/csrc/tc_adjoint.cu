@@ -410,16 +410,16 @@ __global__ void __launch_bounds__(256) k_pc_adj(PCAdjArgs a, Geo g, int T) {
 // (r, m): s_r = (Nbar_+ + Nbar_-), s_t = -i (Nbar_+ - Nbar_-), s_z = Nbar_z.
 __global__ void __launch_bounds__(256) k_zinv_adjin(const double2* __restrict__ Nb, double2* __restrict__ H,
                                                     int N_r, int M, int K, double scale,
-                                                    const double2* __restrict__ tw, Radices rad) {
+                                                    const double2* __restrict__ tw, Radices rad, int r0, int nh) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Pz = rad.n;
     double2* a = reinterpret_cast<double2*>(smem_raw);
     double2* b = a + (size_t)3 * Pz;
     const int m = blockIdx.x % (M + 1);
-    const int r = blockIdx.x / (M + 1);
+    const int rl = blockIdx.x / (M + 1);
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
-    const size_t o = ((size_t)r * (M + 1) + m) * nk;
+    const size_t o = ((size_t)(r0 + rl) * (M + 1) + m) * nk;
     const double cm = (m == 0 ? 1.0 : 0.5) * scale;
     for (int idx = threadIdx.x; idx < 3 * Pz; idx += blockDim.x) {
         const int l = idx / Pz, q = idx - l * Pz;
@@ -437,10 +437,10 @@ __global__ void __launch_bounds__(256) k_zinv_adjin(const double2* __restrict__ 
     }
     __syncthreads();
     double2* res = smem_fft(a, b, 3, tw, true, rad);
-    const size_t fstride = (size_t)N_r * (M + 1) * Pz;
+    const size_t fstride = (size_t)nh * (M + 1) * Pz;
     for (int idx = threadIdx.x; idx < 3 * Pz; idx += blockDim.x) {
         const int l = idx / Pz, z = idx - l * Pz;
-        H[l * fstride + ((size_t)r * (M + 1) + m) * Pz + z] = res[idx];
+        H[l * fstride + ((size_t)rl * (M + 1) + m) * Pz + z] = res[idx];
     }
 }
 
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(256) k_zinv_adjin(const double2* __restrict__ 
 // the (+, -, z) basis: A (u, with -i m m_p d_theta folded in), R (d_r), Z (d_z).
 __global__ void __launch_bounds__(256) k_theta_adj(const double2* __restrict__ H1, const double2* __restrict__ Ha,
                                                    double2* __restrict__ H3, const double* __restrict__ irn,
-                                                   int N_r, int M, int Pz, double mp, int zt,
+                                                   int r0, int nh, int M, int Pz, double mp, int zt,
                                                    const double2* __restrict__ tw, Radices rad) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Pt = rad.n;
@@ -461,9 +461,9 @@ __global__ void __launch_bounds__(256) k_theta_adj(const double2* __restrict__ H
     double2* A = reinterpret_cast<double2*>(smem_raw);
     double2* B = A + (size_t)nbuf * Pt;
     const int tiles = Pz / zt;
-    const int r = blockIdx.x / tiles;
+    const int r = blockIdx.x / tiles;   // row within the staged rows r0 .. r0 + nh - 1
     const int z0 = (blockIdx.x % tiles) * zt;
-    const size_t fstride = (size_t)N_r * (M + 1) * Pz;
+    const size_t fstride = (size_t)nh * (M + 1) * Pz;
     const double2* h = H1 + (size_t)r * (M + 1) * Pz + z0;
     const double2* ha = Ha + (size_t)r * (M + 1) * Pz + z0;
 
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(256) k_theta_adj(const double2* __restrict__ H
     __syncthreads();
     double2* phys = smem_fft(A, B, nl, tw, true, rad);
     double2* out = phys == A ? B : A;
-    const double ir = irn[r];   // 1 / r_j from the plan
+    const double ir = irn[r0 + r];   // 1 / r_j from the plan
     for (int idx = threadIdx.x; idx < zt * Pt; idx += blockDim.x) {
         const int zi = idx / Pt, th = idx - zi * Pt;
         const double2* L0 = phys + (size_t)(zi * 6) * Pt + th;
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(256) k_theta_adj(const double2* __restrict__ H
 template <int PT, int ZT, int NT>
 __global__ void __launch_bounds__(NT) k_theta_adj_s(const double2* __restrict__ H1, const double2* __restrict__ Ha,
                                                    double2* __restrict__ H3, const double* __restrict__ irn,
-                                                   int N_r, int M, int Pz, double mp,
+                                                   int r0, int nh, int M, int Pz, double mp,
                                                    const double2* __restrict__ tw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int Pt = PT, zt = ZT;
@@ -593,9 +593,9 @@ __global__ void __launch_bounds__(NT) k_theta_adj_s(const double2* __restrict__ 
     double2* A = reinterpret_cast<double2*>(smem_raw);
     double2* B = A + (size_t)nbuf * LP;
     const int tiles = Pz / zt;
-    const int r = blockIdx.x / tiles;
+    const int r = blockIdx.x / tiles;   // row within the staged rows r0 .. r0 + nh - 1
     const int z0 = (blockIdx.x % tiles) * zt;
-    const size_t fstride = (size_t)N_r * (M + 1) * Pz;
+    const size_t fstride = (size_t)nh * (M + 1) * Pz;
     const double2* h = H1 + (size_t)r * (M + 1) * Pz + z0;
     const double2* ha = Ha + (size_t)r * (M + 1) * Pz + z0;
 
@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(NT) k_theta_adj_s(const double2* __restrict__ 
     __syncthreads();
     const double2* phys = cft::passes<PT, 0, 1, nl, NT, true, double2, true>(A, B, tw);
     double2* out = phys == A ? B : A;
-    const double ir = irn[r];   // 1 / r_j from the plan
+    const double ir = irn[r0 + r];   // 1 / r_j from the plan
     for (int idx = threadIdx.x; idx < zt * Pt; idx += NT) {
         const int zi = idx / Pt, th = idx - zi * Pt;
         const int pth = cft::pd(th);
@@ -712,18 +712,19 @@ __global__ void __launch_bounds__(NT) k_theta_adj_s(const double2* __restrict__ 
 
 // Per (r, m, component c): unscaled forward DFT along z of A_c, R_c, Z_c, truncation to
 // |k| <= K; ubar_c += A_c - i k k_z Z_c;  Rhat_c = R_c (transposed stencil applied next).
+// Rhat holds the nh staged rows r0 .. r0 + nh - 1.
 __global__ void __launch_bounds__(256) k_zfwd_adj(const double2* __restrict__ H3, double2* __restrict__ ub,
                                                   double2* __restrict__ Rh, int N_r, int M, int K, double kz,
-                                                  const double2* __restrict__ tw, Radices rad) {
+                                                  const double2* __restrict__ tw, Radices rad, int r0, int nh) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Pz = rad.n;
     double2* a = reinterpret_cast<double2*>(smem_raw);
     double2* b = a + (size_t)3 * Pz;
     const int c = blockIdx.x % 3;
     const int rm = blockIdx.x / 3;
-    const int m = rm % (M + 1), r = rm / (M + 1);
-    const size_t fstride = (size_t)N_r * (M + 1) * Pz;
-    const double2* h = H3 + ((size_t)r * (M + 1) + m) * Pz;
+    const int m = rm % (M + 1), rl = rm / (M + 1);
+    const size_t fstride = (size_t)nh * (M + 1) * Pz;
+    const double2* h = H3 + ((size_t)rl * (M + 1) + m) * Pz;
     for (int idx = threadIdx.x; idx < 3 * Pz; idx += blockDim.x) {
         const int l = idx / Pz, z = idx - l * Pz;   // l: 0 A, 1 R, 2 Z of component c
         a[idx] = h[(size_t)(3 * l + c) * fstride + z];
@@ -732,17 +733,18 @@ __global__ void __launch_bounds__(256) k_zfwd_adj(const double2* __restrict__ H3
     double2* res = smem_fft(a, b, 3, tw, false, rad);
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
+    const size_t Sh = (size_t)nh * (M + 1) * nk;
     for (int kk = threadIdx.x; kk < nk; kk += blockDim.x) {
         const int k = kk - K;
         const int q = k < 0 ? k + Pz : k;
         const double2 Av = res[q], Rv = res[Pz + q], Zv = res[2 * Pz + q];
         const double kzk = kz * k;
-        const size_t e = (size_t)c * S + ((size_t)r * (M + 1) + m) * nk + kk;
+        const size_t e = (size_t)c * S + ((size_t)(r0 + rl) * (M + 1) + m) * nk + kk;
         double2 u = ub[e];
         u.x += Av.x + kzk * Zv.y;
         u.y += Av.y - kzk * Zv.x;
         ub[e] = u;
-        Rh[e] = Rv;
+        Rh[(size_t)c * Sh + ((size_t)rl * (M + 1) + m) * nk + kk] = Rv;
     }
 }
 
@@ -751,16 +753,16 @@ __global__ void __launch_bounds__(256) k_zfwd_adj(const double2* __restrict__ H3
 template <int PZ, int NT>
 __global__ void __launch_bounds__(NT) k_zinv_adjin_s(const double2* __restrict__ Nb, double2* __restrict__ H,
                                                      int N_r, int M, int K, double scale,
-                                                     const double2* __restrict__ tw) {
+                                                     const double2* __restrict__ tw, int r0, int nh) {
     constexpr int LP = cft::padded<PZ>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* a = reinterpret_cast<double2*>(smem_raw);
     double2* b = a + 3 * LP;
     const int m = blockIdx.x % (M + 1);
-    const int r = blockIdx.x / (M + 1);
+    const int rl = blockIdx.x / (M + 1);
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
-    const size_t o = ((size_t)r * (M + 1) + m) * nk;
+    const size_t o = ((size_t)(r0 + rl) * (M + 1) + m) * nk;
     const double cm = (m == 0 ? 1.0 : 0.5) * scale;
     for (int q = threadIdx.x; q < PZ; q += NT) {
         const int k = q <= K ? q : q - PZ;
@@ -773,10 +775,10 @@ __global__ void __launch_bounds__(NT) k_zinv_adjin_s(const double2* __restrict__
     }
     __syncthreads();
     const double2* X = cft::passes<PZ, 0, 1, 3, NT, true, double2, true>(a, b, tw, K + 1, PZ - K);
-    const size_t fstride = (size_t)N_r * (M + 1) * PZ;
+    const size_t fstride = (size_t)nh * (M + 1) * PZ;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-        double2* dst = H + l * fstride + ((size_t)r * (M + 1) + m) * PZ;
+        double2* dst = H + l * fstride + ((size_t)rl * (M + 1) + m) * PZ;
         for (int z = threadIdx.x; z < PZ; z += NT) dst[z] = X[l * LP + cft::pd(z)];
     }
 }
@@ -784,16 +786,16 @@ __global__ void __launch_bounds__(NT) k_zinv_adjin_s(const double2* __restrict__
 template <int PZ, int NT>
 __global__ void __launch_bounds__(NT) k_zfwd_adj_s(const double2* __restrict__ H3, double2* __restrict__ ub,
                                                    double2* __restrict__ Rh, int N_r, int M, int K, double kz,
-                                                   const double2* __restrict__ tw) {
+                                                   const double2* __restrict__ tw, int r0, int nh) {
     constexpr int LP = cft::padded<PZ>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* a = reinterpret_cast<double2*>(smem_raw);
     double2* b = a + 3 * LP;
     const int c = blockIdx.x % 3;
     const int rm = blockIdx.x / 3;
-    const int m = rm % (M + 1), r = rm / (M + 1);
-    const size_t fstride = (size_t)N_r * (M + 1) * PZ;
-    const double2* h = H3 + ((size_t)r * (M + 1) + m) * PZ;
+    const int m = rm % (M + 1), rl = rm / (M + 1);
+    const size_t fstride = (size_t)nh * (M + 1) * PZ;
+    const double2* h = H3 + ((size_t)rl * (M + 1) + m) * PZ;
 #pragma unroll
     for (int l = 0; l < 3; ++l)   // l: 0 A, 1 R, 2 Z of component c
         for (int z = threadIdx.x; z < PZ; z += NT) a[l * LP + cft::pd(z)] = h[(size_t)(3 * l + c) * fstride + z];
@@ -801,36 +803,195 @@ __global__ void __launch_bounds__(NT) k_zfwd_adj_s(const double2* __restrict__ H
     const double2* X = cft::passes<PZ, 0, 1, 3, NT, false, double2, true>(a, b, tw);
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
+    const size_t Sh = (size_t)nh * (M + 1) * nk;
     for (int kk = threadIdx.x; kk < nk; kk += NT) {
         const int k = kk - K;
         const int q = cft::pd(k < 0 ? k + PZ : k);
         const double2 Av = X[q], Rv = X[LP + q], Zv = X[2 * LP + q];
         const double kzk = kz * k;
-        const size_t e = (size_t)c * S + ((size_t)r * (M + 1) + m) * nk + kk;
+        const size_t e = (size_t)c * S + ((size_t)(r0 + rl) * (M + 1) + m) * nk + kk;
         double2 u = ub[e];
         u.x += Av.x + kzk * Zv.y;
         u.y += Av.y - kzk * Zv.x;
         ub[e] = u;
-        Rh[e] = Rv;
+        Rh[(size_t)c * Sh + ((size_t)rl * (M + 1) + m) * nk + kk] = Rv;
+    }
+}
+
+// Streamed form of the transposed theta pass for long lines: two lines per z are resident at
+// a time instead of eight, as in the forward k_theta_s, so 1152-point FP64 lines fit a block.
+// Inverse phases, two lines per z each:
+//   0: (s_r, s_t), (u_r, u_t)        1: (s_z, 0), (u_z, d_r u_z)
+//   2: (d_r u_r, d_r u_t), (d_t u_r, d_t u_t)      3: (d_z u_r, d_z u_t), (d_t u_z, d_z u_z)
+// Each physical point is owned by one thread in every phase, which keeps there (n_r, n_t),
+// (u_r, u_t / r), n_z, u_z and the transposed products that need the gradient lines:
+//   b_r = n_r d_r u_r + n_t (d_r u_t + u_t / r) + n_z d_r u_z,
+//   r b_t = n_r (d_t u_r - 2 u_t) + n_t (d_t u_t + u_r) + n_z d_t u_z,
+//   b_z = n_r d_z u_r + n_t d_z u_t + n_z d_z u_z.
+// Forward phases transform the six output pairs of k_theta_adj two per z, grouped so that
+// each group alone fixes the H3 fields it writes: (o2, o5) -> R_+-, Z_+-; (o0, o3) -> A_+-;
+// (o1, o4) -> A_z, R_z, Z_z.
+template <int PT, int ZT, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_theta_adj_st(const double2* __restrict__ H1,
+                                                          const double2* __restrict__ Ha,
+                                                          double2* __restrict__ H3, const double* __restrict__ irn,
+                                                          int r0, int nh, int M, int Pz, double mp,
+                                                          const double2* __restrict__ tw) {
+    using V = double2;
+    constexpr int LP = cft::padded<PT>();
+    constexpr int NL = 2 * ZT;   // resident lines
+    constexpr int NPT = ZT * PT; // physical points of the block
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* A = reinterpret_cast<V*>(smem_raw);
+    V* B = A + NL * LP;
+    V* Nv = B + NL * LP;   // (n_r, n_t)
+    V* Uu = Nv + NPT;      // (u_r, u_t / r)
+    V* Ac = Uu + NPT;      // (b_r, r b_t)
+    double* Nz = reinterpret_cast<double*>(Ac + NPT);
+    double* Uz = Nz + NPT;
+    double* Bz = Uz + NPT;
+    const int tiles = Pz / ZT;
+    const int r = blockIdx.x / tiles;   // row within the staged rows r0 .. r0 + nh - 1
+    const int z0 = (blockIdx.x % tiles) * ZT;
+    const size_t fstride = (size_t)nh * (M + 1) * Pz;
+    const V* h = H1 + (size_t)r * (M + 1) * Pz + z0;
+    const V* ha = Ha + (size_t)r * (M + 1) * Pz + z0;
+    const double ir = irn[r0 + r];   // 1 / r_j from the plan
+    const int zi = threadIdx.x % ZT;
+    const int mstep = NT / ZT;
+
+#pragma unroll 1
+    for (int phase = 0; phase < 4; ++phase) {
+        V* L0 = A + (2 * zi) * LP;
+        V* L1 = L0 + LP;
+        for (int m = (int)threadIdx.x / ZT; m <= M; m += mstep) {
+            const size_t o = (size_t)m * Pz + zi;
+            const double mm = mp * m;
+            if (phase == 0) {
+                cft::put_real2(L0, PT, m, ha[o], ha[fstride + o]);
+                cft::put_pair(L1, PT, m, h[o], h[fstride + o]);
+            } else if (phase == 1) {
+                cft::put_real2(L0, PT, m, ha[2 * fstride + o], make_double2(0.0, 0.0));
+                cft::put_real2(L1, PT, m, h[2 * fstride + o], h[5 * fstride + o]);
+            } else if (phase == 2) {
+                cft::put_pair(L0, PT, m, h[3 * fstride + o], h[4 * fstride + o]);
+                cft::put_pair(L1, PT, m, cft::imul(h[o], mm), cft::imul(h[fstride + o], mm));
+            } else {
+                cft::put_pair(L0, PT, m, h[6 * fstride + o], h[7 * fstride + o]);
+                cft::put_real2(L1, PT, m, cft::imul(h[2 * fstride + o], mm), h[8 * fstride + o]);
+            }
+        }
+        __syncthreads();
+        // the band M < p < PT - M of every line is zero: the first pass does not read it
+        const V* X = cft::passes<PT, 0, 1, NL, NT, true, V, true>(A, B, tw, M + 1, PT - M);
+        for (int pt = threadIdx.x; pt < NPT; pt += NT) {
+            const int z = pt / PT;
+            const int th = pt - z * PT;
+            const V p0 = X[(2 * z) * LP + cft::pd(th)];
+            const V p1 = X[(2 * z + 1) * LP + cft::pd(th)];
+            if (phase == 0) {          // p0 = (n_r, n_t), p1 = (u_r, u_t)
+                const double utr = p1.y * ir;
+                Nv[pt] = p0;
+                Uu[pt] = make_double2(p1.x, utr);
+                Ac[pt] = make_double2(p0.y * utr, p0.y * p1.x - 2.0 * p0.x * p1.y);
+            } else if (phase == 1) {   // p0 = (n_z, 0), p1 = (u_z, d_r u_z)
+                Nz[pt] = p0.x;
+                Uz[pt] = p1.x;
+                Ac[pt].x += p0.x * p1.y;
+            } else if (phase == 2) {   // p0 = d_r (u_r, u_t), p1 = d_t (u_r, u_t)
+                const V n = Nv[pt];
+                V c = Ac[pt];
+                c.x += n.x * p0.x + n.y * p0.y;
+                c.y += n.x * p1.x + n.y * p1.y;
+                Ac[pt] = c;
+            } else {                   // p0 = d_z (u_r, u_t), p1 = (d_t u_z, d_z u_z)
+                const V n = Nv[pt];
+                const double nz = Nz[pt];
+                Bz[pt] = n.x * p0.x + n.y * p0.y + nz * p1.y;
+                Ac[pt].y += nz * p1.x;
+            }
+        }
+        __syncthreads();   // the next fill overwrites the lines
+    }
+
+    const size_t S9 = fstride;
+    auto plus = [](double2 ar, double2 at) { return make_double2(0.5 * (ar.x - at.y), 0.5 * (ar.y + at.x)); };
+    auto minus = [](double2 ar, double2 at) { return make_double2(0.5 * (ar.x + at.y), 0.5 * (ar.y - at.x)); };
+#pragma unroll 1
+    for (int fp = 0; fp < 3; ++fp) {
+        for (int pt = threadIdx.x; pt < NPT; pt += NT) {
+            const int z = pt / PT;
+            const int th = pt - z * PT;
+            const V n = Nv[pt], uu = Uu[pt];
+            V a, b;
+            if (fp == 0) {
+                const double uz = Uz[pt];
+                a = make_double2(uu.x * n.x, uu.x * n.y);         // o2: (d_r u_r, d_r u_t)
+                b = make_double2(uz * n.x, uz * n.y);             // o5: (d_z u_r, d_z u_t)
+            } else if (fp == 1) {
+                const V c = Ac[pt];
+                a = make_double2(c.x, c.y * ir);                  // o0: (u_r, u_t)
+                b = make_double2(uu.y * n.x, uu.y * n.y);         // o3: (d_t u_r, d_t u_t)
+            } else {
+                const double nz = Nz[pt];
+                a = make_double2(Bz[pt], uu.x * nz);              // o1: (u_z, d_r u_z)
+                b = make_double2(uu.y * nz, Uz[pt] * nz);         // o4: (d_t u_z, d_z u_z)
+            }
+            A[(2 * z) * LP + cft::pd(th)] = a;
+            A[(2 * z + 1) * LP + cft::pd(th)] = b;
+        }
+        __syncthreads();
+        const V* Y = cft::passes<PT, 0, 1, NL, NT, false, V, true>(A, B, tw);
+        for (int idx = threadIdx.x; idx < ZT * (M + 1); idx += NT) {
+            const int m = idx / ZT, z = idx - m * ZT;
+            const double cmw = m == 0 ? 1.0 : 2.0;
+            const double mm = mp * m;
+            V Xl[2], Yl[2];
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                const V* Ls = Y + (2 * z + l) * LP;
+                const V Cp = Ls[cft::pd(m)], Cm = cconj(Ls[cft::pd(m ? PT - m : 0)]);
+                Xl[l] = make_double2(0.5 * cmw * (Cp.x + Cm.x), 0.5 * cmw * (Cp.y + Cm.y));
+                Yl[l] = make_double2(0.5 * cmw * (Cp.y - Cm.y), 0.5 * cmw * (Cm.x - Cp.x));
+            }
+            const size_t o = ((size_t)r * (M + 1) + m) * Pz + z0 + z;
+            if (fp == 0) {
+                H3[3 * S9 + o] = plus(Xl[0], Yl[0]);
+                H3[4 * S9 + o] = minus(Xl[0], Yl[0]);
+                H3[6 * S9 + o] = plus(Xl[1], Yl[1]);
+                H3[7 * S9 + o] = minus(Xl[1], Yl[1]);
+            } else if (fp == 1) {
+                const V Ar = make_double2(Xl[0].x + mm * Xl[1].y, Xl[0].y - mm * Xl[1].x);
+                const V At = make_double2(Yl[0].x + mm * Yl[1].y, Yl[0].y - mm * Yl[1].x);
+                H3[0 * S9 + o] = plus(Ar, At);
+                H3[1 * S9 + o] = minus(Ar, At);
+            } else {
+                H3[2 * S9 + o] = make_double2(Xl[0].x + mm * Xl[1].y, Xl[0].y - mm * Xl[1].x);
+                H3[5 * S9 + o] = Yl[0];
+                H3[8 * S9 + o] = Yl[1];
+            }
+        }
+        __syncthreads();   // the next fill overwrites the lines
     }
 }
 
 template <int PZ, int NT>
 static tc_status zadj_s(tc_plan* p, const double2* Nbar, double2* Ha, const double2* H3, double2* ubar,
-                        double2* Rh, cudaStream_t s, bool inverse) {
+                        double2* Rh, cudaStream_t s, bool inverse, int r0, int nh) {
     const size_t sm = (size_t)2 * 3 * cft::padded<PZ>() * sizeof(double2);
     if (inverse) {
         TC_CUDA(p, cudaFuncSetAttribute(k_zinv_adjin_s<PZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int slot = prof_begin(p, kKZinvAdj, s);
-        k_zinv_adjin_s<PZ, NT><<<p->N_r * (p->M + 1), NT, sm, s>>>(Nbar, Ha, p->N_r, p->M, p->K,
-                                                                   1.0 / ((double)p->P_t * (double)p->P_z), p->d_tw_z);
+        k_zinv_adjin_s<PZ, NT><<<nh * (p->M + 1), NT, sm, s>>>(Nbar, Ha, p->N_r, p->M, p->K,
+                                                               1.0 / ((double)p->P_t * (double)p->P_z), p->d_tw_z,
+                                                               r0, nh);
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_zinv_adjin_s");
     } else {
         TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_adj_s<PZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int slot = prof_begin(p, kKZfwdAdj, s);
-        k_zfwd_adj_s<PZ, NT><<<p->N_r * (p->M + 1) * 3, NT, sm, s>>>(H3, ubar, Rh, p->N_r, p->M, p->K, p->k_z,
-                                                                     p->d_tw_z);
+        k_zfwd_adj_s<PZ, NT><<<nh * (p->M + 1) * 3, NT, sm, s>>>(H3, ubar, Rh, p->N_r, p->M, p->K, p->k_z,
+                                                                 p->d_tw_z, r0, nh);
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_zfwd_adj_s");
     }
@@ -844,30 +1005,34 @@ static bool zadj_ok(const tc_plan* p) {
 
 // specialised adjoint z passes where P_z has a compile-time plan (TC_ERR_ARG otherwise)
 static tc_status zadj_dispatch(tc_plan* p, const double2* Nbar, double2* Ha, const double2* H3, double2* ubar,
-                               double2* Rh, cudaStream_t s, bool inverse) {
+                               double2* Rh, cudaStream_t s, bool inverse, int r0, int nh) {
     if (p->theta_zt_forced != 0) return TC_ERR_ARG;
     switch (p->P_z) {
-        case 48: return zadj_s<48, 128>(p, Nbar, Ha, H3, ubar, Rh, s, inverse);
-        case 96: return zadj_s<96, 128>(p, Nbar, Ha, H3, ubar, Rh, s, inverse);
-        case 192: return zadj_s<192, 256>(p, Nbar, Ha, H3, ubar, Rh, s, inverse);
-        case 384: return zadj_s<384, 256>(p, Nbar, Ha, H3, ubar, Rh, s, inverse);
-        case 768: return zadj_s<768, 256>(p, Nbar, Ha, H3, ubar, Rh, s, inverse);
+        case 48: return zadj_s<48, 128>(p, Nbar, Ha, H3, ubar, Rh, s, inverse, r0, nh);
+        case 96: return zadj_s<96, 128>(p, Nbar, Ha, H3, ubar, Rh, s, inverse, r0, nh);
+        case 192: return zadj_s<192, 256>(p, Nbar, Ha, H3, ubar, Rh, s, inverse, r0, nh);
+        case 384: return zadj_s<384, 256>(p, Nbar, Ha, H3, ubar, Rh, s, inverse, r0, nh);
+        case 768: return zadj_s<768, 256>(p, Nbar, Ha, H3, ubar, Rh, s, inverse, r0, nh);
     }
     return TC_ERR_ARG;
 }
 
-// ubar(c, j, mode) += (D1^T Rhat)(c, j, mode)
+// ubar(c, j, mode) += sum over the staged rows i = r0 .. r0 + nh - 1 of D1[i][j] Rhat(c, i, mode)
+// for the columns j = j0 .. j0 + gridDim.x - 1 (the columns those rows' stencils reach)
 __global__ void k_drT(double2* __restrict__ ub, const double2* __restrict__ Rh, const int* __restrict__ trow,
-                      const double* __restrict__ tw, int ntab, Geo g) {
-    // grid: x = radial row (fastest: the gathered rows stay in cache), y over modes, z = component
+                      const double* __restrict__ tw, int ntab, Geo g, int r0, int nh, int j0) {
+    // grid: x = radial column (fastest: the gathered rows stay in cache), y over modes, z = component
     const int mode = blockIdx.y * blockDim.x + threadIdx.x;
     if (mode >= g.nmode) return;
-    const int j = blockIdx.x, c = blockIdx.z;
+    const int j = j0 + blockIdx.x, c = blockIdx.z;
     const size_t e = (size_t)c * g.S + (size_t)j * g.nmode + mode;
+    const size_t Sh = (size_t)nh * g.nmode;
     double2 s = ub[e];
     for (int q = 0; q < ntab; ++q) {
+        const int i = __ldg(&trow[j * ntab + q]) - r0;
+        if (i < 0 || i >= nh) continue;
         const double w = __ldg(&tw[j * ntab + q]);
-        const double2 v = Rh[(size_t)c * g.S + (size_t)__ldg(&trow[j * ntab + q]) * g.nmode + mode];
+        const double2 v = Rh[(size_t)c * Sh + (size_t)i * g.nmode + mode];
         s.x = fma(w, v.x, s.x);
         s.y = fma(w, v.y, s.y);
     }
@@ -899,39 +1064,47 @@ tc_status launch_adjoint_advance(tc_plan* p, const double2* ubar_new, const doub
 }
 
 template <int PT, int ZT, int NT>
-static tc_status theta_adj_s(tc_plan* p, const double2* H1, const double2* Ha, double2* H3, cudaStream_t s) {
+static tc_status theta_adj_s(tc_plan* p, const double2* H1, const double2* Ha, double2* H3, cudaStream_t s,
+                             int r0, int nh) {
     constexpr int nl = 7 * ZT + (ZT + 1) / 2;
     const size_t sm = (size_t)2 * nl * cft::padded<PT>() * sizeof(double2);
     TC_CUDA(p, cudaFuncSetAttribute(k_theta_adj_s<PT, ZT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int slot = prof_begin(p, kKThetaAdj, s);
-    k_theta_adj_s<PT, ZT, NT><<<p->N_r * (p->P_z / ZT), NT, sm, s>>>(H1, Ha, H3, p->d_ir, p->N_r, p->M, p->P_z,
-                                                                    (double)p->m_p, p->d_tw_t);
+    k_theta_adj_s<PT, ZT, NT><<<nh * (p->P_z / ZT), NT, sm, s>>>(H1, Ha, H3, p->d_ir, r0, nh, p->M, p->P_z,
+                                                                (double)p->m_p, p->d_tw_t);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_theta_adj_s");
     return TC_OK;
 }
 
-tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* Nbar, double2* ubar,
-                                   char* ws, cudaStream_t s) {
-    Geo g = geo(p);
-    double2* H1 = reinterpret_cast<double2*>(ws + p->ws.H1);
-    double2* Ha = reinterpret_cast<double2*>(ws + p->ws.H2);
-    double2* H3 = reinterpret_cast<double2*>(ws + p->ws.H3);
-    double2* Rh = reinterpret_cast<double2*>(ws + p->ws.Rhat);
-    // forward lines of u (same kernel as the forward nonlinear term, FP64)
-    tc_status st = launch_zinv_fp64(p, u, H1, s);
-    if (st != TC_OK) return st;
-    const size_t smz = (size_t)2 * 3 * p->P_z * sizeof(double2);
-    int slot;
-    if (zadj_ok(p)) {
-        TC_TRY_STATUS(zadj_dispatch(p, Nbar, Ha, nullptr, nullptr, nullptr, s, true));
-    } else {
-        TC_CUDA(p, cudaFuncSetAttribute(k_zinv_adjin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
-        slot = prof_begin(p, kKZinvAdj, s);
-        k_zinv_adjin<<<p->N_r * (p->M + 1), 256, smz, s>>>(Nbar, Ha, p->N_r, p->M, p->K,
-                                                             1.0 / ((double)p->P_t * (double)p->P_z), p->d_tw_z, p->rad_z);
-        prof_end(p, slot, s);
-        TC_LAUNCHED(p, "k_zinv_adjin");
+template <int PT, int ZT, int NT, int MINB>
+static tc_status theta_adj_st(tc_plan* p, const double2* H1, const double2* Ha, double2* H3, cudaStream_t s,
+                              int r0, int nh) {
+    constexpr int LP = cft::padded<PT>();
+    const size_t sm = ((size_t)2 * 2 * ZT * LP + (size_t)3 * ZT * PT) * sizeof(double2) +
+                      (size_t)3 * ZT * PT * sizeof(double);
+    auto kern = k_theta_adj_st<PT, ZT, NT, MINB>;
+    TC_CUDA(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int slot = prof_begin(p, kKThetaAdj, s);
+    kern<<<nh * (p->P_z / ZT), NT, sm, s>>>(H1, Ha, H3, p->d_ir, r0, nh, p->M, p->P_z, (double)p->m_p, p->d_tw_t);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_theta_adj_st");
+    return TC_OK;
+}
+
+// adjoint theta pass of the staged rows r0 .. r0 + nh - 1: the streamed kernel for 768 and
+// 1152 points, the length-specialised one for 96, 192, 384, the generic one otherwise
+static tc_status theta_adj(tc_plan* p, const double2* H1, const double2* Ha, double2* H3, cudaStream_t s,
+                           int r0, int nh) {
+    const bool spec = p->theta_zt_forced == 0 && 2 * p->M + 1 <= p->P_t;
+    if (spec && p->P_t == 1152) return theta_adj_st<1152, 1, 384, 1>(p, H1, Ha, H3, s, r0, nh);
+    if (spec && p->P_t == 768) return theta_adj_st<768, 1, 256, 2>(p, H1, Ha, H3, s, r0, nh);
+    if (spec && (p->P_t == 96 || p->P_t == 192 || p->P_t == 384) && p->P_z % 2 == 0) {
+        switch (p->P_t) {
+            case 96: return theta_adj_s<96, 2, 256>(p, H1, Ha, H3, s, r0, nh);
+            case 192: return theta_adj_s<192, 2, 256>(p, H1, Ha, H3, s, r0, nh);
+            default: return theta_adj_s<384, 2, 256>(p, H1, Ha, H3, s, r0, nh);
+        }
     }
     int zt = 4;
     auto smem_for = [&](int z) {
@@ -944,35 +1117,68 @@ tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* 
         snprintf(p->err, sizeof(p->err), "adjoint theta pass: P_theta = %d too long for shared memory", p->P_t);
         return TC_ERR_ARG;
     }
-    if (p->theta_zt_forced == 0 && (p->P_t == 96 || p->P_t == 192 || p->P_t == 384) && p->P_z % 2 == 0) {
-        switch (p->P_t) {
-            case 96: TC_TRY_STATUS((theta_adj_s<96, 2, 256>(p, H1, Ha, H3, s))); break;
-            case 192: TC_TRY_STATUS((theta_adj_s<192, 2, 256>(p, H1, Ha, H3, s))); break;
-            default: TC_TRY_STATUS((theta_adj_s<384, 2, 256>(p, H1, Ha, H3, s))); break;
-        }
-    } else {
-        const size_t smt = smem_for(zt);
-        TC_CUDA(p, cudaFuncSetAttribute(k_theta_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt));
-        slot = prof_begin(p, kKThetaAdj, s);
-        k_theta_adj<<<p->N_r * (p->P_z / zt), 256, smt, s>>>(H1, Ha, H3, p->d_ir, p->N_r, p->M, p->P_z,
-                                                               (double)p->m_p, zt, p->d_tw_t, p->rad_t);
-        prof_end(p, slot, s);
-        TC_LAUNCHED(p, "k_theta_adj");
-    }
-    if (zadj_ok(p)) {
-        TC_TRY_STATUS(zadj_dispatch(p, nullptr, nullptr, H3, ubar, Rh, s, false));
-    } else {
-        TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
-        slot = prof_begin(p, kKZfwdAdj, s);
-        k_zfwd_adj<<<p->N_r * (p->M + 1) * 3, 256, smz, s>>>(H3, ubar, Rh, p->N_r, p->M, p->K, p->k_z,
-                                                               p->d_tw_z, p->rad_z);
-        prof_end(p, slot, s);
-        TC_LAUNCHED(p, "k_zfwd_adj");
-    }
-    slot = prof_begin(p, kKDrT, s);
-    k_drT<<<dim3(g.N, ablocks(g.nmode, 128), 3), 128, 0, s>>>(ubar, Rh, p->d_d1t_row, p->d_d1t_w, p->d1t_n, g);
+    const size_t smt = smem_for(zt);
+    TC_CUDA(p, cudaFuncSetAttribute(k_theta_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt));
+    const int slot = prof_begin(p, kKThetaAdj, s);
+    k_theta_adj<<<nh * (p->P_z / zt), 256, smt, s>>>(H1, Ha, H3, p->d_ir, r0, nh, p->M, p->P_z,
+                                                      (double)p->m_p, zt, p->d_tw_t, p->rad_t);
     prof_end(p, slot, s);
-    TC_LAUNCHED(p, "k_drT");
+    TC_LAUNCHED(p, "k_theta_adj");
+    return TC_OK;
+}
+
+// ubar += N'(u)^T Nbar, slab by slab of p->stage_rows radial rows: the transposed transforms of
+// a row read only that row's staging, and the transposed radial stencil of a slab's Rhat rows
+// is added before the next slab overwrites them
+tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* Nbar, double2* ubar,
+                                   char* ws, cudaStream_t s) {
+    Geo g = geo(p);
+    double2* H1 = reinterpret_cast<double2*>(ws + p->ws.H1a);
+    double2* Ha = reinterpret_cast<double2*>(ws + p->ws.Ha);
+    double2* H3 = reinterpret_cast<double2*>(ws + p->ws.H3);
+    double2* Rh = reinterpret_cast<double2*>(ws + p->ws.Rhat);
+    const size_t smz = (size_t)2 * 3 * p->P_z * sizeof(double2);
+    for (int r0 = 0; r0 < p->N_r; r0 += p->stage_rows) {
+        const int nh = p->N_r - r0 < p->stage_rows ? p->N_r - r0 : p->stage_rows;
+        // forward lines of u (same kernel as the forward nonlinear term, FP64)
+        TC_TRY_STATUS(launch_zinv_fp64(p, u, H1, s, r0, nh));
+        int slot;
+        if (zadj_ok(p)) {
+            TC_TRY_STATUS(zadj_dispatch(p, Nbar, Ha, nullptr, nullptr, nullptr, s, true, r0, nh));
+        } else {
+            TC_CUDA(p, cudaFuncSetAttribute(k_zinv_adjin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
+            slot = prof_begin(p, kKZinvAdj, s);
+            k_zinv_adjin<<<nh * (p->M + 1), 256, smz, s>>>(Nbar, Ha, p->N_r, p->M, p->K,
+                                                            1.0 / ((double)p->P_t * (double)p->P_z), p->d_tw_z,
+                                                            p->rad_z, r0, nh);
+            prof_end(p, slot, s);
+            TC_LAUNCHED(p, "k_zinv_adjin");
+        }
+        TC_TRY_STATUS(theta_adj(p, H1, Ha, H3, s, r0, nh));
+        if (zadj_ok(p)) {
+            TC_TRY_STATUS(zadj_dispatch(p, nullptr, nullptr, H3, ubar, Rh, s, false, r0, nh));
+        } else {
+            TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
+            slot = prof_begin(p, kKZfwdAdj, s);
+            k_zfwd_adj<<<nh * (p->M + 1) * 3, 256, smz, s>>>(H3, ubar, Rh, p->N_r, p->M, p->K, p->k_z,
+                                                              p->d_tw_z, p->rad_z, r0, nh);
+            prof_end(p, slot, s);
+            TC_LAUNCHED(p, "k_zfwd_adj");
+        }
+        // columns reached by the stencils of rows r0 .. r0 + nh - 1
+        int jlo = p->N_r, jhi = -1;
+        for (int i = r0; i < r0 + nh; ++i) {
+            jlo = p->col0[i] < jlo ? p->col0[i] : jlo;
+            jhi = p->col0[i] + kStencil - 1 > jhi ? p->col0[i] + kStencil - 1 : jhi;
+        }
+        if (jlo < 0) jlo = 0;
+        if (jhi > p->N_r - 1) jhi = p->N_r - 1;
+        slot = prof_begin(p, kKDrT, s);
+        k_drT<<<dim3(jhi - jlo + 1, ablocks(g.nmode, 128), 3), 128, 0, s>>>(ubar, Rh, p->d_d1t_row, p->d_d1t_w,
+                                                                            p->d1t_n, g, r0, nh, jlo);
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_drT");
+    }
     return TC_OK;
 }
 

@@ -26,7 +26,8 @@ namespace tc {
 __global__ void __launch_bounds__(256) k_zinv(const double2* __restrict__ u, double2* __restrict__ H1,
                                               const double* __restrict__ w1, const int* __restrict__ col0,
                                               int N_r, int M, int K, double kz, int L,
-                                              const double2* __restrict__ tw, Radices rad, int m0) {
+                                              const double2* __restrict__ tw, Radices rad, int m0,
+                                              int r0, int nh) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Pz = rad.n;
     double2* a = reinterpret_cast<double2*>(smem_raw);
@@ -34,8 +35,9 @@ __global__ void __launch_bounds__(256) k_zinv(const double2* __restrict__ u, dou
     const int groups = 9 / L;
     const int g = blockIdx.x % groups;
     const int rm = blockIdx.x / groups;
-    const int r = rm % N_r;        // r fastest: blocks sharing stencil rows run together
-    const int m = m0 + rm / N_r;
+    const int rl = rm % nh;        // r fastest: blocks sharing stencil rows run together
+    const int r = r0 + rl;
+    const int m = m0 + rm / nh;
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
     const size_t colstride = (size_t)(M + 1) * nk;
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(256) k_zinv(const double2* __restrict__ u, dou
         const int l = idx / Pz;
         const int z = idx - l * Pz;
         const int f = g * L + l;
-        H1[(((size_t)f * N_r + r) * (M + 1) + m) * Pz + z] = res[idx];
+        H1[(((size_t)f * nh + rl) * (M + 1) + m) * Pz + z] = res[idx];
     }
 }
 
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(256) k_zinv(const double2* __restrict__ u, dou
 //                                 3 (d_z u_r, d_z u_t)  4 (u_z, d_r u_z)  5 (d_t u_z, d_z u_z)
 template <typename V>
 __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __restrict__ H2,
-                                               const double* __restrict__ irn, int N_r, int M,
+                                               const double* __restrict__ irn, int r0, int nh, int M,
                                                int Pz, double mp, int zt,
                                                const V* __restrict__ tw, Radices rad,
                                                const float* __restrict__ dsc) {
@@ -93,12 +95,12 @@ __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __re
     V* a = reinterpret_cast<V*>(smem_raw);
     V* b = a + (size_t)nl * Pt;
     const int tiles = Pz / zt;
-    const int r = blockIdx.x / tiles;
+    const int r = blockIdx.x / tiles;   // row within the staged rows r0 .. r0 + nh - 1
     const int z0 = (blockIdx.x % tiles) * zt;
-    const size_t fstride = (size_t)N_r * (M + 1) * Pz;
+    const size_t fstride = (size_t)nh * (M + 1) * Pz;
     const V* h = H1 + (size_t)r * (M + 1) * Pz + z0;
     // FP32 lines: d_r u_z enters line 4 scaled by a power of two (1 for FP64 lines)
-    const T ds = sizeof(T) == 4 ? (T)dsc[r] : (T)1, ids = (T)1 / ds;
+    const T ds = sizeof(T) == 4 ? (T)dsc[r0 + r] : (T)1, ids = (T)1 / ds;
 
     for (int idx = threadIdx.x; idx < nl * Pt; idx += blockDim.x) { a[idx].x = 0; a[idx].y = 0; }
     __syncthreads();
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __re
     V* phys = smem_fft(a, b, nl, tw, true, rad);
     V* fw = phys == a ? b : a;
     const int nzl = (zt + 1) / 2;
-    const T ir = (T)irn[r];   // 1 / r_j from the plan
+    const T ir = (T)irn[r0 + r];   // 1 / r_j from the plan
     for (int idx = threadIdx.x; idx < zt * Pt; idx += blockDim.x) {
         const int zi = idx / Pt;
         const int th = idx - zi * Pt;
@@ -183,16 +185,17 @@ __global__ void __launch_bounds__(256) k_theta(const V* __restrict__ H1, V* __re
 __global__ void __launch_bounds__(256) k_zfwd(const double2* __restrict__ H2, double2* __restrict__ N,
                                               int N_r, int M, int K, double scale,
                                               const double2* __restrict__ tw, Radices rad, int Lf,
-                                              int m0, int mcnt) {
+                                              int m0, int mcnt, int r0, int nh) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Pz = rad.n;
     double2* a = reinterpret_cast<double2*>(smem_raw);
     double2* b = a + (size_t)Lf * Pz;
     const int cg = blockIdx.x % (3 / Lf);     // component group (Lf = 3: all three)
     const int m = m0 + (blockIdx.x / (3 / Lf)) % mcnt;
-    const int r = (blockIdx.x / (3 / Lf)) / mcnt;
-    const size_t fstride = (size_t)N_r * (M + 1) * Pz;
-    const double2* h = H2 + ((size_t)r * (M + 1) + m) * Pz;
+    const int rl = (blockIdx.x / (3 / Lf)) / mcnt;
+    const int r = r0 + rl;
+    const size_t fstride = (size_t)nh * (M + 1) * Pz;
+    const double2* h = H2 + ((size_t)rl * (M + 1) + m) * Pz;
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
     for (int idx = threadIdx.x; idx < Lf * Pz; idx += blockDim.x) {
@@ -242,7 +245,7 @@ template <int PZ, int L, int NT>
 __global__ void __launch_bounds__(NT, 2) k_zinv_s64(const double2* __restrict__ u, double2* __restrict__ H1,
                                                     const double* __restrict__ w1, const int* __restrict__ col0,
                                                     int N_r, int M, int K, double kz, const double2* __restrict__ tw,
-                                                    int m0) {
+                                                    int m0, int r0, int nh) {
     constexpr int LP = cft::padded<PZ>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* a = reinterpret_cast<double2*>(smem_raw);
@@ -250,8 +253,9 @@ __global__ void __launch_bounds__(NT, 2) k_zinv_s64(const double2* __restrict__ 
     constexpr int groups = 9 / L;
     const int g = blockIdx.x % groups;
     const int rm = blockIdx.x / groups;
-    const int r = rm % N_r;
-    const int m = m0 + rm / N_r;
+    const int rl = rm % nh;
+    const int r = r0 + rl;
+    const int m = m0 + rm / nh;
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
     const size_t colstride = (size_t)(M + 1) * nk;
@@ -267,7 +271,7 @@ __global__ void __launch_bounds__(NT, 2) k_zinv_s64(const double2* __restrict__ 
     const double2* X = cft::passes<PZ, 0, 1, L, NT, true, double2, true>(a, b, tw, K + 1, PZ - K);
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-        double2* dst = H1 + (((size_t)(g * L + l) * N_r + r) * (M + 1) + m) * PZ;
+        double2* dst = H1 + (((size_t)(g * L + l) * nh + rl) * (M + 1) + m) * PZ;
         for (int z = threadIdx.x; z < PZ; z += NT) dst[z] = X[l * LP + cft::pd(z)];
     }
 }
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(NT, 2) k_zinv_s64(const double2* __restrict__ 
 template <int PZ, int LF, int NT>
 __global__ void __launch_bounds__(NT, 2) k_zfwd_s64(const double2* __restrict__ H2, double2* __restrict__ N,
                                                     int N_r, int M, int K, double scale,
-                                                    const double2* __restrict__ tw, int m0, int mcnt) {
+                                                    const double2* __restrict__ tw, int m0, int mcnt, int r0, int nh) {
     constexpr int LP = cft::padded<PZ>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* a = reinterpret_cast<double2*>(smem_raw);
@@ -283,9 +287,10 @@ __global__ void __launch_bounds__(NT, 2) k_zfwd_s64(const double2* __restrict__ 
     constexpr int groups = 3 / LF;
     const int cg = blockIdx.x % groups;
     const int m = m0 + (blockIdx.x / groups) % mcnt;
-    const int r = (blockIdx.x / groups) / mcnt;
-    const size_t fstride = (size_t)N_r * (M + 1) * PZ;
-    const double2* h = H2 + ((size_t)r * (M + 1) + m) * PZ;
+    const int rl = (blockIdx.x / groups) / mcnt;
+    const int r = r0 + rl;
+    const size_t fstride = (size_t)nh * (M + 1) * PZ;
+    const double2* h = H2 + ((size_t)rl * (M + 1) + m) * PZ;
     const int nk = 2 * K + 1;
     const size_t S = (size_t)N_r * (M + 1) * nk;
 #pragma unroll
@@ -307,17 +312,20 @@ __global__ void __launch_bounds__(NT, 2) k_zfwd_s64(const double2* __restrict__ 
 
 namespace {
 
+// The FP64 staging kernels below process the radial rows r0 .. r0 + nh - 1 and address their
+// staging lines (H1, H2) as nh rows; the spectral arrays keep all N_r rows.
+
 template <int PZ, int L, int LF, int NT>
 tc_status zpass64(tc_plan* p, const double2* u, double2* H1, const double2* H2, double2* N, cudaStream_t s,
-                  bool inverse, int ma, int mb) {
+                  bool inverse, int ma, int mb, int r0, int nh) {
     constexpr int LP = cft::padded<PZ>();
     const int mc = mb - ma;
     if (inverse) {
         const size_t sm = (size_t)2 * L * LP * sizeof(double2);
         TC_CUDA(p, cudaFuncSetAttribute(k_zinv_s64<PZ, L, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int slot = prof_begin(p, kKZinv, s);
-        k_zinv_s64<PZ, L, NT><<<p->N_r * mc * (9 / L), NT, sm, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M,
-                                                                   p->K, p->k_z, p->d_tw_z, ma);
+        k_zinv_s64<PZ, L, NT><<<nh * mc * (9 / L), NT, sm, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M,
+                                                               p->K, p->k_z, p->d_tw_z, ma, r0, nh);
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_zinv_s64");
     } else {
@@ -325,8 +333,8 @@ tc_status zpass64(tc_plan* p, const double2* u, double2* H1, const double2* H2, 
         TC_CUDA(p, cudaFuncSetAttribute(k_zfwd_s64<PZ, LF, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const double scale = 1.0 / ((double)p->P_t * (double)p->P_z);
         const int slot = prof_begin(p, kKZfwd, s);
-        k_zfwd_s64<PZ, LF, NT><<<p->N_r * mc * (3 / LF), NT, sm, s>>>(H2, N, p->N_r, p->M, p->K, scale,
-                                                                     p->d_tw_z, ma, mc);
+        k_zfwd_s64<PZ, LF, NT><<<nh * mc * (3 / LF), NT, sm, s>>>(H2, N, p->N_r, p->M, p->K, scale,
+                                                                 p->d_tw_z, ma, mc, r0, nh);
         prof_end(p, slot, s);
         TC_LAUNCHED(p, "k_zfwd_s64");
     }
@@ -335,19 +343,19 @@ tc_status zpass64(tc_plan* p, const double2* u, double2* H1, const double2* H2, 
 
 // length-specialised FP64 z passes over m in [ma, mb); TC_ERR_ARG if P_z has no compile-time plan
 tc_status zpass64_s(tc_plan* p, const double2* u, double2* H1, const double2* H2, double2* N, cudaStream_t s,
-                    bool inverse, int ma, int mb) {
+                    bool inverse, int ma, int mb, int r0, int nh) {
     switch (p->P_z) {
-        case 12: return zpass64<12, 9, 3, 64>(p, u, H1, H2, N, s, inverse, ma, mb);
-        case 24: return zpass64<24, 9, 3, 64>(p, u, H1, H2, N, s, inverse, ma, mb);
-        case 48: return zpass64<48, 9, 3, 128>(p, u, H1, H2, N, s, inverse, ma, mb);
-        case 96: return zpass64<96, 9, 3, 128>(p, u, H1, H2, N, s, inverse, ma, mb);
-        case 192: return zpass64<192, 9, 3, 256>(p, u, H1, H2, N, s, inverse, ma, mb);
-        case 384: return zpass64<384, 3, 3, 128>(p, u, H1, H2, N, s, inverse, ma, mb);
+        case 12: return zpass64<12, 9, 3, 64>(p, u, H1, H2, N, s, inverse, ma, mb, r0, nh);
+        case 24: return zpass64<24, 9, 3, 64>(p, u, H1, H2, N, s, inverse, ma, mb, r0, nh);
+        case 48: return zpass64<48, 9, 3, 128>(p, u, H1, H2, N, s, inverse, ma, mb, r0, nh);
+        case 96: return zpass64<96, 9, 3, 128>(p, u, H1, H2, N, s, inverse, ma, mb, r0, nh);
+        case 192: return zpass64<192, 9, 3, 256>(p, u, H1, H2, N, s, inverse, ma, mb, r0, nh);
+        case 384: return zpass64<384, 3, 3, 128>(p, u, H1, H2, N, s, inverse, ma, mb, r0, nh);
         // one line per block from 768 on: three FP64 lines would take 76 KB and more
-        case 768: return zpass64<768, 3, 1, 256>(p, u, H1, H2, N, s, inverse, ma, mb);
-        case 1152: return zpass64<1152, 1, 1, 128>(p, u, H1, H2, N, s, inverse, ma, mb);
-        case 1536: return zpass64<1536, 1, 1, 256>(p, u, H1, H2, N, s, inverse, ma, mb);
-        case 2304: return zpass64<2304, 1, 1, 256>(p, u, H1, H2, N, s, inverse, ma, mb);
+        case 768: return zpass64<768, 3, 1, 256>(p, u, H1, H2, N, s, inverse, ma, mb, r0, nh);
+        case 1152: return zpass64<1152, 1, 1, 128>(p, u, H1, H2, N, s, inverse, ma, mb, r0, nh);
+        case 1536: return zpass64<1536, 1, 1, 256>(p, u, H1, H2, N, s, inverse, ma, mb, r0, nh);
+        case 2304: return zpass64<2304, 1, 1, 256>(p, u, H1, H2, N, s, inverse, ma, mb, r0, nh);
     }
     return TC_ERR_ARG;
 }
@@ -362,87 +370,84 @@ bool zpass64_ok(const tc_plan* p) {
 
 }  // namespace
 
-// inverse z pass (with the radial stencil) of the lines of m in [ma, mb)
-static tc_status zinv64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s, int ma, int mb) {
-    if (zpass64_ok(p)) return zpass64_s(p, u, H1, nullptr, nullptr, s, true, ma, mb);
+// inverse z pass (with the radial stencil) of the lines of m in [ma, mb), rows r0 .. r0 + nh - 1
+static tc_status zinv64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s, int ma, int mb, int r0, int nh) {
+    if (zpass64_ok(p)) return zpass64_s(p, u, H1, nullptr, nullptr, s, true, ma, mb, r0, nh);
     const int L = p->zinv_lines;
     const size_t sm1 = (size_t)2 * L * p->P_z * sizeof(double2);
     TC_CUDA(p, cudaFuncSetAttribute(k_zinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
     const int slot = prof_begin(p, kKZinv, s);
-    k_zinv<<<p->N_r * (mb - ma) * (9 / L), p->thr_zinv, sm1, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M, p->K,
-                                                                  p->k_z, L, p->d_tw_z, p->rad_z, ma);
+    k_zinv<<<nh * (mb - ma) * (9 / L), p->thr_zinv, sm1, s>>>(u, H1, p->d_w1, p->d_col0, p->N_r, p->M, p->K,
+                                                             p->k_z, L, p->d_tw_z, p->rad_z, ma, r0, nh);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_zinv");
     return TC_OK;
 }
 
-// forward z pass of the lines of m in [ma, mb) into N
-static tc_status zfwd64(tc_plan* p, const double2* H2, double2* N, cudaStream_t s, int ma, int mb) {
-    if (zpass64_ok(p)) return zpass64_s(p, nullptr, nullptr, H2, N, s, false, ma, mb);
+// forward z pass of the lines of m in [ma, mb), rows r0 .. r0 + nh - 1, into N
+static tc_status zfwd64(tc_plan* p, const double2* H2, double2* N, cudaStream_t s, int ma, int mb, int r0, int nh) {
+    if (zpass64_ok(p)) return zpass64_s(p, nullptr, nullptr, H2, N, s, false, ma, mb, r0, nh);
     const int Lf = p->zfwd_lines;
     const size_t sm3 = (size_t)2 * Lf * p->P_z * sizeof(double2);
     TC_CUDA(p, cudaFuncSetAttribute(k_zfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
     const double scale = 1.0 / ((double)p->P_t * (double)p->P_z);
     const int slot = prof_begin(p, kKZfwd, s);
-    k_zfwd<<<p->N_r * (mb - ma) * (3 / Lf), p->thr_zfwd, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, p->d_tw_z,
-                                                                   p->rad_z, Lf, ma, mb - ma);
+    k_zfwd<<<nh * (mb - ma) * (3 / Lf), p->thr_zfwd, sm3, s>>>(H2, N, p->N_r, p->M, p->K, scale, p->d_tw_z,
+                                                              p->rad_z, Lf, ma, mb - ma, r0, nh);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_zfwd");
     return TC_OK;
 }
 
-static tc_status theta64(tc_plan* p, const double2* H1, double2* H2, cudaStream_t s) {
-    if (p->theta_zt_forced == 0 && theta_s_zt(p, true) > 0) return launch_theta_s64(p, H1, H2, s);
+static tc_status theta64(tc_plan* p, const double2* H1, double2* H2, cudaStream_t s, int r0, int nh) {
+    if (p->theta_zt_forced == 0 && theta_s_zt(p, true) > 0) return launch_theta_s64(p, H1, H2, s, r0, nh);
     const int zt = p->zt;
     const size_t sm2 = (size_t)2 * 6 * zt * p->P_t * sizeof(double2);
     TC_CUDA(p, cudaFuncSetAttribute(k_theta<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     const int slot = prof_begin(p, kKTheta, s);
-    k_theta<double2><<<p->N_r * (p->P_z / zt), p->thr_theta, sm2, s>>>(H1, H2, p->d_ir, p->N_r, p->M, p->P_z,
-                                                                      (double)p->m_p, zt, p->d_tw_t, p->rad_t,
-                                                                      nullptr);
+    k_theta<double2><<<nh * (p->P_z / zt), p->thr_theta, sm2, s>>>(H1, H2, p->d_ir, r0, nh, p->M, p->P_z,
+                                                                  (double)p->m_p, zt, p->d_tw_t, p->rad_t,
+                                                                  nullptr);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_theta");
     return TC_OK;
 }
 
-tc_status launch_zinv_fp64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s) {
-    return zinv64(p, u, H1, s, 0, p->M + 1);
+tc_status launch_zinv_fp64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s, int r0, int nh) {
+    return zinv64(p, u, H1, s, 0, p->M + 1, r0, nh);
 }
 
-// theta pass of the mixed form with the generic kernel: FP32 lines (H1, H2 in float2)
+// theta pass of the mixed form with the generic kernel: FP32 lines (H1, H2 in float2), all rows
 tc_status launch_theta32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t s) {
     const int zt = p->zt32;
     const size_t sm2 = (size_t)2 * 6 * zt * p->P_t * sizeof(float2);
     TC_CUDA(p, cudaFuncSetAttribute(k_theta<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     const int slot = prof_begin(p, kKTheta32, s);
-    k_theta<float2><<<p->N_r * (p->P_z / zt), 256, sm2, s>>>(H1, H2, p->d_ir, p->N_r, p->M, p->P_z, (double)p->m_p,
-                                                             zt, p->d_tw_t32, p->rad_t, p->d_dsc);
+    k_theta<float2><<<p->N_r * (p->P_z / zt), 256, sm2, s>>>(H1, H2, p->d_ir, 0, p->N_r, p->M, p->P_z,
+                                                             (double)p->m_p, zt, p->d_tw_t32, p->rad_t, p->d_dsc);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_theta");
     return TC_OK;
 }
 
-// The nonlinear term in three parts: before the theta pass (per m: the z-inverse lines and,
-// in the mixed form, the FP32 split), the theta pass (all m), after it (per m: z-forward into N)
-tc_status launch_nl_pre(tc_plan* p, const double2* u, char* ws, cudaStream_t s, int ma, int mb) {
-    if (p->precision == TC_MIXED) return launch_nl_pre32(p, u, ws, s, ma, mb);
-    return zinv64(p, u, reinterpret_cast<double2*>(ws + p->ws.H1), s, ma, mb);
-}
-
-tc_status launch_nl_theta(tc_plan* p, char* ws, cudaStream_t s) {
-    if (p->precision == TC_MIXED) return launch_nl_theta32(p, ws, s);
-    return theta64(p, reinterpret_cast<const double2*>(ws + p->ws.H1), reinterpret_cast<double2*>(ws + p->ws.H2), s);
-}
-
-tc_status launch_nl_post(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s, int ma, int mb) {
-    if (p->precision == TC_MIXED) return launch_nl_post32(p, u, N, ws, s, ma, mb);
-    return zfwd64(p, reinterpret_cast<const double2*>(ws + p->ws.H2), N, s, ma, mb);
-}
-
+// The nonlinear term.  FP64 lines: the three transforms slab by slab of p->stage_rows radial
+// rows (a row's transforms read no other row's staging), so the staging holds 12 line sets of
+// stage_rows rows.  Mixed form: FP32 lines of all rows (tc_mixed.cu).
 tc_status launch_nonlinear(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s) {
-    TC_TRY_STATUS(launch_nl_pre(p, u, ws, s, 0, p->M + 1));
-    TC_TRY_STATUS(launch_nl_theta(p, ws, s));
-    return launch_nl_post(p, u, N, ws, s, 0, p->M + 1);
+    if (p->precision == TC_MIXED) {
+        TC_TRY_STATUS(launch_nl_pre32(p, u, ws, s, 0, p->M + 1));
+        TC_TRY_STATUS(launch_nl_theta32(p, ws, s));
+        return launch_nl_post32(p, u, N, ws, s, 0, p->M + 1);
+    }
+    double2* H1 = reinterpret_cast<double2*>(ws + p->ws.H1);
+    double2* H2 = reinterpret_cast<double2*>(ws + p->ws.H2);
+    for (int r0 = 0; r0 < p->N_r; r0 += p->stage_rows) {
+        const int nh = p->N_r - r0 < p->stage_rows ? p->N_r - r0 : p->stage_rows;
+        TC_TRY_STATUS(zinv64(p, u, H1, s, 0, p->M + 1, r0, nh));
+        TC_TRY_STATUS(theta64(p, H1, H2, s, r0, nh));
+        TC_TRY_STATUS(zfwd64(p, H2, N, s, 0, p->M + 1, r0, nh));
+    }
+    return TC_OK;
 }
 
 }  // namespace tc

@@ -237,5 +237,31 @@ __device__ __forceinline__ V* passes_range(V* a, V* b, const V* __restrict__ tw,
     }
 }
 
+// ---------------------------------------------------------------- spectra of two line kinds
+// pair line x = c_r + i c_t from (A, B) = (c_+, c_-): spectrum A_m at m > 0, conj(B_m) at -m,
+// (A_0 + conj B_0)/2 at 0.  Real-pair line x + i y from (X, Y): X_m + i Y_m at m, conj(X_m) +
+// i conj(Y_m) at -m.
+template <typename V>
+__device__ __forceinline__ void put_pair(V* line, int PTn, int m, V A, V B) {
+    using T = typename Elem<V>::T;
+    if (m == 0) {
+        line[0] = vmk<V>((T)0.5 * (A.x + B.x), (T)0.5 * (A.y - B.y));
+    } else {
+        line[pd(m)] = A;
+        line[pd(PTn - m)] = vmk<V>(B.x, -B.y);
+    }
+}
+template <typename V>
+__device__ __forceinline__ void put_real2(V* line, int PTn, int m, V X, V Y) {
+    if (m == 0) {
+        line[0] = vmk<V>(X.x, Y.x);
+    } else {
+        line[pd(m)] = vmk<V>(X.x - Y.y, X.y + Y.x);
+        line[pd(PTn - m)] = vmk<V>(X.x + Y.y, Y.x - X.y);
+    }
+}
+template <typename V>
+__device__ __forceinline__ V imul(V a, typename Elem<V>::T s) { return vmk<V>(-s * a.y, s * a.x); }
+
 }  // namespace cft
 }  // namespace tc

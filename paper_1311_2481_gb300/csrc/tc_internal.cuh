@@ -27,20 +27,25 @@ struct Radices {
 };
 
 // Byte offsets of the workspace regions (all 256-byte aligned).
+// Every region is scratch of one library call; regions that no call uses at the same time
+// share memory (see tc_plan.cu).
 struct Workspace {
-    size_t H1;      // inverse z-pass output: 9 fields x N_r x (M+1) x P_z complex
-    size_t H2;      // theta-pass output: 3 fields x N_r x (M+1) x P_z complex
+    size_t H1;      // inverse z-pass output, 9 line sets [f][r][m][z]: FP64 lines of stage_rows
+                    // rows, or the mixed form's FP32 lines of all N_r rows
+    size_t H2;      // theta-pass output: 3 line sets, rows and precision as H1
     size_t P32;     // mixed form: u', d_r u' in FP32, 6 x S float2
-    size_t Ncur;    // N^i: vector field
+    size_t Ncur;    // N^i: vector field (everything before it is the forward staging)
     size_t uE;      // start-up Euler result: vector field
     size_t pstar;   // split path only: p* (scalar), u* (vector), phi (scalar)
     size_t ustar;
     size_t phi;
-    size_t red;     // diagnostics reduction buffer
-    // adjoint regions (absent with tc_options.no_adjoint)
-    size_t H3;      // adjoint theta-pass output: 9 fields x N_r x (M+1) x P_z complex
+    size_t red;     // diagnostics reduction buffer (diag_red_doubles doubles)
+    // adjoint regions (absent with tc_options.no_adjoint), FP64 lines of stage_rows rows
+    size_t H1a;     // recomputed forward lines of u: 9 line sets
+    size_t Ha;      // adjoint lines of Nbar: 3 line sets
+    size_t H3;      // adjoint theta-pass output: 9 line sets
+    size_t Rhat;    // adjoint d_r lines before the transposed stencil: 3 x stage_rows rows of modes
     size_t Nbar;    // adjoint of N: vector field
-    size_t Rhat;    // adjoint d_r lines before the transposed stencil: vector field
     size_t abar;    // start-up adjoint temporaries: 3 vector fields
     size_t total;
 };
@@ -57,7 +62,8 @@ struct tc_plan {
     bool used = false;  // a compute call has run (tc_plan_set is refused from then on)
     // derived sizes
     size_t S;        // complex entries of a scalar spectral field
-    size_t Hfield;   // complex entries of one z-pass line set: N_r (M+1) P_z
+    size_t Hfield;   // complex entries of one z-pass line set of all rows: N_r (M+1) P_z
+    int stage_rows;  // radial rows per slab of the FP64 transform staging
     int nmode;       // (M+1)(2K+1)
     int nmode_half;  // (M+1)(K+1)
     tc::Radices rad_z, rad_t;
@@ -176,14 +182,11 @@ void prof_end(tc_plan* p, int slot, cudaStream_t s);
 
 // ------------------------------------------------------------------ launchers
 tc_status launch_nonlinear(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s);
-tc_status launch_zinv_fp64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s);
+tc_status launch_zinv_fp64(tc_plan* p, const double2* u, double2* H1, cudaStream_t s, int r0, int nh);
 tc_status launch_theta32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t s);
 int theta_s_zt(const tc_plan* p, bool fp64);
 tc_status launch_theta_s(tc_plan* p, const float2* H1, float2* H2, cudaStream_t s);
-tc_status launch_theta_s64(tc_plan* p, const double2* H1, double2* H2, cudaStream_t s);
-tc_status launch_nl_pre(tc_plan* p, const double2* u, char* ws, cudaStream_t s, int ma, int mb);
-tc_status launch_nl_theta(tc_plan* p, char* ws, cudaStream_t s);
-tc_status launch_nl_post(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s, int ma, int mb);
+tc_status launch_theta_s64(tc_plan* p, const double2* H1, double2* H2, cudaStream_t s, int r0, int nh);
 tc_status launch_nl_pre32(tc_plan* p, const double2* u, char* ws, cudaStream_t s, int ma, int mb);
 tc_status launch_nl_theta32(tc_plan* p, char* ws, cudaStream_t s);
 tc_status launch_nl_post32(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s, int ma, int mb);
@@ -194,6 +197,7 @@ tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const do
 tc_status launch_axpby(tc_plan* p, double2* y, const double2* a, double ca, const double2* b,
                        double cb, size_t n, cudaStream_t s);
 tc_status launch_diagnostics(tc_plan* p, const double2* u, double* red, cudaStream_t s);
+size_t diag_red_doubles(const tc_plan* p);
 tc_status launch_adjoint_advance(tc_plan* p, const double2* ubar_new, const double2* ubar_cur,
                                  const double2* Nbar_cur, double2* u_out, double2* up_out,
                                  double2* N_out, double2* Np_out, cudaStream_t s);

@@ -641,7 +641,8 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     p->thr_theta = choose_threads(rt, 6 * p->zt, p->zt + (p->zt + 1) / 2);
     p->thr_zfwd = choose_threads(rz, p->zfwd_lines, 0);
     if (o.theta_zt < 0 || o.theta_zt > 64 || o.pc_modes < 0 || o.pc_modes > 32 || o.pc_split < -1 || o.pc_split > 1 ||
-        o.theta_variant < 0 || o.theta_variant > 4 || o.pc_partitions < 0 || o.pc_partitions > 2) {
+        o.theta_variant < 0 || o.theta_variant > 4 || o.pc_partitions < 0 || o.pc_partitions > 2 ||
+        o.stage_rows < 0) {
         delete p;
         return TC_ERR_ARG;
     }
@@ -655,14 +656,32 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     }
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o2 = off; off = align256(off + bytes); return o2; };
-    // transform staging in the plan's line precision; the FP64 adjoint also stages its
-    // recomputed forward lines in H1, so a plan with the adjoint keeps FP64-sized lines
     p->adjoint = o.no_adjoint == 0;
-    const size_t lane = (p->precision == TC_MIXED && !p->adjoint) ? sizeof(float2) : cplx;
-    p->ws.H1 = take(9 * p->Hfield * lane);
-    p->ws.H2 = take(3 * p->Hfield * lane);
-    // the mixed form's FP32 u', d_r u', in a region of its own before N^i
-    p->ws.P32 = take(p->precision == TC_MIXED ? 6 * p->S * sizeof(float2) : 0);
+    // FP64 staging rows per slab: the FP64 forward lines (12 line sets) and the adjoint's
+    // (21 line sets and the Rhat rows) of stage_rows rows
+    {
+        const size_t hrow = (size_t)(M + 1) * Pz * cplx;
+        size_t per_row = p->precision == TC_MIXED ? 0 : 12 * hrow;
+        if (p->adjoint) per_row = std::max(per_row, 21 * hrow + 3 * (size_t)p->nmode * cplx);
+        const size_t cap = (size_t)4 << 30;
+        int rows = N_r;
+        if (o.stage_rows > 0) rows = std::min(o.stage_rows, N_r);
+        else if (per_row * (size_t)N_r > cap) rows = (int)std::max<size_t>(1, cap / std::max<size_t>(per_row, 1));
+        p->stage_rows = rows;
+    }
+    // forward transform staging: FP64 lines of stage_rows rows, or the mixed form's FP32
+    // lines of all rows and its FP32 u', d_r u'
+    if (p->precision == TC_MIXED) {
+        p->ws.H1 = take(9 * p->Hfield * sizeof(float2));
+        p->ws.H2 = take(3 * p->Hfield * sizeof(float2));
+        p->ws.P32 = take(6 * p->S * sizeof(float2));
+    } else {
+        const size_t hst = (size_t)p->stage_rows * (M + 1) * Pz;
+        p->ws.H1 = take(9 * hst * cplx);
+        p->ws.H2 = take(3 * hst * cplx);
+        p->ws.P32 = take(0);
+    }
+    const size_t fwd_staging = off;
     p->ws.Ncur = take(3 * p->S * cplx);
     p->ws.uE = take(3 * p->S * cplx);
     // steps 2-5: fused kernel while 8 modes' four columns fit in 96 KB of shared memory,
@@ -678,17 +697,29 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
         std::vector<double>().swap(p->rinv);
         std::vector<uint8_t>().swap(p->piv2);
     }
+    p->ws.red = take(diag_red_doubles(p) * sizeof(double));
+    // The split steps-2-5 buffers (used only inside a forward advance) and the adjoint
+    // step's regions (used only inside an adjoint step, after any advance of the same call)
+    // share one region.
+    const size_t shared0 = off;
     if (p->pc_split) {
         p->ws.pstar = take(p->S * cplx);
         p->ws.ustar = take(3 * p->S * cplx);
         p->ws.phi = take(p->S * cplx);
     }
-    p->ws.red = take(4096 * sizeof(double));
+    const size_t split_end = off;
     if (p->adjoint) {
-        p->ws.H3 = take(9 * p->Hfield * cplx);
+        off = shared0;
+        const size_t hst = (size_t)p->stage_rows * (M + 1) * Pz;
+        p->ws.H1a = take(9 * hst * cplx);
+        p->ws.Ha = take(3 * hst * cplx);
+        p->ws.H3 = take(9 * hst * cplx);
+        p->ws.Rhat = take(3 * (size_t)p->stage_rows * p->nmode * cplx);
         p->ws.Nbar = take(3 * p->S * cplx);
-        p->ws.Rhat = take(3 * p->S * cplx);
-        p->ws.abar = take(9 * p->S * cplx);
+        off = std::max(off, split_end);
+        // tc_adjoint_start's temporaries live from u^{-1} = 2.5 u0 - 1.5 u_E on, after its one
+        // forward nonlinear evaluation: they take the forward staging when it is large enough
+        p->ws.abar = fwd_staging >= 9 * p->S * cplx ? 0 : take(9 * p->S * cplx);
     }
     p->ws.total = off;
     if (!p->host_only) {
@@ -749,6 +780,7 @@ tc_status tc_plan_set(tc_plan* plan, int key, double value) {
             case TC_SET_PC_SPLIT: o.pc_split = v; break;
             case TC_SET_THETA_VARIANT: o.theta_variant = v; break;
             case TC_SET_PC_PARTITIONS: o.pc_partitions = v; break;
+            case TC_SET_STAGE_ROWS: o.stage_rows = v; break;
             default: return TC_ERR_ARG;
         }
     }

@@ -564,7 +564,10 @@ __global__ void k_axpby(double2* __restrict__ y, const double2* __restrict__ a, 
     y[e] = make_double2(ca * x.x + cb * z.x, ca * x.y + cb * z.y);
 }
 
-// Diagnostics: red[0] += energy, red[1] = max |div_h u| (as ordered bits), red[2] += non-finite.
+// Diagnostics: red[1] = max |div_h u| (as ordered bits), red[2] += non-finite, and each
+// block's energy sum in red[kDiagPartials + block]; k_diag_sum adds those in a fixed order into
+// red[0], so the energy does not depend on the order in which blocks finish.
+constexpr int kDiagPartials = 8;
 __global__ void k_diag(const double2* __restrict__ u, double* __restrict__ red,
                        const double* __restrict__ rn, const double* __restrict__ w1,
                        const int* __restrict__ col0, double C1, double C2, Geo g) {
@@ -624,13 +627,33 @@ __global__ void k_diag(const double2* __restrict__ u, double* __restrict__ red,
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        atomicAdd(&red[0], s_e[0]);
+        red[kDiagPartials + (size_t)blockIdx.y * gridDim.x + blockIdx.x] = s_e[0];
         atomicMax(reinterpret_cast<unsigned long long*>(&red[1]), s_d[0]);
         atomicAdd(reinterpret_cast<unsigned long long*>(&red[2]), (unsigned long long)s_n[0]);
     }
 }
 
+// red[0] = sum of the n block partials: each thread a contiguous run, then a tree (one block)
+__global__ void __launch_bounds__(1024) k_diag_sum(double* __restrict__ red, int n) {
+    __shared__ double s[1024];
+    const int per = (n + 1023) / 1024;
+    double a = 0.0;
+    for (int i = threadIdx.x * per; i < (threadIdx.x + 1) * per && i < n; ++i) a += red[kDiagPartials + i];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) red[0] = s[0];
+}
+
 static int blocks_for(size_t n, int bs) { return (int)((n + bs - 1) / bs); }
+
+// doubles of the diagnostics reduction buffer: the fixed slots and one partial per k_diag block
+size_t diag_red_doubles(const tc_plan* p) {
+    return kDiagPartials + (size_t)blocks_for((size_t)p->nmode, 256) * p->N_r;
+}
 
 // modes per block of the fused kernel: four complex columns of N_r rows in shared memory
 // Modes per block of the fused kernel (a power of two): the most (up to 16) that still give every SM a block,
@@ -758,7 +781,11 @@ tc_status launch_diagnostics(tc_plan* p, const double2* u, double* red, cudaStre
     const double C1 = (p->Re_o - eta * p->Re_i) / (1.0 + eta);
     const double C2 = eta * (p->Re_i - eta * p->Re_o) / ((1.0 - eta) * (1.0 - eta * eta));
     TC_CUDA(p, cudaMemsetAsync(red, 0, 4 * sizeof(double), s));
-    { const int slot_ = prof_begin(p, kKDiag, s); k_diag<<<dim3(blocks_for(g.nmode, 256), g.N), 256, 0, s>>>(u, red, p->d_r, p->d_w1, p->d_col0, C1, C2, g); prof_end(p, slot_, s); }
+    const dim3 grid(blocks_for(g.nmode, 256), g.N);
+    const int slot = prof_begin(p, kKDiag, s);
+    k_diag<<<grid, 256, 0, s>>>(u, red, p->d_r, p->d_w1, p->d_col0, C1, C2, g);
+    k_diag_sum<<<1, 1024, 0, s>>>(red, (int)(grid.x * grid.y));
+    prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_diag");
     return TC_OK;
 }

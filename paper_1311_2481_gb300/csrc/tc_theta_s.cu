@@ -18,36 +18,6 @@ namespace tc {
 
 using namespace cft;
 
-namespace {
-
-// ---------------------------------------------------------------- spectra of two line kinds
-// pair line x = c_r + i c_t from (A, B) = (c_+, c_-): spectrum A_m at m > 0, conj(B_m) at -m,
-// (A_0 + conj B_0)/2 at 0.  Real-pair line x + i y from (X, Y): X_m + i Y_m at m, conj(X_m) +
-// i conj(Y_m) at -m.
-template <typename V>
-__device__ __forceinline__ void put_pair(V* line, int PTn, int m, V A, V B) {
-    using T = typename Elem<V>::T;
-    if (m == 0) {
-        line[0] = vmk<V>((T)0.5 * (A.x + B.x), (T)0.5 * (A.y - B.y));
-    } else {
-        line[pd(m)] = A;
-        line[pd(PTn - m)] = vmk<V>(B.x, -B.y);
-    }
-}
-template <typename V>
-__device__ __forceinline__ void put_real2(V* line, int PTn, int m, V X, V Y) {
-    if (m == 0) {
-        line[0] = vmk<V>(X.x, Y.x);
-    } else {
-        line[pd(m)] = vmk<V>(X.x - Y.y, X.y + Y.x);
-        line[pd(PTn - m)] = vmk<V>(X.x + Y.y, Y.x - X.y);
-    }
-}
-template <typename V>
-__device__ __forceinline__ V imul(V a, typename Elem<V>::T s) { return vmk<V>(-s * a.y, s * a.x); }
-
-}  // namespace
-
 // H1 fields: f = 3 d + c, c in {+, -, z}, d in {u, d_r u, d_z u}.
 // Phase 0: lines (u_r, u_t) and (u_z, d_r u_z); phase 1: (d_r u_r, d_r u_t) and
 // (d_t u_r, d_t u_t); phase 2: (d_z u_r, d_z u_t) and (d_t u_z, d_z u_z); then the forward
@@ -59,7 +29,7 @@ __device__ __forceinline__ V imul(V a, typename Elem<V>::T s) { return vmk<V>(-s
 // forward pass (NS = 1) reads N_r + i N_t and N_z from the per-point arrays directly.
 template <typename V, int PT, int ZT, int NT, int MINB, bool R8, bool FUSE = false>
 __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, V* __restrict__ H2,
-                                                      const double* __restrict__ irn, int N_r, int M, int Pz,
+                                                      const double* __restrict__ irn, int r0, int nh, int M, int Pz,
                                                       double mp, const V* __restrict__ tw,
                                                       const float* __restrict__ dsc) {
     using T = typename Elem<V>::T;
@@ -84,15 +54,15 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, 
     V* TW = Nn + NPT;
     const V* twp = TWS ? TW : tw;
     const int tiles = Pz / ZT;
-    const int r = blockIdx.x / tiles;
+    const int r = blockIdx.x / tiles;   // row within the staged rows r0 .. r0 + nh - 1
     const int z0 = (blockIdx.x % tiles) * ZT;
-    const size_t fstride = (size_t)N_r * (M + 1) * Pz;
+    const size_t fstride = (size_t)nh * (M + 1) * Pz;
     const V* h = H1 + (size_t)r * (M + 1) * Pz + z0;
-    const T ir = (T)irn[r];   // 1 / r_j from the plan
+    const T ir = (T)irn[r0 + r];   // 1 / r_j from the plan
     const T mpf = (T)mp;
     // FP32 lines: d_r u_z enters the (u_z, d_r u_z) line scaled by a power of two, so that
     // its rounding does not swamp u_z near the walls; FP64 lines are not scaled
-    const T ds = sizeof(V) == 8 ? (T)dsc[r] : (T)1, ids = (T)1 / ds;
+    const T ds = sizeof(V) == 8 ? (T)dsc[r0 + r] : (T)1, ids = (T)1 / ds;
     const int zi = threadIdx.x % ZT;        // z of this thread in the load and store loops
     const int mstep = NT / ZT;
     if constexpr (TWS) {
@@ -291,14 +261,14 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_s(const V* __restrict__ H1, 
 namespace {
 
 template <typename V, int PT, int ZT, int NT, int MINB, bool R8, bool FUSE = false>
-tc_status run_theta_s(tc_plan* p, const V* H1, V* H2, const V* tw, cudaStream_t s) {
+tc_status run_theta_s(tc_plan* p, const V* H1, V* H2, const V* tw, cudaStream_t s, int r0, int nh) {
     constexpr int LP = padded<PT>();
     const size_t sm = ((size_t)2 * 2 * ZT * LP + (size_t)3 * ZT * PT + (FUSE && PT != 1152 ? PT : 0)) * sizeof(V);
     auto kern = k_theta_s<V, PT, ZT, NT, MINB, R8, FUSE>;
     TC_CUDA(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int slot = prof_begin(p, sizeof(V) == 8 ? kKTheta32 : kKTheta, s);
-    kern<<<p->N_r * (p->P_z / ZT), NT, sm, s>>>(H1, H2, p->d_ir, p->N_r, p->M, p->P_z, (double)p->m_p, tw,
-                                                 sizeof(V) == 8 ? p->d_dsc : nullptr);
+    kern<<<nh * (p->P_z / ZT), NT, sm, s>>>(H1, H2, p->d_ir, r0, nh, p->M, p->P_z, (double)p->m_p, tw,
+                                             sizeof(V) == 8 ? p->d_dsc : nullptr);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_theta_s");
     return TC_OK;
@@ -319,12 +289,12 @@ tc_status theta_s32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t s) {
     constexpr int Zh = Z > 1 ? Z / 2 : 1;
     const int v = p->theta_variant ? p->theta_variant : (PT <= 96 ? 2 : PT >= 384 ? 4 : 1);
     switch (v) {
-        case 2: return run_theta_s<float2, PT, Zh, NT, (NT > 256 ? 3 : 4), true>(p, H1, H2, tw, s);
-        case 3: return run_theta_s<float2, PT, Zh, NT, (NT > 256 ? 2 : 3), true>(p, H1, H2, tw, s);
+        case 2: return run_theta_s<float2, PT, Zh, NT, (NT > 256 ? 3 : 4), true>(p, H1, H2, tw, s, 0, p->N_r);
+        case 3: return run_theta_s<float2, PT, Zh, NT, (NT > 256 ? 2 : 3), true>(p, H1, H2, tw, s, 0, p->N_r);
         case 4:
-            if constexpr (PT >= 384) return run_theta_s<float2, PT, Z, NT, 2, false, true>(p, H1, H2, tw, s);
-            return run_theta_s<float2, PT, Z, NT, 2, false>(p, H1, H2, tw, s);
-        default: return run_theta_s<float2, PT, Z, NT, 2, false>(p, H1, H2, tw, s);
+            if constexpr (PT >= 384) return run_theta_s<float2, PT, Z, NT, 2, false, true>(p, H1, H2, tw, s, 0, p->N_r);
+            return run_theta_s<float2, PT, Z, NT, 2, false>(p, H1, H2, tw, s, 0, p->N_r);
+        default: return run_theta_s<float2, PT, Z, NT, 2, false>(p, H1, H2, tw, s, 0, p->N_r);
     }
 }
 
@@ -366,17 +336,17 @@ tc_status launch_theta_s(tc_plan* p, const float2* H1, float2* H2, cudaStream_t 
     return TC_ERR_ARG;
 }
 
-tc_status launch_theta_s64(tc_plan* p, const double2* H1, double2* H2, cudaStream_t s) {
+tc_status launch_theta_s64(tc_plan* p, const double2* H1, double2* H2, cudaStream_t s, int r0, int nh) {
     if (theta_s_zt(p, true) == 0) return TC_ERR_ARG;
     const double2* tw = p->d_tw_t;
     // the FUSE form measured no faster with FP64 lines (0.4425 vs 0.4445 ms at the bench size):
     // the FP64 pipe, not shared memory, bounds this kernel
     switch (p->P_t) {
-        case 96: return run_theta_s<double2, 96, 4, 128, 3, true>(p, H1, H2, tw, s);
-        case 192: return run_theta_s<double2, 192, 2, 128, 3, true>(p, H1, H2, tw, s);
-        case 384: return run_theta_s<double2, 384, 2, 256, 2, true>(p, H1, H2, tw, s);
-        case 768: return run_theta_s<double2, 768, 1, 256, 2, true>(p, H1, H2, tw, s);
-        case 1152: return run_theta_s<double2, 1152, 1, 384, 1, true>(p, H1, H2, tw, s);
+        case 96: return run_theta_s<double2, 96, 4, 128, 3, true>(p, H1, H2, tw, s, r0, nh);
+        case 192: return run_theta_s<double2, 192, 2, 128, 3, true>(p, H1, H2, tw, s, r0, nh);
+        case 384: return run_theta_s<double2, 384, 2, 256, 2, true>(p, H1, H2, tw, s, r0, nh);
+        case 768: return run_theta_s<double2, 768, 1, 256, 2, true>(p, H1, H2, tw, s, r0, nh);
+        case 1152: return run_theta_s<double2, 1152, 1, 384, 1, true>(p, H1, H2, tw, s, r0, nh);
     }
     return TC_ERR_ARG;
 }
