@@ -555,7 +555,9 @@ def config5_adjoint(tc, torch, I, dev, n_total=100, n_adj=50, checkpoint=17):
     t_sg = ev[2].elapsed_time(ev[3])
     back = (t_sg - t_fwd * n_adj) / n_adj
     finite = all(bool(torch.isfinite(torch.view_as_real(t)).all()) for t in (bar.u, bar.u_prev, bar.N_prev))
-    mem = torch.cuda.max_memory_allocated() / 1e9
+    mem = torch.cuda.max_memory_allocated() / 1e9     # torch's tensors (the plan's factors are not among them)
+    free, total = torch.cuda.mem_get_info()
+    used = (total - free) / 1e9                       # the whole device, torch's cache at its peak included
     # central difference of J(u + h g_u) along g_u = dJ/du, against <g_u, g_u>
     g = bar.u
     del bar
@@ -580,7 +582,7 @@ def config5_adjoint(tc, torch, I, dev, n_total=100, n_adj=50, checkpoint=17):
             "forward_ms_per_step": t_fwd, "state_gradient_ms": t_sg, "backward_ms_per_step": back,
             "adjoint_to_forward_ratio": back / t_fwd, "J": J, "grad_finite": finite,
             "u_slots": slots, "host_checkpoint_gb": -(-n_adj // checkpoint) * 3 * field / 1e9,
-            "device_memory_gb": mem,
+            "device_memory_gb": mem, "device_used_gb": used,
             "fd_along_grad": fd, "grad_norm_sq": gn2, "fd_rel_diff": abs(fd - gn2) / gn2,
             "fd_note": "central difference of J through the mixed forward vs <g, g> from the FP64 adjoint"}
 
@@ -636,9 +638,22 @@ def config5_dot_product(tc, torch, I, dev, h_scale=1.0):
     plan.adjoint_step(st, bar)
     rhs = sum(float(torch.sum(torch.view_as_real(getattr(bar, k)) * torch.view_as_real(b.to(dev))))
               for k, b in zip(names, x))
+    # kernel times of one FP64 adjoint step and one FP64 step at this size (CUDA events)
+    plan.profile(True)
+    plan.adjoint_step(st, bar)
+    torch.cuda.synchronize()
+    adj = {k: v[1] for k, v in plan.profile_read().items()}
+    plan.profile(False)
+    plan.profile(True)
+    plan.step(st, 1)
+    torch.cuda.synchronize()
+    fwd = {k: v[1] for k, v in plan.profile_read().items()}
+    plan.profile(False)
     return {"workload": "N_r=384, m=-384..384, k=-768..768, FP64 step and adjoint step at a started "
                         "state (one step from the broadband initial state)",
             "lhs": lhs, "rhs": rhs, "rel_diff": abs(lhs - rhs) / abs(rhs),
+            "adjoint_step_kernels_ms": adj, "adjoint_step_ms": sum(adj.values()),
+            "fp64_step_kernels_ms": fwd, "fp64_step_ms": sum(fwd.values()),
             "device_memory_gb": torch.cuda.max_memory_allocated() / 1e9}
 
 

@@ -404,6 +404,203 @@ __global__ void __launch_bounds__(256) k_pc_adj(PCAdjArgs a, Geo g, int T) {
     }
 }
 
+// ---------------------------------------------------------------- transposed steps 2-5, per stage
+// The same phases as k_pc_adj as one kernel per stage over all modes, for large N_r: each
+// column lives in global memory, so every transposed substitution runs on its own thread
+// (mode, real / imaginary part) with full warps, where k_pc_adj would hold few modes per
+// block.  Scratch: US (3 fields), PH and PS (one each), the forward split path's buffers.
+// A wall row of PH, US or PS holds no dependence after its solve and is read as zero.
+
+struct AdjT {
+    const double* ir;
+    const int* trow;
+    const double* tw;
+    int ntab;
+};
+
+// sum_e D1[row_e][j] f(row_e) over the rows whose stencil holds column j; wall rows of f
+// dropped when `walls` is false
+__device__ __forceinline__ double2 growT(const double2* __restrict__ f, const AdjT& a, int j, int nmode,
+                                         int mode, int N, bool walls) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int e = 0; e < a.ntab; ++e) {
+        const int row = __ldg(&a.trow[j * a.ntab + e]);
+        if (!walls && (row == 0 || row == N - 1)) continue;
+        const double w = __ldg(&a.tw[j * a.ntab + e]);
+        const double2 v = f[(size_t)row * nmode + mode];
+        s.x = fma(w, v.x, s.x);
+        s.y = fma(w, v.y, s.y);
+    }
+    return s;
+}
+
+// grad_h^T of the vector field v at (j, mode), negated: -(D1^T(v_+ + v_-) - m m_p (v_+ - v_-)/r
+// - i k k_z v_z); wall rows of v read as zero unless `walls`
+__device__ __forceinline__ double2 neg_gradT(const double2* __restrict__ v, const AdjT& a, const Geo& g, int j,
+                                             int mode, bool walls) {
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    const double2 dp = growT(v, a, j, g.nmode, mode, g.N, walls);
+    const double2 dm = growT(v + g.S, a, j, g.nmode, mode, g.N, walls);
+    const bool wall = j == 0 || j == g.N - 1;
+    const size_t e = (size_t)j * g.nmode + mode;
+    const double2 z0 = make_double2(0.0, 0.0);
+    const double2 gp = (walls || !wall) ? v[e] : z0, gm = (walls || !wall) ? v[g.S + e] : z0;
+    const double2 gz = (walls || !wall) ? v[2 * g.S + e] : z0;
+    const double mm = g.mp * m * a.ir[j], kk = g.kz * k;
+    return make_double2(-(dp.x + dm.x - mm * (gp.x - gm.x) + kk * gz.y),
+                        -(dp.y + dm.y - mm * (gp.y - gm.y) - kk * gz.x));
+}
+
+// G': PH = -grad_h^T ubar_new
+__global__ void k_adjT_phi(const double2* __restrict__ ubn, double2* __restrict__ PH, AdjT a, Geo g) {
+    const int mode = blockIdx.y * blockDim.x + threadIdx.x;   // x = radial row
+    if (mode >= g.nmode) return;
+    const int j = blockIdx.x;
+    PH[(size_t)j * g.nmode + mode] = neg_gradT(ubn, a, g, j, mode, true);
+}
+
+// E': US = ubar_new + div_h^T PH (PH's wall rows zero)
+__global__ void k_adjT_ustar(const double2* __restrict__ ubn, const double2* __restrict__ PH,
+                             double2* __restrict__ US, AdjT a, Geo g) {
+    const int mode = blockIdx.y * blockDim.x + threadIdx.x;
+    if (mode >= g.nmode) return;
+    const int j = blockIdx.x;
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    const size_t e = (size_t)j * g.nmode + mode;
+    const double ir = a.ir[j];
+    const double2 d = growT(PH, a, j, g.nmode, mode, g.N, false);
+    const double2 b = (j == 0 || j == g.N - 1) ? make_double2(0.0, 0.0) : PH[e];
+    const double2 tt = make_double2(d.x + b.x * ir, d.y + b.y * ir);
+    const double mm = 0.5 * g.mp * m * ir, kk = g.kz * k;
+    double2 v;
+    v = ubn[e]; v.x += 0.5 * tt.x + mm * b.x; v.y += 0.5 * tt.y + mm * b.y; US[e] = v;
+    v = ubn[g.S + e]; v.x += 0.5 * tt.x - mm * b.x; v.y += 0.5 * tt.y - mm * b.y; US[g.S + e] = v;
+    v = ubn[2 * g.S + e]; v.x += kk * b.y; v.y -= kk * b.x; US[2 * g.S + e] = v;
+}
+
+// C': with rb = US (wall rows zero): u_out = ubar_cur + (2/dt) rb, up_out = -rb/(2 dt),
+// PS = -grad_h^T rb.  u_out may alias ubar_new (no longer read) and up_out ubar_cur (read
+// first, by the same thread).
+__global__ void k_adjT_rhs(const double2* __restrict__ US, const double2* ubc, double2* u_out, double2* up_out,
+                           double2* __restrict__ PS, AdjT a, Geo g) {
+    const int mode = blockIdx.y * blockDim.x + threadIdx.x;
+    if (mode >= g.nmode) return;
+    const int j = blockIdx.x;
+    const size_t e = (size_t)j * g.nmode + mode;
+    const bool wall = j == 0 || j == g.N - 1;
+    const double dt = g.dt;
+    for (int c = 0; c < 3; ++c) {
+        const size_t ec = (size_t)c * g.S + e;
+        const double2 rb = wall ? make_double2(0.0, 0.0) : US[ec];
+        double2 ub = ubc ? ubc[ec] : make_double2(0.0, 0.0);
+        ub.x += 2.0 / dt * rb.x;
+        ub.y += 2.0 / dt * rb.y;
+        u_out[ec] = ub;
+        up_out[ec] = make_double2(-rb.x / (2.0 * dt), -rb.y / (2.0 * dt));
+    }
+    PS[e] = neg_gradT(US, a, g, j, mode, false);
+}
+
+// A': NNbar = -rb + div_h^T(-bpbar on interior rows) and the wall-row terms of Eq. ppBC;
+// N_out = Nbar_cur + 2 NNbar, Np_out = -NNbar (Np_out may alias Nbar_cur: same thread)
+__global__ void k_adjT_nn(const double2* __restrict__ US, const double2* __restrict__ PS, const double2* Nbc,
+                          double2* N_out, double2* Np_out, AdjT a, Geo g) {
+    const int mode = blockIdx.y * blockDim.x + threadIdx.x;
+    if (mode >= g.nmode) return;
+    const int j = blockIdx.x;
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    const size_t e = (size_t)j * g.nmode + mode;
+    const int N = g.N;
+    const bool wall = j == 0 || j == N - 1;
+    const double ir = a.ir[j];
+    const double2 dd = growT(PS, a, j, g.nmode, mode, N, false);
+    const double2 d = make_double2(-dd.x, -dd.y);
+    const double2 bp = PS[e];
+    const double2 v = wall ? make_double2(0.0, 0.0) : make_double2(-bp.x, -bp.y);
+    const double2 tt = make_double2(d.x + v.x * ir, d.y + v.y * ir);
+    const double mm = 0.5 * g.mp * m * ir, kk = g.kz * k;
+    const bool wterm = j == 0 || (j == N - 1 && !(m == 0 && k == 0));
+    double2 q[3];
+    for (int c = 0; c < 3; ++c) {
+        const double2 rb = wall ? make_double2(0.0, 0.0) : US[(size_t)c * g.S + e];
+        q[c] = make_double2(-rb.x, -rb.y);
+    }
+    q[0].x += 0.5 * tt.x + mm * v.x; q[0].y += 0.5 * tt.y + mm * v.y;
+    q[1].x += 0.5 * tt.x - mm * v.x; q[1].y += 0.5 * tt.y - mm * v.y;
+    if (wterm) {
+        q[0].x -= 0.5 * bp.x; q[0].y -= 0.5 * bp.y;
+        q[1].x -= 0.5 * bp.x; q[1].y -= 0.5 * bp.y;
+    }
+    q[2].x += kk * v.y; q[2].y -= kk * v.x;
+    for (int c = 0; c < 3; ++c) {
+        const size_t ec = (size_t)c * g.S + e;
+        double2 nb = Nbc ? Nbc[ec] : make_double2(0.0, 0.0);
+        nb.x += 2.0 * q[c].x;
+        nb.y += 2.0 * q[c].y;
+        N_out[ec] = nb;
+        Np_out[ec] = make_double2(-q[c].x, -q[c].y);
+    }
+}
+
+// Wall Laplacian transposes of Eq. ppBC's wall rows (side 0: r_i, 1: r_o; `sides` of them
+// from `side0`): column c of the wall stencil receives 1/2 (D2 + D1/r)[jw][c] bpbar(jw)
+// (+ the diagonal terms at c = jw), times 2 into u_out and -1 into up_out, for the + and -
+// components.  One thread per (side, stencil column, mode); the two sides touch the same
+// columns only when N_r < 18, and then run as two launches.
+__global__ void k_adjT_wall(const double2* __restrict__ PS, double2* u_out, double2* up_out,
+                            const double* __restrict__ w1, const double* __restrict__ w2,
+                            const int* __restrict__ col0, AdjT a, Geo g, int side0) {
+    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode >= g.nmode) return;
+    const int q = blockIdx.y;
+    const int side = side0 + blockIdx.z;
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    const int jw = side == 0 ? 0 : g.N - 1;
+    if (jw == g.N - 1 && m == 0 && k == 0) return;
+    const int c = col0[jw] + q;
+    const double ir = a.ir[jw], ir2 = ir * ir;
+    const double wq = 0.5 * (w2[jw * kStencil + q] + ir * w1[jw * kStencil + q]);
+    const double2 w = PS[(size_t)jw * g.nmode + mode];
+    const double mm = g.mp * m, kk = g.kz * k;
+    const size_t e = (size_t)c * g.nmode + mode;
+    for (int cc = 0; cc < 2; ++cc) {
+        double coef = wq;
+        if (c == jw) {
+            const double sgn = cc == 0 ? -1.0 : 1.0;
+            coef += 0.5 * (-mm * mm * ir2 - kk * kk - ir2 + sgn * 2.0 * mm * ir2);
+        }
+        if (coef == 0.0) continue;
+        const size_t ec = (size_t)cc * g.S + e;
+        double2 ub = u_out[ec], pb = up_out[ec];
+        ub.x += 2.0 * coef * w.x; ub.y += 2.0 * coef * w.y;
+        pb.x -= coef * w.x; pb.y -= coef * w.y;
+        u_out[ec] = ub;
+        up_out[ec] = pb;
+    }
+}
+
+// x <- A^{-T} x for every mode of nfields consecutive fields (sets set0, set0 + 1, ...):
+// thread (field, mode, part) runs the transposed substitution down its global column
+__global__ void k_band_solve_gT(double2* __restrict__ x, const double* __restrict__ fac,
+                                const uint8_t* __restrict__ piv, int set0, Geo g) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;   // (mode, part); y = field
+    if (t >= 2 * g.nmode) return;
+    const int part = t & 1;
+    const int mode = t >> 1;
+    const int fld = blockIdx.y;
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    const size_t mk = (size_t)m * g.K1 + (k < 0 ? -k : k);
+    const size_t per_set = (size_t)g.N * kBands * g.M1K1;
+    const int set = set0 + fld;
+    smem_band_solve_T(x + (size_t)fld * g.S, g.nmode, mode, part, g.N, fac + (size_t)set * per_set + mk,
+                      piv + (size_t)set * g.N * g.M1K1 + mk, g.M1K1);
+}
+
 // ---------------------------------------------------------------- transposed nonlinear term
 // Transposed forward transform: a physical field x = (1/(P_t P_z)) Re sum_{m>=0,k} w e^{i phi};
 // with the C2R convention (weight 2 for m > 0) the lines carry w/2 for m > 0.  Lines per
@@ -1041,8 +1238,36 @@ __global__ void k_drT(double2* __restrict__ ub, const double2* __restrict__ Rh, 
 
 tc_status launch_adjoint_advance(tc_plan* p, const double2* ubar_new, const double2* ubar_cur,
                                  const double2* Nbar_cur, double2* u_out, double2* up_out,
-                                 double2* N_out, double2* Np_out, cudaStream_t s) {
+                                 double2* N_out, double2* Np_out, char* ws, cudaStream_t s) {
     Geo g = geo(p);
+    if (p->pc_split) {
+        // per-stage transposed steps 2-5 (the forward split path's scratch)
+        double2* PS = reinterpret_cast<double2*>(ws + p->ws.pstar);
+        double2* US = reinterpret_cast<double2*>(ws + p->ws.ustar);
+        double2* PH = reinterpret_cast<double2*>(ws + p->ws.phi);
+        AdjT a{p->d_ir, p->d_d1t_row, p->d_d1t_w, p->d1t_n};
+        const dim3 g1(g.N, ablocks(g.nmode, 128));
+        auto sgrid = [&](int nf) { return dim3(ablocks((size_t)2 * g.nmode, 128), nf); };
+        const int slot = prof_begin(p, kKPCAdj, s);
+        k_adjT_phi<<<g1, 128, 0, s>>>(ubar_new, PH, a, g);
+        k_band_solve_gT<<<sgrid(1), 128, 0, s>>>(PH, p->d_fac, p->d_piv, kSetP, g);
+        k_adjT_ustar<<<g1, 128, 0, s>>>(ubar_new, PH, US, a, g);
+        k_band_solve_gT<<<sgrid(3), 128, 0, s>>>(US, p->d_fac, p->d_piv, kSetHp, g);
+        k_adjT_rhs<<<g1, 128, 0, s>>>(US, ubar_cur, u_out, up_out, PS, a, g);
+        k_band_solve_gT<<<sgrid(1), 128, 0, s>>>(PS, p->d_fac, p->d_piv, kSetP, g);
+        k_adjT_nn<<<g1, 128, 0, s>>>(US, PS, Nbar_cur, N_out, Np_out, a, g);
+        if (g.N >= 2 * kStencil) {
+            k_adjT_wall<<<dim3(ablocks(g.nmode, 128), kStencil, 2), 128, 0, s>>>(PS, u_out, up_out, p->d_w1, p->d_w2,
+                                                                                p->d_col0, a, g, 0);
+        } else {
+            for (int side = 0; side < 2; ++side)
+                k_adjT_wall<<<dim3(ablocks(g.nmode, 128), kStencil, 1), 128, 0, s>>>(PS, u_out, up_out, p->d_w1,
+                                                                                    p->d_w2, p->d_col0, a, g, side);
+        }
+        prof_end(p, slot, s);
+        TC_LAUNCHED(p, "k_adjT");
+        return TC_OK;
+    }
     int T = p->pc_modes > 0 ? p->pc_modes : 8;
     while (T > 1 && (size_t)4 * p->N_r * T * sizeof(double2) > 96 * 1024) T /= 2;
     PCAdjArgs a;
@@ -1260,7 +1485,7 @@ tc_status tc_adjoint_step(tc_plan* plan, const tc_state* fwd, tc_state_bar* bar,
     double2* upb = static_cast<double2*>(bar->u_prev);
     double2* Npb = static_cast<double2*>(bar->N_prev);
     double2* Nb = reinterpret_cast<double2*>(w + plan->ws.Nbar);
-    TC_TRY2(launch_adjoint_advance(plan, ub, upb, Npb, ub, upb, Nb, Npb, s));
+    TC_TRY2(launch_adjoint_advance(plan, ub, upb, Npb, ub, upb, Nb, Npb, w, s));
     return launch_nonlinear_adjoint(plan, static_cast<const double2*>(fwd->u), Nb, ub, w, s);
 }
 
@@ -1299,7 +1524,7 @@ tc_status tc_adjoint_start(tc_plan* plan, const void* u0, const tc_state_bar* ba
     double2* a_up = uE;   // adjoint of its u_prev input
     double2* a_N = Nb;    // adjoint of its N input
     double2* a_Np = Nc;   // adjoint of its N_prev input
-    TC_TRY2(launch_adjoint_advance(plan, uEb, nullptr, nullptr, a_u, a_up, a_N, a_Np, s));
+    TC_TRY2(launch_adjoint_advance(plan, uEb, nullptr, nullptr, a_u, a_up, a_N, a_Np, w, s));
     // u0_bar = ubar + 2.5 m1_bar + a_u + a_up + N'(u0)^T (a_N + a_Np)
     TC_TRY2(launch_axpby(plan, out, out, 1.0, a_up, 1.0, n3, s));
     TC_TRY2(launch_axpby(plan, out, out, 1.0, m1b, 2.5, n3, s));

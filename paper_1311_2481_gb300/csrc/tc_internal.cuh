@@ -200,7 +200,7 @@ tc_status launch_diagnostics(tc_plan* p, const double2* u, double* red, cudaStre
 size_t diag_red_doubles(const tc_plan* p);
 tc_status launch_adjoint_advance(tc_plan* p, const double2* ubar_new, const double2* ubar_cur,
                                  const double2* Nbar_cur, double2* u_out, double2* up_out,
-                                 double2* N_out, double2* Np_out, cudaStream_t s);
+                                 double2* N_out, double2* Np_out, char* ws, cudaStream_t s);
 tc_status launch_energy_gradient(tc_plan* p, const double2* u, double2* g, cudaStream_t s);
 tc_status launch_nonlinear_adjoint(tc_plan* p, const double2* u, const double2* Nbar, double2* ubar,
                                    char* ws, cudaStream_t s);

@@ -698,9 +698,9 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
         std::vector<uint8_t>().swap(p->piv2);
     }
     p->ws.red = take(diag_red_doubles(p) * sizeof(double));
-    // The split steps-2-5 buffers (used only inside a forward advance) and the adjoint
-    // step's regions (used only inside an adjoint step, after any advance of the same call)
-    // share one region.
+    // The split steps-2-5 buffers (scratch of a forward or adjoint advance) and the
+    // transposed nonlinear term's staging (which runs after the advance of its call) share
+    // one region.
     const size_t shared0 = off;
     if (p->pc_split) {
         p->ws.pstar = take(p->S * cplx);
@@ -715,8 +715,8 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
         p->ws.Ha = take(3 * hst * cplx);
         p->ws.H3 = take(9 * hst * cplx);
         p->ws.Rhat = take(3 * (size_t)p->stage_rows * p->nmode * cplx);
-        p->ws.Nbar = take(3 * p->S * cplx);
         off = std::max(off, split_end);
+        p->ws.Nbar = take(3 * p->S * cplx);   // written by the adjoint advance
         // tc_adjoint_start's temporaries live from u^{-1} = 2.5 u0 - 1.5 u_E on, after its one
         // forward nonlinear evaluation: they take the forward staging when it is large enough
         p->ws.abar = fwd_staging >= 9 * p->S * cplx ? 0 : take(9 * p->S * cplx);

@@ -1,5 +1,6 @@
 """FP64 transform staging by radial slab (tc_options.stage_rows), the streamed adjoint theta
-pass of the long lines (P_theta = 768, 1152), the workspace a mixed plan shares with its FP64
+pass of the long lines (P_theta = 768, 1152), the per-stage transposed steps 2-5 (the adjoint
+advance of the split path, large N_r), the workspace a mixed plan shares with its FP64
 adjoint, and the host-checkpointed gradient of a run from a started state
 (adjoint.state_gradient), all through the C ABI against the oracle.
 
@@ -131,6 +132,59 @@ def test_streamed_adjoint_theta_pass_matches_oracle(M, P_theta):
     plan.adjoint_step(gpu_state(plan, st_o), bar)
     for got, want in zip((bar.u, bar.u_prev, bar.N_prev), ref):
         assert rel(host(got), want) <= 1e-11, rel(host(got), want)
+
+
+@pytest.mark.parametrize("cfg", [CFG1, SMALL])   # SMALL: the two wall stencils share columns
+def test_split_adjoint_advance_matches_oracle(cfg):
+    """The per-stage transposed steps 2-5 against the oracle's adjoint step and the fused
+    kernel, and its adjoint start-up against the oracle's."""
+    ops = O.Operators(O.Params(**cfg))
+    u0 = init(ops)
+    st_o = O.step(ops, O.cold_state(u0))
+    sh = (3,) + ops.prm.shape()
+    y = [I.random_spectral(sh, seed=s) for s in (91, 92, 93)]
+    ref = O.adjoint_step(ops, st_o, *y)
+    outs = []
+    for split in (1, -1):
+        plan = tc.Plan(**cfg, pc_split=split)
+        bar = tc.StateBar(*[dev(v) for v in y])
+        plan.adjoint_step(gpu_state(plan, st_o), bar)
+        outs.append([host(b) for b in (bar.u, bar.u_prev, bar.N_prev)])
+        for got, want in zip(outs[-1], ref):
+            assert rel(got, want) <= 1e-11, (split, rel(got, want))
+    for a, b in zip(*outs):
+        assert rel(a, b) <= 1e-13
+    ref0 = O.adjoint_start_up(ops, u0, *y)
+    plan = tc.Plan(**cfg, pc_split=1, stage_rows=5)
+    bar = tc.StateBar(*[dev(v) for v in y])
+    assert rel(host(plan.adjoint_start(dev(u0), bar)), ref0) <= 1e-11
+
+
+def test_split_adjoint_dot_product_to_1e_12():
+    """<ybar, dF(s)[x]> = <F^T ybar, x> with the split forward step's exact central difference
+    on the left and the per-stage transposed steps on the right."""
+    ops = O.Operators(O.Params(**CFG1))
+    st_o = O.step(ops, O.cold_state(init(ops)))
+    plan = tc.Plan(**CFG1, pc_split=1)
+    sh = (3,) + ops.prm.shape()
+    fields = (st_o.u, st_o.u_prev, st_o.N_prev)
+    x = [I.random_spectral(sh, seed=s) for s in (101, 102, 103)]
+    x = [v * (np.linalg.norm(f) / np.linalg.norm(v)) for v, f in zip(x, fields)]
+    y = [I.random_spectral(sh, seed=s) for s in (104, 105, 106)]
+    bar = tc.StateBar(*[dev(v) for v in y])
+    plan.adjoint_step(gpu_state(plan, st_o), bar)
+    rhs = sum(float(np.real(np.vdot(host(a), b))) for a, b in zip((bar.u, bar.u_prev, bar.N_prev), x))
+    outs = []
+    for sg in (1.0, -1.0):
+        st = tc.State(plan, dev(st_o.u + sg * x[0]))
+        st.u_prev.copy_(dev(st_o.u_prev + sg * x[1]))
+        st.N_prev.copy_(dev(st_o.N_prev + sg * x[2]))
+        st.started = True
+        plan.step(st, 1)
+        outs.append([host(st.u), host(st.u_prev), host(st.N_prev)])
+    tl = [(a - b) / 2.0 for a, b in zip(*outs)]
+    lhs = sum(float(np.real(np.vdot(a, b))) for a, b in zip(y, tl))
+    assert abs(lhs - rhs) <= 1e-12 * abs(rhs), (lhs, rhs)
 
 
 def test_mixed_plan_adjoint_step_is_the_fp64_adjoint():
