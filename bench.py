@@ -454,71 +454,73 @@ CFG5 = dict(N_r=384, M=384, K=768, m_p=1, eta=0.5, Re_i=3e4, Re_o=math.sqrt(0.5)
             L_z=2 * math.pi / 3.16, dt=5e-5)
 
 
-def largest_mixed(tc, torch, I, dev, steps=3):
-    """Mixed form at the largest workload, forward only (no adjoint workspace)."""
+def largest(tc, torch, I, dev, steps=3, err_steps=100):
+    """FP64 and mixed step at the largest workload (no adjoint workspace), one after the other
+    (the two plans do not fit the device together), and the mixed form's error against the
+    FP64 step after the workload's 100 steps from the same initial state.  The FP64 plan
+    stages its transforms by radial slab."""
     cfg = {**CFG5, "dt": cfl_dt(CFG5)}
-    t0 = time.perf_counter()
-    plan = tc.Plan(**cfg, precision=tc.TC_MIXED, no_adjoint=True, device=dev)
-    t_plan = time.perf_counter() - t0
-    r = plan.nodes()
-    u0 = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"],
-                                          cfg["Re_o"], kind="broadband", amp=0.05, seed=42)).to(dev)
-    st = tc.State(plan, u0)
-    del u0
-    e_start = plan.diagnostics(st.u).energy
-    plan.step(st, 2)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    plan.step(st, steps)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    plan.profile(True)
-    plan.step(st, 1)
-    torch.cuda.synchronize()
-    kern = {k: v[1] for k, v in plan.profile_read().items()}
-    plan.profile(False)
-    d = plan.diagnostics(st.u)
-    return {"workload": "quasi-Keplerian eta=0.5, Re_i=3e4, Re_o=sqrt(eta) Re_i, N_r=384, m=-384..384, "
-                        "k=-768..768, phys 384x1152x2304, broadband amp 0.05 (seed 42), mixed form",
-            "dt_stated": CFG5["dt"], "dt": cfg["dt"],
-            "gdof": gdof(cfg), "ms_per_step": ms, "steps_per_s": 1e3 / ms,
-            "gdof_steps_per_s": gdof(cfg) / ms / 1e6, "kernels_ms": kern, "plan_create_s": t_plan,
-            "device_memory_gb": torch.cuda.max_memory_allocated() / 1e9, "state_finite": bool(d.finite),
-            "energy_growth": d.energy / e_start}
+    out = {"workload": "quasi-Keplerian eta=0.5, Re_i=3e4, Re_o=sqrt(eta) Re_i, N_r=384, m=-384..384, "
+                       "k=-768..768, phys 384x1152x2304, broadband amp 0.05 (seed 42)",
+           "gdof": gdof(cfg), "dt_stated": CFG5["dt"], "dt": cfg["dt"]}
+    u0h, keep = None, {}
+    for name, prec in (("fp64", tc.TC_FP64), ("mixed", tc.TC_MIXED)):
+        torch.cuda.reset_peak_memory_stats()
+        t0 = time.perf_counter()
+        plan = tc.Plan(**cfg, precision=prec, no_adjoint=True, device=dev)
+        t_plan = time.perf_counter() - t0
+        r = plan.nodes()
+        if u0h is None:
+            u0h = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"],
+                                                   cfg["Re_o"], kind="broadband", amp=0.05, seed=42))
+        st = tc.State(plan, u0h.to(dev))
+        e_start = plan.diagnostics(st.u).energy
+        plan.step(st, 2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.step(st, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        plan.profile(True)
+        plan.step(st, 1)
+        torch.cuda.synchronize()
+        kern = {k: v[1] for k, v in plan.profile_read().items()}
+        plan.profile(False)
+        mem = torch.cuda.max_memory_allocated() / 1e9
+        # the error run: err_steps steps from the initial state
+        st = tc.State(plan, u0h.to(dev))
+        plan.step(st, err_steps)
+        d = plan.diagnostics(st.u)
+        keep[name] = (st.u.to("cpu"), d)
+        out[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "gdof_steps_per_s": gdof(cfg) / ms / 1e6,
+                     "kernels_ms": kern, "plan_create_s": t_plan, "torch_device_memory_gb": mem,
+                     "state_finite": bool(d.finite), f"energy_growth_{err_steps}_steps": d.energy / e_start}
+        del plan, st
+        torch.cuda.empty_cache()
+    out["mixed_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    (ua, da), (ub, db) = keep["fp64"], keep["mixed"]
+    base = torch.from_numpy(I.base_state(r, cfg["M"], cfg["K"], cfg["eta"], cfg["Re_i"], cfg["Re_o"]))
+    ua, ub = ua.to(dev), ub.to(dev)
+    bd = base.to(dev)
+    del base
+    out["mixed_error"] = {
+        "after_steps": err_steps, "dt": cfg["dt"], "against": "FP64 CUDA step",
+        "rel_err_velocity_perturbation": _rel(ua - bd, ub - bd, torch),
+        "rel_err_velocity": _rel(ua, ub, torch),
+        "rel_err_torque_inner": abs(db.torque_inner / da.torque_inner - 1),
+        "rel_err_torque_outer": abs(db.torque_outer / da.torque_outer - 1),
+        "max_div_fp64": da.max_div, "max_div_mixed": db.max_div}
+    del keep, ua, ub, bd
+    torch.cuda.empty_cache()
+    return out
 
 
 def _free_device_bytes(torch):
     """Device memory free for new tensors: the driver's free bytes plus torch's unused cache."""
     free, _ = torch.cuda.mem_get_info()
     return free + torch.cuda.memory_reserved() - torch.cuda.memory_allocated()
-
-
-def largest_fp64(tc, torch, I, dev, steps=2):
-    """FP64 step at the largest workload (no adjoint workspace): the transform staging runs
-    slab by slab, so the FP64 lines of 384 rows never coexist."""
-    cfg = {**CFG5, "dt": cfl_dt(CFG5)}
-    torch.cuda.reset_peak_memory_stats()
-    plan = tc.Plan(**cfg, no_adjoint=True, device=dev)
-    r = plan.nodes()
-    u0 = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"],
-                                          cfg["Re_o"], kind="broadband", amp=0.05, seed=42)).to(dev)
-    st = tc.State(plan, u0)
-    del u0
-    plan.step(st, 1)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    plan.step(st, steps)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    return {"workload": "quasi-Keplerian eta=0.5, Re_i=3e4, N_r=384, m=-384..384, k=-768..768, FP64",
-            "dt": cfg["dt"], "ms_per_step": ms, "steps_per_s": 1e3 / ms,
-            "gdof_steps_per_s": gdof(cfg) / ms / 1e6,
-            "device_memory_gb": torch.cuda.max_memory_allocated() / 1e9,
-            "state_finite": bool(plan.diagnostics(st.u).finite)}
 
 
 def config5_adjoint(tc, torch, I, dev, n_total=100, n_adj=50, checkpoint=17):
@@ -655,6 +657,47 @@ def config5_dot_product(tc, torch, I, dev, h_scale=1.0):
             "adjoint_step_kernels_ms": adj, "adjoint_step_ms": sum(adj.values()),
             "fp64_step_kernels_ms": fwd, "fp64_step_ms": sum(fwd.values()),
             "device_memory_gb": torch.cuda.max_memory_allocated() / 1e9}
+
+
+# profiling case of the long-line transforms: P_theta = 1152, P_z = 192
+CFG_LONG = dict(N_r=32, M=384, K=64, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-6)
+
+
+def run_adjoint_case(args):
+    """--workload adjoint: K timed FP64 adjoint steps (tc_adjoint_step) at a profiling size,
+    after W untimed ones, one JSON line with the per-kernel times (CUDA events)."""
+    import torch
+    from paper_1311_2481_gb300 import build as B
+    from paper_1311_2481_gb300 import inputs as I
+    from paper_1311_2481_gb300 import tc
+    B.build()
+    cfg = {"mid": CFG_MID, "split": CFG_SPLIT, "long": CFG_LONG}.get(args.size, CFG2)
+    plan = tc.Plan(**cfg, device="cuda:0")
+    r = plan.nodes()
+    u0 = torch.from_numpy(I.initial_state(r, cfg["M"], cfg["K"], 1, cfg["L_z"], cfg["eta"], cfg["Re_i"],
+                                          cfg["Re_o"], kind="broadband", amp=1e-2, seed=42)).cuda()
+    st = tc.State(plan, u0)
+    plan.step(st, 1)
+    bar = tc.StateBar(u0.clone(), u0.clone(), u0.clone())
+    for _ in range(args.warmup):
+        plan.adjoint_step(st, bar)
+    torch.cuda.synchronize()
+    plan.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        plan.adjoint_step(st, bar)
+    e1.record()
+    torch.cuda.synchronize()
+    kern = {k: v[1] / args.steps for k, v in plan.profile_read().items()}
+    plan.profile(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"metric": "FP64 adjoint steps/s (profiling case)", "value": 1e3 / ms, "unit": "steps/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": f"FP64 adjoint step at N_r={cfg['N_r']}, M={cfg['M']}, "
+                                             f"K={cfg['K']}, P_theta={3 * cfg['M']}, P_z={3 * cfg['K']}"},
+                      "kernels_ms_per_step": kern}), flush=True)
 
 
 def run_ours(args):
@@ -898,8 +941,7 @@ def run_ours(args):
                 out[key] = {"error": repr(exc)[:300]}
             torch.cuda.empty_cache()
     if args.largest:
-        for key, fn in (("largest", lambda: largest_mixed(tc, torch, I, f"cuda:{local}")),
-                        ("largest_fp64", lambda: largest_fp64(tc, torch, I, f"cuda:{local}")),
+        for key, fn in (("largest", lambda: largest(tc, torch, I, f"cuda:{local}")),
                         ("config5_adjoint", lambda: config5_adjoint(tc, torch, I, f"cuda:{local}")),
                         ("config5_dot_product", lambda: config5_dot_product(tc, torch, I, f"cuda:{local}"))):
             try:
@@ -986,17 +1028,21 @@ def main():
     ap.add_argument("--largest", action="store_true",
                     help="also time the mixed form at N_r = 384 (384 x 1152 x 2304) and the mixed form with "
                          "the FP64 adjoint of its last 50 steps at N_r = 256")
-    ap.add_argument("--workload", default="fp64", choices=["fp64", "mixed"],
-                    help="precision of the main timed step (the reported metric is the FP64 step)")
-    ap.add_argument("--size", default="bench", choices=["bench", "mid", "split"],
+    ap.add_argument("--workload", default="fp64", choices=["fp64", "mixed", "adjoint"],
+                    help="precision of the main timed step (the reported metric is the FP64 step); "
+                         "adjoint: time the FP64 adjoint step at --size instead (profiling)")
+    ap.add_argument("--size", default="bench", choices=["bench", "mid", "split", "long"],
                     help="bench: N_r=64, M=32, K=64; mid: N_r=128, M=128, K=256; split: N_r=256, M=32, "
-                         "K=64 (the per-stage steps-2-5 kernels) -- the last two for profiling")
+                         "K=64 (the per-stage steps-2-5 kernels); long: N_r=32, M=384, K=64 (1152-point "
+                         "theta lines) -- the last three for profiling")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "adjoint":
+        run_adjoint_case(args)
     else:
         run_ours(args)
 

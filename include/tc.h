@@ -258,11 +258,12 @@ tc_status tc_energy_gradient(tc_plan* plan, const void* u, void* g, void* stream
  * (the paper has no counterpart: it is a packaging choice of this library).  Instead of a
  * caller workspace, the staging lines between the transform kernels live in one static
  * 80 MiB device array that every GPU loading the library keeps until the process exits.
- * The staging a plan needs is its workspace before N^i: 12 * N_r * (M+1) * P_z line values
- * (complex128; complex64 for a TC_MIXED plan created with no_adjoint), plus, for TC_MIXED
- * plans, 6 * N_r * (M+1) * (2K+1) complex64 values of the FP32 split of u and d_r u, each
- * region rounded up to 256 bytes; plans that need more than 80 MiB get TC_ERR_ARG before any
- * launch.  Allocates nothing.  The first call on each device looks up the array's address
+ * The staging a plan needs is its workspace before N^i: for TC_FP64 plans 12 line sets of
+ * stage_rows * (M+1) * P_z complex128 values (the transforms run slab by slab of stage_rows
+ * radial rows); for TC_MIXED plans 12 line sets of N_r * (M+1) * P_z complex64 values and
+ * 6 * N_r * (M+1) * (2K+1) complex64 values of the FP32 split of u and d_r u; each region
+ * rounded up to 256 bytes.  Plans that need more than 80 MiB get TC_ERR_ARG before any
+ * launch (a smaller stage_rows brings a TC_FP64 plan's need down).  Allocates nothing.  The first call on each device looks up the array's address
  * once (cudaGetSymbolAddress) and keeps it; make that call before any stream capture, and do
  * not call this entry point after a device reset (cudaDeviceReset or a primary-context reset
  * unloads the array and leaves the kept address stale).  All calls share the array: calls

@@ -12,10 +12,10 @@
 //  - kStaticScratchBytes (80 MiB) of device memory is reserved on every GPU that loads this
 //    library, for as long as the process lives.  Plans whose staging needs more are rejected
 //    with TC_ERR_ARG before anything is launched.  The staging is everything the workspace
-//    holds before N^i: the z-pass lines H1 and H2, 12 * N_r * (M+1) * P_z values (complex128,
-//    or complex64 for a TC_MIXED plan created with no_adjoint), and for TC_MIXED plans the
-//    FP32 split of u and d_r u, 6 * N_r * (M+1) * (2K+1) complex64 values, each region
-//    rounded up to 256 bytes.
+//    holds before N^i: the z-pass lines H1 and H2 (12 line sets: complex128 lines of
+//    stage_rows radial rows for TC_FP64 plans, complex64 lines of all rows for TC_MIXED
+//    plans), and for TC_MIXED plans the FP32 split of u and d_r u, 6 * N_r * (M+1) * (2K+1)
+//    complex64 values, each region rounded up to 256 bytes.
 //  - All calls share the one array, which keeps whatever the last call left in it.  The
 //    kernels overwrite every staging entry before reading it, so nothing has to start at
 //    zero, but two calls whose work overlaps on the GPU (different streams, or different

@@ -58,9 +58,9 @@ def test_noalloc_matches_workspace_path_on_two_calls(cfg):
 
 @pytest.mark.parametrize("no_adjoint", [False, True])
 def test_noalloc_mixed_plan_after_another_layout(no_adjoint):
-    """A TC_MIXED plan (FP64 staging lines with the adjoint regions, FP32 lines without them,
-    and the FP32 split of u in both) through the static array right after a call of an FP64
-    plan of another size has left its own data there, on two calls in a row; the second call
+    """A TC_MIXED plan (FP32 staging lines and the FP32 split of u, with and without the
+    adjoint regions after them) through the static array right after a call of an FP64 plan
+    of another size has left its own data there, on two calls in a row; the second call
     allocates nothing (the device's free memory is unchanged across it)."""
     lib = tc.load_library()
     other = tc.Plan(64, 32, 64, 1, 0.5, 1000.0, 0.0, LZ, 5e-4)
@@ -105,3 +105,20 @@ def test_noalloc_rejects_plans_beyond_the_static_scratch():
                                   ctypes.c_void_p(N.data_ptr()), _stream())
     assert st == tc.TC_ERR_ARG
     assert b"static scratch" in lib.tc_plan_last_error(plan.handle)
+
+
+def test_noalloc_fits_with_fewer_staged_rows():
+    """The same FP64 plan with its transforms staged 16 radial rows at a time needs 77 MB of
+    staging, fits the static array, and gives the workspace path's result."""
+    lib = tc.load_library()
+    plan = tc.Plan(128, 64, 128, 1, 0.5, 100.0, 0.0, LZ, 1e-4, stage_rows=16)
+    r = plan.nodes()
+    u = torch.from_numpy(I.initial_state(r, 64, 128, 1, LZ, 0.5, 100.0, 0.0, kind="box", amp=1e-2,
+                                         seed=3)).cuda()
+    ref = plan.nonlinear(u)
+    got = torch.full_like(u, float("nan"))
+    st = lib.tc_nonlinear_noalloc(plan.handle, ctypes.c_void_p(u.data_ptr()),
+                                  ctypes.c_void_p(got.data_ptr()), _stream())
+    assert st == tc.TC_OK, lib.tc_plan_last_error(plan.handle)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
