@@ -174,6 +174,9 @@ def kernel_rooflines(cfg, prof):
         "k_zinv_f32": (6 * S * 8 + 9 * H * 8, None, "hbm"),
         "k_theta_f32": (9 * H * 8 + 3 * H * 8, None, "hbm"),
         "k_zfwd_f32": (3 * H * 8 + 3 * S * 16 + 3 * S * 16, None, "hbm"),
+        # the mean mode of N by double-FP32 Parseval sums: u read once (~1250 FP32 operations
+        # per (row, mode) make it bound by issue, not bytes)
+        "k_mean00_f32": (3 * S * 16, None, "alu"),
     }
     hbm, src = hbm_peak_gbs()
     out = {}

@@ -435,9 +435,17 @@ tc_status launch_theta32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t 
 // stage_rows rows.  Mixed form: FP32 lines of all rows (tc_mixed.cu).
 tc_status launch_nonlinear(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s) {
     if (p->precision == TC_MIXED) {
+        // the mean mode reads only u: it runs on the plan's second stream beside the FP32
+        // transforms, and its sums replace N's (0, 0) coefficients after the forward z pass
+        TC_CUDA(p, cudaEventRecord(p->mean_ev[0], s));
+        TC_CUDA(p, cudaStreamWaitEvent(p->mean_stream, p->mean_ev[0], 0));
+        TC_TRY_STATUS(launch_mean00_part(p, u, ws, p->mean_stream));
+        TC_CUDA(p, cudaEventRecord(p->mean_ev[1], p->mean_stream));
         TC_TRY_STATUS(launch_nl_pre32(p, u, ws, s, 0, p->M + 1));
         TC_TRY_STATUS(launch_nl_theta32(p, ws, s));
-        return launch_nl_post32(p, u, N, ws, s, 0, p->M + 1);
+        TC_TRY_STATUS(launch_nl_post32(p, u, N, ws, s, 0, p->M + 1));
+        TC_CUDA(p, cudaStreamWaitEvent(s, p->mean_ev[1], 0));
+        return launch_mean00_fin(p, N, ws, s);
     }
     double2* H1 = reinterpret_cast<double2*>(ws + p->ws.H1);
     double2* H2 = reinterpret_cast<double2*>(ws + p->ws.H2);

@@ -34,6 +34,7 @@ struct Workspace {
                     // rows, or the mixed form's FP32 lines of all N_r rows
     size_t H2;      // theta-pass output: 3 line sets, rows and precision as H1
     size_t P32;     // mixed form: u', d_r u' in FP32, 6 x S float2
+    size_t mean;    // mixed form: segment sums of the mean mode of N (mean00_part_doubles)
     size_t Ncur;    // N^i: vector field (everything before it is the forward staging)
     size_t uE;      // start-up Euler result: vector field
     size_t pstar;   // split path only: p* (scalar), u* (vector), phi (scalar)
@@ -122,6 +123,10 @@ struct tc_plan {
     // nonlinear term runs on u, with events for the hand-over (created on first use)
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_ev[2] = {nullptr, nullptr};
+    // mixed form: a second stream on which the mean mode of N runs beside the FP32
+    // transforms, with events for the fork and the join (created with the device plan)
+    cudaStream_t mean_stream = nullptr;
+    cudaEvent_t mean_ev[2] = {nullptr, nullptr};
     // per-kernel CUDA-event tracing
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;         // event pool, two per record
@@ -174,7 +179,7 @@ tc_status check_device_ptr(tc_plan* p, const void* ptr, const char* name, size_t
 enum KernelId {
     kKZinv = 0, kKTheta, kKZfwd, kKRhsPressure, kKSolveP, kKRhsVelocity, kKSolveH, kKRhsDiv,
     kKUpdate, kKAxpby, kKDiag, kKZinv32, kKTheta32, kKZfwd32, kKPC, kKPCAdj,
-    kKZinvAdj, kKThetaAdj, kKZfwdAdj, kKDrT, kKPrep32, kNumKernels
+    kKZinvAdj, kKThetaAdj, kKZfwdAdj, kKDrT, kKPrep32, kKMean00, kNumKernels
 };
 extern const char* const kKernelNames[kNumKernels];
 int prof_begin(tc_plan* p, int kid, cudaStream_t s);
@@ -190,6 +195,9 @@ tc_status launch_theta_s64(tc_plan* p, const double2* H1, double2* H2, cudaStrea
 tc_status launch_nl_pre32(tc_plan* p, const double2* u, char* ws, cudaStream_t s, int ma, int mb);
 tc_status launch_nl_theta32(tc_plan* p, char* ws, cudaStream_t s);
 tc_status launch_nl_post32(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s, int ma, int mb);
+size_t mean00_part_doubles(const tc_plan* p);
+tc_status launch_mean00_part(tc_plan* p, const double2* u, char* ws, cudaStream_t s);
+tc_status launch_mean00_fin(tc_plan* p, double2* N, char* ws, cudaStream_t s);
 tc_status launch_solve(tc_plan* p, int set, double2* x, int nfields, cudaStream_t s);
 tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const double2* Ncur,
                          double2* N_prev, double2* p_out, double2* u_out, char* ws,

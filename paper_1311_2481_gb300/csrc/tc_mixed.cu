@@ -641,6 +641,242 @@ static tc_status launch_sym_m0(tc_plan* p, double2* N, cudaStream_t s) {
     return TC_OK;
 }
 
+// ---------------------------------------------------------------- the mean mode of N
+// The (m, k) = (0, 0) mode of N is the azimuthal and axial mean of u . grad u, and in a
+// step the mean flow changes only through it (the wall torque of Sec. 5.4 is its wall
+// derivative).  In FP32 it is the small residue of large fluctuating products, and it
+// keeps far less relative accuracy than the rest of N.  With P_theta >= 2M+1 and
+// P_z >= 2K+1 no product of two retained modes aliases onto (0, 0), so the mean of a product
+// of real fields f g is exactly the Parseval sum over the stored modes
+//     <f g> = sum_{m >= 0, k} c_m Re(f_mk conj g_mk),  c_0 = 1, c_m = 2,
+// and with d_theta = i m m_p, d_z = i k k_z, u_r = (u_+ + u_-)/2, u_t = -i (u_+ - u_-)/2:
+//     <N_r> = <u_r D u_r> + (1/r) sum c_m m m_p Im(u_t conj u_r) + sum c_m k k_z Im(u_z conj u_r) - (1/r) <u_t u_t>
+//     <N_t> = <u_r D u_t> + sum c_m k k_z Im(u_z conj u_t) + (1/r) <u_r u_t>
+//     <N_z> = <u_r D u_z> + (1/r) sum c_m m m_p Im(u_t conj u_z)
+// (D: the FD stencil of Sec. 3.1).  k_mean00 evaluates these from the FP64 state in
+// double-FP32 arithmetic (each value an unevaluated FP32 pair, error-free products and
+// sums, about 44 significant bits), one thread per (row, k) of a mode line, and writes each
+// warp's sum over its 32 k values; k_mean00_fin adds those in FP64 in a fixed order and
+// overwrites N's (0, 0) coefficients: N_pm = <N_r> +- i <N_t>, N_z = <N_z>.
+
+struct dfl {
+    float h, l;
+};
+__device__ __forceinline__ dfl df_of(double d) {
+    const float2 s = split_hl(d);
+    dfl r;
+    r.h = s.x;
+    r.l = s.y;
+    return r;
+}
+__device__ __forceinline__ dfl df_norm(float s, float t) {   // |t| <= ulp-sized part of s
+    dfl r;
+    r.h = __fadd_rn(s, t);
+    r.l = __fsub_rn(t, __fsub_rn(r.h, s));
+    return r;
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+    float s, t;
+    two_sum(a.h, b.h, s, t);
+    t = __fadd_rn(t, __fadd_rn(a.l, b.l));
+    return df_norm(s, t);
+}
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    float p, e;
+    two_prod(a.h, b.h, p, e);
+    e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+    return df_norm(p, e);
+}
+__device__ __forceinline__ dfl df_neg(dfl a) {
+    a.h = -a.h;
+    a.l = -a.l;
+    return a;
+}
+__device__ __forceinline__ dfl df_half(dfl a) {   // exact
+    a.h = __fmul_rn(a.h, 0.5f);
+    a.l = __fmul_rn(a.l, 0.5f);
+    return a;
+}
+__device__ __forceinline__ double df_val(dfl a) { return f2d_bits(a.h) + f2d_bits(a.l); }
+// Re(f conj g) and Im(f conj g) of complex pairs (fx, fy), (gx, gy)
+__device__ __forceinline__ dfl df_re(dfl fx, dfl fy, dfl gx, dfl gy) { return df_add(df_mul(fx, gx), df_mul(fy, gy)); }
+__device__ __forceinline__ dfl df_im(dfl fx, dfl fy, dfl gx, dfl gy) {
+    return df_add(df_mul(fy, gx), df_neg(df_mul(fx, gy)));
+}
+// s + c += (ah + al)(bh + bl): the exact product of the high parts folded in by an error-free
+// sum, the lower-order parts accumulated in c (compensated dot product, Ogita-Rump-Oishi)
+__device__ __forceinline__ void dot_acc(float& s, float& c, float ah, float al, float bh, float bl) {
+    float p, e, q;
+    two_prod(ah, bh, p, e);
+    e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+    two_sum(s, p, s, q);
+    c = __fadd_rn(c, __fadd_rn(q, e));
+}
+__device__ __forceinline__ dfl df_shfl_down(dfl a, int o) {
+    a.h = __shfl_down_sync(0xffffffffu, a.h, o);
+    a.l = __shfl_down_sync(0xffffffffu, a.l, o);
+    return a;
+}
+
+constexpr int kMeanK = 32;   // k values per block (one warp row)
+constexpr int kMeanR = 8;    // rows per block (one per warp)
+constexpr int kMeanWin = kMeanR + kStencil - 1;
+
+// part[(c * N_r + r) * nseg + m * nkt + kt], c = 0: <N_r>, 1: <N_t>, 2: <N_z>
+__global__ void __launch_bounds__(256) k_mean00(const double2* __restrict__ u, double* __restrict__ part,
+                                                const double* __restrict__ w1, const int* __restrict__ col0,
+                                                const double* __restrict__ irn, int N_r, int M, int K, int nkt,
+                                                int nrc, double mp, double kz) {
+    // window of the three components' rows, each value split once: (hi re, hi im, lo re, lo im)
+    __shared__ float4 win[3][kMeanWin * kMeanK];
+    __shared__ float2 sw[kMeanR * kStencil];
+    int b = blockIdx.x;
+    const int kt = b % nkt;
+    b /= nkt;
+    const int rc = b % nrc;
+    const int m = b / nrc;
+    const int nk = 2 * K + 1;
+    const size_t S = (size_t)N_r * (M + 1) * nk;
+    const size_t colstride = (size_t)(M + 1) * nk;
+    const int r0 = rc * kMeanR;
+    const int r1 = min(r0 + kMeanR, N_r) - 1;
+    const int jlo = col0[r0];
+    const int jhi = col0[r1] + kStencil - 1;
+    const int kk = kt * kMeanK + threadIdx.x;
+    const bool kin = kk < nk;
+    const int tid = threadIdx.y * kMeanK + threadIdx.x;
+    for (int i = tid; i < (r1 - r0 + 1) * kStencil; i += blockDim.x * blockDim.y)
+        sw[i] = split_hl(w1[(size_t)r0 * kStencil + i]);
+    for (int c = 0; c < 3; ++c) {
+        const double2* base = u + (size_t)c * S + (size_t)m * nk + kk;
+        for (int j = jlo + threadIdx.y; j <= jhi; j += blockDim.y) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (kin) {
+                const double2 x = base[(size_t)j * colstride];
+                const float2 a = split_hl(x.x), q = split_hl(x.y);
+                v = make_float4(a.x, q.x, a.y, q.y);
+            }
+            win[c][(j - jlo) * kMeanK + threadIdx.x] = v;
+        }
+    }
+    __syncthreads();
+    const int k = kk - K;
+    const float cm = m == 0 ? 1.f : 2.f;
+    const dfl mm = df_of(mp * m), kzk = df_of(kz * (double)k);   // m m_p and k k_z as in FP64
+    const size_t nseg = (size_t)(M + 1) * nkt;
+    for (int r = r0 + threadIdx.y; r <= r1; r += blockDim.y) {
+        dfl tr = {0.f, 0.f}, tt = {0.f, 0.f}, tz = {0.f, 0.f};
+        if (kin) {
+            dfl x[3], y[3], dx[3], dy[3];   // value and D of (re, im) of u_+, u_-, u_z
+            const int w0 = (col0[r] - jlo) * kMeanK + threadIdx.x;
+            const float2* w = sw + (r - r0) * kStencil;
+            for (int c = 0; c < 3; ++c) {
+                const float4 cen = win[c][(r - jlo) * kMeanK + threadIdx.x];
+                x[c] = df_norm(cen.x, cen.z);
+                y[c] = df_norm(cen.y, cen.w);
+                float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+#pragma unroll
+                for (int t = 0; t < kStencil; ++t) {
+                    const float4 v = win[c][w0 + t * kMeanK];
+                    dot_acc(sx, cx, w[t].x, w[t].y, v.x, v.z);
+                    dot_acc(sy, cy, w[t].x, w[t].y, v.y, v.w);
+                }
+                dx[c] = df_norm(sx, cx);
+                dy[c] = df_norm(sy, cy);
+            }
+            // u_r = (u_+ + u_-)/2, u_t = -i (u_+ - u_-)/2 = ((Im u_+ - Im u_-)/2, -(Re u_+ - Re u_-)/2)
+            const dfl urx = df_half(df_add(x[0], x[1])), ury = df_half(df_add(y[0], y[1]));
+            const dfl utx = df_half(df_add(y[0], df_neg(y[1]))), uty = df_half(df_add(x[1], df_neg(x[0])));
+            const dfl drx = df_half(df_add(dx[0], dx[1])), dry = df_half(df_add(dy[0], dy[1]));
+            const dfl dtx = df_half(df_add(dy[0], df_neg(dy[1]))), dty = df_half(df_add(dx[1], df_neg(dx[0])));
+            const dfl ir = df_of(irn[r]);
+            // <N_r>: u_r D u_r + (1/r) m Im(u_t conj u_r) + k Im(u_z conj u_r) - (1/r) |u_t|^2
+            dfl a1 = df_re(urx, ury, drx, dry);
+            dfl a2 = df_mul(mm, df_im(utx, uty, urx, ury));
+            a2 = df_add(a2, df_neg(df_re(utx, uty, utx, uty)));
+            tr = df_add(df_add(a1, df_mul(kzk, df_im(x[2], y[2], urx, ury))), df_mul(ir, a2));
+            // <N_t>: u_r D u_t + k Im(u_z conj u_t) + (1/r) Re(u_r conj u_t)
+            tt = df_add(df_add(df_re(urx, ury, dtx, dty), df_mul(kzk, df_im(x[2], y[2], utx, uty))),
+                        df_mul(ir, df_re(urx, ury, utx, uty)));
+            // <N_z>: u_r D u_z + (1/r) m Im(u_t conj u_z)
+            tz = df_add(df_re(urx, ury, dx[2], dy[2]), df_mul(ir, df_mul(mm, df_im(utx, uty, x[2], y[2]))));
+            if (cm != 1.f) {   // exact doubling
+                tr.h *= 2.f; tr.l *= 2.f;
+                tt.h *= 2.f; tt.l *= 2.f;
+                tz.h *= 2.f; tz.l *= 2.f;
+            }
+        }
+        // sum over the warp's 32 k values (fixed tree)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tr = df_add(tr, df_shfl_down(tr, o));
+            tt = df_add(tt, df_shfl_down(tt, o));
+            tz = df_add(tz, df_shfl_down(tz, o));
+        }
+        if (threadIdx.x == 0) {
+            const size_t seg = (size_t)m * nkt + kt;
+            part[((size_t)0 * N_r + r) * nseg + seg] = df_val(tr);
+            part[((size_t)1 * N_r + r) * nseg + seg] = df_val(tt);
+            part[((size_t)2 * N_r + r) * nseg + seg] = df_val(tz);
+        }
+    }
+}
+
+// per row: the FP64 sum of the row's segments in a fixed order, into N's (0, 0) coefficients
+__global__ void __launch_bounds__(256) k_mean00_fin(const double* __restrict__ part, double2* __restrict__ N,
+                                                    int N_r, int M, int K, int nseg, size_t S) {
+    __shared__ double sh[3][256];
+    const int r = blockIdx.x;
+    const int per = (nseg + 255) / 256;
+    for (int c = 0; c < 3; ++c) {
+        const double* q = part + ((size_t)c * N_r + r) * nseg;
+        double a = 0.0;
+        for (int i = threadIdx.x * per; i < (threadIdx.x + 1) * per && i < nseg; ++i) a += q[i];
+        sh[c][threadIdx.x] = a;
+    }
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const size_t e = (size_t)r * (M + 1) * (2 * K + 1) + K;   // (m, k) = (0, 0) of row r
+        N[e] = make_double2(sh[0][0], sh[1][0]);
+        N[S + e] = make_double2(sh[0][0], -sh[1][0]);
+        N[2 * S + e] = make_double2(sh[2][0], 0.0);
+    }
+}
+
+size_t mean00_part_doubles(const tc_plan* p) {
+    const int nk = 2 * p->K + 1;
+    return (size_t)3 * p->N_r * (p->M + 1) * ((nk + kMeanK - 1) / kMeanK);
+}
+
+// the segment sums of the mean mode (reads only u and the plan)
+tc_status launch_mean00_part(tc_plan* p, const double2* u, char* ws, cudaStream_t s) {
+    const int nk = 2 * p->K + 1;
+    const int nkt = (nk + kMeanK - 1) / kMeanK;
+    const int nrc = (p->N_r + kMeanR - 1) / kMeanR;
+    double* part = reinterpret_cast<double*>(ws + p->ws.mean);
+    const int slot = prof_begin(p, kKMean00, s);
+    k_mean00<<<(unsigned)(nkt * nrc * (p->M + 1)), dim3(kMeanK, kMeanR), 0, s>>>(
+        u, part, p->d_w1, p->d_col0, p->d_ir, p->N_r, p->M, p->K, nkt, nrc, (double)p->m_p, p->k_z);
+    prof_end(p, slot, s);
+    TC_LAUNCHED(p, "k_mean00");
+    return TC_OK;
+}
+
+// N's (0, 0) coefficients from the segment sums (after the forward z pass wrote N)
+tc_status launch_mean00_fin(tc_plan* p, double2* N, char* ws, cudaStream_t s) {
+    const int nkt = (2 * p->K + 1 + kMeanK - 1) / kMeanK;
+    const double* part = reinterpret_cast<const double*>(ws + p->ws.mean);
+    k_mean00_fin<<<p->N_r, 256, 0, s>>>(part, N, p->N_r, p->M, p->K, (p->M + 1) * nkt, p->S);
+    TC_LAUNCHED(p, "k_mean00_fin");
+    return TC_OK;
+}
+
+
 tc_status launch_nl_post32(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s, int ma, int mb) {
     const float2* H2 = reinterpret_cast<const float2*>(ws + p->ws.H2);
     if (zpass_s_ok(p)) {

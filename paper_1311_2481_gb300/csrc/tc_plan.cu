@@ -397,6 +397,10 @@ static tc_status upload(tc_plan* p) {
     TC_CUDA(p, cudaHostAlloc((void**)&p->h_nonfinite, sizeof(int), cudaHostAllocMapped));
     *p->h_nonfinite = 0;
     TC_CUDA(p, cudaHostGetDevicePointer((void**)&p->d_nonfinite, p->h_nonfinite, 0));
+    if (p->precision == TC_MIXED) {
+        TC_CUDA(p, cudaStreamCreateWithFlags(&p->mean_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : p->mean_ev) TC_CUDA(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     auto put = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
         cudaError_t e = cudaMalloc(dst, bytes);
         if (e != cudaSuccess) return e;
@@ -450,7 +454,7 @@ const char* const kKernelNames[kNumKernels] = {
     "k_zinv", "k_theta", "k_zfwd", "k_rhs_pressure", "k_band_solve_P", "k_rhs_velocity",
     "k_band_solve_H", "k_rhs_div", "k_update", "k_axpby", "k_diag", "k_zinv_f32",
     "k_theta_f32", "k_zfwd_f32", "k_pc", "k_pc_adj", "k_zinv_adjin",
-    "k_theta_adj", "k_zfwd_adj", "k_drT", "k_prep_f32"};
+    "k_theta_adj", "k_zfwd_adj", "k_drT", "k_prep_f32", "k_mean00_f32"};
 
 int prof_begin(tc_plan* p, int kid, cudaStream_t s) {
     if (!p->prof_on) return -1;
@@ -485,6 +489,15 @@ static void free_device(tc_plan* p) {
     if (p->copy_stream) {
         cudaStreamDestroy(p->copy_stream);
         p->copy_stream = nullptr;
+    }
+    for (cudaEvent_t& e : p->mean_ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+    if (p->mean_stream) {
+        cudaStreamDestroy(p->mean_stream);
+        p->mean_stream = nullptr;
     }
     void* ptrs[] = {p->d_r, p->d_ir, p->d_w1, p->d_w1f, p->d_dsc, p->d_w2, p->d_col0, p->d_d1t_row, p->d_d1t_w, p->d_fac, p->d_piv,
                     p->d_fac2, p->d_piv2, p->d_spk, p->d_rinv, p->d_tw_z, p->d_tw_t, p->d_tw_z32, p->d_tw_t32};
@@ -675,11 +688,13 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
         p->ws.H1 = take(9 * p->Hfield * sizeof(float2));
         p->ws.H2 = take(3 * p->Hfield * sizeof(float2));
         p->ws.P32 = take(6 * p->S * sizeof(float2));
+        p->ws.mean = take(mean00_part_doubles(p) * sizeof(double));
     } else {
         const size_t hst = (size_t)p->stage_rows * (M + 1) * Pz;
         p->ws.H1 = take(9 * hst * cplx);
         p->ws.H2 = take(3 * hst * cplx);
         p->ws.P32 = take(0);
+        p->ws.mean = take(0);
     }
     const size_t fwd_staging = off;
     p->ws.Ncur = take(3 * p->S * cplx);

@@ -306,6 +306,29 @@ def test_mixed_nonlinear_error_is_fp32_level_of_the_perturbation_part(cfg):
     assert err <= 1e-8 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("case", ["bench", "quasi_keplerian"])
+def test_mixed_mean_mode_at_fp64_accuracy(case):
+    """The mixed form's (m, k) = (0, 0) mode of N, the mean the torque depends on, comes from
+    the double-FP32 Parseval sum of the FP64 state: against the oracle to 1e-10 of the
+    perturbation's share of that mode (the FP32 transforms alone give 1e-5 there)."""
+    if case == "bench":
+        cfg, kind, amp = CFG2, "taylor", 1e-2
+    else:
+        Re = 3e4
+        cfg = dict(N_r=24, M=24, K=32, m_p=1, eta=0.5, Re_i=Re, Re_o=math.sqrt(0.5) * Re, L_z=LZ, dt=1e-8)
+        kind, amp = "broadband", 0.05
+    ops = O.Operators(O.Params(**cfg))
+    plan = tc.Plan(**cfg, precision=tc.TC_MIXED)
+    u = init(ops, kind=kind, amp=amp)
+    K = ops.prm.K
+    ref = O.nonlinear(ops, u)[:, :, 0, K]
+    base = O.nonlinear(ops, I.base_state(ops.r, ops.prm.M, K, cfg["eta"], cfg["Re_i"], cfg["Re_o"]))[:, :, 0, K]
+    got = host(plan.nonlinear(dev(u)))[:, :, 0, K]
+    for c in range(3):
+        scale = np.linalg.norm(ref[c] - base[c])
+        assert np.linalg.norm(got[c] - ref[c]) <= 1e-10 * scale, (c, np.linalg.norm(got[c] - ref[c]) / scale)
+
+
 def test_mixed_nonlinear_m0_line_is_a_real_field():
     """The mixed form's N keeps the m = 0 symmetry of a real field exactly:
     N_+(0,k) = conj N_-(0,-k) and N_z(0,k) = conj N_z(0,-k)."""
