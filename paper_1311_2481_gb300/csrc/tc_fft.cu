@@ -434,6 +434,11 @@ tc_status launch_theta32(tc_plan* p, const float2* H1, float2* H2, cudaStream_t 
 // rows (a row's transforms read no other row's staging), so the staging holds 12 line sets of
 // stage_rows rows.  Mixed form: FP32 lines of all rows (tc_mixed.cu).
 tc_status launch_nonlinear(tc_plan* p, const double2* u, double2* N, char* ws, cudaStream_t s) {
+    if (p->precision == TC_MIXED && p->opt.mean_fp32) {
+        TC_TRY_STATUS(launch_nl_pre32(p, u, ws, s, 0, p->M + 1));
+        TC_TRY_STATUS(launch_nl_theta32(p, ws, s));
+        return launch_nl_post32(p, u, N, ws, s, 0, p->M + 1);
+    }
     if (p->precision == TC_MIXED) {
         // the mean mode reads only u: it runs on the plan's second stream beside the FP32
         // transforms, and its sums replace N's (0, 0) coefficients after the forward z pass

@@ -655,7 +655,7 @@ tc_status tc_plan_create_ex(tc_plan** out, int N_r, int M, int K, int m_p, doubl
     p->thr_zfwd = choose_threads(rz, p->zfwd_lines, 0);
     if (o.theta_zt < 0 || o.theta_zt > 64 || o.pc_modes < 0 || o.pc_modes > 32 || o.pc_split < -1 || o.pc_split > 1 ||
         o.theta_variant < 0 || o.theta_variant > 4 || o.pc_partitions < 0 || o.pc_partitions > 2 ||
-        o.stage_rows < 0) {
+        o.stage_rows < 0 || o.mean_fp32 < 0 || o.mean_fp32 > 1) {
         delete p;
         return TC_ERR_ARG;
     }
@@ -796,6 +796,7 @@ tc_status tc_plan_set(tc_plan* plan, int key, double value) {
             case TC_SET_THETA_VARIANT: o.theta_variant = v; break;
             case TC_SET_PC_PARTITIONS: o.pc_partitions = v; break;
             case TC_SET_STAGE_ROWS: o.stage_rows = v; break;
+            case TC_SET_MEAN_FP32: o.mean_fp32 = v; break;
             default: return TC_ERR_ARG;
         }
     }

@@ -18,7 +18,7 @@ TC_P_STAR, TC_U_PLUS, TC_U_MINUS, TC_U_Z, TC_PHI = range(5)
 TC_FP64, TC_MIXED = 0, 1
 (TC_SET_ALPHA, TC_SET_P_THETA, TC_SET_P_Z, TC_SET_PRECISION, TC_SET_HOST_ONLY, TC_SET_THETA_ZT,
  TC_SET_PC_MODES, TC_SET_NO_ADJOINT, TC_SET_PC_SPLIT, TC_SET_THETA_VARIANT, TC_SET_PC_PARTITIONS,
- TC_SET_STAGE_ROWS) = range(12)
+ TC_SET_STAGE_ROWS, TC_SET_MEAN_FP32) = range(13)
 
 # every symbol include/tc.h declares, in declaration order
 SYMBOLS = [
@@ -35,7 +35,7 @@ class tc_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("host_only", ctypes.c_int), ("theta_zt", ctypes.c_int),
                 ("pc_modes", ctypes.c_int), ("no_adjoint", ctypes.c_int), ("pc_split", ctypes.c_int),
                 ("theta_variant", ctypes.c_int), ("pc_partitions", ctypes.c_int),
-                ("stage_rows", ctypes.c_int)]
+                ("stage_rows", ctypes.c_int), ("mean_fp32", ctypes.c_int)]
 
 
 class tc_state(ctypes.Structure):
@@ -225,10 +225,10 @@ class Plan:
     def __init__(self, N_r, M, K, m_p, eta, Re_i, Re_o, L_z, dt, fd_order=8, alpha=0.5,
                  P_theta=0, P_z=0, precision=TC_FP64, host_only=False, device=None, theta_zt=0,
                  pc_modes=0, no_adjoint=False, pc_split=0, theta_variant=0, pc_partitions=0,
-                 stage_rows=0):
+                 stage_rows=0, mean_fp32=0):
         opt = tc_options(alpha if alpha != 0.0 else -1.0, P_theta, P_z, precision, int(host_only),
                          theta_zt, pc_modes, int(no_adjoint), pc_split, theta_variant, pc_partitions,
-                         stage_rows)
+                         stage_rows, int(mean_fp32))
         self.N_r, self.M, self.K = N_r, M, K
         self.handle = None
         torch = _torch()

@@ -329,6 +329,21 @@ def test_mixed_mean_mode_at_fp64_accuracy(case):
         assert np.linalg.norm(got[c] - ref[c]) <= 1e-10 * scale, (c, np.linalg.norm(got[c] - ref[c]) / scale)
 
 
+def test_mixed_mean_fp32_option_changes_only_the_mean_mode():
+    """tc_options.mean_fp32 keeps the FP32 transforms' (0,0) mode of N; every other
+    coefficient is bit-identical to the default mixed plan's."""
+    ops = O.Operators(O.Params(**CFG1))
+    u = init(ops, kind="box", amp=1e-2)
+    a = host(tc.Plan(**CFG1, precision=tc.TC_MIXED).nonlinear(dev(u)))
+    b = host(tc.Plan(**CFG1, precision=tc.TC_MIXED, mean_fp32=True).nonlinear(dev(u)))
+    K = ops.prm.K
+    keep = np.ones(a.shape, bool)
+    keep[:, :, 0, K] = False
+    assert np.array_equal(a[keep], b[keep])
+    ref = O.nonlinear(ops, u)
+    assert rel(b, ref) <= 2e-6
+
+
 def test_mixed_nonlinear_m0_line_is_a_real_field():
     """The mixed form's N keeps the m = 0 symmetry of a real field exactly:
     N_+(0,k) = conj N_-(0,-k) and N_z(0,k) = conj N_z(0,-k)."""
