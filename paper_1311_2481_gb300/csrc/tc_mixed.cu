@@ -11,11 +11,13 @@
 //               the result instead of the size of u / dr.           -> P[d][c][r][m][k]
 //   k_zinv_p32  per (r, m): u', d_r u', d_z u' = i k k_z u' of the 3 components, zero-padded
 //               inverse z transforms (FP32).                          -> H1[9][r][m][z]
-//   k_theta_s   length-specialised theta pass with streamed products (tc_theta32.cu), or
+//   k_theta_s   length-specialised theta pass with streamed products (tc_theta_s.cu), or
 //               the generic k_theta with FP32 lines for other lengths -> H2[3][r][m][z]
 //   k_zfwd32    per (r, m): forward z transforms, truncation, 1/(P_theta P_z), plus the
 //               mean-flow terms in double-FP32 arithmetic (error-free products and sums),
 //               assembled into FP64 by exact bit conversion and one FP64 add.
+//   k_mean00    beside them on a second stream: the (0, 0) mode of N by an exact Parseval
+//               sum in double-FP32 (below), which replaces that coefficient at the end.
 //
 // Mean-flow terms (Eq. NS_cyl with u_theta = U + u'_theta, U = Re u_theta^{(0,0)}):
 //   N_pm += (U/r) i m m_p u'_pm + i (U/r)(u'_+ - u'_-) +- (i/2)(d_r U + U/r)(u'_+ + u'_-),
