@@ -151,3 +151,29 @@ def test_plan_set_on_host_plan(lib):
     ws0 = a.ws_bytes
     a.set(tc.TC_SET_NO_ADJOINT, 1)
     assert a.ws_bytes < ws0
+    # staging by radial slab: fewer rows per slab, less workspace; negative rows are refused
+    ws1 = a.ws_bytes
+    a.set(tc.TC_SET_STAGE_ROWS, 5)
+    assert a.ws_bytes < ws1
+    assert a.ws_bytes == tc.Plan(*args, host_only=True, alpha=0.9, no_adjoint=True, stage_rows=5).ws_bytes
+    for key, value in ((tc.TC_SET_STAGE_ROWS, -1.0), (tc.TC_SET_MEAN_FP32, 2.0)):
+        with pytest.raises(tc.TCError) as e:
+            a.set(key, value)
+        assert e.value.status == tc.TC_ERR_ARG, (key, value)
+    a.set(tc.TC_SET_MEAN_FP32, 1)   # accepted on any plan; only the mixed form reads it
+
+
+def test_stage_rows_workspace_layout():
+    """The FP64 staging of a plan holds 12 line sets of stage_rows radial rows (21 with the
+    adjoint); all rows while they fit 4 GiB.  A mixed plan's FP32 forward staging keeps all
+    rows whatever stage_rows is."""
+    L = 2 * math.pi / 3.16
+    args = (40, 8, 16, 1, 0.5, 50.0, 0.0, L, 1e-3)
+    line = 9 * 48 * 16                          # (M+1) P_z complex128 values of one row
+    full = tc.Plan(*args, host_only=True, no_adjoint=True).ws_bytes
+    part = tc.Plan(*args, host_only=True, no_adjoint=True, stage_rows=10).ws_bytes
+    assert full - part >= 12 * 30 * line         # 12 line sets of 30 rows fewer (256-byte rounding aside)
+    assert full - part < 12 * 30 * line + 4 * 256
+    m_full = tc.Plan(*args, host_only=True, no_adjoint=True, precision=tc.TC_MIXED).ws_bytes
+    m_part = tc.Plan(*args, host_only=True, no_adjoint=True, precision=tc.TC_MIXED, stage_rows=10).ws_bytes
+    assert m_full == m_part
