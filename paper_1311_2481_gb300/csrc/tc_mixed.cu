@@ -657,8 +657,8 @@ static tc_status launch_sym_m0(tc_plan* p, double2* N, cudaStream_t s) {
 //     <N_z> = <u_r D u_z> + (1/r) sum c_m m m_p Im(u_t conj u_z)
 // (D: the FD stencil of Sec. 3.1).  k_mean00 evaluates these from the FP64 state in
 // double-FP32 arithmetic (each value an unevaluated FP32 pair, error-free products and
-// sums, about 44 significant bits), one thread per (row, k) of a mode line, and writes each
-// warp's sum over its 32 k values; k_mean00_fin adds those in FP64 in a fixed order and
+// sums, about 44 significant bits), one thread per (row, mode), and writes each
+// warp's sum over its 32 modes; k_mean00_fin adds those in FP64 in a fixed order and
 // overwrites N's (0, 0) coefficients: N_pm = <N_r> +- i <N_t>, N_z = <N_z>.
 
 struct dfl {
@@ -724,37 +724,36 @@ constexpr int kMeanK = 32;   // k values per block (one warp row)
 constexpr int kMeanR = 8;    // rows per block (one per warp)
 constexpr int kMeanWin = kMeanR + kStencil - 1;
 
-// part[(c * N_r + r) * nseg + m * nkt + kt], c = 0: <N_r>, 1: <N_t>, 2: <N_z>
+// part[(c * N_r + r) * ntile + tile], c = 0: <N_r>, 1: <N_t>, 2: <N_z>
 __global__ void __launch_bounds__(256) k_mean00(const double2* __restrict__ u, double* __restrict__ part,
                                                 const double* __restrict__ w1, const int* __restrict__ col0,
-                                                const double* __restrict__ irn, int N_r, int M, int K, int nkt,
+                                                const double* __restrict__ irn, int N_r, int M, int K, int ntile,
                                                 int nrc, double mp, double kz) {
     // window of the three components' rows, each value split once: (hi re, hi im, lo re, lo im)
     __shared__ float4 win[3][kMeanWin * kMeanK];
     __shared__ float2 sw[kMeanR * kStencil];
-    int b = blockIdx.x;
-    const int kt = b % nkt;
-    b /= nkt;
-    const int rc = b % nrc;
-    const int m = b / nrc;
+    // a block takes 32 consecutive modes of the flattened (m, k) index, so no lane idles at
+    // the end of an m line
+    const int tile = blockIdx.x % ntile;
+    const int rc = blockIdx.x / ntile;
     const int nk = 2 * K + 1;
-    const size_t S = (size_t)N_r * (M + 1) * nk;
-    const size_t colstride = (size_t)(M + 1) * nk;
+    const int nmode = (M + 1) * nk;
+    const size_t S = (size_t)N_r * nmode;
     const int r0 = rc * kMeanR;
     const int r1 = min(r0 + kMeanR, N_r) - 1;
     const int jlo = col0[r0];
     const int jhi = col0[r1] + kStencil - 1;
-    const int kk = kt * kMeanK + threadIdx.x;
-    const bool kin = kk < nk;
+    const int mode = tile * kMeanK + threadIdx.x;
+    const bool kin = mode < nmode;
     const int tid = threadIdx.y * kMeanK + threadIdx.x;
     for (int i = tid; i < (r1 - r0 + 1) * kStencil; i += blockDim.x * blockDim.y)
         sw[i] = split_hl(w1[(size_t)r0 * kStencil + i]);
     for (int c = 0; c < 3; ++c) {
-        const double2* base = u + (size_t)c * S + (size_t)m * nk + kk;
+        const double2* base = u + (size_t)c * S + mode;
         for (int j = jlo + threadIdx.y; j <= jhi; j += blockDim.y) {
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (kin) {
-                const double2 x = base[(size_t)j * colstride];
+                const double2 x = base[(size_t)j * nmode];
                 const float2 a = split_hl(x.x), q = split_hl(x.y);
                 v = make_float4(a.x, q.x, a.y, q.y);
             }
@@ -762,10 +761,11 @@ __global__ void __launch_bounds__(256) k_mean00(const double2* __restrict__ u, d
         }
     }
     __syncthreads();
-    const int k = kk - K;
+    const int m = kin ? mode / nk : 0;
+    const int k = kin ? mode - m * nk - K : 0;
     const float cm = m == 0 ? 1.f : 2.f;
     const dfl mm = df_of(mp * m), kzk = df_of(kz * (double)k);   // m m_p and k k_z as in FP64
-    const size_t nseg = (size_t)(M + 1) * nkt;
+    const size_t nseg = (size_t)ntile;
     for (int r = r0 + threadIdx.y; r <= r1; r += blockDim.y) {
         dfl tr = {0.f, 0.f}, tt = {0.f, 0.f}, tz = {0.f, 0.f};
         if (kin) {
@@ -808,7 +808,7 @@ __global__ void __launch_bounds__(256) k_mean00(const double2* __restrict__ u, d
                 tz.h *= 2.f; tz.l *= 2.f;
             }
         }
-        // sum over the warp's 32 k values (fixed tree)
+        // sum over the warp's 32 modes (fixed tree)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             tr = df_add(tr, df_shfl_down(tr, o));
@@ -816,7 +816,7 @@ __global__ void __launch_bounds__(256) k_mean00(const double2* __restrict__ u, d
             tz = df_add(tz, df_shfl_down(tz, o));
         }
         if (threadIdx.x == 0) {
-            const size_t seg = (size_t)m * nkt + kt;
+            const size_t seg = (size_t)tile;
             part[((size_t)0 * N_r + r) * nseg + seg] = df_val(tr);
             part[((size_t)1 * N_r + r) * nseg + seg] = df_val(tt);
             part[((size_t)2 * N_r + r) * nseg + seg] = df_val(tz);
@@ -850,20 +850,18 @@ __global__ void __launch_bounds__(256) k_mean00_fin(const double* __restrict__ p
     }
 }
 
-size_t mean00_part_doubles(const tc_plan* p) {
-    const int nk = 2 * p->K + 1;
-    return (size_t)3 * p->N_r * (p->M + 1) * ((nk + kMeanK - 1) / kMeanK);
-}
+static int mean00_tiles(const tc_plan* p) { return (p->nmode + kMeanK - 1) / kMeanK; }
+
+size_t mean00_part_doubles(const tc_plan* p) { return (size_t)3 * p->N_r * mean00_tiles(p); }
 
 // the segment sums of the mean mode (reads only u and the plan)
 tc_status launch_mean00_part(tc_plan* p, const double2* u, char* ws, cudaStream_t s) {
-    const int nk = 2 * p->K + 1;
-    const int nkt = (nk + kMeanK - 1) / kMeanK;
+    const int ntile = mean00_tiles(p);
     const int nrc = (p->N_r + kMeanR - 1) / kMeanR;
     double* part = reinterpret_cast<double*>(ws + p->ws.mean);
     const int slot = prof_begin(p, kKMean00, s);
-    k_mean00<<<(unsigned)(nkt * nrc * (p->M + 1)), dim3(kMeanK, kMeanR), 0, s>>>(
-        u, part, p->d_w1, p->d_col0, p->d_ir, p->N_r, p->M, p->K, nkt, nrc, (double)p->m_p, p->k_z);
+    k_mean00<<<(unsigned)(ntile * nrc), dim3(kMeanK, kMeanR), 0, s>>>(
+        u, part, p->d_w1, p->d_col0, p->d_ir, p->N_r, p->M, p->K, ntile, nrc, (double)p->m_p, p->k_z);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_mean00");
     return TC_OK;
@@ -871,9 +869,8 @@ tc_status launch_mean00_part(tc_plan* p, const double2* u, char* ws, cudaStream_
 
 // N's (0, 0) coefficients from the segment sums (after the forward z pass wrote N)
 tc_status launch_mean00_fin(tc_plan* p, double2* N, char* ws, cudaStream_t s) {
-    const int nkt = (2 * p->K + 1 + kMeanK - 1) / kMeanK;
     const double* part = reinterpret_cast<const double*>(ws + p->ws.mean);
-    k_mean00_fin<<<p->N_r, 256, 0, s>>>(part, N, p->N_r, p->M, p->K, (p->M + 1) * nkt, p->S);
+    k_mean00_fin<<<p->N_r, 256, 0, s>>>(part, N, p->N_r, p->M, p->K, mean00_tiles(p), p->S);
     TC_LAUNCHED(p, "k_mean00_fin");
     return TC_OK;
 }
