@@ -544,3 +544,28 @@ def test_step_host_matches_device_step():
     bad = {k: getattr(ref, k) for k in ("u", "u_prev", "N_prev", "p")}   # device tensors
     with pytest.raises(tc.TCError):
         plan.step_host(tc.State(plan, dev(u0)), bad, {}, 1)
+
+
+@pytest.mark.parametrize("prec", [tc.TC_FP64, tc.TC_MIXED])
+def test_step_captured_in_a_cuda_graph(prec):
+    """tc_step records into a CUDA graph (the mixed form's second-stream fork and join
+    included), and replaying the graph gives the eager steps bit for bit."""
+    ops = O.Operators(O.Params(**CFG1))
+    plan = tc.Plan(**CFG1, precision=prec)
+    u0 = dev(init(ops, amp=1e-2))
+    a = tc.State(plan, u0)
+    b = tc.State(plan, u0)
+    plan.step(a, 1)
+    plan.step(b, 1)
+    plan.step(a, 3)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.step(b, 1)                      # recorded, not run
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    for name in ("u", "u_prev", "N_prev", "p"):
+        assert torch.equal(getattr(a, name), getattr(b, name)), name
