@@ -16,6 +16,7 @@
 
 #include "tc_internal.cuh"
 #include "tc_solve_core.cuh"
+#include "tc_split.cuh"
 
 namespace tc {
 
@@ -511,6 +512,227 @@ __global__ void k_update(double2* u, double2* up, const double2* Nc, double2* Np
     }
 }
 
+// ---------------------------------------------------------------- split path, mixed form
+// The same four per-stage kernels for TC_MIXED plans, with each radial stencil (of X, p*,
+// u*_+ + u*_- and phi) in double-FP32 instead of FP64: the FP64 pipe, which bounds these
+// kernels, then carries only the rest.  A block takes a tile of 32 modes x 32 rows; the
+// tile's window of rows is read once and each value split once into an exact FP32 pair
+// (hi, lo) in shared memory, the stencil is a compensated dot product of the pairs (about 44
+// significant bits, against FP32 transforms elsewhere in the form), and the result is
+// assembled in FP64.  Everything else keeps the FP64 arithmetic of the FP64 kernels.
+constexpr int kXsM = 32;                     // modes per tile (one warp row)
+constexpr int kXsR = 32;                     // rows per tile
+constexpr int kXsWin = kXsR + kStencil - 1;  // window rows
+
+struct XsTile {
+    int mode;   // this thread's mode
+    bool in;    // mode < g.mhi
+    int r0, r1, jlo;
+};
+
+__device__ __forceinline__ XsTile xs_tile(const int* __restrict__ col0, const Geo& g) {
+    XsTile t;
+    t.mode = g.mlo + blockIdx.x * kXsM + threadIdx.x;
+    t.in = t.mode < g.mhi;
+    t.r0 = blockIdx.y * kXsR;
+    t.r1 = min(t.r0 + kXsR, g.N) - 1;
+    t.jlo = col0[t.r0];
+    return t;
+}
+
+// the tile's stencil weights and the window of f (or of f + f2), split once
+__device__ __forceinline__ void xs_load(const double2* __restrict__ f, const double2* __restrict__ f2,
+                                        const double* __restrict__ w1, const int* __restrict__ col0,
+                                        float4* win, float2* sw, const XsTile& t, const Geo& g) {
+    const int tid = threadIdx.y * kXsM + threadIdx.x;
+    for (int i = tid; i < (t.r1 - t.r0 + 1) * kStencil; i += blockDim.x * blockDim.y)
+        sw[i] = xs::split_hl(w1[(size_t)t.r0 * kStencil + i]);
+    const int jhi = col0[t.r1] + kStencil - 1;
+    for (int j = t.jlo + threadIdx.y; j <= jhi; j += blockDim.y) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t.in) {
+            double2 x = f[(size_t)j * g.nmode + t.mode];
+            if (f2) {
+                const double2 y = f2[(size_t)j * g.nmode + t.mode];
+                x.x += y.x;
+                x.y += y.y;
+            }
+            const float2 a = xs::split_hl(x.x), q = xs::split_hl(x.y);
+            v = make_float4(a.x, q.x, a.y, q.y);
+        }
+        win[(j - t.jlo) * kXsM + threadIdx.x] = v;
+    }
+    __syncthreads();
+}
+
+// D1 of the window's field at row r for this thread's mode, assembled in FP64
+__device__ __forceinline__ double2 xs_drow(const float4* win, const float2* sw, const int* __restrict__ col0,
+                                           const XsTile& t, int r) {
+    const int w0 = (col0[r] - t.jlo) * kXsM + threadIdx.x;
+    const float2* w = sw + (r - t.r0) * kStencil;
+    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+#pragma unroll
+    for (int q = 0; q < kStencil; ++q) {
+        const float4 v = win[w0 + q * kXsM];
+        xs::dot_acc(sx, cx, w[q].x, w[q].y, v.x, v.z);
+        xs::dot_acc(sy, cy, w[q].x, w[q].y, v.y, v.w);
+    }
+    return make_double2(xs::f2d_bits(sx) + xs::f2d_bits(cx), xs::f2d_bits(sy) + xs::f2d_bits(cy));
+}
+
+__global__ void __launch_bounds__(256) k_rhs_pressure_mx(const double2* __restrict__ u, const double2* __restrict__ up,
+                                                         const double2* __restrict__ Nc, const double2* __restrict__ Np,
+                                                         const double2* __restrict__ X, double2* __restrict__ b,
+                                                         const double* __restrict__ rn, const double* __restrict__ irn,
+                                                         const double* __restrict__ w1, const double* __restrict__ w2,
+                                                         const int* __restrict__ col0, Geo g) {
+    __shared__ float4 win[kXsWin * kXsM];
+    __shared__ float2 sw[kXsR * kStencil];
+    const XsTile t = xs_tile(col0, g);
+    xs_load(X, nullptr, w1, col0, win, sw, t, g);
+    if (!t.in) return;
+    const int mode = t.mode;
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    const double mm = g.mp * m, kk = g.kz * k;
+    for (int j = t.r0 + threadIdx.y; j <= t.r1; j += blockDim.y) {
+        const size_t e = (size_t)j * g.nmode + mode;
+        const double r = rn[j], ir = irn[j];
+        double2 out = make_double2(0.0, 0.0);
+        if (j == 0 || j == g.N - 1) {
+            if (!(j == g.N - 1 && m == 0 && k == 0)) {
+                const double2 x = X[e];
+                const double2 l0 = lap_r(u, w1, w2, col0, r, j, mode, mm, kk, g);
+                const double2 l1 = lap_r(up, w1, w2, col0, r, j, mode, mm, kk, g);
+                out.x = -x.x + 2.0 * l0.x - l1.x;
+                out.y = -x.y + 2.0 * l0.y - l1.y;
+            }
+        } else {
+            const double2 d = xs_drow(win, sw, col0, t, j);
+            const double2 x = X[e];
+            const double2 n1 = Nc[e], n0 = Np[e], m1 = Nc[g.S + e], m0 = Np[g.S + e];
+            const double2 z1 = Nc[2 * g.S + e], z0 = Np[2 * g.S + e];
+            const double dpx = (2.0 * n1.x - n0.x) - (2.0 * m1.x - m0.x);
+            const double dpy = (2.0 * n1.y - n0.y) - (2.0 * m1.y - m0.y);
+            const double nzx = 2.0 * z1.x - z0.x, nzy = 2.0 * z1.y - z0.y;
+            out.x = -(d.x + x.x * ir + 0.5 * mm * ir * dpx - kk * nzy);
+            out.y = -(d.y + x.y * ir + 0.5 * mm * ir * dpy + kk * nzx);
+        }
+        b[e] = out;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_rhs_velocity_mx(const double2* __restrict__ u, const double2* __restrict__ up,
+                                                         const double2* __restrict__ Nc, const double2* __restrict__ Np,
+                                                         const double2* __restrict__ ps, double2* __restrict__ rhs,
+                                                         double2* __restrict__ p_out, const double* __restrict__ irn,
+                                                         const double* __restrict__ w1, const int* __restrict__ col0,
+                                                         double Re_i, double Re_o, Geo g) {
+    __shared__ float4 win[kXsWin * kXsM];
+    __shared__ float2 sw[kXsR * kStencil];
+    const XsTile t = xs_tile(col0, g);
+    xs_load(ps, nullptr, w1, col0, win, sw, t, g);
+    if (!t.in) return;
+    const int mode = t.mode;
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    for (int j = t.r0 + threadIdx.y; j <= t.r1; j += blockDim.y) {
+        const size_t e = (size_t)j * g.nmode + mode;
+        const double2 pv = ps[e];
+        if (p_out) p_out[e] = pv;
+        if (j == 0 || j == g.N - 1) {
+            const double Re = (m == 0 && k == 0) ? (j == 0 ? Re_i : Re_o) : 0.0;
+            rhs[e] = make_double2(0.0, Re);
+            rhs[g.S + e] = make_double2(0.0, -Re);
+            rhs[2 * g.S + e] = make_double2(0.0, 0.0);
+            continue;
+        }
+        const double2 d = xs_drow(win, sw, col0, t, j);
+        const double tt = g.mp * m * irn[j], kk = g.kz * k;
+        const double2 gp[3] = {make_double2(d.x - tt * pv.x, d.y - tt * pv.y),
+                               make_double2(d.x + tt * pv.x, d.y + tt * pv.y),
+                               make_double2(-kk * pv.y, kk * pv.x)};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t ec = (size_t)c * g.S + e;
+            const double2 a = u[ec], q = up[ec], n1 = Nc[ec], n0 = Np[ec];
+            rhs[ec] = make_double2((4.0 * a.x - q.x) * g.c1 - (2.0 * n1.x - n0.x) - gp[c].x,
+                                   (4.0 * a.y - q.y) * g.c1 - (2.0 * n1.y - n0.y) - gp[c].y);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_rhs_div_mx(const double2* __restrict__ us, double2* __restrict__ b,
+                                                    const double* __restrict__ irn, const double* __restrict__ w1,
+                                                    const int* __restrict__ col0, Geo g) {
+    __shared__ float4 win[kXsWin * kXsM];
+    __shared__ float2 sw[kXsR * kStencil];
+    const XsTile t = xs_tile(col0, g);
+    xs_load(us, us + g.S, w1, col0, win, sw, t, g);   // the stencil of u*_+ + u*_-
+    if (!t.in) return;
+    const int mode = t.mode;
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    const double mm = g.mp * m, kk = g.kz * k;
+    for (int j = t.r0 + threadIdx.y; j <= t.r1; j += blockDim.y) {
+        const size_t e = (size_t)j * g.nmode + mode;
+        if (j == 0 || j == g.N - 1) {
+            b[e] = make_double2(0.0, 0.0);
+            continue;
+        }
+        const double ir = irn[j];
+        const double2 d = xs_drow(win, sw, col0, t, j);
+        const double2 vp = us[e], vm = us[g.S + e], vz = us[2 * g.S + e];
+        b[e] = make_double2(0.5 * d.x + 0.5 * (vp.x + vm.x) * ir + 0.5 * mm * ir * (vp.x - vm.x) - kk * vz.y,
+                            0.5 * d.y + 0.5 * (vp.y + vm.y) * ir + 0.5 * mm * ir * (vp.y - vm.y) + kk * vz.x);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_update_mx(double2* u, double2* up, const double2* Nc, double2* Np, double2* p,
+                                                   const double2* __restrict__ us, const double2* __restrict__ phi,
+                                                   double2* __restrict__ u_out, const double* __restrict__ irn,
+                                                   const double* __restrict__ w1, const int* __restrict__ col0,
+                                                   int commit, int* __restrict__ nonfinite, Geo g) {
+    __shared__ float4 win[kXsWin * kXsM];
+    __shared__ float2 sw[kXsR * kStencil];
+    const XsTile t = xs_tile(col0, g);
+    xs_load(phi, nullptr, w1, col0, win, sw, t, g);
+    if (!t.in) return;
+    const int mode = t.mode;
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    bool bad = false;
+    for (int j = t.r0 + threadIdx.y; j <= t.r1; j += blockDim.y) {
+        const size_t e = (size_t)j * g.nmode + mode;
+        const double2 f = phi[e];
+        const double2 d = xs_drow(win, sw, col0, t, j);
+        const double tt = g.mp * m * irn[j], kk = g.kz * k;
+        const double2 gph[3] = {make_double2(d.x - tt * f.x, d.y - tt * f.y),
+                                make_double2(d.x + tt * f.x, d.y + tt * f.y),
+                                make_double2(-kk * f.y, kk * f.x)};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t ec = (size_t)c * g.S + e;
+            const double2 s = us[ec];
+            const double2 un = make_double2(s.x - gph[c].x, s.y - gph[c].y);
+            bad |= nonfinite2(un);
+            if (commit) {
+                up[ec] = u[ec];
+                u[ec] = un;
+                Np[ec] = Nc[ec];
+            } else {
+                u_out[ec] = un;
+            }
+        }
+        if (commit) {
+            const double q = 3.0 * g.c1;
+            const double2 a = p[e];
+            p[e] = make_double2(a.x + q * f.x, a.y + q * f.y);
+        }
+    }
+    if (bad && nonfinite) *nonfinite = 1;
+}
+
 // x <- A^{-1} x for every mode of nfields consecutive fields (system sets set0, set0+1, ...):
 // thread (field, mode, part) runs the register-window substitution down its global column.
 __global__ void k_band_solve_g(double2* __restrict__ x, const double* __restrict__ fac,
@@ -696,9 +918,17 @@ static tc_status launch_advance_split(tc_plan* p, const double2* u, double2* u_p
     double2* phi = reinterpret_cast<double2*>(ws + p->ws.phi);   // also holds X before phi
     const dim3 g1(g.N, blocks_for(nm, 128));
     auto sgrid = [&](int nf) { return dim3(blocks_for((size_t)2 * nm, 128), nf); };
+    // mixed form: the radial stencils in double-FP32 (the *_mx kernels), tiles of 32 x 32
+    const bool mx = p->precision == TC_MIXED;
+    const dim3 gx(blocks_for(nm, kXsM), blocks_for(g.N, kXsR)), bx(kXsM, 8);
     int slot = prof_begin(p, kKRhsPressure, s);
     k_nn_r<<<g1, 128, 0, s>>>(Ncur, N_prev, phi, g);
-    k_rhs_pressure<<<g1, 128, 0, s>>>(u, u_prev, Ncur, N_prev, phi, ps, p->d_r, p->d_ir, p->d_w1, p->d_w2, p->d_col0, g);
+    if (mx)
+        k_rhs_pressure_mx<<<gx, bx, 0, s>>>(u, u_prev, Ncur, N_prev, phi, ps, p->d_r, p->d_ir, p->d_w1, p->d_w2,
+                                            p->d_col0, g);
+    else
+        k_rhs_pressure<<<g1, 128, 0, s>>>(u, u_prev, Ncur, N_prev, phi, ps, p->d_r, p->d_ir, p->d_w1, p->d_w2,
+                                          p->d_col0, g);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_rhs_pressure");
     slot = prof_begin(p, kKSolveP, s);
@@ -706,8 +936,12 @@ static tc_status launch_advance_split(tc_plan* p, const double2* u, double2* u_p
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_band_solve_g");
     slot = prof_begin(p, kKRhsVelocity, s);
-    k_rhs_velocity<<<g1, 128, 0, s>>>(u, u_prev, Ncur, N_prev, ps, us, commit ? p_out : nullptr, p->d_ir, p->d_w1,
-                                       p->d_col0, p->Re_i, p->Re_o, g);
+    if (mx)
+        k_rhs_velocity_mx<<<gx, bx, 0, s>>>(u, u_prev, Ncur, N_prev, ps, us, commit ? p_out : nullptr, p->d_ir,
+                                            p->d_w1, p->d_col0, p->Re_i, p->Re_o, g);
+    else
+        k_rhs_velocity<<<g1, 128, 0, s>>>(u, u_prev, Ncur, N_prev, ps, us, commit ? p_out : nullptr, p->d_ir,
+                                          p->d_w1, p->d_col0, p->Re_i, p->Re_o, g);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_rhs_velocity");
     slot = prof_begin(p, kKSolveH, s);
@@ -715,7 +949,10 @@ static tc_status launch_advance_split(tc_plan* p, const double2* u, double2* u_p
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_band_solve_g");
     slot = prof_begin(p, kKRhsDiv, s);
-    k_rhs_div<<<g1, 128, 0, s>>>(us, phi, p->d_ir, p->d_w1, p->d_col0, g);
+    if (mx)
+        k_rhs_div_mx<<<gx, bx, 0, s>>>(us, phi, p->d_ir, p->d_w1, p->d_col0, g);
+    else
+        k_rhs_div<<<g1, 128, 0, s>>>(us, phi, p->d_ir, p->d_w1, p->d_col0, g);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_rhs_div");
     slot = prof_begin(p, kKSolveP, s);
@@ -723,8 +960,12 @@ static tc_status launch_advance_split(tc_plan* p, const double2* u, double2* u_p
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_band_solve_g");
     slot = prof_begin(p, kKUpdate, s);
-    k_update<<<g1, 128, 0, s>>>(const_cast<double2*>(u), u_prev, Ncur, N_prev, p_out, us, phi, u_out, p->d_ir,
-                                p->d_w1, p->d_col0, commit ? 1 : 0, p->d_nonfinite, g);
+    if (mx)
+        k_update_mx<<<gx, bx, 0, s>>>(const_cast<double2*>(u), u_prev, Ncur, N_prev, p_out, us, phi, u_out, p->d_ir,
+                                      p->d_w1, p->d_col0, commit ? 1 : 0, p->d_nonfinite, g);
+    else
+        k_update<<<g1, 128, 0, s>>>(const_cast<double2*>(u), u_prev, Ncur, N_prev, p_out, us, phi, u_out, p->d_ir,
+                                    p->d_w1, p->d_col0, commit ? 1 : 0, p->d_nonfinite, g);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_update");
     return TC_OK;

@@ -437,6 +437,25 @@ def test_mixed_twenty_steps_track_fp64():
     assert rel(got, ref.u) <= 1e-8
 
 
+def test_mixed_split_path_stencils():
+    """The mixed form's per-stage steps 2-5 (radial stencils in double-FP32) against its fused
+    kernel (FP64 stencils) and the oracle, over 20 steps; the wall row N_r = 9 < 32 and the
+    tile edges (N_r = 37) included."""
+    for cfg in (CFG1, dict(CFG1, N_r=37), dict(CFG1, N_r=9, M=4, K=6)):
+        ops = O.Operators(O.Params(**cfg))
+        u0 = init(ops, amp=1e-2)
+        ref = O.run(ops, O.cold_state(u0), 20)
+        outs = []
+        for split in (1, -1):
+            plan = tc.Plan(**cfg, precision=tc.TC_MIXED, pc_split=split)
+            st = tc.State(plan, dev(u0))
+            plan.step(st, 20)
+            outs.append([host(getattr(st, k)) for k in ("u", "u_prev", "N_prev", "p")])
+        for a, b in zip(*outs):
+            assert rel(a, b) <= 1e-11, (cfg["N_r"], rel(a, b))
+        assert rel(outs[0][0], ref.u) <= 1e-8
+
+
 def test_mixed_at_the_bench_workload_against_oracle():
     """The mixed form at the bench workload (N_r = 64, m = -32..32, k = -64..64, Re_i = 1000,
     Taylor-vortex-like start) over 20 steps at the largest stable dt (the stated 5e-4 halved
