@@ -114,7 +114,11 @@ __device__ __forceinline__ void spike_combine(const PCArgs& a, const Geo& g, dou
 // Steps 2-5 of Sec. 3.2 for the T modes of this block: pressure prediction (Eq. pressure
 // with the Neumann rows of Eq. ppBC), velocity prediction (Eq. vel), correction potential
 // (Eq. correction) and update (Eq. update).
-template <int NTH>
+// MX (mixed form): the four radial stencils -- of X, p*, u*_+ + u*_- and phi -- in
+// double-FP32: the column is split once into exact FP32 pairs in shared memory (XS, with the
+// split weights SW), the stencil is a compensated dot product of the pairs, the result is
+// assembled in FP64; the solves and everything else stay FP64.
+template <int NTH, bool MX>
 __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     extern __shared__ double2 sm[];
     const int N = g.N;
@@ -123,6 +127,37 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     double2* C1 = sm + items;
     double2* C2 = C1 + items;
     double2* C3 = C2 + items;
+    float4* XS = reinterpret_cast<float4*>(C3 + items) + 3 * T * 16 / 2;   // after the spike scratch
+    float2* SW = reinterpret_cast<float2*>(XS + items);
+    if (MX) {
+        for (int i = threadIdx.x; i < N * kStencil; i += blockDim.x) SW[i] = xs::split_hl(a.w1[i]);
+    }
+    // XS <- split of the column(s) (F + F2), then a barrier
+    auto split_cols = [&](const double2* F, const double2* F2) {
+        for (int i = threadIdx.x; i < items; i += blockDim.x) {
+            double2 x = F[i];
+            if (F2) {
+                x.x += F2[i].x;
+                x.y += F2[i].y;
+            }
+            const float2 p = xs::split_hl(x.x), q = xs::split_hl(x.y);
+            XS[i] = make_float4(p.x, q.x, p.y, q.y);
+        }
+        __syncthreads();
+    };
+    // D1 of the split column at row j, mode t, assembled in FP64
+    auto xsrow = [&](int j, int t) {
+        const int c0 = a.col0[j];
+        float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+#pragma unroll
+        for (int q = 0; q < kStencil; ++q) {
+            const float4 v = XS[(c0 + q) * T + t];
+            const float2 w = SW[j * kStencil + q];
+            xs::dot_acc(sx, cx, w.x, w.y, v.x, v.z);
+            xs::dot_acc(sy, cy, w.x, w.y, v.y, v.w);
+        }
+        return make_double2(xs::f2d_bits(sx) + xs::f2d_bits(cx), xs::f2d_bits(sy) + xs::f2d_bits(cy));
+    };
     const int mode0 = g.mlo + blockIdx.x * T;
     const int nT = min(T, g.mhi - mode0);
     const size_t per_set = (size_t)N * kBands * g.M1K1;
@@ -149,6 +184,10 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
             x.y = 0.5 * ((2.0 * n1.y - n0.y) + (2.0 * m1.y - m0.y));
         }
         C1[idx] = x;
+        if (MX) {
+            const float2 p = xs::split_hl(x.x), q = xs::split_hl(x.y);
+            XS[idx] = make_float4(p.x, q.x, p.y, q.y);
+        }
     }
     __syncthreads();
     // A2: pressure right-hand side into C0
@@ -169,7 +208,7 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
                     out.y = -X.y + 2.0 * l0.y - l1.y;
                 }
             } else {
-                const double2 d = sdrow(C1, a.w1, a.col0, j, T, t);
+                const double2 d = MX ? xsrow(j, t) : sdrow(C1, a.w1, a.col0, j, T, t);
                 const double2 X = C1[idx];
                 const double2 n1 = a.Nc[e], n0 = a.Np[e], m1 = a.Nc[g.S + e], m0 = a.Np[g.S + e];
                 const double2 z1 = a.Nc[2 * g.S + e], z0 = a.Np[2 * g.S + e];
@@ -236,6 +275,7 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     }
     __syncthreads();
     if (sp) spike_combine(a, g, C0, 1, kSetP, T, nT, mode0, Xr);
+    if (MX) split_cols(C0, nullptr);
     // C: velocity right-hand sides: subtract grad_h p* on interior rows; p <- p* (commit)
     for (int j = threadIdx.x / T; j < N && tq < nT; j += jstep) {
         const int idx = j * T + tq, t = tq;
@@ -243,7 +283,7 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
         const double2 pv = C0[idx];
         if (a.commit) a.p[(size_t)j * g.nmode + mode] = pv;
         if (j == 0 || j == N - 1) continue;
-        const double2 d = sdrow(C0, a.w1, a.col0, j, T, t);
+        const double2 d = MX ? xsrow(j, t) : sdrow(C0, a.w1, a.col0, j, T, t);
         const double tt = mmq * a.ir[j];
         const double kk = kkq;
         double2 v;
@@ -292,15 +332,22 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
         }
     }
     // E: div_h u* into C0 (homogeneous Neumann / Dirichlet rows)
+    if (MX) split_cols(C1, C2);   // the stencil of u*_+ + u*_-
     for (int j = threadIdx.x / T; j < N; j += jstep) {
         const int idx = j * T + tq, t = tq;
         double2 out = make_double2(0.0, 0.0);
         if (t < nT && j > 0 && j < N - 1) {
             const double mm = mmq, kk = kkq, ir = a.ir[j];
-            const double2 dp = sdrow(C1, a.w1, a.col0, j, T, t), dm = sdrow(C2, a.w1, a.col0, j, T, t);
+            double2 ds;
+            if (MX) {
+                ds = xsrow(j, t);
+            } else {
+                const double2 dp = sdrow(C1, a.w1, a.col0, j, T, t), dm = sdrow(C2, a.w1, a.col0, j, T, t);
+                ds = make_double2(dp.x + dm.x, dp.y + dm.y);
+            }
             const double2 vp = C1[idx], vm = C2[idx], vz = C3[idx];
-            out.x = 0.5 * (dp.x + dm.x) + 0.5 * (vp.x + vm.x) * ir + 0.5 * mm * ir * (vp.x - vm.x) - kk * vz.y;
-            out.y = 0.5 * (dp.y + dm.y) + 0.5 * (vp.y + vm.y) * ir + 0.5 * mm * ir * (vp.y - vm.y) + kk * vz.x;
+            out.x = 0.5 * ds.x + 0.5 * (vp.x + vm.x) * ir + 0.5 * mm * ir * (vp.x - vm.x) - kk * vz.y;
+            out.y = 0.5 * ds.y + 0.5 * (vp.y + vm.y) * ir + 0.5 * mm * ir * (vp.y - vm.y) + kk * vz.x;
         }
         C0[idx] = out;
     }
@@ -319,13 +366,14 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     }
     __syncthreads();
     if (sp) spike_combine(a, g, C0, 1, kSetP, T, nT, mode0, Xr);
+    if (MX) split_cols(C0, nullptr);
     // G: u^{i+1} = u* - grad_h phi, p^{i+1} = p* + 3 phi / (2 dt), history rotation
     bool bad = false;
     for (int j = threadIdx.x / T; j < N && tq < nT; j += jstep) {
         const int idx = j * T + tq, t = tq;
         const size_t e = (size_t)j * g.nmode + modeq;
         const double2 f = C0[idx];
-        const double2 d = sdrow(C0, a.w1, a.col0, j, T, t);
+        const double2 d = MX ? xsrow(j, t) : sdrow(C0, a.w1, a.col0, j, T, t);
         const double tt = mmq * a.ir[j];
         const double kk = kkq;
         const double2 gph[3] = {make_double2(d.x - tt * f.x, d.y - tt * f.y),
@@ -994,16 +1042,19 @@ tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const do
     a.commit = commit ? 1 : 0;
     // two partitions while the 12 T substitution threads of the Helmholtz phase fit the block
     g.sh = (p->part_h > 0 && 12 * T <= (T <= 8 ? 128 : 256)) ? p->part_h : 0;
-    const size_t sm = (size_t)4 * p->N_r * T * sizeof(double2) + (size_t)3 * T * 16 * sizeof(double);
+    // mixed form: the split column and weights of the double-FP32 stencils after the rest
+    const bool mx = p->precision == TC_MIXED;
+    const size_t sm = (size_t)4 * p->N_r * T * sizeof(double2) + (size_t)3 * T * 16 * sizeof(double) +
+                      (mx ? (size_t)p->N_r * T * sizeof(float4) + (size_t)p->N_r * kStencil * sizeof(float2) : 0);
     // 128 threads up to 8 modes per block, 256 beyond (6T substitution threads plus helpers)
     const int slot = prof_begin(p, kKPC, s);
-    if (T <= 8) {
-        TC_CUDA(p, cudaFuncSetAttribute(k_pc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_pc<128><<<blocks_for(g.mhi - g.mlo, T), 128, sm, s>>>(a, g, T);
-    } else {
-        TC_CUDA(p, cudaFuncSetAttribute(k_pc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_pc<256><<<blocks_for(g.mhi - g.mlo, T), 256, sm, s>>>(a, g, T);
-    }
+    auto run = [&](auto kern, int nth) -> tc_status {
+        TC_CUDA(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        kern<<<blocks_for(g.mhi - g.mlo, T), nth, sm, s>>>(a, g, T);
+        return TC_OK;
+    };
+    if (T <= 8) TC_TRY_STATUS(mx ? run(k_pc<128, true>, 128) : run(k_pc<128, false>, 128));
+    else TC_TRY_STATUS(mx ? run(k_pc<256, true>, 256) : run(k_pc<256, false>, 256));
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_pc");
     return TC_OK;

@@ -507,16 +507,17 @@ def test_plan_set_gives_the_created_plan(key, value, kw):
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("T", [4, 16])
-def test_pc_modes_bit_identical(T):
+@pytest.mark.parametrize("T,prec", [(4, tc.TC_FP64), (16, tc.TC_FP64), (4, tc.TC_MIXED), (16, tc.TC_MIXED)])
+def test_pc_modes_bit_identical(T, prec):
     """The fused steps-2-5 kernel with 4 or 16 modes per block (128 or 256 threads) gives the
-    same state as the default 8, bit for bit: each mode's arithmetic is the same."""
+    same state as the default 8, bit for bit: each mode's arithmetic is the same (the mixed
+    form's double-FP32 stencils included)."""
     cfg = dict(N_r=32, M=12, K=16, m_p=1, eta=0.5, Re_i=100.0, Re_o=0.0, L_z=LZ, dt=1e-4)
     ops = O.Operators(O.Params(**cfg))
     u0 = init(ops, kind="broadband", amp=1e-2, seed=10)
     out = []
     for modes in (8, T):
-        plan = tc.Plan(**cfg, pc_modes=modes)
+        plan = tc.Plan(**cfg, pc_modes=modes, precision=prec)
         st = tc.State(plan, dev(u0))
         plan.step(st, 5)
         out.append([host(getattr(st, k)) for k in ("u", "u_prev", "N_prev", "p")])
