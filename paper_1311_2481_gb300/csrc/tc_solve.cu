@@ -111,13 +111,31 @@ __device__ __forceinline__ void spike_combine(const PCArgs& a, const Geo& g, dou
     __syncthreads();
 }
 
+// Mixed form: the radial stencil sum_q w_q f_q over the 9 values v[q] of one complex column,
+// stored as exact FP32 pairs (hi re, hi im, lo re, lo im), with split weights w: a compensated
+// dot product (Ogita-Rump-Oishi), assembled in FP64.  The pairs carry 47 bits of each value,
+// so the error is about 2^-46 of sum |w_q f_q|.
+__device__ __forceinline__ double2 xs_stencil(const float4* v, int vstride, const float2* w) {
+    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+#pragma unroll
+    for (int q = 0; q < kStencil; ++q) {
+        const float4 f = v[q * vstride];
+        xs::dot_acc(sx, cx, w[q].x, w[q].y, f.x, f.z);
+        xs::dot_acc(sy, cy, w[q].x, w[q].y, f.y, f.w);
+    }
+    return make_double2(xs::f2d_bits(sx) + xs::f2d_bits(cx), xs::f2d_bits(sy) + xs::f2d_bits(cy));
+}
+
 // Steps 2-5 of Sec. 3.2 for the T modes of this block: pressure prediction (Eq. pressure
 // with the Neumann rows of Eq. ppBC), velocity prediction (Eq. vel), correction potential
 // (Eq. correction) and update (Eq. update).
 // MX (mixed form): the four radial stencils -- of X, p*, u*_+ + u*_- and phi -- in
 // double-FP32: the column is split once into exact FP32 pairs in shared memory (XS, with the
-// split weights SW), the stencil is a compensated dot product of the pairs, the result is
-// assembled in FP64; the solves and everything else stay FP64.
+// split weights SW), the stencil is a compensated dot product of the pairs (xs_stencil), the
+// result is assembled in FP64; the solves and everything else stay FP64.
+// The (0, 0) mode's stencils stay FP64 too (the mean flow, see the per-stage kernels): the
+// block that holds it computes that column's stencils in one pass, a row per thread, before
+// each phase (D00), so its warps do not diverge into FP64 stencils in the phase itself.
 template <int NTH, bool MX>
 __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     extern __shared__ double2 sm[];
@@ -129,11 +147,27 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
     double2* C3 = C2 + items;
     float4* XS = reinterpret_cast<float4*>(C3 + items) + 3 * T * 16 / 2;   // after the spike scratch
     float2* SW = reinterpret_cast<float2*>(XS + items);
+    double2* D00 = reinterpret_cast<double2*>(SW + ((N * kStencil + 1) & ~1));   // 16-byte aligned
+    const int mode0 = g.mlo + blockIdx.x * T;
+    const int nT = min(T, g.mhi - mode0);
+    // column of the (0, 0) mode in this block, or -1
+    const int t00 = (g.K >= mode0 && g.K < mode0 + nT) ? g.K - mode0 : -1;
     if (MX) {
         for (int i = threadIdx.x; i < N * kStencil; i += blockDim.x) SW[i] = xs::split_hl(a.w1[i]);
     }
-    // XS <- split of the column(s) (F + F2), then a barrier
+    // XS <- split of the column(s) (F + F2), D00 <- the FP64 stencil of column t00, a barrier
     auto split_cols = [&](const double2* F, const double2* F2) {
+        if (t00 >= 0) {
+            for (int j = threadIdx.x; j < N; j += blockDim.x) {
+                double2 d = sdrow(F, a.w1, a.col0, j, T, t00);
+                if (F2) {
+                    const double2 d2 = sdrow(F2, a.w1, a.col0, j, T, t00);
+                    d.x += d2.x;
+                    d.y += d2.y;
+                }
+                D00[j] = d;
+            }
+        }
         for (int i = threadIdx.x; i < items; i += blockDim.x) {
             double2 x = F[i];
             if (F2) {
@@ -145,21 +179,11 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
         }
         __syncthreads();
     };
-    // D1 of the split column at row j, mode t, assembled in FP64
+    // D1 of the split column at row j, mode t; the (0, 0) column's from D00
     auto xsrow = [&](int j, int t) {
-        const int c0 = a.col0[j];
-        float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
-#pragma unroll
-        for (int q = 0; q < kStencil; ++q) {
-            const float4 v = XS[(c0 + q) * T + t];
-            const float2 w = SW[j * kStencil + q];
-            xs::dot_acc(sx, cx, w.x, w.y, v.x, v.z);
-            xs::dot_acc(sy, cy, w.x, w.y, v.y, v.w);
-        }
-        return make_double2(xs::f2d_bits(sx) + xs::f2d_bits(cx), xs::f2d_bits(sy) + xs::f2d_bits(cy));
+        if (t == t00) return D00[j];
+        return xs_stencil(XS + a.col0[j] * T + t, T, SW + j * kStencil);
     };
-    const int mode0 = g.mlo + blockIdx.x * T;
-    const int nT = min(T, g.mhi - mode0);
     const size_t per_set = (size_t)N * kBands * g.M1K1;
     const double c1 = g.c1;   // 1 / (2 dt)
     // T divides the block size, so every element a thread visits in the element loops below
@@ -190,6 +214,10 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_pc(PCArgs a, Geo g, int T) {
         }
     }
     __syncthreads();
+    if (MX && t00 >= 0) {   // the (0, 0) column's stencil of X in FP64
+        for (int j = threadIdx.x; j < N; j += blockDim.x) D00[j] = sdrow(C1, a.w1, a.col0, j, T, t00);
+        __syncthreads();
+    }
     // A2: pressure right-hand side into C0
     for (int j = threadIdx.x / T; j < N; j += jstep) {
         const int idx = j * T + tq, t = tq;
@@ -413,8 +441,8 @@ __global__ void k_nn_r(const double2* __restrict__ Nc, const double2* __restrict
                         0.5 * ((2.0 * n1.y - n0.y) + (2.0 * m1.y - m0.y)));
 }
 
-// Step 2 right-hand side: interior rows div_h(-(2N - N_prev)); wall rows the consistent
-// Neumann value of Eq. ppBC; (0,0) at r_o the Dirichlet value 0.
+// Step 2 right-hand side on the interior rows: div_h(-(2N - N_prev)) (the wall rows:
+// k_rhs_pressure_walls).
 __global__ void k_rhs_pressure(const double2* __restrict__ u, const double2* __restrict__ up,
                                const double2* __restrict__ Nc, const double2* __restrict__ Np,
                                const double2* __restrict__ X, double2* __restrict__ b,
@@ -425,22 +453,14 @@ __global__ void k_rhs_pressure(const double2* __restrict__ u, const double2* __r
     // the stencil's rows stay in cache), y over modes
     const int mode = g.mlo + blockIdx.y * blockDim.x + threadIdx.x;
     if (mode >= g.mhi) return;
-    const int j = blockIdx.x;
+    const int j = blockIdx.x + 1;   // interior rows (k_rhs_pressure_walls takes the walls)
     const size_t e = (size_t)j * g.nmode + mode;
     const int m = mode / g.nk;
     const int k = mode - m * g.nk - g.K;
     const double mm = g.mp * m, kk = g.kz * k;
-    const double r = rn[j], ir = irn[j];
+    const double ir = irn[j];
     double2 out = make_double2(0.0, 0.0);
-    if (j == 0 || j == g.N - 1) {
-        if (!(j == g.N - 1 && m == 0 && k == 0)) {
-            const double2 x = X[e];
-            const double2 l0 = lap_r(u, w1, w2, col0, r, j, mode, mm, kk, g);
-            const double2 l1 = lap_r(up, w1, w2, col0, r, j, mode, mm, kk, g);
-            out.x = -x.x + 2.0 * l0.x - l1.x;
-            out.y = -x.y + 2.0 * l0.y - l1.y;
-        }
-    } else {
+    {
         const double2 d = drow(X, w1, col0, j, g.nmode, mode);
         const double2 x = X[e];
         const double2 n1 = Nc[e], n0 = Np[e], m1 = Nc[g.S + e], m0 = Np[g.S + e];
@@ -450,6 +470,32 @@ __global__ void k_rhs_pressure(const double2* __restrict__ u, const double2* __r
         const double nzx = 2.0 * z1.x - z0.x, nzy = 2.0 * z1.y - z0.y;
         out.x = -(d.x + x.x * ir + 0.5 * mm * ir * dpx - kk * nzy);
         out.y = -(d.y + x.y * ir + 0.5 * mm * ir * dpy + kk * nzx);
+    }
+    b[e] = out;
+}
+
+// Step 2 right-hand side on the two wall rows: the consistent Neumann value of Eq. ppBC
+// (the wall Laplacian of u and u_prev), or the Dirichlet value 0 for (0,0) at r_o; kept apart
+// from the interior rows, whose kernel then needs far fewer registers
+__global__ void k_rhs_pressure_walls(const double2* __restrict__ u, const double2* __restrict__ up,
+                                     const double2* __restrict__ X, double2* __restrict__ b,
+                                     const double* __restrict__ rn, const double* __restrict__ w1,
+                                     const double* __restrict__ w2, const int* __restrict__ col0, Geo g) {
+    const int mode = g.mlo + blockIdx.x * blockDim.x + threadIdx.x;   // y = wall (0: r_i, 1: r_o)
+    if (mode >= g.mhi) return;
+    const int j = blockIdx.y == 0 ? 0 : g.N - 1;
+    const size_t e = (size_t)j * g.nmode + mode;
+    const int m = mode / g.nk;
+    const int k = mode - m * g.nk - g.K;
+    double2 out = make_double2(0.0, 0.0);
+    if (!(j == g.N - 1 && m == 0 && k == 0)) {
+        const double mm = g.mp * m, kk = g.kz * k;
+        const double r = rn[j];
+        const double2 x = X[e];
+        const double2 l0 = lap_r(u, w1, w2, col0, r, j, mode, mm, kk, g);
+        const double2 l1 = lap_r(up, w1, w2, col0, r, j, mode, mm, kk, g);
+        out.x = -x.x + 2.0 * l0.x - l1.x;
+        out.y = -x.y + 2.0 * l0.y - l1.y;
     }
     b[e] = out;
 }
@@ -563,7 +609,10 @@ __global__ void k_update(double2* u, double2* up, const double2* Nc, double2* Np
 // ---------------------------------------------------------------- split path, mixed form
 // The same four per-stage kernels for TC_MIXED plans, with each radial stencil (of X, p*,
 // u*_+ + u*_- and phi) in double-FP32 instead of FP64: the FP64 pipe, which bounds these
-// kernels, then carries only the rest.  A block takes a tile of 32 modes x 32 rows; the
+// kernels, then carries only the rest.  The (0, 0) mode keeps the FP64 stencil: it carries
+// the mean flow, a smooth profile some 1e5 times larger near the clustered walls than the
+// differences of neighbouring rows its derivative rests on, so the 47 bits of the split
+// would cost it 1e-9 of the wall shear (and the torque follows it).  A block takes a tile of 32 modes x 32 rows; the
 // tile's window of rows is read once and each value split once into an exact FP32 pair
 // (hi, lo) in shared memory, the stencil is a compensated dot product of the pairs (about 44
 // significant bits, against FP32 transforms elsewhere in the form), and the result is
@@ -613,19 +662,11 @@ __device__ __forceinline__ void xs_load(const double2* __restrict__ f, const dou
     __syncthreads();
 }
 
-// D1 of the window's field at row r for this thread's mode, assembled in FP64
+// D1 of the window's field at row r for this thread's mode
 __device__ __forceinline__ double2 xs_drow(const float4* win, const float2* sw, const int* __restrict__ col0,
                                            const XsTile& t, int r) {
     const int w0 = (col0[r] - t.jlo) * kXsM + threadIdx.x;
-    const float2* w = sw + (r - t.r0) * kStencil;
-    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
-#pragma unroll
-    for (int q = 0; q < kStencil; ++q) {
-        const float4 v = win[w0 + q * kXsM];
-        xs::dot_acc(sx, cx, w[q].x, w[q].y, v.x, v.z);
-        xs::dot_acc(sy, cy, w[q].x, w[q].y, v.y, v.w);
-    }
-    return make_double2(xs::f2d_bits(sx) + xs::f2d_bits(cx), xs::f2d_bits(sy) + xs::f2d_bits(cy));
+    return xs_stencil(win + w0, kXsM, sw + (r - t.r0) * kStencil);
 }
 
 __global__ void __launch_bounds__(256) k_rhs_pressure_mx(const double2* __restrict__ u, const double2* __restrict__ up,
@@ -642,21 +683,15 @@ __global__ void __launch_bounds__(256) k_rhs_pressure_mx(const double2* __restri
     const int mode = t.mode;
     const int m = mode / g.nk;
     const int k = mode - m * g.nk - g.K;
+    const bool mode00 = m == 0 && k == 0;
     const double mm = g.mp * m, kk = g.kz * k;
     for (int j = t.r0 + threadIdx.y; j <= t.r1; j += blockDim.y) {
+        if (j == 0 || j == g.N - 1) continue;   // k_rhs_pressure_walls
         const size_t e = (size_t)j * g.nmode + mode;
-        const double r = rn[j], ir = irn[j];
+        const double ir = irn[j];
         double2 out = make_double2(0.0, 0.0);
-        if (j == 0 || j == g.N - 1) {
-            if (!(j == g.N - 1 && m == 0 && k == 0)) {
-                const double2 x = X[e];
-                const double2 l0 = lap_r(u, w1, w2, col0, r, j, mode, mm, kk, g);
-                const double2 l1 = lap_r(up, w1, w2, col0, r, j, mode, mm, kk, g);
-                out.x = -x.x + 2.0 * l0.x - l1.x;
-                out.y = -x.y + 2.0 * l0.y - l1.y;
-            }
-        } else {
-            const double2 d = xs_drow(win, sw, col0, t, j);
+        {
+            const double2 d = mode00 ? drow(X, w1, col0, j, g.nmode, mode) : xs_drow(win, sw, col0, t, j);
             const double2 x = X[e];
             const double2 n1 = Nc[e], n0 = Np[e], m1 = Nc[g.S + e], m0 = Np[g.S + e];
             const double2 z1 = Nc[2 * g.S + e], z0 = Np[2 * g.S + e];
@@ -684,6 +719,7 @@ __global__ void __launch_bounds__(256) k_rhs_velocity_mx(const double2* __restri
     const int mode = t.mode;
     const int m = mode / g.nk;
     const int k = mode - m * g.nk - g.K;
+    const bool mode00 = m == 0 && k == 0;
     for (int j = t.r0 + threadIdx.y; j <= t.r1; j += blockDim.y) {
         const size_t e = (size_t)j * g.nmode + mode;
         const double2 pv = ps[e];
@@ -695,7 +731,7 @@ __global__ void __launch_bounds__(256) k_rhs_velocity_mx(const double2* __restri
             rhs[2 * g.S + e] = make_double2(0.0, 0.0);
             continue;
         }
-        const double2 d = xs_drow(win, sw, col0, t, j);
+        const double2 d = mode00 ? drow(ps, w1, col0, j, g.nmode, mode) : xs_drow(win, sw, col0, t, j);
         const double tt = g.mp * m * irn[j], kk = g.kz * k;
         const double2 gp[3] = {make_double2(d.x - tt * pv.x, d.y - tt * pv.y),
                                make_double2(d.x + tt * pv.x, d.y + tt * pv.y),
@@ -721,6 +757,7 @@ __global__ void __launch_bounds__(256) k_rhs_div_mx(const double2* __restrict__ 
     const int mode = t.mode;
     const int m = mode / g.nk;
     const int k = mode - m * g.nk - g.K;
+    const bool mode00 = m == 0 && k == 0;
     const double mm = g.mp * m, kk = g.kz * k;
     for (int j = t.r0 + threadIdx.y; j <= t.r1; j += blockDim.y) {
         const size_t e = (size_t)j * g.nmode + mode;
@@ -729,7 +766,13 @@ __global__ void __launch_bounds__(256) k_rhs_div_mx(const double2* __restrict__ 
             continue;
         }
         const double ir = irn[j];
-        const double2 d = xs_drow(win, sw, col0, t, j);
+        double2 d;
+        if (mode00) {
+            const double2 dp = drow(us, w1, col0, j, g.nmode, mode), dm = drow(us + g.S, w1, col0, j, g.nmode, mode);
+            d = make_double2(dp.x + dm.x, dp.y + dm.y);
+        } else {
+            d = xs_drow(win, sw, col0, t, j);
+        }
         const double2 vp = us[e], vm = us[g.S + e], vz = us[2 * g.S + e];
         b[e] = make_double2(0.5 * d.x + 0.5 * (vp.x + vm.x) * ir + 0.5 * mm * ir * (vp.x - vm.x) - kk * vz.y,
                             0.5 * d.y + 0.5 * (vp.y + vm.y) * ir + 0.5 * mm * ir * (vp.y - vm.y) + kk * vz.x);
@@ -749,11 +792,12 @@ __global__ void __launch_bounds__(256) k_update_mx(double2* u, double2* up, cons
     const int mode = t.mode;
     const int m = mode / g.nk;
     const int k = mode - m * g.nk - g.K;
+    const bool mode00 = m == 0 && k == 0;
     bool bad = false;
     for (int j = t.r0 + threadIdx.y; j <= t.r1; j += blockDim.y) {
         const size_t e = (size_t)j * g.nmode + mode;
         const double2 f = phi[e];
-        const double2 d = xs_drow(win, sw, col0, t, j);
+        const double2 d = mode00 ? drow(phi, w1, col0, j, g.nmode, mode) : xs_drow(win, sw, col0, t, j);
         const double tt = g.mp * m * irn[j], kk = g.kz * k;
         const double2 gph[3] = {make_double2(d.x - tt * f.x, d.y - tt * f.y),
                                 make_double2(d.x + tt * f.x, d.y + tt * f.y),
@@ -975,8 +1019,10 @@ static tc_status launch_advance_split(tc_plan* p, const double2* u, double2* u_p
         k_rhs_pressure_mx<<<gx, bx, 0, s>>>(u, u_prev, Ncur, N_prev, phi, ps, p->d_r, p->d_ir, p->d_w1, p->d_w2,
                                             p->d_col0, g);
     else
-        k_rhs_pressure<<<g1, 128, 0, s>>>(u, u_prev, Ncur, N_prev, phi, ps, p->d_r, p->d_ir, p->d_w1, p->d_w2,
-                                          p->d_col0, g);
+        k_rhs_pressure<<<dim3(g.N - 2, blocks_for(nm, 128)), 128, 0, s>>>(u, u_prev, Ncur, N_prev, phi, ps, p->d_r,
+                                                                        p->d_ir, p->d_w1, p->d_w2, p->d_col0, g);
+    k_rhs_pressure_walls<<<dim3(blocks_for(nm, 128), 2), 128, 0, s>>>(u, u_prev, phi, ps, p->d_r, p->d_w1, p->d_w2,
+                                                                     p->d_col0, g);
     prof_end(p, slot, s);
     TC_LAUNCHED(p, "k_rhs_pressure");
     slot = prof_begin(p, kKSolveP, s);
@@ -1045,7 +1091,9 @@ tc_status launch_advance(tc_plan* p, const double2* u, double2* u_prev, const do
     // mixed form: the split column and weights of the double-FP32 stencils after the rest
     const bool mx = p->precision == TC_MIXED;
     const size_t sm = (size_t)4 * p->N_r * T * sizeof(double2) + (size_t)3 * T * 16 * sizeof(double) +
-                      (mx ? (size_t)p->N_r * T * sizeof(float4) + (size_t)p->N_r * kStencil * sizeof(float2) : 0);
+                      (mx ? (size_t)p->N_r * T * sizeof(float4) +
+                                (size_t)((p->N_r * kStencil + 1) & ~1) * sizeof(float2) +
+                                (size_t)p->N_r * sizeof(double2) : 0);
     // 128 threads up to 8 modes per block, 256 beyond (6T substitution threads plus helpers)
     const int slot = prof_begin(p, kKPC, s);
     auto run = [&](auto kern, int nth) -> tc_status {
