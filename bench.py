@@ -26,7 +26,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) of one FP64 theta-pass launch at the bench workload, from ncu
-THETA_TRAFFIC = 61.57e6
+# (58.44 MB read + 2.99 MB written; the H2 lines stay in L2)
+THETA_TRAFFIC = 61.43e6
 CFG2 = dict(N_r=64, M=32, K=64, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)
 # mid-size case for profiling (inputs larger than L2, a few GB on the device)
 CFG_MID = dict(N_r=128, M=128, K=256, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=2 * math.pi / 3.16, dt=5e-4)

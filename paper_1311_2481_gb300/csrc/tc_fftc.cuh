@@ -62,9 +62,32 @@ template <typename V> __device__ __forceinline__ V vmul(V a, V b) {
 template <bool INV, typename V> __device__ __forceinline__ V rot(V a) {
     return INV ? vmk<V>(-a.y, a.x) : vmk<V>(a.y, -a.x);
 }
+template <typename V> __device__ __forceinline__ V vneg(V a) { return vmk<V>(-a.x, -a.y); }
+// a + b and a - b where ZA / ZB say that a / b is known to be zero at compile time: the sum
+// is then the other operand, exactly (up to the sign of a zero result)
+template <bool ZA, bool ZB, typename V> __device__ __forceinline__ V zadd(V a, V b) {
+    static_assert(!(ZA && ZB), "both operands zero");
+    if constexpr (ZB) return a;
+    else if constexpr (ZA) return b;
+    else return vadd(a, b);
+}
+template <bool ZA, bool ZB, typename V> __device__ __forceinline__ V zsub(V a, V b) {
+    static_assert(!(ZA && ZB), "both operands zero");
+    if constexpr (ZB) return a;
+    else if constexpr (ZA) return vneg(b);
+    else return vsub(a, b);
+}
+// bits i0, i1, i2, i3 of a zero mask, as the mask of a 4-input codelet
+template <unsigned Z, int I0, int I1, int I2, int I3> __host__ __device__ constexpr unsigned sub4() {
+    return ((Z >> I0) & 1u) | (((Z >> I1) & 1u) << 1) | (((Z >> I2) & 1u) << 2) | (((Z >> I3) & 1u) << 3);
+}
 
 // ---------------------------------------------------------------- in-register DFTs
-// X_k = sum_n x_n exp(s 2 pi i n k / R), s = +1 (inverse) or -1 (forward), in natural order
+// X_k = sum_n x_n exp(s 2 pi i n k / R), s = +1 (inverse) or -1 (forward), in natural order.
+// The radix-4, 8 and 16 codelets take a compile-time mask Z of inputs known to be zero (bit n
+// for x_n; the first pass of an inverse transform over the zero band of a dealiased
+// spectrum): the additions with those inputs are left out, which changes no result bit but
+// the sign of a zero.
 template <bool INV, typename V> __device__ __forceinline__ void dft2(V* v) {
     const V a = v[0];
     v[0] = vadd(a, v[1]);
@@ -80,9 +103,10 @@ template <bool INV, typename V> __device__ __forceinline__ void dft3(V* v) {
     v[1] = vadd(m1, m2);
     v[2] = vsub(m1, m2);
 }
-template <bool INV, typename V> __device__ __forceinline__ void dft4(V* v) {
-    const V a0 = vadd(v[0], v[2]), a1 = vsub(v[0], v[2]);
-    const V a2 = vadd(v[1], v[3]), a3 = rot<INV>(vsub(v[1], v[3]));
+template <bool INV, unsigned Z = 0, typename V> __device__ __forceinline__ void dft4(V* v) {
+    constexpr bool z0 = Z & 1u, z1 = (Z >> 1) & 1u, z2 = (Z >> 2) & 1u, z3 = (Z >> 3) & 1u;
+    const V a0 = zadd<z0, z2>(v[0], v[2]), a1 = zsub<z0, z2>(v[0], v[2]);
+    const V a2 = zadd<z1, z3>(v[1], v[3]), a3 = rot<INV>(zsub<z1, z3>(v[1], v[3]));
     v[0] = vadd(a0, a2);
     v[2] = vsub(a0, a2);
     v[1] = vadd(a1, a3);
@@ -103,12 +127,12 @@ template <bool INV, int J, typename V> __device__ __forceinline__ V w16(V a) {
     else if constexpr (J == 4) return rot<INV>(a);
     else return rot<INV>(vmul(a, vmk<V>(h, s * h)));
 }
-template <bool INV, typename V> __device__ __forceinline__ void dft8(V* v) {
+template <bool INV, unsigned Z = 0, typename V> __device__ __forceinline__ void dft8(V* v) {
     // two DFT-4 of the even and odd samples, then the W8 butterflies
     V e[4] = {v[0], v[2], v[4], v[6]};
     V o[4] = {v[1], v[3], v[5], v[7]};
-    dft4<INV>(e);
-    dft4<INV>(o);
+    dft4<INV, sub4<Z, 0, 2, 4, 6>()>(e);
+    dft4<INV, sub4<Z, 1, 3, 5, 7>()>(o);
     o[1] = w16<INV, 2>(o[1]);
     o[2] = rot<INV>(o[2]);
     o[3] = w16<INV, 6>(o[3]);
@@ -118,15 +142,28 @@ template <bool INV, typename V> __device__ __forceinline__ void dft8(V* v) {
         v[k + 4] = vsub(e[k], o[k]);
     }
 }
-template <bool INV, typename V> __device__ __forceinline__ void dft16(V* v) {
+template <bool INV, int N2, unsigned Z, typename V> __device__ __forceinline__ void dft16_col(const V* v, V (*y)[4]) {
+    V t[4] = {v[N2], v[N2 + 4], v[N2 + 8], v[N2 + 12]};
+    dft4<INV, sub4<Z, N2, N2 + 4, N2 + 8, N2 + 12>()>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) y[N2][k1] = t[k1];
+}
+template <bool INV, unsigned Z = 0, typename V> __device__ __forceinline__ void dft16(V* v) {
     // 16 = 4 x 4: DFT-4 over n1 for each n2, twiddle W16^(n2 k1), DFT-4 over n2
     V y[4][4];
+    if constexpr (Z == 0) {
 #pragma unroll
-    for (int n2 = 0; n2 < 4; ++n2) {
-        V t[4] = {v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]};
-        dft4<INV>(t);
+        for (int n2 = 0; n2 < 4; ++n2) {
+            V t[4] = {v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]};
+            dft4<INV>(t);
 #pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = t[k1];
+            for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = t[k1];
+        }
+    } else {
+        dft16_col<INV, 0, Z>(v, y);
+        dft16_col<INV, 1, Z>(v, y);
+        dft16_col<INV, 2, Z>(v, y);
+        dft16_col<INV, 3, Z>(v, y);
     }
     y[1][1] = w16<INV, 1>(y[1][1]);
     y[1][2] = w16<INV, 2>(y[1][2]);
@@ -149,12 +186,13 @@ template <bool INV, typename V> __device__ __forceinline__ void dft16(V* v) {
         for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
     }
 }
-template <int R, bool INV, typename V> __device__ __forceinline__ void dftR(V* v) {
+template <int R, bool INV, unsigned Z = 0, typename V> __device__ __forceinline__ void dftR(V* v) {
+    static_assert(Z == 0 || R >= 4, "zero masks only for radix 4, 8, 16");
     if constexpr (R == 2) dft2<INV>(v);
     else if constexpr (R == 3) dft3<INV>(v);
-    else if constexpr (R == 4) dft4<INV>(v);
-    else if constexpr (R == 8) dft8<INV>(v);
-    else dft16<INV>(v);
+    else if constexpr (R == 4) dft4<INV, Z>(v);
+    else if constexpr (R == 8) dft8<INV, Z>(v);
+    else dft16<INV, Z>(v);
 }
 
 // ---------------------------------------------------------------- Stockham passes
@@ -168,8 +206,9 @@ template <bool TWS, typename V> __device__ __forceinline__ V twiddle(const V* __
     else return __ldg(&tw[j]);
 }
 
-template <int PT, int R, int NS, int NL, int NT, bool INV, typename V, bool TWS = false>
-__device__ __forceinline__ void pass(const V* in, V* out, const V* __restrict__ tw, int zlo, int zhi) {
+// ZM: inputs q of every butterfly known to be zero (the caller has checked the band)
+template <int PT, int R, int NS, int NL, int NT, bool INV, typename V, bool TWS, unsigned ZM>
+__device__ __forceinline__ void pass_body(const V* in, V* out, const V* __restrict__ tw, int zlo, int zhi) {
     constexpr int NB = PT / R;
     constexpr int STEP = PT / (NS * R);
     constexpr int LP = padded<PT>();
@@ -183,7 +222,7 @@ __device__ __forceinline__ void pass(const V* in, V* out, const V* __restrict__ 
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int pos = j + q * NB;
-            v[q] = (pos >= zlo && pos < zhi) ? vmk<V>(0, 0) : src[pd(pos)];
+            v[q] = ((ZM >> q) & 1u) || (pos >= zlo && pos < zhi) ? vmk<V>(0, 0) : src[pd(pos)];
         }
         if (NS > 1 && k) {
 #pragma unroll
@@ -193,12 +232,33 @@ __device__ __forceinline__ void pass(const V* in, V* out, const V* __restrict__ 
                 v[q] = vmul(v[q], w);
             }
         }
-        dftR<R, INV>(v);
+        dftR<R, INV, ZM>(v);
         const int o = (j / NS) * NS * R + k;
 #pragma unroll
         for (int q = 0; q < R; ++q) dst[pd(o + q * NS)] = v[q];
     }
     __syncthreads();
+}
+// inputs q of a first-pass radix-8 (16) butterfly that fall in [3 PT / 8, 5 PT / 8)
+template <int R> __host__ __device__ constexpr unsigned band_mask() {
+    unsigned z = 0;
+    for (int q = 3 * R / 8; q < 5 * R / 8; ++q) z |= 1u << q;
+    return z;
+}
+template <int PT, int R, int NS, int NL, int NT, bool INV, typename V, bool TWS = false>
+__device__ __forceinline__ void pass(const V* in, V* out, const V* __restrict__ tw, int zlo, int zhi) {
+    // A first pass of radix 8 or 16 reads input q of butterfly j at j + q PT / R.  When the
+    // zero band [zlo, zhi) holds [3 PT / 8, 5 PT / 8) (a dealiased spectrum, |m| <= PT / 3),
+    // inputs 3R/8 .. 5R/8 - 1 are zero in every butterfly.  Taken for FP64 lines only, where
+    // the FP64 pipe bounds the pass; FP32 lines, bound by latency, ran no faster with it.
+    if constexpr (NS == 1 && (R == 8 || R == 16) && sizeof(V) == 16) {
+        constexpr int NB = PT / R;
+        if (zlo <= (3 * R / 8) * NB && zhi >= (5 * R / 8) * NB) {
+            pass_body<PT, R, NS, NL, NT, INV, V, TWS, band_mask<R>()>(in, out, tw, zlo, zhi);
+            return;
+        }
+    }
+    pass_body<PT, R, NS, NL, NT, INV, V, TWS, 0u>(in, out, tw, zlo, zhi);
 }
 
 // all passes of the plan; returns the buffer that holds the result
