@@ -84,10 +84,10 @@ template <unsigned Z, int I0, int I1, int I2, int I3> __host__ __device__ conste
 
 // ---------------------------------------------------------------- in-register DFTs
 // X_k = sum_n x_n exp(s 2 pi i n k / R), s = +1 (inverse) or -1 (forward), in natural order.
-// The radix-4, 8 and 16 codelets take a compile-time mask Z of inputs known to be zero (bit n
-// for x_n; the first pass of an inverse transform over the zero band of a dealiased
-// spectrum): the additions with those inputs are left out, which changes no result bit but
-// the sign of a zero.
+// The radix-4 and 8 codelets take a compile-time mask Z of inputs known to be zero (bit n for
+// x_n; the first pass of an inverse transform over the zero band of a dealiased spectrum):
+// the additions with those inputs are left out, which changes no result bit but the sign of
+// a zero.
 template <bool INV, typename V> __device__ __forceinline__ void dft2(V* v) {
     const V a = v[0];
     v[0] = vadd(a, v[1]);
@@ -142,28 +142,15 @@ template <bool INV, unsigned Z = 0, typename V> __device__ __forceinline__ void 
         v[k + 4] = vsub(e[k], o[k]);
     }
 }
-template <bool INV, int N2, unsigned Z, typename V> __device__ __forceinline__ void dft16_col(const V* v, V (*y)[4]) {
-    V t[4] = {v[N2], v[N2 + 4], v[N2 + 8], v[N2 + 12]};
-    dft4<INV, sub4<Z, N2, N2 + 4, N2 + 8, N2 + 12>()>(t);
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) y[N2][k1] = t[k1];
-}
-template <bool INV, unsigned Z = 0, typename V> __device__ __forceinline__ void dft16(V* v) {
+template <bool INV, typename V> __device__ __forceinline__ void dft16(V* v) {
     // 16 = 4 x 4: DFT-4 over n1 for each n2, twiddle W16^(n2 k1), DFT-4 over n2
     V y[4][4];
-    if constexpr (Z == 0) {
 #pragma unroll
-        for (int n2 = 0; n2 < 4; ++n2) {
-            V t[4] = {v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]};
-            dft4<INV>(t);
+    for (int n2 = 0; n2 < 4; ++n2) {
+        V t[4] = {v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]};
+        dft4<INV>(t);
 #pragma unroll
-            for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = t[k1];
-        }
-    } else {
-        dft16_col<INV, 0, Z>(v, y);
-        dft16_col<INV, 1, Z>(v, y);
-        dft16_col<INV, 2, Z>(v, y);
-        dft16_col<INV, 3, Z>(v, y);
+        for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = t[k1];
     }
     y[1][1] = w16<INV, 1>(y[1][1]);
     y[1][2] = w16<INV, 2>(y[1][2]);
@@ -187,12 +174,12 @@ template <bool INV, unsigned Z = 0, typename V> __device__ __forceinline__ void 
     }
 }
 template <int R, bool INV, unsigned Z = 0, typename V> __device__ __forceinline__ void dftR(V* v) {
-    static_assert(Z == 0 || R >= 4, "zero masks only for radix 4, 8, 16");
+    static_assert(Z == 0 || R == 4 || R == 8, "zero masks only for radix 4 and 8");
     if constexpr (R == 2) dft2<INV>(v);
     else if constexpr (R == 3) dft3<INV>(v);
     else if constexpr (R == 4) dft4<INV, Z>(v);
     else if constexpr (R == 8) dft8<INV, Z>(v);
-    else dft16<INV, Z>(v);
+    else dft16<INV>(v);
 }
 
 // ---------------------------------------------------------------- Stockham passes
@@ -239,22 +226,16 @@ __device__ __forceinline__ void pass_body(const V* in, V* out, const V* __restri
     }
     __syncthreads();
 }
-// inputs q of a first-pass radix-8 (16) butterfly that fall in [3 PT / 8, 5 PT / 8)
-template <int R> __host__ __device__ constexpr unsigned band_mask() {
-    unsigned z = 0;
-    for (int q = 3 * R / 8; q < 5 * R / 8; ++q) z |= 1u << q;
-    return z;
-}
 template <int PT, int R, int NS, int NL, int NT, bool INV, typename V, bool TWS = false>
 __device__ __forceinline__ void pass(const V* in, V* out, const V* __restrict__ tw, int zlo, int zhi) {
-    // A first pass of radix 8 or 16 reads input q of butterfly j at j + q PT / R.  When the
-    // zero band [zlo, zhi) holds [3 PT / 8, 5 PT / 8) (a dealiased spectrum, |m| <= PT / 3),
-    // inputs 3R/8 .. 5R/8 - 1 are zero in every butterfly.  Taken for FP64 lines only, where
-    // the FP64 pipe bounds the pass; FP32 lines, bound by latency, ran no faster with it.
-    if constexpr (NS == 1 && (R == 8 || R == 16) && sizeof(V) == 16) {
-        constexpr int NB = PT / R;
-        if (zlo <= (3 * R / 8) * NB && zhi >= (5 * R / 8) * NB) {
-            pass_body<PT, R, NS, NL, NT, INV, V, TWS, band_mask<R>()>(in, out, tw, zlo, zhi);
+    // A first radix-8 pass reads input q of butterfly j at j + q PT / 8.  When the zero band
+    // [zlo, zhi) holds [3 PT / 8, 5 PT / 8) (a dealiased spectrum, |m| <= PT / 3), inputs 3
+    // and 4 are zero in every butterfly.  Taken for FP64 lines only, where the FP64 pipe
+    // bounds the pass; FP32 lines, bound by latency, ran no faster with it.
+    if constexpr (NS == 1 && R == 8 && sizeof(V) == 16) {
+        constexpr int NB = PT / 8;
+        if (zlo <= 3 * NB && zhi >= 5 * NB) {
+            pass_body<PT, R, NS, NL, NT, INV, V, TWS, (1u << 3) | (1u << 4)>(in, out, tw, zlo, zhi);
             return;
         }
     }
