@@ -392,6 +392,22 @@ def test_fp64_theta_pass_lengths(M, K):
         assert rel(host(plan.nonlinear(dev(u))), ref) <= 1e-12, zt
 
 
+@pytest.mark.parametrize("M,K,P_theta,P_z", [(35, 71, 96, 192), (36, 72, 96, 192),
+                                             (32, 64, 96, 192), (24, 48, 96, 192)])
+def test_fp64_first_pass_zero_band_both_sides(M, K, P_theta, P_z):
+    """The FP64 first inverse radix-8 pass leaves out inputs 3 and 4 of its butterflies only when
+    the zero band M < m < P - M holds [3P/8, 5P/8): M = 35 on P = 96 (band 36..60) is the last
+    such case, M = 36 (band 37..59) takes the full pass; likewise K = 71 / 72 on P_z = 192.
+    Both sides, and the default and a wider band, match the oracle on the same lengths to
+    1e-12 (with P < 3M the product is aliased on both sides alike)."""
+    cfg = dict(N_r=12, M=M, K=K, m_p=1, eta=0.5, Re_i=1000.0, Re_o=0.0, L_z=LZ, dt=1e-4)
+    ops = O.Operators(O.Params(**cfg, P_theta=P_theta, P_z=P_z))
+    u = init(ops, kind="broadband", amp=1e-2, seed=9)
+    ref = O.nonlinear(ops, u)
+    plan = tc.Plan(**cfg, P_theta=P_theta, P_z=P_z)
+    assert rel(host(plan.nonlinear(dev(u))), ref) <= 1e-12
+
+
 @pytest.mark.parametrize("K", [128, 256, 384, 512])
 def test_fp64_z_pass_lengths(K):
     """The length-specialised FP64 z passes (P_z = 384 ... 1536) and the generic ones
