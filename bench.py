@@ -1039,10 +1039,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and large-size measurements")
     ap.add_argument("--largest", action="store_true",
-                    help="also time the mixed form at N_r = 384 (384 x 1152 x 2304) and the mixed form with "
-                         "the FP64 adjoint of its last 50 steps at N_r = 256")
+                    help="also time the FP64 and mixed steps at N_r = 384 (384 x 1152 x 2304), the mixed "
+                         "form there with the FP64 adjoint of its last 50 steps, and one FP64 adjoint step "
+                         "with its dot-product test at that size")
     ap.add_argument("--workload", default="fp64", choices=["fp64", "mixed", "adjoint"],
-                    help="precision of the main timed step (the reported metric is the FP64 step); "
+                    help="form of the main timed step: the headline metric is the FP64 step at the "
+                         "bench size; mixed (or another --size) names its form and size in the metric; "
                          "adjoint: time the FP64 adjoint step at --size instead (profiling)")
     ap.add_argument("--size", default="bench", choices=["bench", "mid", "split", "long"],
                     help="bench: N_r=64, M=32, K=64; mid: N_r=128, M=128, K=256; split: N_r=256, M=32, "
