@@ -168,7 +168,8 @@ def state_gradient(plan, st, nsteps, checkpoint=10, slots=None, spill=True, host
         if s0 > 0:
             del ckpts[s0]
     restore(ckpts[0])
-    torch.cuda.current_stream().synchronize()   # the pinned checkpoints are released after the copies
+    if spill:
+        torch.cuda.current_stream().synchronize()   # the pinned checkpoints are released after the copies
     del ckpts
     return J, bar
 

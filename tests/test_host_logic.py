@@ -1,5 +1,6 @@
 """Host-side logic that needs no GPU: the real-field projection of the optimal-perturbation
-iteration (adjoint.optimal_perturbation)."""
+iteration (adjoint.optimal_perturbation), and the checkpoint and slot schedule of
+adjoint.state_gradient, run against a counting stand-in for the plan."""
 import numpy as np
 import pytest
 
@@ -26,3 +27,76 @@ def test_real_field_projection_of_the_m0_line():
     r = (d - p)[:, :, 0, :].numpy()
     q = A._real_field_m0(torch.from_numpy(rng.standard_normal(shape) + 1j * rng.standard_normal(shape)))
     assert abs(np.real(np.vdot(r, q[:, :, 0, :].numpy()))) <= 1e-12 * np.linalg.norm(r) * np.linalg.norm(q.numpy())
+
+
+class _CountingPlan:
+    """Stands in for a plan in adjoint.state_gradient: a step adds 1 to every field, so the
+    velocity of forward state j is j; an adjoint step records the velocity it is given."""
+
+    def __init__(self):
+        self.steps = 0
+        self.read = []
+
+    def step(self, st, n):
+        for _ in range(n):
+            st.u += 1
+            st.u_prev += 1
+            st.N_prev += 1
+            self.steps += 1
+
+    def diagnostics(self, u):
+        return type("D", (), {"energy": float(u.real.sum())})()
+
+    def energy_gradient(self, u):
+        return u.clone()
+
+    def adjoint_step(self, fwd, bar):
+        self.read.append(int(fwd.u.real.flatten()[0]))
+
+
+def _counting_state():
+    st = type("S", (), {})()
+    st.u = torch.zeros((3, 2, 2, 3), dtype=torch.complex128)
+    st.u_prev = torch.full_like(st.u, -1.0)
+    st.N_prev = torch.full_like(st.u, 5.0)
+    st.p = torch.zeros((2, 2, 3), dtype=torch.complex128)
+    st.started = True
+    return st
+
+
+@pytest.mark.parametrize("nsteps,checkpoint,slots", [(1, 1, None), (7, 3, None), (7, 3, 2), (10, 10, 1),
+                                                     (50, 17, 7), (12, 5, 5), (9, 4, 3)])
+def test_state_gradient_reverses_every_step_once(nsteps, checkpoint, slots):
+    """adjoint.state_gradient's schedule: the adjoint steps read the forward velocities
+    u^{n-1}, ..., u^0 once each and in that order, whatever the checkpoint interval and the
+    number of device slots; the final energy is that of u^n; the working state is given back
+    with its initial fields; and each segment of C steps reversed in passes of k slots is
+    recomputed once per pass."""
+    plan, st = _CountingPlan(), _counting_state()
+    J, bar = A.state_gradient(plan, st, nsteps, checkpoint=checkpoint, slots=slots, spill=False)
+    assert plan.read == list(range(nsteps - 1, -1, -1))
+    assert J == float(nsteps * st.u.numel())
+    assert torch.equal(bar.u, torch.full_like(st.u, float(nsteps)))
+    assert torch.all(st.u == 0) and torch.all(st.u_prev == -1) and torch.all(st.N_prev == 5)
+    k = checkpoint if slots is None else max(1, min(slots, checkpoint))
+    recompute = 0
+    for s0 in range(0, nsteps, checkpoint):
+        hi = min(s0 + checkpoint, nsteps)
+        while hi > s0:
+            recompute += hi - 1 - s0      # steps from the checkpoint to the last state of the pass
+            hi = max(s0, hi - k)
+    assert plan.steps == nsteps + recompute
+
+
+def test_state_gradient_refuses_an_unstarted_state_and_oversized_host_checkpoints(monkeypatch):
+    plan, st = _CountingPlan(), _counting_state()
+    st.started = False
+    with pytest.raises(ValueError, match="started"):
+        A.state_gradient(plan, st, 3)
+    st.started = True
+    with pytest.raises(ValueError, match=">= 1"):
+        A.state_gradient(plan, st, 3, checkpoint=0)
+    monkeypatch.setattr(A, "_host_bytes_available", lambda: 1000)
+    with pytest.raises(ValueError, match="host checkpoints"):
+        A.state_gradient(plan, st, 30, checkpoint=10, spill=True)
+    assert plan.steps == 0
