@@ -54,19 +54,18 @@ class FinalEnergy(torch.autograd.Function):
             plan.step(st, 1)
             if (i + 1) % checkpoint == 0 and i + 1 < nsteps:
                 ckpts[i + 1] = _clone_state(plan, st)
-        ctx.plan, ctx.nsteps, ctx.checkpoint, ctx.ckpts = plan, nsteps, checkpoint, ckpts
+        ctx.plan, ctx.nsteps, ctx.ckpts = plan, nsteps, ckpts
         ctx.save_for_backward(u0.detach(), st.u.clone())
         return torch.tensor(_energy(plan, st.u), dtype=torch.float64, device=u0.device)
 
     @staticmethod
     def backward(ctx, gJ):
-        plan, n, C, ckpts = ctx.plan, ctx.nsteps, ctx.checkpoint, ctx.ckpts
+        plan, n, ckpts = ctx.plan, ctx.nsteps, ctx.ckpts
         u0, uN = ctx.saved_tensors
         ub = plan.energy_gradient(uN) * gJ.to(torch.float64)
         bar = tc.StateBar(ub.contiguous(), torch.zeros_like(ub), torch.zeros_like(ub))
         starts = sorted(ckpts)
         for s0 in reversed(starts):
-            s1 = min(s0 + C, n) if s0 + C <= n else n
             seg_end = min([s for s in starts if s > s0] + [n])
             st = _clone_state(plan, ckpts[s0])
             us = [st.u.clone()]
@@ -75,7 +74,6 @@ class FinalEnergy(torch.autograd.Function):
                 us.append(st.u.clone())
             for u in reversed(us):
                 plan.adjoint_step(_ForwardU(u), bar)
-            del s1
         g = plan.adjoint_start(u0, bar)
         return g, None, None, None
 

@@ -100,3 +100,38 @@ def test_state_gradient_refuses_an_unstarted_state_and_oversized_host_checkpoint
     with pytest.raises(ValueError, match="host checkpoints"):
         A.state_gradient(plan, st, 30, checkpoint=10, spill=True)
     assert plan.steps == 0
+
+
+class _CountingColdPlan(_CountingPlan):
+    """The counting plan with what adjoint.FinalEnergy also needs: a device, the scalar shape,
+    the history step (nsteps = 0) and the adjoint of the cold start (here the identity)."""
+
+    device = "cpu"
+
+    def scalar_shape(self):
+        return (2, 2, 3)
+
+    def step(self, st, n):
+        st.started = True
+        super().step(st, n)
+
+    def adjoint_start(self, u0, bar):
+        return bar.u.clone()
+
+
+@pytest.mark.parametrize("nsteps,checkpoint", [(1, 1), (1, 20), (6, 2), (7, 3), (20, 20), (21, 20), (9, 4)])
+def test_final_energy_backward_reverses_every_step_once(nsteps, checkpoint):
+    """FinalEnergy's backward pass: the adjoint steps read u^{n-1}, ..., u^0 once each and in
+    that order, for any checkpoint interval, and the gradient is what the cold-start adjoint
+    returns for the energy gradient of u^n scaled by the incoming gradient."""
+    plan = _CountingColdPlan()
+    u0 = torch.zeros((3, 2, 2, 3), dtype=torch.complex128, requires_grad=True)
+    J = A.final_energy(u0, plan, nsteps, checkpoint=checkpoint)
+    assert float(J.detach()) == float(nsteps * u0.numel())
+    plan.steps = 0
+    (2.0 * J).backward()
+    assert plan.read == list(range(nsteps - 1, -1, -1))
+    assert torch.equal(u0.grad, torch.full_like(u0, 2.0 * nsteps))
+    starts = sorted({0} | {s for s in range(checkpoint, nsteps, checkpoint)})
+    ends = starts[1:] + [nsteps]
+    assert plan.steps == sum(e - 1 - s for s, e in zip(starts, ends))
