@@ -1,6 +1,7 @@
 """Host-side logic that needs no GPU: the real-field projection of the optimal-perturbation
-iteration (adjoint.optimal_perturbation), and the checkpoint and slot schedule of
-adjoint.state_gradient, run against a counting stand-in for the plan."""
+iteration (adjoint.optimal_perturbation) and the iteration itself on a linear map with a known
+largest gain, and the checkpoint and slot schedules of adjoint.final_energy and
+adjoint.state_gradient, run against stand-ins for the plan."""
 import numpy as np
 import pytest
 
@@ -135,3 +136,49 @@ def test_final_energy_backward_reverses_every_step_once(nsteps, checkpoint):
     starts = sorted({0} | {s for s in range(checkpoint, nsteps, checkpoint)})
     ends = starts[1:] + [nsteps]
     assert plan.steps == sum(e - 1 - s for s, e in zip(starts, ends))
+
+
+class _DiagonalPlan(_CountingColdPlan):
+    """A linear step u <- a u (coefficient-wise) with the energy J = 1/2 sum W |u|^2: its
+    adjoint step multiplies by conj(a), so every quantity of the power iteration is known in
+    closed form."""
+
+    def __init__(self, a, W):
+        super().__init__()
+        self.a, self.W = a, W
+
+    def step(self, st, n):
+        st.started = True
+        for _ in range(n):
+            st.u = self.a * st.u
+
+    def diagnostics(self, u):
+        return type("D", (), {"energy": 0.5 * float((self.W * u.abs() ** 2).sum())})()
+
+    def energy_gradient(self, u):
+        return self.W * u
+
+    def adjoint_step(self, fwd, bar):
+        bar.u = torch.conj(self.a) * bar.u
+
+
+def test_optimal_perturbation_finds_the_largest_gain_of_a_linear_map():
+    """adjoint.optimal_perturbation on a diagonal linear step: the gain converges to the
+    largest |a|^(2n) over the admissible coefficients (interior rows), the iterate to that
+    coefficient, and the wall rows stay zero; a larger |a| on a wall row is not admissible."""
+    shape = (3, 5, 3, 7)                       # [c][r][m][k], N_r = 5, M = 2, K = 3
+    a = torch.full(shape, 0.5, dtype=torch.complex128)
+    a[1, 2, 1, 5] = 0.9 * np.exp(0.3j)         # the leading interior coefficient (m = 1)
+    a[0, 0, 2, 1] = 0.99                       # larger, but on the inner wall row
+    W = 1.0 + torch.arange(5, dtype=torch.float64).reshape(1, 5, 1, 1).expand(shape).contiguous()
+    plan = _DiagonalPlan(a, W)
+    rng = np.random.default_rng(3)
+    d0 = torch.from_numpy(rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+    n = 3
+    d, gains = A.optimal_perturbation(plan, torch.zeros(shape, dtype=torch.complex128), n, d0,
+                                      energy=1e-6, iters=8, checkpoint=2)
+    assert abs(gains[-1] - 0.9 ** (2 * n)) <= 1e-9 * 0.9 ** (2 * n)
+    assert all(g1 >= g0 - 1e-12 for g0, g1 in zip(gains, gains[1:]))
+    assert torch.all(d[:, 0] == 0) and torch.all(d[:, -1] == 0)
+    lead = d[1, 2, 1, 5].abs() ** 2
+    assert float((d.abs() ** 2).sum() - lead) <= 1e-12 * float(lead)
