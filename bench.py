@@ -193,7 +193,7 @@ def kernel_rooflines(cfg, prof):
         out[name] = e
     return {"kernels": out, "hbm_peak_gbs": hbm, "hbm_peak_source": src,
             "fp64_peak_tflops": FP64_PEAK / 1e12,
-            "note": "k_pc: DP instructions ~322 per (row, mode), bound by FP64 issue (16 cycles per warp instruction)"}
+            "note": "k_pc: DP instructions ~380 per (row, mode) in its two-partition form (ncu: 103 M per launch at the bench size), bound by FP64 issue (16 cycles per warp instruction)"}
 
 
 def cufft_comparison(torch, cfg, dev, reps=20):
