@@ -182,3 +182,23 @@ def test_optimal_perturbation_finds_the_largest_gain_of_a_linear_map():
     assert torch.all(d[:, 0] == 0) and torch.all(d[:, -1] == 0)
     lead = d[1, 2, 1, 5].abs() ** 2
     assert float((d.abs() ** 2).sum() - lead) <= 1e-12 * float(lead)
+
+
+def test_roofline_arithmetic_at_the_bench_workload():
+    """bench.py's per-launch algorithmic figures at N_r = 64, M = 32, K = 64 (P_theta = 96,
+    P_z = 192): the theta-pass reads the 9 H1 line sets and writes the 3 H2 ones (77.9 MB)
+    and counts 0.32 GFLOP; a launch of 0.4292 ms is then 0.747 TFLOP/s, 0.594 of the FP64
+    peak of 152 SMs x 2 DFMA x 2 flop x 2.07 GHz."""
+    import bench
+    cfg = dict(N_r=64, M=32, K=64)
+    H = 64 * 33 * 192
+    rf = bench.kernel_rooflines(cfg, {"k_theta": (1, 0.4292), "k_zinv": (1, 0.2052), "k_pc": (2, 0.4926)})
+    th = rf["kernels"]["k_theta"]
+    assert th["bytes"] == 12 * H * 16 == 77_856_768
+    assert abs(th["flops"] - 320.79e6) <= 0.01e6
+    assert abs(th["flops"] / 0.4292e-3 / 1e12 - 0.747) <= 0.001
+    assert abs(th["fp64_frac"] - 0.594) <= 0.001
+    assert bench.FP64_PEAK == pytest.approx(1.25856e12)
+    assert rf["kernels"]["k_zinv"]["bytes"] == 3 * 64 * 33 * 129 * 16 + 9 * H * 16
+    assert rf["kernels"]["k_pc"]["ms"] == pytest.approx(0.2463)
+    assert "flops" not in rf["kernels"]["k_pc"]
